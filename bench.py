@@ -1,0 +1,356 @@
+"""Benchmark of the ParO hot path on one GB300 (or N independent replicas).
+
+A step is one ParO outer iteration (Step 3: N shifted source problems by
+batched PCG with float64 refinement; Step 4: Rayleigh-Ritz; Step 5: the
+|delta lambda| test) over the 3-D harmonic-oscillator workload: V = r^2/2 on
+[-8, 8]^3, 64^3 Q1 cells (250 047 interior nodes), N = 20 orbitals, sigma = 0,
+seeded Gaussian initial orbitals.  The metric unit is one interior node of one
+orbital updated by one outer iteration (DOF.orbital updates/s).
+
+Lines printed (rank 0, one JSON line):
+  value        device-resident throughput (inputs in HBM; CUDA events on the
+               library's stream; L2 flushed between steps, outside the events)
+  e2e          the same through the C ABI with host buffers: H2D of U, the
+               call, D2H of U and lambda inside the timed region
+  roofline     the CG operator kernel (q = A p), timed per launch with CUDA
+               events inside the timed steps, algorithmic bytes / duration
+  time_to_converge  mixed vs plain float64 GPU ParO from the initial guess to
+               max |lambda - lambda_discrete| < 1e-6 Ha (discrete values stored
+               under tests/golden, written from the CPU oracle by shift-invert)
+  cpu_baseline the CPU FP64 oracle, one outer iteration of the same workload
+``--impl reference`` times the oracle alone on the same workload.
+Multi-GPU (torchrun): independent replicas, one per rank, no collective on the
+data path; value = all ranks' units / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ParO dof·orbital updates/s & time-to-converge at 1e-6 Ha vs plain FP64 GPU"
+UNIT = "dof*orbital updates/s"
+NC, L, NORB, SIGMA = 64, 8.0, 20, 0.0
+WORKLOAD = "harmonic oscillator V=r^2/2, [-8,8]^3, 64^3 Q1 cells (250047 dofs), N=20, sigma=0"
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+GOLD = os.path.join(ROOT, "tests", "golden", "discrete_spectra.json")
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def problem(rank):
+    from paper_1405_0260_gb300 import workloads as W
+
+    return W.harmonic(nc=NC, L=L, N=NORB, seed=2000 + rank, sigma=SIGMA)
+
+
+def peaks():
+    try:
+        with open(PEAKS) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p is not None:
+            time.sleep(0.25)
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def flush_l2(buf):
+    buf.add_(1.0)  # 256 MiB write: larger than the 129 MB L2
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+
+    from paper_1405_0260_gb300 import binding as B
+
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.Stream()
+    p = problem(rank)
+    nI, N = p.n_interior, p.N
+    m = B.Mesh(p.n, p.lo, p.hi, B.PARO_MIXED, stream=stream)
+    with torch.cuda.stream(stream):
+        Vq = torch.from_numpy(p.Vq).cuda()
+        m.set_potential(Vq, p.sigma)
+        U = torch.from_numpy(np.ascontiguousarray(p.U0)).cuda()
+        X = torch.empty_like(U)
+    lam, _ = m.rayleigh_ritz(U, X)
+    U.copy_(X)
+    torch.cuda.synchronize()
+    params = B.paro_default_params(fixed_outer=1, solve_tol=1e-10, inner_tol=1e-4)
+    for _ in range(args.warmup):
+        _, lam, _ = m.iterate(U, lam, params)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    prof = B.paro_default_params(fixed_outer=1, solve_tol=1e-10, inner_tol=1e-4, profile=1)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches = 0
+    prof_ms = 0.0
+    prof_n = 0
+    prof_units = 0
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush_l2(flush)
+            stream.synchronize()
+            ev[i][0].record(stream)
+            _, lam, st = m.iterate(U, lam, prof)
+            ev[i][1].record(stream)
+            launches += st.kernel_launches
+            prof_ms += st.prof_ms
+            prof_n += st.prof_launches
+            prof_units += st.prof_dof_orb
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    if dist is not None:
+        dist.barrier()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    t_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    units = nI * N * args.steps * ws
+    value = units / (t_max * 1e-3)
+
+    # roofline of the CG operator kernel: per unit (node x orbital) it reads r and
+    # p_old and writes p_new and q (4 x 4 B in float32); per node and launch it
+    # needs the operator data once (8 float32 potential values per cell, about one
+    # cell per node, + the Jacobi diagonal: 36 B).
+    peak, peak_kind = peaks()
+    roof = None
+    if prof_n > 0 and prof_ms > 0:
+        alg_bytes = 16.0 * prof_units + 36.0 * nI * prof_n
+        achieved = alg_bytes / (prof_ms * 1e-3) / 1e9
+        roof = {"kernel": "k_cg_q<float> (p = D^-1 r + beta p; q = A p; (p,q))", "bound": "hbm",
+                "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "launches": prof_n, "avg_launch_us": round(1e3 * prof_ms / prof_n, 2),
+                "alg_bytes_per_launch": round(alg_bytes / prof_n)}
+
+    # end to end through the C ABI with host buffers
+    Uh = torch.empty((nI, N), dtype=torch.float64, pin_memory=True)
+    Uh.copy_(U.cpu())
+    e2e_ms = 0.0
+    for i in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush_l2(flush)
+        stream.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        with torch.cuda.stream(stream):
+            U.copy_(Uh, non_blocking=True)
+        _, lam, _ = m.iterate(U, lam, params)
+        with torch.cuda.stream(stream):
+            Uh.copy_(U, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        e2e_ms += a.elapsed_time(b)
+    e2e = {"value": nI * N * args.steps / (e2e_ms * 1e-3), "unit": UNIT,
+           "h2d_bytes_per_step": nI * N * 8, "d2h_bytes_per_step": nI * N * 8 + N * 8}
+
+    ttc = None
+    if not args.skip_converge and rank == 0:
+        ttc = time_to_converge(B, torch, p, stream)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.skip_cpu:
+        cpu = cpu_baseline(p)
+    m.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 CG + f64 refinement/RR",
+            "data": "synthetic (seeded Gaussian initial orbitals, analytic potential)",
+            "config": {"workload": WORKLOAD, "precision": "mixed", "parallelism": f"replicas x{ws}",
+                       "l2": "flushed (256 MiB write) between steps, outside the timed events",
+                       "step": "one ParO outer iteration (source problems to 1e-10 + Rayleigh-Ritz)"},
+            "e2e": e2e, "gpu_launches": launches, "roofline": roof, "clocks": clk.summary(),
+            "cpu_baseline": cpu, "time_to_converge": ttc, "wall_s_timed_region": wall,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def time_to_converge(B, torch, p, stream, max_outer=400):
+    """Device time from the initial guess until max |lambda - lambda_discrete| < 1e-6 Ha."""
+    try:
+        with open(GOLD) as f:
+            gold = np.array(json.load(f)["harmonic_64_L8"]["values"][: p.N])
+    except Exception as e:  # stored values missing
+        return {"error": f"no discrete reference values: {e}"}
+    out = {"target": "max_i |lambda_i - lambda_i(discrete, shift-invert Lanczos)| < 1e-6 Ha"}
+    for name, prec, params in (
+        ("mixed", B.PARO_MIXED, B.paro_default_params(fixed_outer=1, solve_tol=1e-10, inner_tol=1e-4)),
+        ("fp64", B.PARO_FP64, B.paro_default_params(fixed_outer=1, solve_tol=1e-10)),
+    ):
+        m = B.Mesh(p.n, p.lo, p.hi, prec, stream=stream)
+        with torch.cuda.stream(stream):
+            Vq = torch.from_numpy(p.Vq).cuda()
+            m.set_potential(Vq, p.sigma)
+            U = torch.from_numpy(np.ascontiguousarray(p.U0)).cuda()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        t0 = time.perf_counter()
+        lam = None
+        outer = 0
+        err = float("inf")
+        while outer < max_outer:
+            _, lam, _ = m.iterate(U, lam, params)
+            outer += 1
+            err = float(np.max(np.abs(lam - gold)))
+            if err < 1e-6:
+                break
+        b.record(stream)
+        b.synchronize()
+        out[name] = {"seconds": a.elapsed_time(b) * 1e-3, "wall_s": time.perf_counter() - t0,
+                     "outer_iters": outer, "final_err_ha": err, "reached": err < 1e-6}
+        m.close()
+    if out["mixed"]["reached"] and out["fp64"]["reached"]:
+        out["speedup_mixed_vs_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    return out
+
+
+def oracle_outer_step(ops, U, lam):
+    from oracle import paro as O
+
+    sol = O.source_problems(ops, U, lam, 1e-10, 5000)
+    rr = O.rayleigh_ritz(ops, sol.X)
+    return rr.U, rr.lam
+
+
+def cpu_baseline(p, steps=1):
+    """The oracle, as it stands, for `steps` outer iterations of the same workload."""
+    from oracle import paro as O
+
+    ops = O.assemble(O.Mesh(p.n, p.lo, p.hi), p.Vq, p.sigma)
+    rr = O.rayleigh_ritz(ops, p.U0)
+    U, lam = rr.U, rr.lam
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        U, lam = oracle_outer_step(ops, U, lam)
+    dt = time.perf_counter() - t0
+    return {"value": p.n_interior * p.N * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} outer iteration(s) of the full workload after the initial Rayleigh-Ritz "
+                      f"({dt:.1f} s); scipy sparse products run on one thread"}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    from oracle import paro as O
+
+    p = problem(0)
+    ops = O.assemble(O.Mesh(p.n, p.lo, p.hi), p.Vq, p.sigma)
+    rr = O.rayleigh_ritz(ops, p.U0)
+    U, lam = rr.U, rr.lam
+    for _ in range(args.warmup):
+        U, lam = oracle_outer_step(ops, U, lam)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        U, lam = oracle_outer_step(ops, U, lam)
+    dt = time.perf_counter() - t0
+    v = p.n_interior * p.N * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": "fp64 (CPU oracle)", "parallelism": "host cores"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "kind": "oracle", "cores": 1,
+                             "sample": "each step one full outer iteration of the workload"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--skip-cpu", action="store_true", help="omit the cpu_baseline leg")
+    ap.add_argument("--skip-converge", action="store_true", help="omit the time-to-converge leg")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,164 @@
+/*
+ * paro.h -- C ABI of the GB300 (sm_103a) parallel orbital-updating library.
+ *
+ * The method (Dai, Gong, Zhou, Zhu, "A parallel orbital-updating approach for
+ * electronic structure calculations"): given orbitals u_i and eigenvalue
+ * estimates lambda_i, Step 3 of Algorithms 1.1, 3.1 and A.1 solves N independent
+ * source problems a(u_i^(n+1/2), v) = lambda_i (u_i, v) (eq. alg-bvp), Step 4
+ * projects onto span{u_i^(n+1/2)} (Rayleigh-Ritz, eq. alg-evp), Step 5 loops.
+ *
+ * Discretisation: Q1 finite elements on a uniform nx x ny x nz hexahedral mesh
+ * of the box [lo, hi], homogeneous Dirichlet data on the whole boundary (the
+ * truncated domain of Section 2.2).  The bilinear form is the linear part of
+ * eq. (2.7):  a(w, v) = 1/2 (grad w, grad v) + (V w, v), with V given at the
+ * 2x2x2 Gauss points of every cell.  Discrete operators on interior nodes:
+ *     H = K/2 + M_V,   M = mass,   A = H + sigma M   (SPD for a suitable sigma).
+ * The source problem is solved in its shifted form
+ *     A x_i = (lambda_i + sigma) M u_i,
+ * whose solution spans the same space as the paper's (sigma = 0 is the paper's
+ * form; the shift keeps every system SPD when lambda_1 < 0).
+ *
+ * Conventions shared by every entry point
+ *  - All array arguments marked "device" are caller-owned device pointers; the
+ *    library never frees them.  Host arrays are caller-owned host memory.
+ *  - Orbital blocks U, X are float64, row-major (n_interior x N): the row of
+ *    interior node (i, j, k) (1 <= i <= nx-1, ...) is ((k-1)(ny-1) + (j-1))(nx-1)
+ *    + (i-1), i.e. x varies fastest, and the N orbital values of a node are
+ *    contiguous.
+ *  - Vq (potential) is float64, 8 values per cell, order [cz][cy][cx][qz][qy][qx],
+ *    Gauss abscissae (1 -/+ 1/sqrt 3)/2 in the cell's unit coordinates (q = 0 is
+ *    the smaller one).
+ *  - Every call is ordered on the handle's CUDA stream and returns a paro_status;
+ *    calls that return host values (eigenvalues, statistics) synchronise that
+ *    stream.  No exception crosses the ABI; paro_last_error() gives a message.
+ *  - The library owns the handle and its workspace (device memory sized for the
+ *    largest N seen, allocated on first use and released by paro_mesh_destroy).
+ *  - A handle must not be used from two host threads at once.
+ */
+#ifndef PARO_H
+#define PARO_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+typedef enum {
+  PARO_OK = 0,
+  PARO_ERR_ARG = -1,           /* invalid argument (null pointer, size out of range) */
+  PARO_ERR_CUDA = -2,          /* a CUDA runtime call failed (message has the CUDA error) */
+  PARO_ERR_NOT_SPD = -3,       /* p^T A p <= 0 in CG, or a non-positive Cholesky pivot */
+  PARO_ERR_NOT_CONVERGED = -4, /* an iteration limit was reached before its tolerance */
+  PARO_ERR_NONFINITE = -5,     /* NaN/Inf met in a reduction */
+  PARO_ERR_TIMEOUT = -6,       /* reserved: a bounded device-side wait ran out */
+  PARO_ERR_OOM = -7,           /* device allocation failed */
+  PARO_ERR_STATE = -8          /* call out of order (e.g. no potential set) */
+} paro_status;
+
+/* Precision modes of a mesh handle. */
+#define PARO_FP64 0  /* every operator apply, CG and projection in float64 */
+#define PARO_MIXED 1 /* float32 CG inside float64-residual iterative refinement */
+
+/* Operators for paro_apply. */
+#define PARO_OP_A 0 /* A = K/2 + M_V + sigma M */
+#define PARO_OP_H 1 /* H = K/2 + M_V            */
+#define PARO_OP_M 2 /* M                       */
+
+/* Arithmetic type for paro_apply. */
+#define PARO_F64 0
+#define PARO_F32 1
+
+typedef struct paro_mesh_s* paro_mesh;
+
+/* Solver controls.  paro_default_params fills the defaults noted here. */
+typedef struct {
+  double tol;         /* paro_iterate: stop when max_i |lambda_i^(n+1) - lambda_i^(n)| < tol (1e-10) */
+  int max_outer;      /* paro_iterate: outer-iteration limit (500) */
+  int n_check;        /* paro_iterate: test only the lowest n_check values; 0 = all N (0) */
+  double solve_tol;   /* source problem: stop orbital i when ||b_i - A x_i||_2 <= solve_tol ||b_i||_2 (1e-12) */
+  int pcg_maxit;      /* CG iteration limit per solve (FP64 mode) or per correction solve (mixed) (5000) */
+  double inner_tol;   /* mixed: relative tolerance of each float32 correction solve (1e-4) */
+  int max_refine;     /* mixed: refinement sweeps per source problem (20) */
+  int check_every;    /* CG iterations between host convergence checks (16) */
+  int fixed_outer;    /* paro_iterate: if > 0, run exactly this many outer iterations (0) */
+  int profile;        /* if != 0, time every launch of the CG operator kernel (q = A p) with CUDA
+                         events on the handle's stream and report it in paro_stats.prof_* (0) */
+} paro_params;
+
+/* Statistics of a call.  Counters and times (cg_iters*, ms_*, stencil_applies,
+ * kernel_launches, prof_*) are ADDED to what the struct holds, so zero it first;
+ * the other fields are overwritten.  Counts are summed over orbitals. */
+typedef struct {
+  int outer_iters;             /* outer iterations done by paro_iterate */
+  int refine_sweeps;           /* mixed mode: refinement sweeps in the last source solve */
+  long long cg_iters;          /* CG updates, summed over orbitals and solves */
+  long long cg_iters_f32;      /* of which in float32 */
+  int cg_iters_max;            /* largest per-orbital CG count in the last source solve */
+  double max_relres;           /* largest final ||b - A x|| / ||b|| of the last source solve (float64 residual) */
+  double max_dlambda;          /* last max |delta lambda| */
+  double ms_solve;             /* device time in source problems (CUDA events) */
+  double ms_rr;                /* device time in Rayleigh-Ritz */
+  long long stencil_applies;   /* orbital-operator applies (one orbital, one apply = 1) */
+  long long kernel_launches;   /* CUDA kernels this library launched during the call */
+  long long prof_launches;     /* profile != 0: launches of the CG operator kernel that were timed */
+  double prof_ms;              /* profile != 0: their summed device time (ms) */
+  long long prof_dof_orb;      /* profile != 0: sum over those launches of n_interior x orbitals processed */
+} paro_stats;
+
+void paro_default_params(paro_params* p);
+
+/* Create a handle for the uniform Q1 mesh of [lo, hi] with nx x ny x nz cells
+ * (each >= 2, at most 1024), Dirichlet on all faces.
+ * precision: PARO_FP64 or PARO_MIXED.  cuda_stream: a cudaStream_t (NULL = legacy
+ * default stream) on which every later call is ordered.  Allocates the operator
+ * storage (27 stencil weights per node in float64 and float32). */
+int paro_mesh_create(paro_mesh* out, int nx, int ny, int nz, const double lo[3], const double hi[3],
+                     int precision, void* cuda_stream);
+
+/* Release the handle and all library-owned device memory.  Synchronises the stream. */
+int paro_mesh_destroy(paro_mesh m);
+
+/* Set the potential and shift: builds A = K/2 + M_{V+sigma} as 27 weights per
+ * interior node (M_{V+sigma} by 2x2x2 Gauss quadrature, exact for sigma M) and
+ * its Jacobi diagonal.  Vq: device, 8*nx*ny*nz float64 in the layout above.
+ * eq. (2.7) with V = V_ext (+ V_H + V_xc for Kohn-Sham, supplied by the caller). */
+int paro_set_potential(paro_mesh m, const double* Vq, double sigma);
+
+/* Step 3 (eq. alg-bvp), all N orbitals at once:  A x_i = (lambda_i + sigma) M u_i,
+ * warm start x_i = u_i, Jacobi-preconditioned CG per orbital with its own
+ * convergence mask.  FP64 mode: float64 CG to solve_tol.  Mixed mode: float64
+ * residual, float32 CG correction to inner_tol, x += d, repeated until solve_tol
+ * or max_refine.  lambda: host[N].  U, X: device (n_interior x N) float64; X may
+ * not alias U.  Returns PARO_ERR_NOT_CONVERGED (X still written) if a limit was hit. */
+int paro_orbital_solve(paro_mesh m, int N, const double* lambda, const double* U, double* X,
+                       const paro_params* p, paro_stats* s);
+
+/* Step 4 (eq. alg-evp): Rayleigh-Ritz on span(X).  G_A = X^T H X, G_B = X^T M X,
+ * Cholesky G_B = L L^T, symmetric eigen of L^-1 G_A L^-T (ascending), C = L^-T Q,
+ * U_out = X C (M-orthonormal), lambda_out = Ritz values.  X, U_out: device
+ * (n_interior x N) float64, may alias (the rotation goes through workspace).
+ * lambda_out: host[N].  PARO_ERR_NOT_SPD if G_B is not positive definite
+ * (X rank-deficient). */
+int paro_rayleigh_ritz(paro_mesh m, int N, const double* X, double* U_out, double* lambda_out,
+                       paro_stats* s);
+
+/* Steps 3-5 repeated (Algorithm A.1 with a fixed potential; Algorithm 3.2 when
+ * n_check < N).  U: device (n_interior x N) float64, in: initial orbitals, out:
+ * final M-orthonormal Ritz vectors.  lambda: host[N], in: estimates, or NaN in
+ * lambda[0] to start with one Rayleigh-Ritz step on span(U); out: Ritz values.
+ * Stops on max |delta lambda| < tol (or after fixed_outer iterations). */
+int paro_iterate(paro_mesh m, int N, double* U, double* lambda, const paro_params* p, paro_stats* s);
+
+/* Y = op X for a block of N orbitals (op: PARO_OP_A/H/M), in float64 (dtype
+ * PARO_F64: X, Y double) or float32 (PARO_F32: X, Y float, float32 weights).
+ * X, Y: device (n_interior x N), must not alias.  The kernel the CG iterations use. */
+int paro_apply(paro_mesh m, int N, int op, int dtype, const void* X, void* Y);
+
+/* Message describing the last error on this handle ("" if none).  NULL handle:
+ * the last paro_mesh_create failure.  The string lives until the next call. */
+const char* paro_last_error(paro_mesh m);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PARO_H */

@@ -368,15 +368,23 @@ def paro(ops: Operators, U0: np.ndarray, tol: float = 1e-10, max_outer: int = 50
 
 
 def subspace_angles_M(M: sp.csr_matrix, U: np.ndarray, W: np.ndarray) -> np.ndarray:
-    """Principal angles between span(U) and span(W) in the M inner product."""
+    """Principal angles between span(U) and span(W) (same dimension) in the M inner product.
+
+    Taken from the sines: with M-orthonormal bases Qu, Qw, the singular values
+    of the M-orthogonal residual Qw - Qu (Qu^T M Qw), measured in the M norm, are
+    the sines of the angles.  The cosine form (arccos of the singular values of
+    Qu^T M Qw) cannot resolve angles below sqrt(2 eps) ~ 1.5e-8.
+    """
     GU = U.T @ (M @ U)
     GW = W.T @ (M @ W)
     LU = np.linalg.cholesky(GU)
     LW = np.linalg.cholesky(GW)
     Qu = U @ np.linalg.inv(LU).T
     Qw = W @ np.linalg.inv(LW).T
-    s = np.linalg.svd(Qu.T @ (M @ Qw), compute_uv=False)
-    return np.arccos(np.clip(s, -1.0, 1.0))
+    R = Qw - Qu @ (Qu.T @ (M @ Qw))
+    G = R.T @ (M @ R)
+    s2 = np.clip(np.linalg.eigvalsh(0.5 * (G + G.T)), 0.0, 1.0)
+    return np.sort(np.arcsin(np.sqrt(s2)))
 
 
 def eigen_residuals(ops: Operators, U: np.ndarray, lam: np.ndarray) -> np.ndarray:

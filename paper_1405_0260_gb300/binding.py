@@ -1,0 +1,228 @@
+"""Thin ctypes binding of ``libparo.so`` (declared in ``include/paro.h``).
+
+Argument marshalling only: every arithmetic step runs in the CUDA kernels of
+the library.  Device arrays are torch CUDA tensors passed by ``data_ptr()``;
+host arrays are numpy float64.  The library is loaded from this package's
+directory on first use; if it has not been built the call raises (there is no
+CPU fallback).
+
+Functions keep the C names: ``paro_mesh_create``, ``paro_set_potential``,
+``paro_orbital_solve``, ``paro_rayleigh_ritz``, ``paro_iterate``,
+``paro_apply``, ``paro_mesh_destroy``, ``paro_last_error``,
+``paro_default_params``.  ``Mesh`` bundles a handle with its stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libparo.so")
+
+PARO_OK = 0
+STATUS = {
+    0: "PARO_OK", -1: "PARO_ERR_ARG", -2: "PARO_ERR_CUDA", -3: "PARO_ERR_NOT_SPD",
+    -4: "PARO_ERR_NOT_CONVERGED", -5: "PARO_ERR_NONFINITE", -6: "PARO_ERR_TIMEOUT",
+    -7: "PARO_ERR_OOM", -8: "PARO_ERR_STATE",
+}
+PARO_FP64, PARO_MIXED = 0, 1
+PARO_OP_A, PARO_OP_H, PARO_OP_M = 0, 1, 2
+PARO_F64, PARO_F32 = 0, 1
+
+
+class paro_params(C.Structure):
+    _fields_ = [
+        ("tol", C.c_double), ("max_outer", C.c_int), ("n_check", C.c_int),
+        ("solve_tol", C.c_double), ("pcg_maxit", C.c_int), ("inner_tol", C.c_double),
+        ("max_refine", C.c_int), ("check_every", C.c_int), ("fixed_outer", C.c_int),
+        ("profile", C.c_int),
+    ]
+
+
+class paro_stats(C.Structure):
+    _fields_ = [
+        ("outer_iters", C.c_int), ("refine_sweeps", C.c_int), ("cg_iters", C.c_longlong),
+        ("cg_iters_f32", C.c_longlong), ("cg_iters_max", C.c_int), ("max_relres", C.c_double),
+        ("max_dlambda", C.c_double), ("ms_solve", C.c_double), ("ms_rr", C.c_double),
+        ("stencil_applies", C.c_longlong), ("kernel_launches", C.c_longlong),
+        ("prof_launches", C.c_longlong), ("prof_ms", C.c_double), ("prof_dof_orb", C.c_longlong),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ParoError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() (no CPU fallback exists)")
+    L = C.CDLL(LIB_PATH)
+    vp, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.c_int
+    L.paro_default_params.argtypes = [C.POINTER(paro_params)]
+    L.paro_default_params.restype = None
+    L.paro_mesh_create.argtypes = [C.POINTER(vp), ip, ip, ip, dp, dp, ip, vp]
+    L.paro_mesh_destroy.argtypes = [vp]
+    L.paro_set_potential.argtypes = [vp, vp, C.c_double]
+    L.paro_orbital_solve.argtypes = [vp, ip, dp, vp, vp, C.POINTER(paro_params), C.POINTER(paro_stats)]
+    L.paro_rayleigh_ritz.argtypes = [vp, ip, vp, vp, dp, C.POINTER(paro_stats)]
+    L.paro_iterate.argtypes = [vp, ip, vp, dp, C.POINTER(paro_params), C.POINTER(paro_stats)]
+    L.paro_apply.argtypes = [vp, ip, ip, ip, vp, vp]
+    L.paro_last_error.argtypes = [vp]
+    L.paro_last_error.restype = C.c_char_p
+    for f in ("paro_mesh_create", "paro_mesh_destroy", "paro_set_potential", "paro_orbital_solve",
+              "paro_rayleigh_ritz", "paro_iterate", "paro_apply"):
+        getattr(L, f).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _check(rc, handle, allow=()):
+    if rc != PARO_OK and rc not in allow:
+        raise ParoError(rc, paro_last_error(handle))
+    return rc
+
+
+def paro_last_error(handle) -> str:
+    s = lib().paro_last_error(handle)
+    return s.decode() if s else ""
+
+
+def paro_default_params(**over) -> paro_params:
+    p = paro_params()
+    lib().paro_default_params(C.byref(p))
+    for k, v in over.items():
+        setattr(p, k, v)
+    return p
+
+
+def paro_mesh_create(n, lo, hi, precision=PARO_FP64, stream=0):
+    h = C.c_void_p()
+    lo_a = np.ascontiguousarray(lo, dtype=np.float64)
+    hi_a = np.ascontiguousarray(hi, dtype=np.float64)
+    rc = lib().paro_mesh_create(C.byref(h), int(n[0]), int(n[1]), int(n[2]), _dptr(lo_a), _dptr(hi_a),
+                                int(precision), C.c_void_p(stream))
+    _check(rc, None)
+    return h
+
+
+def paro_mesh_destroy(h):
+    return lib().paro_mesh_destroy(h)
+
+
+def paro_set_potential(h, Vq_ptr: int, sigma: float):
+    return _check(lib().paro_set_potential(h, C.c_void_p(Vq_ptr), float(sigma)), h)
+
+
+def paro_orbital_solve(h, N, lam: np.ndarray, U_ptr, X_ptr, params=None, stats=None, allow=()):
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    rc = lib().paro_orbital_solve(h, int(N), _dptr(lam), C.c_void_p(U_ptr), C.c_void_p(X_ptr),
+                                  C.byref(params) if params is not None else None,
+                                  C.byref(stats) if stats is not None else None)
+    return _check(rc, h, allow)
+
+
+def paro_rayleigh_ritz(h, N, X_ptr, U_ptr, lam_out: np.ndarray, stats=None):
+    assert lam_out.dtype == np.float64 and lam_out.flags.c_contiguous and lam_out.size >= N
+    rc = lib().paro_rayleigh_ritz(h, int(N), C.c_void_p(X_ptr), C.c_void_p(U_ptr), _dptr(lam_out),
+                                  C.byref(stats) if stats is not None else None)
+    return _check(rc, h)
+
+
+def paro_iterate(h, N, U_ptr, lam: np.ndarray, params=None, stats=None, allow=()):
+    assert lam.dtype == np.float64 and lam.flags.c_contiguous and lam.size >= N
+    rc = lib().paro_iterate(h, int(N), C.c_void_p(U_ptr), _dptr(lam),
+                            C.byref(params) if params is not None else None,
+                            C.byref(stats) if stats is not None else None)
+    return _check(rc, h, allow)
+
+
+def paro_apply(h, N, op, dtype, X_ptr, Y_ptr):
+    return _check(lib().paro_apply(h, int(N), int(op), int(dtype), C.c_void_p(X_ptr), C.c_void_p(Y_ptr)), h)
+
+
+class Mesh:
+    """A mesh handle bound to a torch CUDA stream (torch tensors in and out)."""
+
+    def __init__(self, n, lo, hi, precision=PARO_FP64, stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("libparo needs a CUDA device (no CPU fallback)")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.n = tuple(int(v) for v in n)
+        self.n_interior = (self.n[0] - 1) * (self.n[1] - 1) * (self.n[2] - 1)
+        self.h = paro_mesh_create(self.n, lo, hi, precision, self.stream.cuda_stream)
+        self._keep = []
+
+    def close(self):
+        if self.h is not None:
+            paro_mesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _dev(self, t, dtype=None):
+        import torch
+
+        dtype = dtype or torch.float64
+        if not (t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+            raise ValueError(f"expected a contiguous CUDA {dtype} tensor")
+        return t.data_ptr()
+
+    def set_potential(self, Vq, sigma):
+        self._keep = [Vq]
+        paro_set_potential(self.h, self._dev(Vq), sigma)
+
+    def orbital_solve(self, lam, U, X, params=None, allow=()):
+        st = paro_stats()
+        rc = paro_orbital_solve(self.h, U.shape[1], np.asarray(lam, dtype=np.float64), self._dev(U), self._dev(X),
+                                params, st, allow)
+        return rc, st
+
+    def rayleigh_ritz(self, X, U_out):
+        N = X.shape[1]
+        lam = np.zeros(N)
+        st = paro_stats()
+        paro_rayleigh_ritz(self.h, N, self._dev(X), self._dev(U_out), lam, st)
+        return lam, st
+
+    def iterate(self, U, lam=None, params=None, allow=()):
+        N = U.shape[1]
+        lam = np.full(N, np.nan) if lam is None else np.array(lam, dtype=np.float64)
+        st = paro_stats()
+        rc = paro_iterate(self.h, N, self._dev(U), lam, params, st, allow)
+        return rc, lam, st
+
+    def apply(self, op, X, Y):
+        import torch
+
+        dt = PARO_F32 if X.dtype == torch.float32 else PARO_F64
+        paro_apply(self.h, X.shape[1], op, dt, self._dev(X, X.dtype), self._dev(Y, X.dtype))

@@ -1,0 +1,642 @@
+// C ABI of libparo (declared in include/paro.h): handle, workspace and the host
+// orchestration of Steps 3-5 of the parallel orbital-updating method.  Every
+// arithmetic step runs in the kernels of stencil.cu, pcg.cu and rr.cu; this file
+// only sequences launches on the handle's stream and reads back the per-orbital
+// convergence counters and the Ritz values.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/paro.h"
+#include "common.cuh"
+
+using namespace paro;
+
+struct paro_mesh_s {
+  Grid g{};
+  int precision = PARO_FP64;
+  cudaStream_t st = nullptr;
+  std::string err;
+  double sigma = 0.0;
+  bool have_pot = false;
+  double* coef64 = nullptr;
+  float* coef32 = nullptr;
+  double* dinv64 = nullptr;
+  float* dinv32 = nullptr;
+  Weights27 mw{};
+  // workspace sized for Np_alloc orbitals
+  int Np_alloc = 0;
+  double *u = nullptr, *x = nullptr, *b = nullptr, *r = nullptr, *p0 = nullptr, *p1 = nullptr, *q = nullptr;
+  float *b32 = nullptr, *x32 = nullptr, *r32 = nullptr, *p32a = nullptr, *p32b = nullptr, *q32 = nullptr;
+  double *gpart = nullptr, *GA = nullptr, *GB = nullptr, *C = nullptr, *theta = nullptr, *eigwork = nullptr;
+  double* dscal = nullptr;  // per-orbital double scalars
+  int* dint = nullptr;      // per-orbital int scalars
+  double* partial = nullptr;
+  unsigned int* ticket = nullptr;
+  double* h_dbl = nullptr;  // pinned host staging
+  int* h_int = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  std::vector<void*> allocs;
+  // launch accounting and optional per-launch timing of the CG operator kernel
+  long long launches = 0;
+  unsigned long long* work = nullptr;  // device counter written by cg_q
+  int profile = 0;
+  std::vector<cudaEvent_t> pev;       // kProfPairs start/stop pairs
+  int pev_used = 0;
+  long long prof_launches = 0;
+  double prof_ms = 0.0;
+};
+
+static std::string g_create_err;
+
+namespace {
+
+#define CK(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) {                                                          \
+      m->err = std::string(#call) + ": " + cudaGetErrorString(e_);                    \
+      return e_ == cudaErrorMemoryAllocation ? PARO_ERR_OOM : PARO_ERR_CUDA;          \
+    }                                                                                 \
+  } while (0)
+
+#define TRY(expr)                  \
+  do {                             \
+    int rc_ = (expr);              \
+    if (rc_ != PARO_OK) return rc_; \
+  } while (0)
+
+// A library kernel launch (nk kernels): checked and counted.
+#define LAUNCH(nk, call)     \
+  do {                       \
+    CK(call);                \
+    m->launches += (nk);     \
+  } while (0)
+
+constexpr int kProfPairs = 256;
+
+int fail(paro_mesh m, int code, const std::string& msg) {
+  m->err = msg;
+  return code;
+}
+
+template <typename T>
+int dalloc(paro_mesh m, T** p, size_t count, bool zero = true) {
+  void* v = nullptr;
+  cudaError_t e = cudaMalloc(&v, count * sizeof(T) > 0 ? count * sizeof(T) : 16);
+  if (e != cudaSuccess) {
+    m->err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? PARO_ERR_OOM : PARO_ERR_CUDA;
+  }
+  m->allocs.push_back(v);
+  if (zero) {
+    e = cudaMemsetAsync(v, 0, count * sizeof(T), m->st);
+    if (e != cudaSuccess) return fail(m, PARO_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+  }
+  *p = static_cast<T*>(v);
+  return PARO_OK;
+}
+
+void dfree(paro_mesh m, void* p) {
+  if (!p) return;
+  for (auto& a : m->allocs)
+    if (a == p) {
+      cudaFree(a);
+      a = nullptr;
+    }
+}
+
+// Per-orbital scalar slots in dscal (doubles) and dint (ints), each kMaxN long.
+enum { S_RZ, S_PQ, S_ALPHA, S_BETA, S_BB, S_RR, S_RBB, S_RRR, S_SCALE, S_COUNT };
+enum { I_ACTIVE, I_ITERS, I_SKIP, I_COUNT };
+// then single ints after 3*kMaxN: n_active, status
+
+CGState cg_state(paro_mesh m, bool refine) {
+  CGState s;
+  s.rz = m->dscal + S_RZ * kMaxN;
+  s.pq = m->dscal + S_PQ * kMaxN;
+  s.alpha = m->dscal + S_ALPHA * kMaxN;
+  s.beta = m->dscal + S_BETA * kMaxN;
+  s.bb = m->dscal + (refine ? S_RBB : S_BB) * kMaxN;
+  s.rr = m->dscal + (refine ? S_RRR : S_RR) * kMaxN;
+  s.active = m->dint + I_ACTIVE * kMaxN;
+  s.iters = m->dint + I_ITERS * kMaxN;
+  s.skip = m->dint + I_SKIP * kMaxN;
+  s.n_active = m->dint + I_COUNT * kMaxN;
+  s.status = m->dint + I_COUNT * kMaxN + 1;
+  s.partial = m->partial;
+  s.ticket = m->ticket;
+  s.work = m->profile ? m->work : nullptr;
+  return s;
+}
+
+int ensure_workspace(paro_mesh m, int Np) {
+  if (Np == m->Np_alloc) return PARO_OK;
+  // release the previous vector workspace
+  void* olds[] = {m->u, m->x, m->b, m->r, m->p0, m->p1, m->q, m->b32, m->x32, m->r32, m->p32a, m->p32b, m->q32,
+                  m->gpart, m->GA, m->GB, m->C, m->theta, m->eigwork};
+  CK(cudaStreamSynchronize(m->st));
+  for (void* p : olds) dfree(m, p);
+  size_t n = (size_t)m->g.G * Np;
+  TRY(dalloc(m, &m->u, n));
+  TRY(dalloc(m, &m->x, n));
+  TRY(dalloc(m, &m->b, n));
+  TRY(dalloc(m, &m->r, n));
+  TRY(dalloc(m, &m->p0, n));
+  TRY(dalloc(m, &m->p1, n));
+  TRY(dalloc(m, &m->q, n));
+  if (m->precision == PARO_MIXED) {
+    TRY(dalloc(m, &m->b32, n));
+    TRY(dalloc(m, &m->x32, n));
+    TRY(dalloc(m, &m->r32, n));
+    TRY(dalloc(m, &m->p32a, n));
+    TRY(dalloc(m, &m->p32b, n));
+    TRY(dalloc(m, &m->q32, n));
+  }
+  TRY(dalloc(m, &m->gpart, gram_partial_doubles(m->g, Np)));
+  TRY(dalloc(m, &m->GA, (size_t)Np * Np));
+  TRY(dalloc(m, &m->GB, (size_t)Np * Np));
+  TRY(dalloc(m, &m->C, (size_t)Np * Np));
+  TRY(dalloc(m, &m->theta, (size_t)Np));
+  TRY(dalloc(m, &m->eigwork, (size_t)4 * Np * Np));
+  m->Np_alloc = Np;
+  return PARO_OK;
+}
+
+int check_status(paro_mesh m, const char* where) {
+  int* st = m->dint + I_COUNT * kMaxN + 1;
+  CK(cudaMemcpyAsync(m->h_int, st, sizeof(int), cudaMemcpyDeviceToHost, m->st));
+  CK(cudaStreamSynchronize(m->st));
+  int bits = m->h_int[0];
+  if (bits == 0) return PARO_OK;
+  CK(cudaMemsetAsync(st, 0, sizeof(int), m->st));
+  if (bits & kStatNonFinite) return fail(m, PARO_ERR_NONFINITE, std::string(where) + ": non-finite value in a reduction");
+  if (bits & kStatNotSPD)
+    return fail(m, PARO_ERR_NOT_SPD, std::string(where) + ": operator or Gram matrix not positive definite");
+  if (bits & kStatNotConverged)
+    return fail(m, PARO_ERR_NOT_CONVERGED, std::string(where) + ": iteration limit reached");
+  return PARO_OK;
+}
+
+int read_n_active(paro_mesh m, int* out) {
+  CK(cudaMemcpyAsync(m->h_int, m->dint + I_COUNT * kMaxN, sizeof(int), cudaMemcpyDeviceToHost, m->st));
+  CK(cudaStreamSynchronize(m->st));
+  *out = m->h_int[0];
+  return PARO_OK;
+}
+
+// Sum and max of the per-orbital CG counts of the last solve.
+int read_iters(paro_mesh m, int N, long long* sum, int* mx) {
+  CK(cudaMemcpyAsync(m->h_int, m->dint + I_ITERS * kMaxN, sizeof(int) * N, cudaMemcpyDeviceToHost, m->st));
+  CK(cudaStreamSynchronize(m->st));
+  long long s = 0;
+  int x = 0;
+  for (int i = 0; i < N; ++i) {
+    s += m->h_int[i];
+    if (m->h_int[i] > x) x = m->h_int[i];
+  }
+  *sum = s;
+  *mx = x;
+  return PARO_OK;
+}
+
+// Sum the recorded start/stop pairs (the stream has been synchronised).
+int drain_profile(paro_mesh m) {
+  for (int i = 0; i < m->pev_used; ++i) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, m->pev[2 * i], m->pev[2 * i + 1]));
+    m->prof_ms += ms;
+    m->prof_launches += 1;
+  }
+  m->pev_used = 0;
+  return PARO_OK;
+}
+
+template <typename T>
+int run_cg(paro_mesh m, int N, int Np, const CGVectors<T>& v, const CGState& s, bool x_zero, double tol, int maxit,
+           int check_every, long long* it_sum, int* it_max) {
+  LAUNCH(1, launch_cg_init<T>(m->g, N, Np, v, s, x_zero, tol, maxit, m->st));
+  int nact = 0;
+  TRY(read_n_active(m, &nact));
+  int parity = 0;
+  int done = 0;
+  if (m->profile && check_every > kProfPairs) check_every = kProfPairs;
+  while (nact > 0 && done < maxit) {
+    int k = check_every;
+    if (k > maxit - done) k = maxit - done;
+    for (int i = 0; i < k; ++i) {
+      if (m->profile) CK(cudaEventRecord(m->pev[2 * m->pev_used], m->st));
+      LAUNCH(1, launch_cg_q<T>(m->g, Np, v, s, parity, m->st));
+      if (m->profile) {
+        CK(cudaEventRecord(m->pev[2 * m->pev_used + 1], m->st));
+        m->pev_used++;
+      }
+      LAUNCH(1, launch_cg_update<T>(m->g, Np, v, s, parity, tol, maxit, m->st));
+      parity ^= 1;
+    }
+    done += k;
+    TRY(read_n_active(m, &nact));
+    if (m->profile) TRY(drain_profile(m));
+  }
+  TRY(read_iters(m, N, it_sum, it_max));
+  return PARO_OK;
+}
+
+// Step 3 on the packed buffers: u (current orbitals) -> x (source solutions).
+int solve_packed(paro_mesh m, int N, const double* lam, const paro_params& p, paro_stats* st) {
+  const int Np = m->Np_alloc;
+  Grid& g = m->g;
+  // b = (lambda + sigma) M u
+  for (int i = 0; i < Np; ++i) m->h_dbl[i] = i < N ? lam[i] + m->sigma : 0.0;
+  double* scale = m->dscal + S_SCALE * kMaxN;
+  CK(cudaMemcpyAsync(scale, m->h_dbl, sizeof(double) * Np, cudaMemcpyHostToDevice, m->st));
+  LAUNCH(1, launch_apply_f64(g, Np, nullptr, &m->mw, 0.0, m->u, m->b, scale, m->st));
+  CK(cudaMemcpyAsync(m->x, m->u, sizeof(double) * g.G * Np, cudaMemcpyDeviceToDevice, m->st));
+  long long its = 0;
+  int itmax = 0;
+  if (m->precision == PARO_FP64) {
+    CGVectors<double> v{m->x, m->b, m->r, {m->p0, m->p1}, m->q, m->coef64, m->dinv64};
+    CGState s = cg_state(m, false);
+    s.skip = nullptr;
+    TRY(run_cg<double>(m, N, Np, v, s, false, p.solve_tol, p.pcg_maxit, p.check_every, &its, &itmax));
+    if (st) {
+      st->cg_iters += its;
+      st->cg_iters_max = itmax;
+      st->refine_sweeps = 0;
+      st->stencil_applies += its + N;
+    }
+    // float64 true residual for the statistics
+    CGState rs = cg_state(m, true);
+    LAUNCH(1, launch_refine_residual(g, N, Np, m->coef64, m->x, m->b, nullptr, rs, p.solve_tol, m->st));
+  } else {
+    CGVectors<float> v{m->x32, m->b32, m->r32, {m->p32a, m->p32b}, m->q32, m->coef32, m->dinv32};
+    CGState rs = cg_state(m, true);
+    CGState s = cg_state(m, false);
+    int sweep = 0;
+    long long its32 = 0;
+    int maxit_seen = 0;
+    for (;;) {
+      LAUNCH(1, launch_refine_residual(g, N, Np, m->coef64, m->x, m->b, m->b32, rs, p.solve_tol, m->st));
+      if (st) st->stencil_applies += N;
+      int open = 0;
+      TRY(read_n_active(m, &open));
+      if (open == 0) break;
+      if (sweep >= p.max_refine) {
+        if (st) st->refine_sweeps = sweep;
+        TRY(check_status(m, "orbital_solve"));
+        m->err = "mixed refinement: max_refine sweeps reached";
+        return PARO_ERR_NOT_CONVERGED;
+      }
+      long long i1 = 0;
+      int imx = 0;
+      TRY(run_cg<float>(m, N, Np, v, s, true, p.inner_tol, p.pcg_maxit, p.check_every, &i1, &imx));
+      // an inner limit is not fatal: refinement carries on from the partial correction
+      int* stw = m->dint + I_COUNT * kMaxN + 1;
+      CK(cudaMemcpyAsync(m->h_int, stw, sizeof(int), cudaMemcpyDeviceToHost, m->st));
+      CK(cudaStreamSynchronize(m->st));
+      if (m->h_int[0] & kStatNotConverged) {
+        m->h_int[0] &= ~kStatNotConverged;
+        CK(cudaMemcpyAsync(stw, m->h_int, sizeof(int), cudaMemcpyHostToDevice, m->st));
+      }
+      TRY(check_status(m, "orbital_solve (float32 correction)"));
+      LAUNCH(1, launch_refine_update(g, Np, m->x, m->x32, s.skip, m->st));
+      its32 += i1;
+      if (imx > maxit_seen) maxit_seen = imx;
+      ++sweep;
+    }
+    if (st) {
+      st->cg_iters += its32;
+      st->cg_iters_f32 += its32;
+      st->cg_iters_max = maxit_seen;
+      st->refine_sweeps = sweep;
+      st->stencil_applies += its32;
+    }
+  }
+  if (st) {
+    double* rr = m->dscal + S_RRR * kMaxN;
+    double* bb = m->dscal + S_RBB * kMaxN;
+    CK(cudaMemcpyAsync(m->h_dbl, rr, sizeof(double) * N, cudaMemcpyDeviceToHost, m->st));
+    CK(cudaMemcpyAsync(m->h_dbl + kMaxN, bb, sizeof(double) * N, cudaMemcpyDeviceToHost, m->st));
+    CK(cudaStreamSynchronize(m->st));
+    double worst = 0.0;
+    for (int i = 0; i < N; ++i) {
+      double b = m->h_dbl[kMaxN + i];
+      double rel = b > 0 ? std::sqrt(m->h_dbl[i] / b) : std::sqrt(m->h_dbl[i]);
+      if (rel > worst) worst = rel;
+    }
+    st->max_relres = worst;
+  }
+  return check_status(m, "orbital_solve");
+}
+
+// Step 4 on packed buffers: src -> dst (Ritz vectors), lam (host, ascending).
+int rr_packed(paro_mesh m, int N, const double* src, double* dst, double* lam) {
+  const int Np = m->Np_alloc;
+  Grid& g = m->g;
+  LAUNCH(1, launch_apply_f64(g, Np, m->coef64, &m->mw, m->sigma, src, m->r, nullptr, m->st));  // H = A - sigma M
+  LAUNCH(1, launch_apply_f64(g, Np, nullptr, &m->mw, 0.0, src, m->q, nullptr, m->st));         // M
+  LAUNCH(2, launch_gram2(g, N, Np, src, m->r, m->q, m->gpart, nullptr, m->GA, m->GB, m->st));
+  LAUNCH(1, launch_small_eig(N, m->GA, m->GB, m->eigwork, m->C, m->theta, m->dint + I_COUNT * kMaxN + 1, m->st));
+  TRY(check_status(m, "rayleigh_ritz"));
+  LAUNCH(1, launch_rotate(g, N, Np, src, m->C, dst, m->st));
+  CK(cudaMemcpyAsync(m->h_dbl, m->theta, sizeof(double) * N, cudaMemcpyDeviceToHost, m->st));
+  CK(cudaStreamSynchronize(m->st));
+  for (int i = 0; i < N; ++i) lam[i] = m->h_dbl[i];
+  return PARO_OK;
+}
+
+int check_common(paro_mesh m, int N) {
+  if (!m) return PARO_ERR_ARG;
+  if (N < 1 || N > kMaxN) return fail(m, PARO_ERR_ARG, "N out of range [1, 1024]");
+  if (!m->have_pot) return fail(m, PARO_ERR_STATE, "paro_set_potential has not been called");
+  return PARO_OK;
+}
+
+struct Timer {
+  paro_mesh m;
+  double* acc;
+  Timer(paro_mesh mm, double* a) : m(mm), acc(a) {
+    if (acc) cudaEventRecord(m->e0, m->st);
+  }
+  void stop() {
+    if (!acc) return;
+    cudaEventRecord(m->e1, m->st);
+    cudaEventSynchronize(m->e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, m->e0, m->e1);
+    *acc += ms;
+    acc = nullptr;
+  }
+  ~Timer() { stop(); }
+};
+
+// Per-call accounting: kernel launches, and (params.profile) the timed CG
+// operator launches with the work they processed.
+struct CallScope {
+  paro_mesh m;
+  paro_stats* s;
+  long long l0;
+  CallScope(paro_mesh mm, paro_stats* ss, int profile) : m(mm), s(ss), l0(mm->launches) {
+    m->profile = 0;
+    m->prof_launches = 0;
+    m->prof_ms = 0.0;
+    m->pev_used = 0;
+    if (!profile || !s) return;
+    if (m->pev.empty()) {
+      m->pev.resize(2 * kProfPairs, nullptr);
+      for (auto& e : m->pev)
+        if (cudaEventCreate(&e) != cudaSuccess) {
+          m->pev.clear();
+          return;
+        }
+    }
+    if (cudaMemsetAsync(m->work, 0, sizeof(unsigned long long), m->st) != cudaSuccess) return;
+    m->profile = 1;
+  }
+  ~CallScope() {
+    if (s) {
+      s->kernel_launches += m->launches - l0;
+      if (m->profile) {
+        unsigned long long w = 0;
+        if (cudaMemcpyAsync(m->h_dbl, m->work, sizeof(w), cudaMemcpyDeviceToHost, m->st) == cudaSuccess &&
+            cudaStreamSynchronize(m->st) == cudaSuccess)
+          std::memcpy(&w, m->h_dbl, sizeof(w));
+        s->prof_launches += m->prof_launches;
+        s->prof_ms += m->prof_ms;
+        s->prof_dof_orb += (long long)w;
+      }
+    }
+    m->profile = 0;
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+void paro_default_params(paro_params* p) {
+  if (!p) return;
+  p->tol = 1e-10;
+  p->max_outer = 500;
+  p->n_check = 0;
+  p->solve_tol = 1e-12;
+  p->pcg_maxit = 5000;
+  p->inner_tol = 1e-4;
+  p->max_refine = 20;
+  p->check_every = 16;
+  p->fixed_outer = 0;
+}
+
+int paro_mesh_create(paro_mesh* out, int nx, int ny, int nz, const double lo[3], const double hi[3], int precision,
+                     void* cuda_stream) {
+  if (!out || !lo || !hi) {
+    g_create_err = "null argument";
+    return PARO_ERR_ARG;
+  }
+  *out = nullptr;
+  if (nx < 2 || ny < 2 || nz < 2 || nx > 1024 || ny > 1024 || nz > 1024) {
+    g_create_err = "cells per axis must be in [2, 1024]";
+    return PARO_ERR_ARG;
+  }
+  if (precision != PARO_FP64 && precision != PARO_MIXED) {
+    g_create_err = "precision must be PARO_FP64 or PARO_MIXED";
+    return PARO_ERR_ARG;
+  }
+  for (int d = 0; d < 3; ++d)
+    if (!(hi[d] > lo[d]) || !std::isfinite(lo[d]) || !std::isfinite(hi[d])) {
+      g_create_err = "box must satisfy lo < hi (finite)";
+      return PARO_ERR_ARG;
+    }
+  paro_mesh m = new paro_mesh_s();
+  m->precision = precision;
+  m->st = static_cast<cudaStream_t>(cuda_stream);
+  Grid& g = m->g;
+  g.nx = nx;
+  g.ny = ny;
+  g.nz = nz;
+  g.Px = nx + 1;
+  g.Py = ny + 1;
+  g.Pz = nz + 1;
+  g.G = (long long)g.Px * g.Py * g.Pz;
+  g.nI = (nx - 1) * (ny - 1) * (nz - 1);
+  g.hx = (hi[0] - lo[0]) / nx;
+  g.hy = (hi[1] - lo[1]) / ny;
+  g.hz = (hi[2] - lo[2]) / nz;
+  mass_weights(g, &m->mw);
+  int rc = PARO_OK;
+  cudaError_t e;
+  if ((rc = dalloc(m, &m->coef64, (size_t)27 * g.G)) || (rc = dalloc(m, &m->coef32, (size_t)27 * g.G)) ||
+      (rc = dalloc(m, &m->dinv64, (size_t)g.G)) || (rc = dalloc(m, &m->dinv32, (size_t)g.G)) ||
+      (rc = dalloc(m, &m->dscal, (size_t)S_COUNT * kMaxN)) ||
+      (rc = dalloc(m, &m->dint, (size_t)I_COUNT * kMaxN + 8)) ||
+      (rc = dalloc(m, &m->partial, (size_t)3 * kMaxRedBlocks * kMaxN)) || (rc = dalloc(m, &m->ticket, 4)) ||
+      (rc = dalloc(m, &m->work, 1))) {
+    g_create_err = m->err;
+    paro_mesh_destroy(m);
+    return rc;
+  }
+  if ((e = cudaMallocHost(&m->h_dbl, sizeof(double) * 2 * kMaxN)) != cudaSuccess ||
+      (e = cudaMallocHost(&m->h_int, sizeof(int) * kMaxN)) != cudaSuccess ||
+      (e = cudaEventCreate(&m->e0)) != cudaSuccess || (e = cudaEventCreate(&m->e1)) != cudaSuccess) {
+    g_create_err = std::string("host setup: ") + cudaGetErrorString(e);
+    paro_mesh_destroy(m);
+    return PARO_ERR_CUDA;
+  }
+  if ((e = cudaStreamSynchronize(m->st)) != cudaSuccess) {
+    g_create_err = std::string("stream: ") + cudaGetErrorString(e);
+    paro_mesh_destroy(m);
+    return PARO_ERR_CUDA;
+  }
+  *out = m;
+  return PARO_OK;
+}
+
+int paro_mesh_destroy(paro_mesh m) {
+  if (!m) return PARO_ERR_ARG;
+  cudaStreamSynchronize(m->st);
+  for (void* p : m->allocs)
+    if (p) cudaFree(p);
+  if (m->h_dbl) cudaFreeHost(m->h_dbl);
+  if (m->h_int) cudaFreeHost(m->h_int);
+  if (m->e0) cudaEventDestroy(m->e0);
+  if (m->e1) cudaEventDestroy(m->e1);
+  for (auto e : m->pev)
+    if (e) cudaEventDestroy(e);
+  delete m;
+  return PARO_OK;
+}
+
+int paro_set_potential(paro_mesh m, const double* Vq, double sigma) {
+  if (!m) return PARO_ERR_ARG;
+  if (!Vq) return fail(m, PARO_ERR_ARG, "Vq is null");
+  if (!std::isfinite(sigma)) return fail(m, PARO_ERR_ARG, "sigma must be finite");
+  LAUNCH(1, launch_build_coef(m->g, Vq, sigma, m->coef64, m->coef32, m->dinv64, m->dinv32, m->st));
+  m->sigma = sigma;
+  m->have_pot = true;
+  return PARO_OK;
+}
+
+int paro_orbital_solve(paro_mesh m, int N, const double* lambda, const double* U, double* X, const paro_params* p,
+                       paro_stats* s) {
+  TRY(check_common(m, N));
+  if (!lambda || !U || !X) return fail(m, PARO_ERR_ARG, "null pointer");
+  if (U == X) return fail(m, PARO_ERR_ARG, "X must not alias U");
+  paro_params pp;
+  if (p) pp = *p;
+  else paro_default_params(&pp);
+  if (pp.check_every < 1) pp.check_every = 1;
+  const int Np = (N + 3) / 4 * 4;
+  TRY(ensure_workspace(m, Np));
+  CallScope cs(m, s, pp.profile);
+  LAUNCH(1, launch_pack(m->g, N, Np, U, m->u, m->st));
+  Timer t(m, s ? &s->ms_solve : nullptr);
+  int rc = solve_packed(m, N, lambda, pp, s);
+  t.stop();
+  if (rc != PARO_OK && rc != PARO_ERR_NOT_CONVERGED) return rc;
+  LAUNCH(1, launch_unpack(m->g, N, Np, m->x, X, m->st));
+  CK(cudaStreamSynchronize(m->st));
+  return rc;
+}
+
+int paro_rayleigh_ritz(paro_mesh m, int N, const double* X, double* U_out, double* lambda_out, paro_stats* s) {
+  TRY(check_common(m, N));
+  if (!X || !U_out || !lambda_out) return fail(m, PARO_ERR_ARG, "null pointer");
+  const int Np = (N + 3) / 4 * 4;
+  TRY(ensure_workspace(m, Np));
+  CallScope cs(m, s, 0);
+  LAUNCH(1, launch_pack(m->g, N, Np, X, m->x, m->st));
+  Timer t(m, s ? &s->ms_rr : nullptr);
+  TRY(rr_packed(m, N, m->x, m->u, lambda_out));
+  t.stop();
+  LAUNCH(1, launch_unpack(m->g, N, Np, m->u, U_out, m->st));
+  CK(cudaStreamSynchronize(m->st));
+  return PARO_OK;
+}
+
+int paro_iterate(paro_mesh m, int N, double* U, double* lambda, const paro_params* p, paro_stats* s) {
+  TRY(check_common(m, N));
+  if (!U || !lambda) return fail(m, PARO_ERR_ARG, "null pointer");
+  paro_params pp;
+  if (p) pp = *p;
+  else paro_default_params(&pp);
+  if (pp.check_every < 1) pp.check_every = 1;
+  const int Np = (N + 3) / 4 * 4;
+  TRY(ensure_workspace(m, Np));
+  CallScope cs(m, s, pp.profile);
+  LAUNCH(1, launch_pack(m->g, N, Np, U, m->u, m->st));
+  std::vector<double> lam(lambda, lambda + N), lam_new(N);
+  if (std::isnan(lambda[0])) {
+    Timer t(m, s ? &s->ms_rr : nullptr);
+    TRY(rr_packed(m, N, m->u, m->x, lam.data()));
+    t.stop();
+    std::swap(m->u, m->x);
+  }
+  const int nchk = (pp.n_check > 0 && pp.n_check < N) ? pp.n_check : N;
+  int outer = 0;
+  int rc = PARO_ERR_NOT_CONVERGED;
+  const int limit = pp.fixed_outer > 0 ? pp.fixed_outer : pp.max_outer;
+  double dl = INFINITY;
+  while (outer < limit) {
+    {
+      Timer t(m, s ? &s->ms_solve : nullptr);
+      int r1 = solve_packed(m, N, lam.data(), pp, s);
+      if (r1 != PARO_OK) return r1;
+    }
+    {
+      Timer t(m, s ? &s->ms_rr : nullptr);
+      TRY(rr_packed(m, N, m->x, m->u, lam_new.data()));
+    }
+    dl = 0.0;
+    for (int i = 0; i < nchk; ++i) dl = std::fmax(dl, std::fabs(lam_new[i] - lam[i]));
+    lam = lam_new;
+    ++outer;
+    if (pp.fixed_outer <= 0 && dl < pp.tol) {
+      rc = PARO_OK;
+      break;
+    }
+  }
+  if (pp.fixed_outer > 0) rc = PARO_OK;
+  if (s) {
+    s->outer_iters = outer;
+    s->max_dlambda = dl;
+  }
+  for (int i = 0; i < N; ++i) lambda[i] = lam[i];
+  LAUNCH(1, launch_unpack(m->g, N, Np, m->u, U, m->st));
+  CK(cudaStreamSynchronize(m->st));
+  if (rc != PARO_OK) m->err = "paro_iterate: max_outer reached before tol";
+  return rc;
+}
+
+int paro_apply(paro_mesh m, int N, int op, int dtype, const void* X, void* Y) {
+  TRY(check_common(m, N));
+  if (!X || !Y || X == Y) return fail(m, PARO_ERR_ARG, "X, Y must be non-null and distinct");
+  if (op < PARO_OP_A || op > PARO_OP_M) return fail(m, PARO_ERR_ARG, "unknown op");
+  if (dtype != PARO_F64 && dtype != PARO_F32) return fail(m, PARO_ERR_ARG, "unknown dtype");
+  if (dtype == PARO_F32 && op != PARO_OP_A) return fail(m, PARO_ERR_ARG, "float32 apply supports PARO_OP_A only");
+  if (dtype == PARO_F32 && m->precision != PARO_MIXED)
+    return fail(m, PARO_ERR_ARG, "float32 apply needs a PARO_MIXED handle");
+  const int Np = (N + 3) / 4 * 4;
+  TRY(ensure_workspace(m, Np));
+  if (dtype == PARO_F64) {
+    LAUNCH(1, launch_pack(m->g, N, Np, static_cast<const double*>(X), m->u, m->st));
+    if (op == PARO_OP_A) LAUNCH(1, launch_apply_f64(m->g, Np, m->coef64, nullptr, 0.0, m->u, m->x, nullptr, m->st));
+    else if (op == PARO_OP_H) LAUNCH(1, launch_apply_f64(m->g, Np, m->coef64, &m->mw, m->sigma, m->u, m->x, nullptr, m->st));
+    else LAUNCH(1, launch_apply_f64(m->g, Np, nullptr, &m->mw, 0.0, m->u, m->x, nullptr, m->st));
+    LAUNCH(1, launch_unpack(m->g, N, Np, m->x, static_cast<double*>(Y), m->st));
+  } else {
+    LAUNCH(1, launch_pack_f32(m->g, N, Np, static_cast<const float*>(X), m->b32, m->st));
+    LAUNCH(1, launch_apply_f32(m->g, Np, m->coef32, m->b32, m->q32, m->st));
+    LAUNCH(1, launch_unpack_f32(m->g, N, Np, m->q32, static_cast<float*>(Y), m->st));
+  }
+  CK(cudaStreamSynchronize(m->st));
+  return PARO_OK;
+}
+
+const char* paro_last_error(paro_mesh m) {
+  if (!m) return g_create_err.c_str();
+  return m->err.c_str();
+}
+
+}  // extern "C"

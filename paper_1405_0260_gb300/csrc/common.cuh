@@ -1,0 +1,161 @@
+// Internal definitions shared by the CUDA translation units of libparo.
+//
+// Storage (all device, library-owned unless noted):
+//   node grid   padded with the Dirichlet boundary layer: Px = nx+1, Py = ny+1,
+//               Pz = nz+1 nodes per axis, node g = (k*Py + j)*Px + i.  Boundary
+//               rows of every vector are zero and are never written by a kernel,
+//               which makes the 27-point stencil branch-free.
+//   vectors     T[G][Np]: node-major, orbital-minor, Np = N rounded up to 4, so a
+//               thread owns 4 consecutive orbitals of one node (16 B float /
+//               32 B double vector access, coalesced across a warp).
+//   operator    27 weights per node, SoA: coef[o][g], o = (dz+1)*9 + (dy+1)*3 + (dx+1),
+//               plus the inverse diagonal dinv[g], in float64 and float32.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace paro {
+
+constexpr int kMaxN = 1024;        // orbitals per block handled by one handle
+constexpr int kRedThreads = 256;   // threads per block of the node-wise kernels
+constexpr int kMaxRedBlocks = 1216;  // 152 SMs x 8: grid cap of the reducing kernels
+
+// Device-side status bits (OR-ed into Grid::status).
+constexpr int kStatNotSPD = 1;
+constexpr int kStatNonFinite = 2;
+constexpr int kStatNotConverged = 4;
+
+struct Grid {
+  int nx, ny, nz;      // cells
+  int Px, Py, Pz;      // padded nodes per axis
+  long long G;         // padded node count
+  int nI;              // interior node count
+  double hx, hy, hz;
+};
+
+template <typename T>
+struct V4 {
+  T a, b, c, d;
+};
+
+__device__ __forceinline__ V4<float> ld4(const float* p) {
+  float4 v = *reinterpret_cast<const float4*>(p);
+  return {v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ V4<double> ld4(const double* p) {
+  double2 u = reinterpret_cast<const double2*>(p)[0];
+  double2 v = reinterpret_cast<const double2*>(p)[1];
+  return {u.x, u.y, v.x, v.y};
+}
+__device__ __forceinline__ void st4(float* p, V4<float> v) {
+  *reinterpret_cast<float4*>(p) = make_float4(v.a, v.b, v.c, v.d);
+}
+__device__ __forceinline__ void st4(double* p, V4<double> v) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v.a, v.b);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v.c, v.d);
+}
+
+// Mapping of a thread of a node-wise kernel: `groups` threads per node (4 orbitals
+// each), `npb` nodes per block; threads tid >= groups*npb idle.
+struct NodeMap {
+  int groups;  // Np / 4
+  int npb;     // nodes per block pass
+};
+
+__host__ __device__ inline NodeMap node_map(int Np) {
+  NodeMap m;
+  m.groups = Np / 4;
+  m.npb = kRedThreads / m.groups;
+  if (m.npb < 1) m.npb = 1;
+  return m;
+}
+
+// Interior linear index n -> padded node index.
+__device__ __forceinline__ long long interior_to_padded(const Grid& g, int n) {
+  int ix = g.nx - 1, iy = g.ny - 1;
+  int i = n % ix + 1;
+  int t = n / ix;
+  int j = t % iy + 1;
+  int k = t / iy + 1;
+  return ((long long)k * g.Py + j) * g.Px + i;
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launch wrappers (defined in stencil.cu, pcg.cu, rr.cu)
+// ---------------------------------------------------------------------------
+
+// Operator weights (constant part) for op selection in apply kernels.
+struct Weights27 {
+  double w[27];
+};
+
+// stencil.cu
+cudaError_t launch_build_coef(const Grid& g, const double* Vq, double sigma, double* coef64, float* coef32,
+                              double* dinv64, float* dinv32, cudaStream_t st);
+void mass_weights(const Grid& g, Weights27* mw);  // constant mass stencil M
+// y = scale_o * (op x), op = coef (+ cw * wsub) ; T = float or double.  scale may be null.
+cudaError_t launch_apply_f64(const Grid& g, int Np, const double* coef, const Weights27* cw, double csub,
+                             const double* x, double* y, const double* scale, cudaStream_t st);
+cudaError_t launch_apply_f32(const Grid& g, int Np, const float* coef, const float* x, float* y, cudaStream_t st);
+cudaError_t launch_pack(const Grid& g, int N, int Np, const double* src, double* dst, cudaStream_t st);
+cudaError_t launch_unpack(const Grid& g, int N, int Np, const double* src, double* dst, cudaStream_t st);
+cudaError_t launch_pack_f32(const Grid& g, int N, int Np, const float* src, float* dst, cudaStream_t st);
+cudaError_t launch_unpack_f32(const Grid& g, int N, int Np, const float* src, float* dst, cudaStream_t st);
+
+// pcg.cu: per-orbital CG state, in device memory.
+struct CGState {
+  double* rz;      // (r, z)
+  double* pq;      // (p, A p)
+  double* alpha;
+  double* beta;
+  double* bb;      // ||b||^2
+  double* rr;      // ||r||^2
+  int* active;
+  int* iters;
+  int* skip;       // orbitals excluded from this solve (mixed: already converged)
+  int* n_active;   // orbitals still iterating
+  int* status;     // OR of kStat* bits
+  double* partial; // [3][kMaxRedBlocks][Np]
+  unsigned int* ticket;
+  unsigned long long* work;  // cg_q adds (interior nodes) x (orbitals it processed) per launch
+};
+
+template <typename T>
+struct CGVectors {
+  T* x;
+  T* b;
+  T* r;
+  T* p[2];
+  T* q;
+  const T* coef;
+  const T* dinv;
+};
+
+int red_blocks(const Grid& g, int Np);
+
+template <typename T>
+cudaError_t launch_cg_init(const Grid& g, int N, int Np, const CGVectors<T>& v, const CGState& s, bool x_zero,
+                           double tol, int maxit, cudaStream_t st);
+// One CG iteration = launch_cg_q (p update, q = A p, (p, q)) then launch_cg_update.
+template <typename T>
+cudaError_t launch_cg_q(const Grid& g, int Np, const CGVectors<T>& v, const CGState& s, int parity, cudaStream_t st);
+template <typename T>
+cudaError_t launch_cg_update(const Grid& g, int Np, const CGVectors<T>& v, const CGState& s, int parity, double tol,
+                             int maxit, cudaStream_t st);
+// Mixed refinement: r64 = b64 - A64 x64 -> rhs32 (float); convergence flags in s.skip.
+cudaError_t launch_refine_residual(const Grid& g, int N, int Np, const double* coef64, const double* x64,
+                                   const double* b64, float* rhs32, const CGState& s, double tol, cudaStream_t st);
+cudaError_t launch_refine_update(const Grid& g, int Np, double* x64, const float* d32, const int* skip,
+                                 cudaStream_t st);
+
+// rr.cu
+cudaError_t launch_gram2(const Grid& g, int N, int Np, const double* X, const double* Y1, const double* Y2,
+                         double* part, int* n_chunks, double* G1, double* G2, cudaStream_t st);
+size_t gram_partial_doubles(const Grid& g, int Np);
+cudaError_t launch_small_eig(int N, const double* GA, const double* GB, double* work, double* C, double* theta,
+                             int* status, cudaStream_t st);
+cudaError_t launch_rotate(const Grid& g, int N, int Np, const double* X, const double* C, double* U,
+                          cudaStream_t st);
+
+}  // namespace paro

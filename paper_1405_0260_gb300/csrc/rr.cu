@@ -1,0 +1,337 @@
+// Rayleigh-Ritz on span(X) (Step 4 of Algorithms 3.1 / A.1, eq. alg-evp):
+//   G_A = X^T H X, G_B = X^T M X                    (gram2: tall-skinny, float64)
+//   G_B = L L^T, L^-1 G_A L^-T = Q Theta Q^T         (small_eig: one CTA, float64)
+//   C = L^-T Q (columns sorted by ascending theta), U = X C   (rotate)
+#include <cmath>
+
+#include "common.cuh"
+
+namespace paro {
+
+namespace {
+
+constexpr int kTile = 32;      // Gram output tile (rows a, columns b)
+constexpr int kGramRows = 32;  // nodes staged per step
+
+// Partial Grams over a chunk of padded nodes.  Block (16 x 16) computes a 32 x 32
+// tile of both G1 = X^T Y1 and G2 = X^T Y2, each thread 2 x 2 entries of each.
+__global__ void __launch_bounds__(256) k_gram2(long long G, int Np, const double* __restrict__ X,
+                                               const double* __restrict__ Y1, const double* __restrict__ Y2,
+                                               double* __restrict__ part, int nch, long long chunk) {
+  __shared__ double xs[kGramRows][kTile + 1];
+  __shared__ double y1s[kGramRows][kTile + 1];
+  __shared__ double y2s[kGramRows][kTile + 1];
+  int ntile = (Np + kTile - 1) / kTile;
+  int tile = blockIdx.x % (ntile * ntile);
+  int ch = blockIdx.x / (ntile * ntile);
+  int a0 = (tile / ntile) * kTile, b0 = (tile % ntile) * kTile;
+  int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  double g1[2][2] = {}, g2[2][2] = {};
+  long long beg = ch * chunk, end = beg + chunk;
+  if (end > G) end = G;
+  for (long long n0 = beg; n0 < end; n0 += kGramRows) {
+    for (int t = threadIdx.x; t < kGramRows * kTile; t += 256) {
+      int r = t / kTile, c = t % kTile;
+      long long n = n0 + r;
+      bool ok = n < end;
+      xs[r][c] = (ok && a0 + c < Np) ? X[n * Np + a0 + c] : 0.0;
+      y1s[r][c] = (ok && b0 + c < Np) ? Y1[n * Np + b0 + c] : 0.0;
+      y2s[r][c] = (ok && b0 + c < Np) ? Y2[n * Np + b0 + c] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int r = 0; r < kGramRows; ++r) {
+      double xa0 = xs[r][2 * ty], xa1 = xs[r][2 * ty + 1];
+      double yb0 = y1s[r][2 * tx], yb1 = y1s[r][2 * tx + 1];
+      double zb0 = y2s[r][2 * tx], zb1 = y2s[r][2 * tx + 1];
+      g1[0][0] += xa0 * yb0; g1[0][1] += xa0 * yb1; g1[1][0] += xa1 * yb0; g1[1][1] += xa1 * yb1;
+      g2[0][0] += xa0 * zb0; g2[0][1] += xa0 * zb1; g2[1][0] += xa1 * zb0; g2[1][1] += xa1 * zb1;
+    }
+    __syncthreads();
+  }
+  long long NN = (long long)Np * Np;
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) {
+      int a = a0 + 2 * ty + i, b = b0 + 2 * tx + j;
+      if (a < Np && b < Np) {
+        part[(2LL * ch) * NN + (long long)a * Np + b] = g1[i][j];
+        part[(2LL * ch + 1) * NN + (long long)a * Np + b] = g2[i][j];
+      }
+    }
+  (void)nch;
+}
+
+__global__ void k_gram_reduce(int Np, int nch, const double* __restrict__ part, double* __restrict__ G1,
+                              double* __restrict__ G2) {
+  long long NN = (long long)Np * Np;
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * NN) return;
+  int w = (int)(t / NN);
+  long long e = t % NN;
+  double s = 0.0;
+  for (int c = 0; c < nch; ++c) s += part[(2LL * c + w) * NN + e];
+  (w == 0 ? G1 : G2)[e] = s;
+}
+
+// Round-robin ("circle") pairing of m = even indices: round r, slot k.
+__device__ __forceinline__ void rr_pair(int m, int r, int k, int* p, int* q) {
+  int a = (k == 0) ? 0 : ((k - 1 + r) % (m - 1)) + 1;
+  int b = ((m - 2 - k + r) % (m - 1)) + 1;
+  *p = a < b ? a : b;
+  *q = a < b ? b : a;
+}
+
+// One CTA: Cholesky of G_B, two triangular solves, parallel cyclic Jacobi on
+// S = L^-1 G_A L^-T, sort, back-substitution C = L^-T Q.  All matrices N x N
+// row-major (ld N) in `work` (4 N^2 doubles); inputs G_A, G_B and output C have
+// ld Np, C zero-padded to Np x Np.
+__global__ void __launch_bounds__(1024) k_small_eig(int N, int Np, const double* __restrict__ GA,
+                                                    const double* __restrict__ GB, double* __restrict__ work,
+                                                    double* __restrict__ C, double* __restrict__ theta,
+                                                    int* __restrict__ status) {
+  __shared__ int fail;
+  __shared__ double red[1024 / 32][2];
+  __shared__ double cs[kMaxN / 2 + 1][2];
+  __shared__ int pr[kMaxN / 2 + 1][2];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  double* L = work;
+  double* S = work + (long long)N * N;
+  double* V = work + 2LL * N * N;
+  double* W = work + 3LL * N * N;
+  if (tid == 0) fail = 0;
+  for (int t = tid; t < N * N; t += nt) {
+    int i = t / N, j = t % N;
+    L[t] = 0.5 * (GB[(long long)i * Np + j] + GB[(long long)j * Np + i]);
+    S[t] = 0.5 * (GA[(long long)i * Np + j] + GA[(long long)j * Np + i]);
+    V[t] = (i == j) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  // Cholesky, right-looking, lower triangle of L.
+  for (int k = 0; k < N; ++k) {
+    if (tid == 0) {
+      double d = L[k * N + k];
+      if (!(d > 0.0) || !isfinite(d)) fail = 1;
+      else L[k * N + k] = sqrt(d);
+    }
+    __syncthreads();
+    if (fail) break;
+    double lkk = L[k * N + k];
+    for (int i = k + 1 + tid; i < N; i += nt) L[i * N + k] /= lkk;
+    __syncthreads();
+    int m = N - k - 1;
+    for (int t = tid; t < m * m; t += nt) {
+      int i = k + 1 + t / m, j = k + 1 + t % m;
+      if (j <= i) L[i * N + j] -= L[i * N + k] * L[j * N + k];
+    }
+    __syncthreads();
+  }
+  if (fail) {
+    if (tid == 0) atomicOr(status, kStatNotSPD);
+    return;
+  }
+  for (int t = tid; t < N * N; t += nt) {
+    int i = t / N, j = t % N;
+    if (j > i) L[t] = 0.0;
+  }
+  __syncthreads();
+  // W = L^-1 S  (column j by thread j)
+  for (int j = tid; j < N; j += nt)
+    for (int i = 0; i < N; ++i) {
+      double s = S[i * N + j];
+      for (int k = 0; k < i; ++k) s -= L[i * N + k] * W[k * N + j];
+      W[i * N + j] = s / L[i * N + i];
+    }
+  __syncthreads();
+  // S = L^-1 W^T = L^-1 S L^-T
+  for (int j = tid; j < N; j += nt)
+    for (int i = 0; i < N; ++i) {
+      double s = W[j * N + i];
+      for (int k = 0; k < i; ++k) s -= L[i * N + k] * S[k * N + j];
+      S[i * N + j] = s / L[i * N + i];
+    }
+  __syncthreads();
+  for (int t = tid; t < N * N; t += nt) {
+    int i = t / N, j = t % N;
+    if (j > i) {
+      double a = 0.5 * (S[i * N + j] + S[j * N + i]);
+      S[i * N + j] = a;
+      S[j * N + i] = a;
+    }
+  }
+  __syncthreads();
+  // Parallel cyclic Jacobi.
+  const int m = (N % 2 == 0) ? N : N + 1;
+  const int half = m / 2;
+  for (int sweep = 0; sweep < 40 && N > 1; ++sweep) {
+    double off = 0.0, all = 0.0;
+    for (int t = tid; t < N * N; t += nt) {
+      double v = S[t];
+      all += v * v;
+      if (t / N != t % N) off += v * v;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      all += __shfl_xor_sync(0xffffffffu, all, o);
+    }
+    if (tid % 32 == 0) {
+      red[tid / 32][0] = off;
+      red[tid / 32][1] = all;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double a = 0.0, b = 0.0;
+      for (int w = 0; w < nt / 32; ++w) {
+        a += red[w][0];
+        b += red[w][1];
+      }
+      red[0][0] = a;
+      red[0][1] = b;
+    }
+    __syncthreads();
+    off = red[0][0];
+    all = red[0][1];
+    __syncthreads();
+    if (!(off > 1e-30 * all)) break;
+    for (int r = 0; r < m - 1; ++r) {
+      for (int k = tid; k < half; k += nt) {
+        int p, q;
+        rr_pair(m, r, k, &p, &q);
+        double c = 1.0, s = 0.0;
+        if (q < N) {
+          double apq = S[p * N + q];
+          if (apq != 0.0) {
+            double tau = (S[q * N + q] - S[p * N + p]) / (2.0 * apq);
+            double t = (tau >= 0.0) ? 1.0 / (tau + sqrt(1.0 + tau * tau)) : -1.0 / (-tau + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + t * t);
+            s = t * c;
+          }
+        }
+        cs[k][0] = c;
+        cs[k][1] = s;
+        pr[k][0] = p;
+        pr[k][1] = q;
+      }
+      __syncthreads();
+      // rows p, q of S <- J^T S
+      for (int t = tid; t < half * N; t += nt) {
+        int k = t / N, col = t % N;
+        int p = pr[k][0], q = pr[k][1];
+        if (q >= N) continue;
+        double c = cs[k][0], s = cs[k][1];
+        double sp = S[p * N + col], sq = S[q * N + col];
+        S[p * N + col] = c * sp - s * sq;
+        S[q * N + col] = s * sp + c * sq;
+      }
+      __syncthreads();
+      // columns p, q of S <- S J ; V <- V J
+      for (int t = tid; t < half * N; t += nt) {
+        int k = t / N, row = t % N;
+        int p = pr[k][0], q = pr[k][1];
+        if (q >= N) continue;
+        double c = cs[k][0], s = cs[k][1];
+        double sp = S[row * N + p], sq = S[row * N + q];
+        S[row * N + p] = c * sp - s * sq;
+        S[row * N + q] = s * sp + c * sq;
+        double vp = V[row * N + p], vq = V[row * N + q];
+        V[row * N + p] = c * vp - s * vq;
+        V[row * N + q] = s * vp + c * vq;
+      }
+      __syncthreads();
+    }
+  }
+  // Sort by ascending Ritz value (ties by index) and back-substitute C = L^-T V.
+  for (int j = tid; j < N; j += nt) {
+    double tj = S[j * N + j];
+    int rank = 0;
+    for (int i = 0; i < N; ++i) {
+      double ti = S[i * N + i];
+      if (ti < tj || (ti == tj && i < j)) ++rank;
+    }
+    theta[rank] = tj;
+    for (int i = N - 1; i >= 0; --i) {
+      double s = V[i * N + j];
+      for (int k = i + 1; k < N; ++k) s -= L[k * N + i] * C[(long long)k * Np + rank];
+      C[(long long)i * Np + rank] = s / L[i * N + i];
+    }
+  }
+  for (int t = tid; t < Np * Np; t += nt) {
+    int i = t / Np, j = t % Np;
+    if (i >= N || j >= N) C[t] = 0.0;
+  }
+}
+
+// U[g, b] = sum_a X[g, a] C[a, b], interior nodes, 4 columns per thread.
+__global__ void __launch_bounds__(kRedThreads) k_rotate(Grid g, int N, int Np, const double* __restrict__ X,
+                                                        const double* __restrict__ C, double* __restrict__ U) {
+  NodeMap nm = node_map(Np);
+  int grp = threadIdx.x % nm.groups;
+  int nl = threadIdx.x / nm.groups;
+  if (nl >= nm.npb) return;
+  for (int n = blockIdx.x * nm.npb + nl; n < g.nI; n += gridDim.x * nm.npb) {
+    long long gp = interior_to_padded(g, n);
+    const double* xr = X + gp * Np;
+    double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    for (int a = 0; a < N; ++a) {
+      double xa = xr[a];
+      V4<double> c = ld4(C + (long long)a * Np + 4 * grp);
+      a0 += xa * c.a;
+      a1 += xa * c.b;
+      a2 += xa * c.c;
+      a3 += xa * c.d;
+    }
+    st4(U + gp * Np + 4 * grp, V4<double>{a0, a1, a2, a3});
+  }
+}
+
+}  // namespace
+
+static void gram_shape(const Grid& g, int Np, int* nch, long long* chunk) {
+  int ntile = (Np + kTile - 1) / kTile;
+  long long want = (1216 + ntile * ntile - 1) / (ntile * ntile);
+  long long maxch = (g.G + kGramRows - 1) / kGramRows;
+  if (want > maxch) want = maxch;
+  if (want < 1) want = 1;
+  long long ch = (g.G + want - 1) / want;
+  ch = (ch + kGramRows - 1) / kGramRows * kGramRows;
+  *chunk = ch;
+  *nch = (int)((g.G + ch - 1) / ch);
+}
+
+size_t gram_partial_doubles(const Grid& g, int Np) {
+  int nch;
+  long long chunk;
+  gram_shape(g, Np, &nch, &chunk);
+  return (size_t)nch * 2 * Np * Np;
+}
+
+cudaError_t launch_gram2(const Grid& g, int N, int Np, const double* X, const double* Y1, const double* Y2,
+                         double* part, int* n_chunks, double* G1, double* G2, cudaStream_t st) {
+  (void)N;
+  int nch;
+  long long chunk;
+  gram_shape(g, Np, &nch, &chunk);
+  int ntile = (Np + kTile - 1) / kTile;
+  k_gram2<<<ntile * ntile * nch, 256, 0, st>>>(g.G, Np, X, Y1, Y2, part, nch, chunk);
+  long long work = 2LL * Np * Np;
+  k_gram_reduce<<<(unsigned)((work + 255) / 256), 256, 0, st>>>(Np, nch, part, G1, G2);
+  if (n_chunks) *n_chunks = nch;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_small_eig(int N, const double* GA, const double* GB, double* work, double* C, double* theta,
+                             int* status, cudaStream_t st) {
+  int Np = (N + 3) / 4 * 4;
+  k_small_eig<<<1, 1024, 0, st>>>(N, Np, GA, GB, work, C, theta, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rotate(const Grid& g, int N, int Np, const double* X, const double* C, double* U,
+                          cudaStream_t st) {
+  NodeMap nm = node_map(Np);
+  long long need = (g.nI + nm.npb - 1) / nm.npb;
+  int nb = (int)(need < 152 * 16 ? need : 152 * 16);
+  k_rotate<<<nb, kRedThreads, 0, st>>>(g, N, Np, X, C, U);
+  return cudaGetLastError();
+}
+
+}  // namespace paro

@@ -1,0 +1,206 @@
+// Operator set-up and the 27-point Q1 stencil apply.
+//
+// Discrete form (eq. 2.7, linear part, with the shift of the source problems):
+//   A = K/2 + M_{V+sigma}
+// K/2 is built from its Kronecker closed form: with the 1-D Q1 matrices
+//   k(0) = 2/h, k(+-1) = -1/h,   m(0) = 4h/6, m(+-1) = h/6,
+// K = k_x m_y m_z + m_x k_y m_z + m_x m_y k_z  (weight of offset (dx,dy,dz)).
+// M_{V+sigma} is integrated cell by cell with the 2x2x2 Gauss rule at which V is
+// given; the rule is exact for sigma * mass, so sigma folds into V.
+// The weights of a node are the 27 entries of its row of A.
+#include "common.cuh"
+
+namespace paro {
+
+namespace {
+
+__host__ __device__ inline double k1(int d, double h) { return d == 0 ? 2.0 / h : -1.0 / h; }
+__host__ __device__ inline double m1(int d, double h) { return d == 0 ? 4.0 * h / 6.0 : h / 6.0; }
+
+// Gauss abscissae on [0, 1] and the two linear shape functions.
+__device__ inline double gauss_xi(int q) {
+  const double s = 0.57735026918962576451;  // 1/sqrt(3)
+  return q == 0 ? 0.5 * (1.0 - s) : 0.5 * (1.0 + s);
+}
+__device__ inline double shape1(int a, double xi) { return a == 0 ? 1.0 - xi : xi; }
+
+__global__ void k_build_coef(Grid g, const double* __restrict__ Vq, double sigma, double* __restrict__ coef64,
+                             float* __restrict__ coef32, double* __restrict__ dinv64, float* __restrict__ dinv32) {
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= g.nI) return;
+  int ix = g.nx - 1, iy = g.ny - 1;
+  int i = n % ix + 1;
+  int t = n / ix;
+  int j = t % iy + 1;
+  int k = t / iy + 1;
+  long long gp = ((long long)k * g.Py + j) * g.Px + i;
+  double w[27];
+  for (int dz = -1; dz <= 1; ++dz)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        double kk = k1(dx, g.hx) * m1(dy, g.hy) * m1(dz, g.hz) + m1(dx, g.hx) * k1(dy, g.hy) * m1(dz, g.hz) +
+                    m1(dx, g.hx) * m1(dy, g.hy) * k1(dz, g.hz);
+        w[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)] = 0.5 * kk;
+      }
+  const double wq = g.hx * g.hy * g.hz / 8.0;
+  // The 8 cells around the node; (cx, cy, cz) selects the cell, the node sits at
+  // local corner a = (1-cx, 1-cy, 1-cz) of it.
+  for (int cz = 0; cz < 2; ++cz)
+    for (int cy = 0; cy < 2; ++cy)
+      for (int cx = 0; cx < 2; ++cx) {
+        int ex = i - 1 + cx, ey = j - 1 + cy, ez = k - 1 + cz;
+        long long cell = ((long long)ez * g.ny + ey) * g.nx + ex;
+        const double* v = Vq + cell * 8;
+        int ax = 1 - cx, ay = 1 - cy, az = 1 - cz;
+        for (int bz = 0; bz < 2; ++bz)
+          for (int by = 0; by < 2; ++by)
+            for (int bx = 0; bx < 2; ++bx) {
+              double acc = 0.0;
+              for (int qz = 0; qz < 2; ++qz)
+                for (int qy = 0; qy < 2; ++qy)
+                  for (int qx = 0; qx < 2; ++qx) {
+                    double px = shape1(ax, gauss_xi(qx)) * shape1(bx, gauss_xi(qx));
+                    double py = shape1(ay, gauss_xi(qy)) * shape1(by, gauss_xi(qy));
+                    double pz = shape1(az, gauss_xi(qz)) * shape1(bz, gauss_xi(qz));
+                    acc += (v[qz * 4 + qy * 2 + qx] + sigma) * px * py * pz;
+                  }
+              int o = (bz - az + 1) * 9 + (by - ay + 1) * 3 + (bx - ax + 1);
+              w[o] += wq * acc;
+            }
+      }
+  for (int o = 0; o < 27; ++o) {
+    coef64[(long long)o * g.G + gp] = w[o];
+    coef32[(long long)o * g.G + gp] = (float)w[o];
+  }
+  dinv64[gp] = 1.0 / w[13];
+  dinv32[gp] = 1.0f / (float)w[13];
+}
+
+// MODE 0: y = coef x.  MODE 1: y = (coef - csub * cw) x.  MODE 2: y = cw x.
+// Optional per-orbital scale of the result.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kRedThreads) k_apply(Grid g, int Np, const T* __restrict__ coef, Weights27 cw,
+                                                       double csub, const T* __restrict__ x, T* __restrict__ y,
+                                                       const double* __restrict__ scale) {
+  NodeMap nm = node_map(Np);
+  int grp = threadIdx.x % nm.groups;
+  int nl = threadIdx.x / nm.groups;
+  if (nl >= nm.npb) return;
+  V4<double> s = {1.0, 1.0, 1.0, 1.0};
+  if (scale != nullptr) s = {scale[4 * grp], scale[4 * grp + 1], scale[4 * grp + 2], scale[4 * grp + 3]};
+  for (int n = blockIdx.x * nm.npb + nl; n < g.nI; n += gridDim.x * nm.npb) {
+    long long gp = interior_to_padded(g, n);
+    T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+#pragma unroll
+    for (int o = 0; o < 27; ++o) {
+      const int dz = o / 9 - 1, dy = (o / 3) % 3 - 1, dx = o % 3 - 1;
+      long long nb = gp + ((long long)dz * g.Py + dy) * g.Px + dx;
+      T w;
+      if (MODE == 0) w = coef[(long long)o * g.G + gp];
+      else if (MODE == 1) w = (T)(coef[(long long)o * g.G + gp] - csub * cw.w[o]);
+      else w = (T)cw.w[o];
+      V4<T> v = ld4(x + nb * Np + 4 * grp);
+      a0 += w * v.a;
+      a1 += w * v.b;
+      a2 += w * v.c;
+      a3 += w * v.d;
+    }
+    V4<T> out = {(T)(a0 * s.a), (T)(a1 * s.b), (T)(a2 * s.c), (T)(a3 * s.d)};
+    st4(y + gp * Np + 4 * grp, out);
+  }
+}
+
+int apply_blocks(const Grid& g, int Np) {
+  NodeMap nm = node_map(Np);
+  long long need = (g.nI + nm.npb - 1) / nm.npb;
+  long long cap = 152LL * 16;
+  return (int)(need < cap ? need : cap);
+}
+
+__global__ void k_pack(Grid g, int N, int Np, const double* __restrict__ src, double* __restrict__ dst) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)g.nI * Np) return;
+  int n = (int)(t / Np), o = (int)(t % Np);
+  long long gp = interior_to_padded(g, n);
+  dst[gp * Np + o] = o < N ? src[(long long)n * N + o] : 0.0;
+}
+
+__global__ void k_unpack(Grid g, int N, int Np, const double* __restrict__ src, double* __restrict__ dst) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)g.nI * N) return;
+  int n = (int)(t / N), o = (int)(t % N);
+  long long gp = interior_to_padded(g, n);
+  dst[t] = src[gp * Np + o];
+}
+
+__global__ void k_pack_f32(Grid g, int N, int Np, const float* __restrict__ src, float* __restrict__ dst) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)g.nI * Np) return;
+  int n = (int)(t / Np), o = (int)(t % Np);
+  long long gp = interior_to_padded(g, n);
+  dst[gp * Np + o] = o < N ? src[(long long)n * N + o] : 0.0f;
+}
+
+__global__ void k_unpack_f32(Grid g, int N, int Np, const float* __restrict__ src, float* __restrict__ dst) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)g.nI * N) return;
+  int n = (int)(t / N), o = (int)(t % N);
+  long long gp = interior_to_padded(g, n);
+  dst[t] = src[gp * Np + o];
+}
+
+inline unsigned nblk(long long work, int threads) { return (unsigned)((work + threads - 1) / threads); }
+
+}  // namespace
+
+void mass_weights(const Grid& g, Weights27* mw) {
+  for (int dz = -1; dz <= 1; ++dz)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx)
+        mw->w[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)] = m1(dx, g.hx) * m1(dy, g.hy) * m1(dz, g.hz);
+}
+
+cudaError_t launch_build_coef(const Grid& g, const double* Vq, double sigma, double* coef64, float* coef32,
+                              double* dinv64, float* dinv32, cudaStream_t st) {
+  k_build_coef<<<nblk(g.nI, 128), 128, 0, st>>>(g, Vq, sigma, coef64, coef32, dinv64, dinv32);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_f64(const Grid& g, int Np, const double* coef, const Weights27* cw, double csub,
+                             const double* x, double* y, const double* scale, cudaStream_t st) {
+  Weights27 w{};
+  if (cw) w = *cw;
+  int nb = apply_blocks(g, Np);
+  if (coef == nullptr)
+    k_apply<double, 2><<<nb, kRedThreads, 0, st>>>(g, Np, coef, w, csub, x, y, scale);
+  else if (cw != nullptr)
+    k_apply<double, 1><<<nb, kRedThreads, 0, st>>>(g, Np, coef, w, csub, x, y, scale);
+  else
+    k_apply<double, 0><<<nb, kRedThreads, 0, st>>>(g, Np, coef, w, csub, x, y, scale);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_f32(const Grid& g, int Np, const float* coef, const float* x, float* y, cudaStream_t st) {
+  Weights27 w{};
+  k_apply<float, 0><<<apply_blocks(g, Np), kRedThreads, 0, st>>>(g, Np, coef, w, 0.0, x, y, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const Grid& g, int N, int Np, const double* src, double* dst, cudaStream_t st) {
+  k_pack<<<nblk((long long)g.nI * Np, 256), 256, 0, st>>>(g, N, Np, src, dst);
+  return cudaGetLastError();
+}
+cudaError_t launch_unpack(const Grid& g, int N, int Np, const double* src, double* dst, cudaStream_t st) {
+  k_unpack<<<nblk((long long)g.nI * N, 256), 256, 0, st>>>(g, N, Np, src, dst);
+  return cudaGetLastError();
+}
+cudaError_t launch_pack_f32(const Grid& g, int N, int Np, const float* src, float* dst, cudaStream_t st) {
+  k_pack_f32<<<nblk((long long)g.nI * Np, 256), 256, 0, st>>>(g, N, Np, src, dst);
+  return cudaGetLastError();
+}
+cudaError_t launch_unpack_f32(const Grid& g, int N, int Np, const float* src, float* dst, cudaStream_t st) {
+  k_unpack_f32<<<nblk((long long)g.nI * N, 256), 256, 0, st>>>(g, N, Np, src, dst);
+  return cudaGetLastError();
+}
+
+}  // namespace paro

@@ -39,6 +39,11 @@ def main():
         "what": "lowest 20 discrete eigenvalues, V=r^2/2, [-8,8]^3, 32^3 Q1 cells, Dirichlet",
         "values": lowest(p, 20, 1.0),
     }
+    p = W.harmonic(nc=64, L=8.0, N=1, seed=1)
+    out["harmonic_64_L8"] = {
+        "what": "lowest 20 discrete eigenvalues, V=r^2/2, [-8,8]^3, 64^3 Q1 cells, Dirichlet",
+        "values": lowest(p, 20, 1.0),
+    }
     with open(os.path.join(HERE, "discrete_spectra.json"), "w") as f:
         json.dump(out, f, indent=1)
         f.write("\n")

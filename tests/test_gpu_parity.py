@@ -1,0 +1,292 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Every case runs the same seeded inputs through both sides.  Tolerances:
+  * float64 operator applies: rounding of a 27-term sum, |err| <= 1e-13 (|A| |x|)
+  * float32 applies: 27 float32 products and sums, |err| <= 4e-6 (|A| |x|)
+  * source problems (both sides CG to ||r|| <= 1e-12 ||b||): solutions agree
+    within the solve tolerance times the condition number the mesh gives
+  * eigenvalues of the float64 path: 1e-10 relative to the oracle, taken
+    iterate by iterate for a fixed number of outer iterations
+  * eigenvalues of the mixed path: 1e-6 Ha, orbital subspace angles < 1e-5
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import paro as O
+from paper_1405_0260_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1405_0260_gb300 import binding
+
+    binding.lib()
+    return binding
+
+
+def dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.double().cpu().numpy()
+
+
+def make_mesh(B, p, precision=None):
+    prec = B.PARO_FP64 if precision is None else precision
+    m = B.Mesh(p.n, p.lo, p.hi, prec)
+    Vq = dev(p.Vq)
+    m.set_potential(Vq, p.sigma)
+    m._vq = Vq
+    return m
+
+
+def oracle_ops(p):
+    return O.assemble(O.Mesh(p.n, p.lo, p.hi), p.Vq, p.sigma)
+
+
+def rough_potential(n, lo, hi, seed):
+    """A smooth well plus seeded noise at the Gauss points (exercises every weight)."""
+    x, y, z = W.gauss_point_coords(n, lo, hi)
+    rng = np.random.default_rng(seed)
+    V = 0.3 * (x ** 2 + y ** 2 + z ** 2) - 1.0 / np.sqrt(x ** 2 + y ** 2 + z ** 2 + 0.3)
+    return np.ascontiguousarray((V + 0.2 * rng.standard_normal(V.shape)).ravel())
+
+
+APPLY_CASES = [((2, 2, 2), 1), ((5, 4, 6), 3), ((7, 6, 9), 4), ((9, 11, 8), 5), ((12, 10, 13), 13),
+               ((17, 9, 11), 40)]
+
+
+@pytest.mark.parametrize("n,N", APPLY_CASES)
+def test_apply_fp64_matches_assembled_operators(B, n, N):
+    lo, hi = (-1.5, -2.0, -1.0), (2.5, 1.0, 1.75)
+    rng = np.random.default_rng(100 + N)
+    nI = (n[0] - 1) * (n[1] - 1) * (n[2] - 1)
+    p = W.Problem("apply", n, lo, hi, rough_potential(n, lo, hi, N), 0.7, rng.standard_normal((nI, N)), 0)
+    ops = oracle_ops(p)
+    m = make_mesh(B, p)
+    X = dev(p.U0)
+    Y = torch.empty_like(X)
+    for op, A in ((B.PARO_OP_A, ops.A), (B.PARO_OP_H, ops.H), (B.PARO_OP_M, ops.M)):
+        m.apply(op, X, Y)
+        ref = A @ p.U0
+        bound = abs(A) @ np.abs(p.U0)
+        err = np.abs(host(Y) - ref)
+        assert np.all(err <= 1e-13 * bound + 1e-300), (op, err.max(), bound.max())
+    m.close()
+
+
+@pytest.mark.parametrize("n,N", APPLY_CASES[1:])
+def test_apply_fp32_matches_assembled_operator(B, n, N):
+    lo, hi = (-2.0, -2.0, -2.0), (2.0, 2.0, 2.0)
+    rng = np.random.default_rng(200 + N)
+    nI = (n[0] - 1) * (n[1] - 1) * (n[2] - 1)
+    U = rng.standard_normal((nI, N)).astype(np.float32).astype(np.float64)
+    p = W.Problem("apply32", n, lo, hi, rough_potential(n, lo, hi, 7 + N), 1.3, U, 0)
+    ops = oracle_ops(p)
+    m = make_mesh(B, p, B.PARO_MIXED)
+    X = dev(U, torch.float32)
+    Y = torch.empty_like(X)
+    m.apply(B.PARO_OP_A, X, Y)
+    ref = ops.A @ U
+    bound = abs(ops.A) @ np.abs(U)
+    err = np.abs(host(Y) - ref)
+    assert np.all(err <= 4e-6 * bound), err.max()
+    m.close()
+
+
+def test_apply_free_box_sine_mode_is_exact_eigenvector(B):
+    # closed form: the discrete (K/2, M) eigenpairs are products of sine modes
+    n, L = (16, 12, 10), (1.0, 0.75, 0.6)
+    lo, hi = tuple(-v for v in L), L
+    p = W.Problem("box", n, lo, hi, np.zeros(8 * 16 * 12 * 10), 0.0, np.zeros((1, 1)), 0)
+    xyz = W.interior_node_coords(n, lo, hi)
+    modes = [(1, 1, 1), (2, 1, 3), (5, 4, 2)]
+    U = np.stack([np.sin(a * math.pi * (xyz[:, 0] + L[0]) / (2 * L[0])) *
+                  np.sin(b * math.pi * (xyz[:, 1] + L[1]) / (2 * L[1])) *
+                  np.sin(c * math.pi * (xyz[:, 2] + L[2]) / (2 * L[2])) for a, b, c in modes], axis=1)
+    m = make_mesh(B, p)
+    X = dev(U)
+    HX = torch.empty_like(X)
+    MX = torch.empty_like(X)
+    m.apply(B.PARO_OP_H, X, HX)
+    m.apply(B.PARO_OP_M, X, MX)
+    hx = [2 * L[d] / n[d] for d in range(3)]
+    for j, mode in enumerate(modes):
+        mu = [6 * (1 - math.cos(k * math.pi / n[d])) / (hx[d] ** 2 * (2 + math.cos(k * math.pi / n[d])))
+              for d, k in enumerate(mode)]
+        lam = 0.5 * sum(mu)
+        r = host(HX)[:, j] - lam * host(MX)[:, j]
+        assert np.linalg.norm(r) < 1e-12 * np.linalg.norm(host(HX)[:, j])
+    m.close()
+
+
+def test_orbital_solve_fp64_matches_oracle(B):
+    p = W.hydrogen(nc=12, L=6.0, N=5, seed=1100, sigma=2.0)
+    ops = oracle_ops(p)
+    rr = O.rayleigh_ritz(ops, p.U0)
+    ref = O.source_problems(ops, rr.U, rr.lam, 1e-12, 5000)
+    m = make_mesh(B, p)
+    U = dev(rr.U)
+    X = torch.empty_like(U)
+    params = B.paro_default_params(solve_tol=1e-12, pcg_maxit=5000, check_every=4)
+    rc, st = m.orbital_solve(rr.lam, U, X, params)
+    x = host(X)
+    assert rc == 0
+    assert np.max(np.abs(x - ref.X)) < 1e-9 * np.max(np.abs(ref.X))
+    # same recurrences in the same precision: iteration counts agree up to rounding
+    assert abs(st.cg_iters - int(ref.iters.sum())) <= 2 * p.N
+    assert st.max_relres < 1e-11
+    assert st.kernel_launches > 0
+    m.close()
+
+
+def test_orbital_solve_mixed_refinement_reaches_fp64_tolerance(B):
+    p = W.harmonic(nc=14, L=6.0, N=7, seed=2100, sigma=0.0)
+    ops = oracle_ops(p)
+    rr = O.rayleigh_ritz(ops, p.U0)
+    ref = O.source_problems(ops, rr.U, rr.lam, 1e-12, 5000)
+    m = make_mesh(B, p, B.PARO_MIXED)
+    U = dev(rr.U)
+    X = torch.empty_like(U)
+    params = B.paro_default_params(solve_tol=1e-11, inner_tol=1e-4)
+    rc, st = m.orbital_solve(rr.lam, U, X, params)
+    assert rc == 0 and st.refine_sweeps >= 2 and st.cg_iters_f32 > 0
+    assert st.max_relres <= 1e-11
+    assert np.max(np.abs(host(X) - ref.X)) < 1e-8 * np.max(np.abs(ref.X))
+    m.close()
+
+
+@pytest.mark.parametrize("N", [1, 6, 11])
+def test_rayleigh_ritz_matches_oracle(B, N):
+    p = W.harmonic(nc=10, L=5.0, N=N, seed=3100 + N)
+    ops = oracle_ops(p)
+    ref = O.rayleigh_ritz(ops, p.U0)
+    m = make_mesh(B, p)
+    X = dev(p.U0)
+    U = torch.empty_like(X)
+    lam, st = m.rayleigh_ritz(X, U)
+    assert np.max(np.abs(lam - ref.lam) / np.abs(ref.lam)) < 1e-11
+    u = host(U)
+    G = u.T @ (ops.M @ u)
+    assert np.max(np.abs(G - np.eye(N))) < 1e-12
+    assert np.max(O.subspace_angles_M(ops.M, u, ref.U)) < 1e-8
+    # column by column (Ritz values are simple here): same vector up to sign
+    for j in range(N):
+        s = np.sign(u[:, j] @ (ops.M @ ref.U[:, j]))
+        assert np.max(np.abs(s * u[:, j] - ref.U[:, j])) < 1e-7 * np.max(np.abs(ref.U[:, j]))
+    # rotation in place: X and U_out may alias
+    lam2, _ = m.rayleigh_ritz(X, X)
+    assert np.max(np.abs(lam2 - lam)) < 1e-13 * np.max(np.abs(lam))
+    assert np.max(np.abs(host(X) - u)) < 1e-13 * np.max(np.abs(u))
+    m.close()
+
+
+def test_iterate_fp64_iterate_by_iterate(B):
+    # fixed number of outer iterations from identical inputs, both sides in float64
+    p = W.hydrogen(nc=12, L=8.0, N=5, seed=1200, sigma=2.0)
+    ops = oracle_ops(p)
+    ref = O.paro(ops, p.U0, pcg_tol=1e-12, fixed_outer=6)
+    m = make_mesh(B, p)
+    U = dev(p.U0)
+    params = B.paro_default_params(fixed_outer=6, solve_tol=1e-12, check_every=8)
+    rc, lam, st = m.iterate(U, None, params)
+    assert rc == 0 and st.outer_iters == 6
+    assert np.max(np.abs(lam - ref.lam) / np.abs(ref.lam)) < 1e-10
+    u = host(U)
+    assert np.max(np.abs(u.T @ (ops.M @ u) - np.eye(5))) < 1e-12
+    assert np.max(O.subspace_angles_M(ops.M, u, ref.U)) < 1e-7
+    m.close()
+
+
+def test_hydrogen_32_converges_to_discrete_spectrum(B):
+    # full 32^3 hydrogen workload: tol 1e-8 on |delta lambda|, sigma = 2
+    with open(os.path.join(HERE, "golden", "discrete_spectra.json")) as f:
+        gold = np.array(json.load(f)["hydrogen_32_L10"]["values"][:5])
+    p = W.hydrogen(nc=32, L=10.0, N=5, seed=1000, sigma=2.0)
+    m = make_mesh(B, p)
+    U = dev(p.U0)
+    params = B.paro_default_params(tol=1e-8, max_outer=400, solve_tol=1e-12)
+    rc, lam, st = m.iterate(U, None, params)
+    assert rc == 0, B.paro_last_error(m.h)
+    # stopping at |delta lambda| < 1e-8 leaves ~1e-7 on the slowest level
+    assert np.max(np.abs(lam - gold)) < 1e-6, (lam, gold)
+    assert np.all(lam >= gold - 1e-9)  # Ritz values bound the discrete ones from above
+    u = host(U)
+    ops = oracle_ops(p)
+    assert np.max(np.abs(u.T @ (ops.M @ u) - np.eye(5))) < 1e-12
+    m.close()
+
+
+def test_mixed_iterate_matches_oracle_to_1e6(B):
+    p = W.harmonic(nc=16, L=6.0, N=10, seed=2200, sigma=0.0)
+    ops = oracle_ops(p)
+    ref = O.paro(ops, p.U0, tol=1e-12, max_outer=300, pcg_tol=1e-12)
+    m = make_mesh(B, p, B.PARO_MIXED)
+    U = dev(p.U0)
+    # the vector error is about the square root of the eigenvalue change at the
+    # stop, so angles below 1e-5 need |delta lambda| well below 1e-10
+    params = B.paro_default_params(tol=1e-12, max_outer=400, solve_tol=1e-11)
+    rc, lam, st = m.iterate(U, None, params)
+    assert rc == 0
+    assert np.max(np.abs(lam - ref.lam)) < 1e-6
+    assert st.cg_iters_f32 > 0
+    u = host(U)
+    # clusters of (numerically) equal values are compared as subspaces
+    for a, b in ((0, 1), (1, 4), (4, 10)):
+        assert np.max(O.subspace_angles_M(ops.M, u[:, a:b], ref.U[:, a:b])) < 1e-5
+    m.close()
+
+
+def test_harmonic_32_mixed_converges_to_discrete_spectrum(B):
+    with open(os.path.join(HERE, "golden", "discrete_spectra.json")) as f:
+        gold = np.array(json.load(f)["harmonic_32_L8"]["values"][:10])
+    p = W.harmonic(nc=32, L=8.0, N=10, seed=2300, sigma=0.0)
+    m = make_mesh(B, p, B.PARO_MIXED)
+    U = dev(p.U0)
+    params = B.paro_default_params(tol=1e-9, max_outer=400, solve_tol=1e-10)
+    rc, lam, st = m.iterate(U, None, params)
+    assert rc == 0
+    assert np.max(np.abs(lam - gold)) < 1e-6
+    m.close()
+
+
+def test_errors_are_reported_not_raised_on_device(B):
+    p = W.hydrogen(nc=8, L=6.0, N=3, seed=1300, sigma=-3.0)  # A = H - 3M is indefinite
+    m = make_mesh(B, p)
+    U = dev(p.U0)
+    X = torch.empty_like(U)
+    rc, _ = m.orbital_solve(np.array([-0.4, -0.1, -0.1]), U, X, allow=(-3, -4))
+    assert rc == -3  # PARO_ERR_NOT_SPD
+    with pytest.raises(B.ParoError):
+        m.orbital_solve(np.zeros(3), U, U)  # X aliases U
+    # the handle stays usable after an error
+    m.set_potential(m._vq, 2.0)
+    rc, _ = m.orbital_solve(np.array([-0.4, -0.1, -0.1]), U, X)
+    assert rc == 0
+    Ubad = U.clone()
+    Ubad[3, 1] = float("nan")
+    rc, _ = m.orbital_solve(np.zeros(3), Ubad, X, allow=(-5,))
+    assert rc == -5  # PARO_ERR_NONFINITE
+    m.close()
+    m2 = B.Mesh(p.n, p.lo, p.hi)
+    with pytest.raises(B.ParoError) as e:
+        m2.rayleigh_ritz(U, X)
+    assert e.value.code == -8  # no potential yet
+    m2.close()

@@ -1,0 +1,89 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports
+every function ``include/paro.h`` declares, and the ctypes structures of the
+binding have the C layout."""
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "paro.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(paro_\w+)\s*\(", text, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1405_0260_gb300 import binding
+
+    if not os.path.exists(binding.LIB_PATH):
+        import __graft_entry__
+
+        __graft_entry__.build()
+    return binding.lib()
+
+
+def test_header_declares_the_entry_points():
+    names = declared_functions()
+    for f in ("paro_mesh_create", "paro_mesh_destroy", "paro_set_potential", "paro_orbital_solve",
+              "paro_rayleigh_ritz", "paro_iterate", "paro_apply", "paro_last_error", "paro_default_params"):
+        assert f in names
+
+
+def test_library_exports_every_declared_function(lib):
+    for f in declared_functions():
+        assert hasattr(lib, f), f
+
+
+def test_default_params_and_null_handle_errors(lib):
+    from paper_1405_0260_gb300 import binding as B
+
+    p = B.paro_default_params()
+    assert p.tol == 1e-10 and p.solve_tol == 1e-12 and p.max_outer == 500 and p.profile == 0
+    # argument errors are caught before any CUDA call
+    h = ctypes.c_void_p()
+    lo = (ctypes.c_double * 3)(-1, -1, -1)
+    hi = (ctypes.c_double * 3)(1, 1, 1)
+    rc = lib.paro_mesh_create(ctypes.byref(h), 1, 4, 4, lo, hi, 0, None)
+    assert rc == -1 and "cells per axis" in B.paro_last_error(None)
+    rc = lib.paro_mesh_create(ctypes.byref(h), 4, 4, 4, hi, lo, 0, None)
+    assert rc == -1 and "lo < hi" in B.paro_last_error(None)
+    rc = lib.paro_mesh_create(ctypes.byref(h), 4, 4, 4, lo, hi, 7, None)
+    assert rc == -1
+    assert lib.paro_mesh_destroy(None) == -1
+    assert lib.paro_iterate(None, 1, None, None, None, None) == -1
+
+
+def test_ctypes_structs_match_c_layout(lib):
+    from paper_1405_0260_gb300 import binding as B
+
+    src = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "paro.h"
+int main(void) {
+  printf("%zu %zu\n", sizeof(paro_params), sizeof(paro_stats));
+  printf("%zu %zu %zu\n", offsetof(paro_params, profile), offsetof(paro_stats, prof_ms),
+         offsetof(paro_stats, prof_dof_orb));
+  return 0;
+}
+'''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        exe = os.path.join(d, "t")
+        open(c, "w").write(src)
+        subprocess.run(["gcc", "-I", os.path.dirname(HEADER), c, "-o", exe], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
+    sizes = [int(v) for v in out]
+    assert sizes[0] == ctypes.sizeof(B.paro_params)
+    assert sizes[1] == ctypes.sizeof(B.paro_stats)
+    assert sizes[2] == B.paro_params.profile.offset
+    assert sizes[3] == B.paro_stats.prof_ms.offset
+    assert sizes[4] == B.paro_stats.prof_dof_orb.offset

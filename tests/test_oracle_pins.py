@@ -243,3 +243,14 @@ def test_subspace_angles_of_same_span_are_zero():
     T = rng.standard_normal((4, 4))
     ang = O.subspace_angles_M(ops.M, p.U0, p.U0 @ T)
     assert np.max(ang) < 1e-6
+
+
+def test_subspace_angles_of_known_rotation():
+    # span{e1, e2} against span{e1, cos t e2 + sin t e3} in the Euclidean (M = I) product:
+    # one zero angle and one angle t, resolved down to tiny t by the sine form
+    M = sp.identity(5, format="csr")
+    U = np.eye(5)[:, :2]
+    for t in (0.3, 1e-6, 1e-10):
+        W = np.stack([np.eye(5)[:, 0], math.cos(t) * np.eye(5)[:, 1] + math.sin(t) * np.eye(5)[:, 2]], axis=1)
+        ang = O.subspace_angles_M(M, U, W)
+        assert abs(ang[0]) < 1e-15 and abs(ang[1] - t) < 1e-6 * t
