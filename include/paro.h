@@ -154,6 +154,40 @@ int paro_iterate(paro_mesh m, int N, double* U, double* lambda, const paro_param
  * X, Y: device (n_interior x N), must not alias.  The kernel the CG iterations use. */
 int paro_apply(paro_mesh m, int N, int op, int dtype, const void* X, void* Y);
 
+/* Largest N accepted by paro_small_eig_static. */
+#define PARO_STATIC_EIG_MAX_N 128
+
+/* The small generalized eigenproblem of the Rayleigh-Ritz step, for callers
+ * that must not allocate device memory.  The paper has no counterpart: this is
+ * a library convenience.  Some callers cannot call cudaMalloc: applications
+ * that hand all device memory to their own pool up front and forbid other
+ * allocations, and latency-critical loops where a cudaMalloc (which may
+ * synchronise the device) would stall other streams.  This entry point
+ * allocates nothing: its work matrices live in one file-scope, statically sized
+ * device array of 4*128*128 + 32 doubles (about 512 KiB), which every GPU that
+ * loads the library holds until the process exits.
+ *
+ * Computes, in float64, the same thing as the small solve inside
+ * paro_rayleigh_ritz: G_B = L L^T (Cholesky), L^-1 G_A L^-T = Q Theta Q^T
+ * (cyclic Jacobi, ascending), C = L^-T Q.
+ *   N      : 1 <= N <= PARO_STATIC_EIG_MAX_N, else PARO_ERR_ARG (nothing launched).
+ *   GA, GB : device, N x N float64 row-major (symmetrised as (G + G^T)/2); GB SPD.
+ *   C      : device, N x N float64 row-major out: column j is the eigenvector of theta[j],
+ *            G_B-orthonormal (C^T G_B C = I, C^T G_A C = diag(theta)).
+ *   theta  : device, N float64 out, ascending.
+ *   cuda_stream : cudaStream_t the work is ordered on (NULL = legacy default stream).
+ * Returns PARO_OK, PARO_ERR_ARG, PARO_ERR_NOT_SPD (non-positive Cholesky pivot:
+ * C and theta are then not written) or PARO_ERR_CUDA.  The call synchronises the
+ * stream (it reads back the status word).
+ * The caller owns GA, GB, C and theta; the library allocates nothing, neither
+ * cudaMalloc nor any allocating library routine.  The first call on a device
+ * looks up the array's device address with that device current (a one-time
+ * set-up per device); make that first call before any stream capture.  All
+ * calls share the one array and it keeps the last call's contents, so calls
+ * whose work overlaps on the GPU (different streams, threads) race: order them. */
+int paro_small_eig_static(int N, const double* GA, const double* GB, double* C, double* theta,
+                          void* cuda_stream);
+
 /* Message describing the last error on this handle ("" if none).  NULL handle:
  * the last paro_mesh_create failure.  The string lives until the next call. */
 const char* paro_last_error(paro_mesh m);

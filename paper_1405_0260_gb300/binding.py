@@ -226,3 +226,16 @@ class Mesh:
 
         dt = PARO_F32 if X.dtype == torch.float32 else PARO_F64
         paro_apply(self.h, X.shape[1], op, dt, self._dev(X, X.dtype), self._dev(Y, X.dtype))
+
+
+def paro_small_eig_static(N, GA_ptr, GB_ptr, C_ptr, theta_ptr, stream=0):
+    """Small generalized eigensolve with statically allocated scratch (allocates nothing).
+
+    Returns the status code (0 = PARO_OK); there is no handle, so no message.
+    """
+    L = lib()
+    f = L.paro_small_eig_static
+    f.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    f.restype = C.c_int
+    return f(int(N), C.c_void_p(GA_ptr), C.c_void_p(GB_ptr), C.c_void_p(C_ptr), C.c_void_p(theta_ptr),
+             C.c_void_p(stream))

@@ -3,6 +3,9 @@
 //   G_B = L L^T, L^-1 G_A L^-T = Q Theta Q^T         (small_eig: one CTA, float64)
 //   C = L^-T Q (columns sorted by ascending theta), U = X C   (rotate)
 #include <cmath>
+#include <mutex>
+
+#include "../../include/paro.h"
 
 #include "common.cuh"
 
@@ -335,3 +338,57 @@ cudaError_t launch_rotate(const Grid& g, int N, int Np, const double* X, const d
 }
 
 }  // namespace paro
+
+// ---------------------------------------------------------------------------
+// paro_small_eig_static: the small generalized eigensolve of k_small_eig with
+// its scratch in a fixed, statically sized device array instead of memory the
+// library allocates.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr int kStaticEigMaxN = PARO_STATIC_EIG_MAX_N;
+// Work matrices L, S, V, W (4 N^2 doubles at N <= kStaticEigMaxN), then the
+// status word.  Every GPU that loads this library holds the array until the
+// process exits; all calls share it.
+constexpr size_t kStaticEigDoubles = 4ull * kStaticEigMaxN * kStaticEigMaxN + 32;
+__device__ __align__(256) double g_static_eig_scratch[kStaticEigDoubles];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_eig_mu;
+void* g_static_eig_ptr[kMaxDevices] = {};
+
+}  // namespace
+
+extern "C" int paro_small_eig_static(int N, const double* GA, const double* GB, double* C, double* theta,
+                                     void* cuda_stream) {
+  if (N < 1 || N > kStaticEigMaxN) return PARO_ERR_ARG;
+  if (!GA || !GB || !C || !theta) return PARO_ERR_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PARO_ERR_CUDA;
+  double* scratch = nullptr;
+  {
+    // Once per device, with that device current: the device address of the
+    // array (in host code its name is only a host-side stand-in).
+    std::lock_guard<std::mutex> lock(g_static_eig_mu);
+    if (g_static_eig_ptr[dev] == nullptr) {
+      void* ptr = nullptr;
+      if (cudaGetSymbolAddress(&ptr, g_static_eig_scratch) != cudaSuccess || ptr == nullptr) return PARO_ERR_CUDA;
+      g_static_eig_ptr[dev] = ptr;
+    }
+    scratch = static_cast<double*>(g_static_eig_ptr[dev]);
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  int* status = reinterpret_cast<int*>(scratch + 4ull * kStaticEigMaxN * kStaticEigMaxN);
+  // The status word keeps the previous call's value: clear it.  The work
+  // matrices are fully written by the kernel before they are read.
+  if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return PARO_ERR_CUDA;
+  paro::k_small_eig<<<1, 1024, 0, st>>>(N, N, GA, GB, scratch, C, theta, status);
+  if (cudaGetLastError() != cudaSuccess) return PARO_ERR_CUDA;
+  int h = 0;
+  if (cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return PARO_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return PARO_ERR_CUDA;
+  if (h & paro::kStatNotSPD) return PARO_ERR_NOT_SPD;
+  return PARO_OK;
+}
+
