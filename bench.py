@@ -147,12 +147,8 @@ def run_ours(args, ws, rank, local):
     for _ in range(args.warmup):
         _, lam, _ = m.iterate(U, lam, params)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-    prof = B.paro_default_params(fixed_outer=1, solve_tol=1e-10, inner_tol=1e-4, profile=1)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     launches = 0
-    prof_ms = 0.0
-    prof_n = 0
-    prof_units = 0
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
@@ -163,14 +159,25 @@ def run_ours(args, ws, rank, local):
                 flush_l2(flush)
             stream.synchronize()
             ev[i][0].record(stream)
-            _, lam, st = m.iterate(U, lam, prof)
+            _, lam, st = m.iterate(U, lam, params)
             ev[i][1].record(stream)
             launches += st.kernel_launches
-            prof_ms += st.prof_ms
-            prof_n += st.prof_launches
-            prof_units += st.prof_dof_orb
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
+    # Second timed region, same workload: the CG loop launched from the host
+    # (no graph) with CUDA events around every launch of the operator kernel.
+    prof = B.paro_default_params(fixed_outer=1, solve_tol=1e-10, inner_tol=1e-4, profile=1)
+    prof_ms = 0.0
+    prof_n = 0
+    prof_units = 0
+    for i in range(max(1, min(args.steps, 3))):
+        with torch.cuda.stream(stream):
+            flush_l2(flush)
+        stream.synchronize()
+        _, lam, st = m.iterate(U, lam, prof)
+        prof_ms += st.prof_ms
+        prof_n += st.prof_launches
+        prof_units += st.prof_dof_orb
     if dist is not None:
         dist.barrier()
     ms = sum(a.elapsed_time(b) for a, b in ev)
@@ -191,7 +198,7 @@ def run_ours(args, ws, rank, local):
     if prof_n > 0 and prof_ms > 0:
         alg_bytes = 16.0 * prof_units + 36.0 * nI * prof_n
         achieved = alg_bytes / (prof_ms * 1e-3) / 1e9
-        roof = {"kernel": "k_cg_q<float> (p = D^-1 r + beta p; q = A p; (p,q))", "bound": "hbm",
+        roof = {"kernel": "k_cg_q<float> (TMA-tiled: p = D^-1 r + beta p; q = A p; (p,q))", "bound": "hbm",
                 "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": None,
                 "launches": prof_n, "avg_launch_us": round(1e3 * prof_ms / prof_n, 2),

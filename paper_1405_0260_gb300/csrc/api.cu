@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/paro.h"
+#include "cg.cuh"
 #include "common.cuh"
 
 using namespace paro;
@@ -37,16 +38,27 @@ struct paro_mesh_s {
   unsigned int* ticket = nullptr;
   double* h_dbl = nullptr;  // pinned host staging
   int* h_int = nullptr;
+  // pinned staging of the CG controls only: h_dbl may still be the source of a
+  // queued copy (the per-orbital right-hand-side scales) when a solve starts
+  double* h_ctl = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   std::vector<void*> allocs;
   // launch accounting and optional per-launch timing of the CG operator kernel
   long long launches = 0;
-  unsigned long long* work = nullptr;  // device counter written by cg_q
   int profile = 0;
   std::vector<cudaEvent_t> pev;       // kProfPairs start/stop pairs
   int pev_used = 0;
   long long prof_launches = 0;
   double prof_ms = 0.0;
+  // batched CG: device state, partial sums, TMA-layout operator, plans (graphs)
+  int nsm = 152;
+  CGDevState* cgst = nullptr;
+  double* cgpart = nullptr;
+  int wpitch = 0, dpitch = 0;
+  float *w32 = nullptr, *dt32 = nullptr;
+  double *w64 = nullptr, *dt64 = nullptr;
+  CGPlan<float>* plan32 = nullptr;
+  CGPlan<double>* plan64 = nullptr;
 };
 
 static std::string g_create_err;
@@ -123,20 +135,81 @@ CGState cg_state(paro_mesh m, bool refine) {
   s.rr = m->dscal + (refine ? S_RRR : S_RR) * kMaxN;
   s.active = m->dint + I_ACTIVE * kMaxN;
   s.iters = m->dint + I_ITERS * kMaxN;
-  s.skip = m->dint + I_SKIP * kMaxN;
-  s.n_active = m->dint + I_COUNT * kMaxN;
-  s.status = m->dint + I_COUNT * kMaxN + 1;
+  s.skip = m->cgst->skip;
+  s.n_active = &m->cgst->n_active;
+  s.status = &m->cgst->status;
   s.partial = m->partial;
   s.ticket = m->ticket;
-  s.work = m->profile ? m->work : nullptr;
+  s.work = nullptr;
   return s;
+}
+
+void free_plans(paro_mesh m) {
+  if (m->plan32) {
+    if (m->plan32->exec_zero) cudaGraphExecDestroy(m->plan32->exec_zero);
+    if (m->plan32->exec_warm) cudaGraphExecDestroy(m->plan32->exec_warm);
+    delete m->plan32;
+    m->plan32 = nullptr;
+  }
+  if (m->plan64) {
+    if (m->plan64->exec_zero) cudaGraphExecDestroy(m->plan64->exec_zero);
+    if (m->plan64->exec_warm) cudaGraphExecDestroy(m->plan64->exec_warm);
+    delete m->plan64;
+    m->plan64 = nullptr;
+  }
+}
+
+template <typename T>
+int make_plan(paro_mesh m, int Np, CGPlan<T>** out, T* x, T* b, T* r, T* p, T* q, const T* dinv, const T* dinv_tma,
+              const T* wcoef, const T* coef) {
+  CGPlan<T>* P = new CGPlan<T>();
+  P->nsm = m->nsm;
+  P->args.g = m->g;
+  P->args.N = Np;  // set per solve
+  P->args.Np = Np;
+  P->args.x = x;
+  P->args.b = b;
+  P->args.r = r;
+  P->args.p = p;
+  P->args.q = q;
+  P->args.dinv = dinv;
+  P->args.part = m->cgpart;
+  P->args.st = m->cgst;
+  P->args.in_graph = 0;
+  P->dpitch = m->dpitch;
+  P->wpitch = m->wpitch;
+  P->dinv_tma = dinv_tma;
+  P->wcoef = wcoef;
+  int bw = 0;
+  cudaError_t e = cg_plan_geometry<T>(m->g, Np, m->nsm, &P->geo, &bw);
+  if (e == cudaSuccess) e = cg_prepare<T>(P);
+  if (e != cudaSuccess) {
+    delete P;
+    return fail(m, PARO_ERR_CUDA, std::string("CG plan: ") + cudaGetErrorString(e));
+  }
+  Grid g = m->g;
+  P->add_apply = [g, Np, coef, x, q](cudaGraph_t gr, cudaGraphNode_t* node) {
+    return graph_add_apply<T>(gr, node, g, Np, coef, x, q);
+  };
+  *out = P;
+  return PARO_OK;
+}
+
+int make_plans(paro_mesh m, int Np) {
+  free_plans(m);
+  TRY(make_plan<double>(m, Np, &m->plan64, m->x, m->b, m->r, m->p0, m->q, m->dinv64, m->dt64, m->w64, m->coef64));
+  if (m->precision == PARO_MIXED)
+    TRY(make_plan<float>(m, Np, &m->plan32, m->x32, m->b32, m->r32, m->p32a, m->q32, m->dinv32, m->dt32, m->w32,
+                         m->coef32));
+  return PARO_OK;
 }
 
 int ensure_workspace(paro_mesh m, int Np) {
   if (Np == m->Np_alloc) return PARO_OK;
+  free_plans(m);
   // release the previous vector workspace
   void* olds[] = {m->u, m->x, m->b, m->r, m->p0, m->p1, m->q, m->b32, m->x32, m->r32, m->p32a, m->p32b, m->q32,
-                  m->gpart, m->GA, m->GB, m->C, m->theta, m->eigwork};
+                  m->gpart, m->GA, m->GB, m->C, m->theta, m->eigwork, m->cgpart};
   CK(cudaStreamSynchronize(m->st));
   for (void* p : olds) dfree(m, p);
   size_t n = (size_t)m->g.G * Np;
@@ -161,12 +234,14 @@ int ensure_workspace(paro_mesh m, int Np) {
   TRY(dalloc(m, &m->C, (size_t)Np * Np));
   TRY(dalloc(m, &m->theta, (size_t)Np));
   TRY(dalloc(m, &m->eigwork, (size_t)4 * Np * Np));
+  TRY(dalloc(m, &m->cgpart, (size_t)3 * 4 * m->nsm * Np));
   m->Np_alloc = Np;
+  TRY(make_plans(m, Np));
   return PARO_OK;
 }
 
 int check_status(paro_mesh m, const char* where) {
-  int* st = m->dint + I_COUNT * kMaxN + 1;
+  int* st = &m->cgst->status;
   CK(cudaMemcpyAsync(m->h_int, st, sizeof(int), cudaMemcpyDeviceToHost, m->st));
   CK(cudaStreamSynchronize(m->st));
   int bits = m->h_int[0];
@@ -175,13 +250,15 @@ int check_status(paro_mesh m, const char* where) {
   if (bits & kStatNonFinite) return fail(m, PARO_ERR_NONFINITE, std::string(where) + ": non-finite value in a reduction");
   if (bits & kStatNotSPD)
     return fail(m, PARO_ERR_NOT_SPD, std::string(where) + ": operator or Gram matrix not positive definite");
+  if (bits & kStatTimeout)
+    return fail(m, PARO_ERR_TIMEOUT, std::string(where) + ": a bounded device-side wait ran out");
   if (bits & kStatNotConverged)
     return fail(m, PARO_ERR_NOT_CONVERGED, std::string(where) + ": iteration limit reached");
   return PARO_OK;
 }
 
 int read_n_active(paro_mesh m, int* out) {
-  CK(cudaMemcpyAsync(m->h_int, m->dint + I_COUNT * kMaxN, sizeof(int), cudaMemcpyDeviceToHost, m->st));
+  CK(cudaMemcpyAsync(m->h_int, &m->cgst->n_active, sizeof(int), cudaMemcpyDeviceToHost, m->st));
   CK(cudaStreamSynchronize(m->st));
   *out = m->h_int[0];
   return PARO_OK;
@@ -189,7 +266,7 @@ int read_n_active(paro_mesh m, int* out) {
 
 // Sum and max of the per-orbital CG counts of the last solve.
 int read_iters(paro_mesh m, int N, long long* sum, int* mx) {
-  CK(cudaMemcpyAsync(m->h_int, m->dint + I_ITERS * kMaxN, sizeof(int) * N, cudaMemcpyDeviceToHost, m->st));
+  CK(cudaMemcpyAsync(m->h_int, m->cgst->iters, sizeof(int) * N, cudaMemcpyDeviceToHost, m->st));
   CK(cudaStreamSynchronize(m->st));
   long long s = 0;
   int x = 0;
@@ -214,31 +291,65 @@ int drain_profile(paro_mesh m) {
   return PARO_OK;
 }
 
+cudaError_t launch_apply_T(paro_mesh m, CGPlan<double>* P) {
+  return launch_apply_f64(m->g, P->args.Np, m->coef64, nullptr, 0.0, P->args.x, P->args.q, nullptr, m->st);
+}
+cudaError_t launch_apply_T(paro_mesh m, CGPlan<float>* P) {
+  return launch_apply_f32(m->g, P->args.Np, m->coef32, P->args.x, P->args.q, m->st);
+}
+
+// One batched CG solve with the plan P: A x = b from x (warm) or from x = 0.
+// Graph mode: one graph launch (init + device-side while loop).  Profile
+// mode: the same kernels launched from the host with CUDA events around every
+// operator (K1) launch; the host tests the active count every check_every.
 template <typename T>
-int run_cg(paro_mesh m, int N, int Np, const CGVectors<T>& v, const CGState& s, bool x_zero, double tol, int maxit,
-           int check_every, long long* it_sum, int* it_max) {
-  LAUNCH(1, launch_cg_init<T>(m->g, N, Np, v, s, x_zero, tol, maxit, m->st));
+int run_cg(paro_mesh m, CGPlan<T>* P, int N, bool warm, double tol, int maxit, int check_every, long long* it_sum,
+           int* it_max) {
+  P->args.N = N;
+  // controls
+  // the previous solve's copies from h_ctl completed: every run_cg ends with a stream synchronisation
+  m->h_ctl[0] = tol;
+  int* ctl_int = reinterpret_cast<int*>(m->h_ctl + 1);
+  ctl_int[0] = maxit;
+  CK(cudaMemcpyAsync(&m->cgst->tol, m->h_ctl, sizeof(double), cudaMemcpyHostToDevice, m->st));
+  CK(cudaMemcpyAsync(&m->cgst->maxit, ctl_int, sizeof(int), cudaMemcpyHostToDevice, m->st));
+  if (!m->profile) {
+    // N is baked into the graph arguments: rebuild when it changes
+    cudaGraphExec_t* ex = warm ? &P->exec_warm : &P->exec_zero;
+    if (P->graph_N != N) {
+      if (P->exec_warm) cudaGraphExecDestroy(P->exec_warm);
+      if (P->exec_zero) cudaGraphExecDestroy(P->exec_zero);
+      P->exec_warm = P->exec_zero = nullptr;
+      P->graph_N = N;
+    }
+    if (!*ex) {
+      cudaError_t e = cg_build_graph<T>(P, m->st, warm);
+      if (e != cudaSuccess) return fail(m, PARO_ERR_CUDA, std::string("CG graph: ") + cudaGetErrorString(e));
+    }
+    CK(cudaGraphLaunch(*ex, m->st));
+    TRY(read_iters(m, N, it_sum, it_max));
+    m->launches += (warm ? 1 : 0) + 1 + 2LL * (*it_max);
+    return PARO_OK;
+  }
+  if (warm) LAUNCH(1, launch_apply_T(m, P));
+  LAUNCH(1, cg_launch_init<T>(P, m->st, !warm));
   int nact = 0;
   TRY(read_n_active(m, &nact));
-  int parity = 0;
   int done = 0;
-  if (m->profile && check_every > kProfPairs) check_every = kProfPairs;
+  if (check_every > kProfPairs) check_every = kProfPairs;
   while (nact > 0 && done < maxit) {
     int k = check_every;
     if (k > maxit - done) k = maxit - done;
     for (int i = 0; i < k; ++i) {
-      if (m->profile) CK(cudaEventRecord(m->pev[2 * m->pev_used], m->st));
-      LAUNCH(1, launch_cg_q<T>(m->g, Np, v, s, parity, m->st));
-      if (m->profile) {
-        CK(cudaEventRecord(m->pev[2 * m->pev_used + 1], m->st));
-        m->pev_used++;
-      }
-      LAUNCH(1, launch_cg_update<T>(m->g, Np, v, s, parity, tol, maxit, m->st));
-      parity ^= 1;
+      CK(cudaEventRecord(m->pev[2 * m->pev_used], m->st));
+      LAUNCH(1, cg_launch_k1<T>(P, m->st));
+      CK(cudaEventRecord(m->pev[2 * m->pev_used + 1], m->st));
+      m->pev_used++;
+      LAUNCH(1, cg_launch_k2<T>(P, m->st));
     }
     done += k;
     TRY(read_n_active(m, &nact));
-    if (m->profile) TRY(drain_profile(m));
+    TRY(drain_profile(m));
   }
   TRY(read_iters(m, N, it_sum, it_max));
   return PARO_OK;
@@ -257,10 +368,8 @@ int solve_packed(paro_mesh m, int N, const double* lam, const paro_params& p, pa
   long long its = 0;
   int itmax = 0;
   if (m->precision == PARO_FP64) {
-    CGVectors<double> v{m->x, m->b, m->r, {m->p0, m->p1}, m->q, m->coef64, m->dinv64};
-    CGState s = cg_state(m, false);
-    s.skip = nullptr;
-    TRY(run_cg<double>(m, N, Np, v, s, false, p.solve_tol, p.pcg_maxit, p.check_every, &its, &itmax));
+    CK(cudaMemsetAsync(m->cgst->skip, 0, sizeof(int) * kMaxN, m->st));
+    TRY(run_cg<double>(m, m->plan64, N, true, p.solve_tol, p.pcg_maxit, p.check_every, &its, &itmax));
     if (st) {
       st->cg_iters += its;
       st->cg_iters_max = itmax;
@@ -271,13 +380,12 @@ int solve_packed(paro_mesh m, int N, const double* lam, const paro_params& p, pa
     CGState rs = cg_state(m, true);
     LAUNCH(1, launch_refine_residual(g, N, Np, m->coef64, m->x, m->b, nullptr, rs, p.solve_tol, m->st));
   } else {
-    CGVectors<float> v{m->x32, m->b32, m->r32, {m->p32a, m->p32b}, m->q32, m->coef32, m->dinv32};
     CGState rs = cg_state(m, true);
-    CGState s = cg_state(m, false);
     int sweep = 0;
     long long its32 = 0;
     int maxit_seen = 0;
     for (;;) {
+      // r = b - A x in float64; its float32 rounding is the correction right-hand side
       LAUNCH(1, launch_refine_residual(g, N, Np, m->coef64, m->x, m->b, m->b32, rs, p.solve_tol, m->st));
       if (st) st->stencil_applies += N;
       int open = 0;
@@ -291,9 +399,9 @@ int solve_packed(paro_mesh m, int N, const double* lam, const paro_params& p, pa
       }
       long long i1 = 0;
       int imx = 0;
-      TRY(run_cg<float>(m, N, Np, v, s, true, p.inner_tol, p.pcg_maxit, p.check_every, &i1, &imx));
+      TRY(run_cg<float>(m, m->plan32, N, false, p.inner_tol, p.pcg_maxit, p.check_every, &i1, &imx));
       // an inner limit is not fatal: refinement carries on from the partial correction
-      int* stw = m->dint + I_COUNT * kMaxN + 1;
+      int* stw = &m->cgst->status;
       CK(cudaMemcpyAsync(m->h_int, stw, sizeof(int), cudaMemcpyDeviceToHost, m->st));
       CK(cudaStreamSynchronize(m->st));
       if (m->h_int[0] & kStatNotConverged) {
@@ -301,7 +409,7 @@ int solve_packed(paro_mesh m, int N, const double* lam, const paro_params& p, pa
         CK(cudaMemcpyAsync(stw, m->h_int, sizeof(int), cudaMemcpyHostToDevice, m->st));
       }
       TRY(check_status(m, "orbital_solve (float32 correction)"));
-      LAUNCH(1, launch_refine_update(g, Np, m->x, m->x32, s.skip, m->st));
+      LAUNCH(1, launch_refine_update(g, Np, m->x, m->x32, m->cgst->skip, m->st));
       its32 += i1;
       if (imx > maxit_seen) maxit_seen = imx;
       ++sweep;
@@ -338,7 +446,7 @@ int rr_packed(paro_mesh m, int N, const double* src, double* dst, double* lam) {
   LAUNCH(1, launch_apply_f64(g, Np, m->coef64, &m->mw, m->sigma, src, m->r, nullptr, m->st));  // H = A - sigma M
   LAUNCH(1, launch_apply_f64(g, Np, nullptr, &m->mw, 0.0, src, m->q, nullptr, m->st));         // M
   LAUNCH(2, launch_gram2(g, N, Np, src, m->r, m->q, m->gpart, nullptr, m->GA, m->GB, m->st));
-  LAUNCH(1, launch_small_eig(N, m->GA, m->GB, m->eigwork, m->C, m->theta, m->dint + I_COUNT * kMaxN + 1, m->st));
+  LAUNCH(1, launch_small_eig(N, m->GA, m->GB, m->eigwork, m->C, m->theta, &m->cgst->status, m->st));
   TRY(check_status(m, "rayleigh_ritz"));
   LAUNCH(1, launch_rotate(g, N, Np, src, m->C, dst, m->st));
   CK(cudaMemcpyAsync(m->h_dbl, m->theta, sizeof(double) * N, cudaMemcpyDeviceToHost, m->st));
@@ -392,7 +500,7 @@ struct CallScope {
           return;
         }
     }
-    if (cudaMemsetAsync(m->work, 0, sizeof(unsigned long long), m->st) != cudaSuccess) return;
+    if (cudaMemsetAsync(&m->cgst->work, 0, sizeof(unsigned long long), m->st) != cudaSuccess) return;
     m->profile = 1;
   }
   ~CallScope() {
@@ -400,7 +508,7 @@ struct CallScope {
       s->kernel_launches += m->launches - l0;
       if (m->profile) {
         unsigned long long w = 0;
-        if (cudaMemcpyAsync(m->h_dbl, m->work, sizeof(w), cudaMemcpyDeviceToHost, m->st) == cudaSuccess &&
+        if (cudaMemcpyAsync(m->h_dbl, &m->cgst->work, sizeof(w), cudaMemcpyDeviceToHost, m->st) == cudaSuccess &&
             cudaStreamSynchronize(m->st) == cudaSuccess)
           std::memcpy(&w, m->h_dbl, sizeof(w));
         s->prof_launches += m->prof_launches;
@@ -465,6 +573,14 @@ int paro_mesh_create(paro_mesh* out, int nx, int ny, int nz, const double lo[3],
   g.hy = (hi[1] - lo[1]) / ny;
   g.hz = (hi[2] - lo[2]) / nz;
   mass_weights(g, &m->mw);
+  m->wpitch = (nx - 1 + 3) / 4 * 4;
+  m->dpitch = (g.Px + 3) / 4 * 4;
+  {
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0)
+      m->nsm = nsm;
+  }
   int rc = PARO_OK;
   cudaError_t e;
   if ((rc = dalloc(m, &m->coef64, (size_t)27 * g.G)) || (rc = dalloc(m, &m->coef32, (size_t)27 * g.G)) ||
@@ -472,12 +588,16 @@ int paro_mesh_create(paro_mesh* out, int nx, int ny, int nz, const double lo[3],
       (rc = dalloc(m, &m->dscal, (size_t)S_COUNT * kMaxN)) ||
       (rc = dalloc(m, &m->dint, (size_t)I_COUNT * kMaxN + 8)) ||
       (rc = dalloc(m, &m->partial, (size_t)3 * kMaxRedBlocks * kMaxN)) || (rc = dalloc(m, &m->ticket, 4)) ||
-      (rc = dalloc(m, &m->work, 1))) {
+      (rc = dalloc(m, &m->cgst, 1)) || (rc = dalloc(m, &m->w32, (size_t)27 * g.Pz * (ny - 1) * m->wpitch)) ||
+      (rc = dalloc(m, &m->w64, (size_t)27 * g.Pz * (ny - 1) * m->wpitch)) ||
+      (rc = dalloc(m, &m->dt32, (size_t)g.Pz * g.Py * m->dpitch)) ||
+      (rc = dalloc(m, &m->dt64, (size_t)g.Pz * g.Py * m->dpitch))) {
     g_create_err = m->err;
     paro_mesh_destroy(m);
     return rc;
   }
   if ((e = cudaMallocHost(&m->h_dbl, sizeof(double) * 2 * kMaxN)) != cudaSuccess ||
+      (e = cudaMallocHost(&m->h_ctl, sizeof(double) * 2)) != cudaSuccess ||
       (e = cudaMallocHost(&m->h_int, sizeof(int) * kMaxN)) != cudaSuccess ||
       (e = cudaEventCreate(&m->e0)) != cudaSuccess || (e = cudaEventCreate(&m->e1)) != cudaSuccess) {
     g_create_err = std::string("host setup: ") + cudaGetErrorString(e);
@@ -496,10 +616,12 @@ int paro_mesh_create(paro_mesh* out, int nx, int ny, int nz, const double lo[3],
 int paro_mesh_destroy(paro_mesh m) {
   if (!m) return PARO_ERR_ARG;
   cudaStreamSynchronize(m->st);
+  free_plans(m);
   for (void* p : m->allocs)
     if (p) cudaFree(p);
   if (m->h_dbl) cudaFreeHost(m->h_dbl);
   if (m->h_int) cudaFreeHost(m->h_int);
+  if (m->h_ctl) cudaFreeHost(m->h_ctl);
   if (m->e0) cudaEventDestroy(m->e0);
   if (m->e1) cudaEventDestroy(m->e1);
   for (auto e : m->pev)
@@ -513,6 +635,10 @@ int paro_set_potential(paro_mesh m, const double* Vq, double sigma) {
   if (!Vq) return fail(m, PARO_ERR_ARG, "Vq is null");
   if (!std::isfinite(sigma)) return fail(m, PARO_ERR_ARG, "sigma must be finite");
   LAUNCH(1, launch_build_coef(m->g, Vq, sigma, m->coef64, m->coef32, m->dinv64, m->dinv32, m->st));
+  LAUNCH(2, launch_build_tma_operator<double>(m->g, m->coef64, m->dinv64, m->w64, m->wpitch, m->dt64, m->dpitch,
+                                               m->st));
+  LAUNCH(2, launch_build_tma_operator<float>(m->g, m->coef32, m->dinv32, m->w32, m->wpitch, m->dt32, m->dpitch,
+                                              m->st));
   m->sigma = sigma;
   m->have_pot = true;
   return PARO_OK;
@@ -571,7 +697,8 @@ int paro_iterate(paro_mesh m, int N, double* U, double* lambda, const paro_param
     Timer t(m, s ? &s->ms_rr : nullptr);
     TRY(rr_packed(m, N, m->u, m->x, lam.data()));
     t.stop();
-    std::swap(m->u, m->x);
+    // copy rather than swap: the CG plans hold the addresses of the workspace vectors
+    CK(cudaMemcpyAsync(m->u, m->x, sizeof(double) * m->g.G * Np, cudaMemcpyDeviceToDevice, m->st));
   }
   const int nchk = (pp.n_check > 0 && pp.n_check < N) ? pp.n_check : N;
   int outer = 0;

@@ -1,0 +1,867 @@
+// Batched Jacobi-preconditioned CG for the N source problems of Step 3
+// (Algorithms 3.1 / A.1, eq. 3.2, in the shifted SPD form A x_i = b_i), one
+// independent CG per orbital with its own convergence mask, run on the device
+// as one CUDA graph:
+//
+//   init (streaming)      r = b - A x0, p = 0, (r, D^-1 r), (r, r), (b, b)
+//   while (any orbital active) {
+//     K1 cg_q  (TMA tiles) p = D^-1 r + beta p on the staged tile + halo, q = A p, (p, q)
+//     K2 cg_upd (streaming) p, x += alpha p, r -= alpha q, (r, D^-1 r), (r, r)
+//   }
+//
+// K1 is persistent: each CTA walks (orbital block, z segment, y, x) tiles; a
+// tile is TX x TY interior nodes marching in z.  For every input plane it
+// stages, by TMA into a 4-slot shared-memory ring, r and p_old on the tile plus
+// a one-node halo, D^-1 on the same region, and the 27 operator weights of the
+// plane keyed by input plane (see operator.cu).  Each input plane is read from
+// shared memory once (9 loads per output node and orbital group) and feeds the
+// three output planes it touches, accumulated in registers.
+//
+// Every kernel reduces its per-orbital dot products deterministically: block
+// sums in fixed order, per-CTA partials, and the last CTA to finish (atomic
+// ticket) sums the partials in fixed order and updates the per-orbital scalars
+// (alpha, beta, masks, counts); K2's last CTA also sets the graph's while
+// condition.  All mbarrier waits are bounded.
+#include <cmath>
+#include <cstring>
+
+#include "cg.cuh"
+#include "tma.cuh"
+
+namespace paro {
+
+namespace {
+
+constexpr int kNT = 64;  // node slots per pass in K1 (threads = kNT * G4)
+constexpr int kSlots = 4;
+
+template <typename T>
+struct Vec4 {
+  T v[4];
+};
+
+template <typename T>
+__device__ __forceinline__ Vec4<T> lds4(const T* p) {
+  Vec4<T> r;
+  if constexpr (sizeof(T) == 4) {
+    float4 a = *reinterpret_cast<const float4*>(p);
+    r.v[0] = a.x, r.v[1] = a.y, r.v[2] = a.z, r.v[3] = a.w;
+  } else {
+    double2 a = reinterpret_cast<const double2*>(p)[0];
+    double2 b = reinterpret_cast<const double2*>(p)[1];
+    r.v[0] = a.x, r.v[1] = a.y, r.v[2] = b.x, r.v[3] = b.y;
+  }
+  return r;
+}
+
+template <typename T>
+__device__ __forceinline__ void sts4(T* p, const Vec4<T>& r) {
+  if constexpr (sizeof(T) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(r.v[0], r.v[1], r.v[2], r.v[3]);
+  } else {
+    reinterpret_cast<double2*>(p)[0] = make_double2(r.v[0], r.v[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(r.v[2], r.v[3]);
+  }
+}
+
+__device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
+
+// p_new = D^-1 r + beta p_old (the same expression in K1 and K2).
+template <typename T>
+__device__ __forceinline__ T pnew(T di, T r, T beta, T pold) {
+  return fmaT(beta, pold, di * r);
+}
+
+// Deterministic reduction of K per-orbital partial vectors over the CTAs of a
+// kernel, run by the last CTA: tot[k*Np + o] = sum_b part[(k*G + b)*Np + o].
+// Threads take (item, slice) pairs; slices are summed in order.
+template <int K>
+__device__ void reduce_over_ctas(const double* part, int G, int Np, double* sm, double* tot) {
+  const int items = K * Np;
+  const int nt = blockDim.x;
+  int S = nt / items;
+  if (S < 1) S = 1;
+  if (S > 32) S = 32;
+  for (int t = threadIdx.x; t < items * S; t += nt) {
+    int item = t % items, sl = t / items;
+    int k = item / Np, o = item % Np;
+    const double* base = part + (long long)k * G * Np + o;
+    double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    int b = sl;
+    for (; b + 3 * S < G; b += 4 * S) {
+      a0 += __ldcg(base + (long long)b * Np);
+      a1 += __ldcg(base + (long long)(b + S) * Np);
+      a2 += __ldcg(base + (long long)(b + 2 * S) * Np);
+      a3 += __ldcg(base + (long long)(b + 3 * S) * Np);
+    }
+    for (; b < G; b += S) a0 += __ldcg(base + (long long)b * Np);
+    sm[sl * items + item] = (a0 + a1) + (a2 + a3);
+  }
+  __syncthreads();
+  for (int item = threadIdx.x; item < items; item += nt) {
+    double s = 0.0;
+    for (int sl = 0; sl < S; ++sl) s += sm[sl * items + item];
+    tot[item] = s;
+  }
+  __syncthreads();
+}
+
+// Writes this CTA's partials, takes a ticket; true in the last CTA.
+__device__ bool last_cta(unsigned int* ticket) {
+  __shared__ bool am_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned prev = atomicAdd(ticket, 1u);
+    am_last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (am_last) __threadfence();
+  return am_last;
+}
+
+// ---------------------------------------------------------------------------
+// init: r = b - q0 (q0 = A x0, or x0 = 0), p = 0, partials (r,z), (r,r), (b,b)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_cg_init(CGArgs<T> a, int x_zero, cudaGraphConditionalHandle cond) {
+  extern __shared__ double dsm[];
+  const int G4 = a.Np / 4;
+  const int nt = blockDim.x;  // multiple of G4
+  const int g = threadIdx.x % G4;
+  double acc[3][4] = {};
+  const long long rowlen = (long long)(a.g.nx - 1) * G4;  // float4 groups per interior row
+  const long long nrows = (long long)(a.g.ny - 1) * (a.g.nz - 1);
+  const long long total = rowlen * nrows;
+  for (long long i = (long long)blockIdx.x * nt + threadIdx.x; i < total; i += (long long)gridDim.x * nt) {
+    long long row = i / rowlen;
+    long long off = i - row * rowlen;
+    int y = (int)(row % (a.g.ny - 1)) + 1, z = (int)(row / (a.g.ny - 1)) + 1;
+    long long node = ((long long)z * a.g.Py + y) * a.g.Px + 1 + off / G4;
+    long long e = node * a.Np + 4 * g;
+    Vec4<T> b = lds4(a.b + e);
+    Vec4<T> r = b;
+    if (!x_zero) {
+      Vec4<T> q = lds4(a.q + e);
+      for (int c = 0; c < 4; ++c) r.v[c] = b.v[c] - q.v[c];
+    } else {
+      sts4(a.x + e, Vec4<T>{});
+    }
+    sts4(a.r + e, r);
+    sts4(a.p + e, Vec4<T>{});
+    T di = a.dinv[node];
+    for (int c = 0; c < 4; ++c) {
+      acc[0][c] += (double)(r.v[c] * (di * r.v[c]));
+      acc[1][c] += (double)r.v[c] * (double)r.v[c];
+      acc[2][c] += (double)b.v[c] * (double)b.v[c];
+    }
+  }
+  // block reduce over threads of equal group
+  double* red = dsm;  // [nt/G4][Np] per k
+  const int NTs = nt / G4;
+  const int j = threadIdx.x / G4;
+  for (int k = 0; k < 3; ++k) {
+    for (int c = 0; c < 4; ++c) red[(k * NTs + j) * a.Np + 4 * g + c] = acc[k][c];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < 3 * a.Np; t += nt) {
+    int k = t / a.Np, o = t % a.Np;
+    double s = 0.0;
+    for (int jj = 0; jj < NTs; ++jj) s += red[(k * NTs + jj) * a.Np + o];
+    a.part[((long long)k * gridDim.x + blockIdx.x) * a.Np + o] = s;
+  }
+  if (!last_cta(&a.st->ticket)) return;
+  // slices of the cross-CTA sum use dsm[0 .. 32*3*Np); totals follow
+  double* tot = dsm + 3 * a.Np * 33;
+  reduce_over_ctas<3>(a.part, gridDim.x, a.Np, dsm, tot);
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  const double tol = a.st->tol;
+  const int maxit = a.st->maxit;
+  for (int o = threadIdx.x; o < a.Np; o += nt) {
+    double rz = tot[o], rr = tot[a.Np + o], bb = tot[2 * a.Np + o];
+    a.st->rz[o] = rz;
+    a.st->rr[o] = rr;
+    a.st->bb[o] = bb;
+    a.st->iters[o] = 0;
+    a.st->alpha[o] = 0.0;
+    a.st->beta[o] = 0.0;
+    bool skip = (o >= a.N) || a.st->skip[o] != 0;
+    bool act = !skip && maxit > 0 && rr > tol * tol * bb;
+    if (!skip && !(isfinite(rr) && isfinite(bb) && isfinite(rz))) {
+      atomicOr(&a.st->status, kStatNonFinite);
+      act = false;
+    } else if (act && !(rz > 0.0)) {
+      atomicOr(&a.st->status, kStatNotSPD);
+      act = false;
+    }
+    a.st->active[o] = act ? 1 : 0;
+    if (act) atomicAdd(&cnt, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    a.st->n_active = cnt;
+    a.st->ticket = 0u;
+    if (a.in_graph) cudaGraphSetConditional(cond, cnt > 0 ? 1u : 0u);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K1: tiled stencil.  q = A p_new, p_new = D^-1 r + beta p_old, partial (p, q)
+// ---------------------------------------------------------------------------
+template <typename T, int G4>
+__global__ void __launch_bounds__(kNT* G4) k_cg_q(CGArgs<T> a, K1Geom geo, const __grid_constant__ CUtensorMap mr,
+                                                  const __grid_constant__ CUtensorMap mp,
+                                                  const __grid_constant__ CUtensorMap md,
+                                                  const __grid_constant__ CUtensorMap mw) {
+  constexpr int bw = 4 * G4;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int TX = geo.TX, TY = geo.TY;
+  const int HX = TX + 2, HY = TY + 2;
+  const int tid = threadIdx.x;
+  const int g = tid % G4, j = tid / G4;
+  (void)HY;
+  // shared layout: barriers, kSlots ring slots (r, p, D^-1, W), then reduction space
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+  unsigned char* base = smem + 128;
+  auto slotR = [&](int s) { return reinterpret_cast<T*>(base + (size_t)s * geo.slot_bytes); };
+  auto slotP = [&](int s) { return reinterpret_cast<T*>(base + (size_t)s * geo.slot_bytes + geo.off_p); };
+  auto slotD = [&](int s) { return reinterpret_cast<T*>(base + (size_t)s * geo.slot_bytes + geo.off_d); };
+  auto slotW = [&](int s) { return reinterpret_cast<T*>(base + (size_t)s * geo.slot_bytes + geo.off_w); };
+  double* sacc = reinterpret_cast<double*>(base + (size_t)kSlots * geo.slot_bytes);  // [Np]
+  double* sred = sacc + a.Np;                                                       // [kNT][bw]
+  __shared__ int abort_flag;
+  __shared__ T sbeta[kMaxN];
+  __shared__ int sact[kMaxN / 4];
+  __shared__ int sblk[kMaxN / 4];
+
+  // Static split of the column-planes over the CTAs: f = ((ob*ncy + ty)*ncx + tx)*nzo + (z - 1),
+  // CTA c takes [F c / G, F (c+1) / G) as runs of consecutive output planes of one column.
+  const int nzo = a.g.nz - 1;
+  const long long F = (long long)geo.nob * geo.ncy * geo.ncx * nzo;
+  const long long fbeg = F * blockIdx.x / gridDim.x;
+  const long long fend = F * (blockIdx.x + 1) / gridDim.x;
+  if (tid == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < kSlots; ++s) mbar_init(&bars[s], 1);
+    fence_mbar_init();
+    prefetch_tmap(&mr);
+    prefetch_tmap(&mp);
+    prefetch_tmap(&md);
+    prefetch_tmap(&mw);
+  }
+  for (int o = tid; o < a.Np; o += blockDim.x) {
+    sacc[o] = 0.0;
+    sbeta[o] = (T)a.st->beta[o];
+  }
+  for (int q = tid; q < a.Np / 4; q += blockDim.x)
+    sact[q] = a.st->active[4 * q] | a.st->active[4 * q + 1] | a.st->active[4 * q + 2] | a.st->active[4 * q + 3];
+  __syncthreads();
+  for (int ob = tid; ob < geo.nob; ob += blockDim.x) {
+    int any = 0;
+    for (int q = ob * G4; q < ob * G4 + G4 && q < a.Np / 4; ++q) any |= sact[q];
+    sblk[ob] = any;
+  }
+  __syncthreads();
+
+  // Segment starting at column-plane f: orbital offset, column origin, output planes [z0, z1).
+  auto seg_at = [&](long long f, int& o0, int& x0, int& y0, int& z0, int& z1) {
+    const long long col = f / nzo;
+    const int zl = (int)(f - col * nzo);
+    const long long rem = fend - f;
+    const int zh = (rem < (long long)(nzo - zl)) ? zl + (int)rem : nzo;
+    const int tx = (int)(col % geo.ncx);
+    const long long r = col / geo.ncx;
+    const int ty = (int)(r % geo.ncy);
+    const int ob = (int)(r / geo.ncy);
+    o0 = ob * bw;
+    x0 = 1 + tx * TX;
+    y0 = 1 + ty * TY;
+    z0 = 1 + zl;
+    z1 = 1 + zh;
+  };
+  const uint32_t slot_tx = geo.tx_bytes;
+
+  // Loader cursor (thread 0 only): segment start and input plane within the segment.
+  long long lf = fbeg;
+  int ls = 0, lz0 = 0, lz1 = 0, lo0 = 0, lx0 = 0, ly0 = 0;
+  bool lhave = false;
+  int lstep = 0;  // loads issued
+  auto issue_next = [&]() {
+    while (lf < fend) {
+      if (!lhave) {
+        seg_at(lf, lo0, lx0, ly0, lz0, lz1);
+        lhave = true;
+        ls = 0;
+        if (!sblk[lo0 / bw]) {  // every orbital of the block has converged: nothing to stage
+          lf += lz1 - lz0;
+          lhave = false;
+          continue;
+        }
+      }
+      const int zin = lz0 - 1 + ls;
+      if (zin <= lz1) {
+        const int slot = lstep % kSlots;
+        mbar_arrive_expect_tx(&bars[slot], slot_tx);
+        tma_load_4d(slotR(slot), &mr, lo0, lx0 - 1, ly0 - 1, zin, &bars[slot]);
+        tma_load_4d(slotP(slot), &mp, lo0, lx0 - 1, ly0 - 1, zin, &bars[slot]);
+        tma_load_3d(slotD(slot), &md, lx0 - 1, ly0 - 1, zin, &bars[slot]);
+        tma_load_4d(slotW(slot), &mw, lx0 - 1, ly0 - 1, 0, zin, &bars[slot]);
+        ++lstep;
+        ++ls;
+        return;
+      }
+      lf += lz1 - lz0;
+      lhave = false;
+    }
+  };
+  if (tid == 0)
+    for (int k = 0; k < kSlots; ++k) issue_next();
+
+  int cstep = 0;                    // consumer steps done
+  const int npt = (TX * TY) / kNT;  // nodes per thread per plane (1 or 2)
+  for (long long f = fbeg; f < fend;) {
+    int o0, x0, y0, z0, z1;
+    seg_at(f, o0, x0, y0, z0, z1);
+    f += z1 - z0;
+    if (!sblk[o0 / bw]) continue;
+    // a ragged last block: groups at orbitals >= Np are staged as zeros and never stored
+    const bool gact = (o0 + 4 * g < a.Np) && sact[o0 / 4 + g] != 0;
+    const T be0 = gact ? sbeta[o0 + 4 * g] : T(0), be1 = gact ? sbeta[o0 + 4 * g + 1] : T(0),
+            be2 = gact ? sbeta[o0 + 4 * g + 2] : T(0), be3 = gact ? sbeta[o0 + 4 * g + 3] : T(0);
+    // Rolling accumulators of the three output planes an input plane touches:
+    // aD = output s-1 (completed at step s), aC = output s, aU = output s+1.
+    Vec4<T> aD[2], aC[2], aU[2], pcPrev[2], pcCur[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) aD[k] = aC[k] = aU[k] = pcPrev[k] = pcCur[k] = Vec4<T>{};
+    double dot0 = 0, dot1 = 0, dot2 = 0, dot3 = 0;
+    for (int s = z0 - 1; s <= z1; ++s) {
+      const int slot = cstep % kSlots;
+      const uint32_t par = (cstep / kSlots) & 1;
+      if (!mbar_wait(&bars[slot], par)) abort_flag = 1;
+      __syncthreads();
+      if (abort_flag) goto bail;
+      if (gact) {
+        // p_new = D^-1 r + beta p_old on tile + halo, in place
+        const T* D = slotD(slot);
+        T* P = slotP(slot);
+        const T* R = slotR(slot);
+        for (int h = j; h < HX * HY; h += kNT) {
+          const int hy = h / HX, hx = h - hy * HX;
+          const T di = D[hy * geo.DX + hx];
+          Vec4<T> rv = lds4(R + h * bw + 4 * g);
+          Vec4<T> pv = lds4(P + h * bw + 4 * g);
+          pv.v[0] = pnew<T>(di, rv.v[0], be0, pv.v[0]);
+          pv.v[1] = pnew<T>(di, rv.v[1], be1, pv.v[1]);
+          pv.v[2] = pnew<T>(di, rv.v[2], be2, pv.v[2]);
+          pv.v[3] = pnew<T>(di, rv.v[3], be3, pv.v[3]);
+          sts4(P + h * bw + 4 * g, pv);
+        }
+        // these generic-proxy writes precede the TMA write that later refills the slot
+        fence_proxy_async_smem();
+      }
+      __syncthreads();
+      if (gact) {
+        const T* P = slotP(slot);
+        const T* W = slotW(slot);
+        const int TXY = TX * TY;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          if (k < npt) {
+            const int n = j + k * kNT;
+            const int ty = n / TX, tx = n - ty * TX;
+#pragma unroll
+            for (int dy = -1; dy <= 1; ++dy) {
+#pragma unroll
+              for (int dx = -1; dx <= 1; ++dx) {
+                const int h = (ty + 1 + dy) * HX + (tx + 1 + dx);
+                const Vec4<T> v = lds4(P + h * bw + 4 * g);
+                const int o = (dy + 1) * 3 + (dx + 1);
+                const T wu = W[o * TXY + n];         // dz = -1 of output s+1
+                const T wc = W[(9 + o) * TXY + n];   // dz =  0 of output s
+                const T wd = W[(18 + o) * TXY + n];  // dz = +1 of output s-1
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                  aU[k].v[c] = fmaT(wu, v.v[c], aU[k].v[c]);
+                  aC[k].v[c] = fmaT(wc, v.v[c], aC[k].v[c]);
+                  aD[k].v[c] = fmaT(wd, v.v[c], aD[k].v[c]);
+                }
+                if (dy == 0 && dx == 0) pcCur[k] = v;
+              }
+            }
+            // output s-1 is complete
+            const int tz = s - 1;
+            if (tz >= z0 && tz < z1) {
+              const int x = x0 + tx, y = y0 + ty;
+              if (x <= a.g.nx - 1 && y <= a.g.ny - 1) {
+                const long long node = ((long long)tz * a.g.Py + y) * a.g.Px + x;
+                dot0 += (double)(pcPrev[k].v[0] * aD[k].v[0]);
+                dot1 += (double)(pcPrev[k].v[1] * aD[k].v[1]);
+                dot2 += (double)(pcPrev[k].v[2] * aD[k].v[2]);
+                dot3 += (double)(pcPrev[k].v[3] * aD[k].v[3]);
+                sts4(a.q + node * a.Np + o0 + 4 * g, aD[k]);
+              }
+            }
+            aD[k] = aC[k];
+            aC[k] = aU[k];
+            aU[k] = Vec4<T>{};
+            pcPrev[k] = pcCur[k];
+          }
+        }
+      }
+      __syncthreads();
+      ++cstep;
+      if (tid == 0) issue_next();
+    }
+    // per-segment block reduction of (p, q) into sacc[o0 .. o0+bw)
+    sred[j * bw + 4 * g + 0] = dot0;
+    sred[j * bw + 4 * g + 1] = dot1;
+    sred[j * bw + 4 * g + 2] = dot2;
+    sred[j * bw + 4 * g + 3] = dot3;
+    __syncthreads();
+    for (int o = tid; o < bw && o0 + o < a.Np; o += blockDim.x) {
+      double sum = 0.0;
+      for (int jj = 0; jj < kNT; ++jj) sum += sred[jj * bw + o];
+      sacc[o0 + o] += sum;
+    }
+    __syncthreads();
+  }
+bail:
+  __syncthreads();
+  if (abort_flag) {
+    if (tid == 0) atomicOr(&a.st->status, kStatTimeout);
+    // wait (bounded) for copies still in flight before the CTA's shared memory goes away
+    if (tid == 0)
+      for (int k = cstep; k < lstep; ++k) mbar_wait(&bars[k % kSlots], (k / kSlots) & 1);
+    __syncthreads();
+  }
+  for (int o = tid; o < a.Np; o += blockDim.x) a.part[(long long)blockIdx.x * a.Np + o] = sacc[o];
+  if (!last_cta(&a.st->ticket)) return;
+  double* tot = sred;
+  double* scratch = sred + a.Np;
+  reduce_over_ctas<1>(a.part, gridDim.x, a.Np, scratch, tot);
+  if (tid == 0) {
+    unsigned long long w = 0;
+    for (int q4 = 0; q4 < a.Np / 4; ++q4)
+      if (sact[q4]) w += 4ull * a.g.nI;
+    a.st->work += w;
+  }
+  for (int o = tid; o < a.Np; o += blockDim.x) {
+    double pq = tot[o];
+    a.st->pq[o] = pq;
+    double alpha = 0.0;
+    if (a.st->active[o]) {
+      if (!isfinite(pq)) {
+        atomicOr(&a.st->status, kStatNonFinite);
+        a.st->active[o] = 0;
+      } else if (!(pq > 0.0)) {
+        atomicOr(&a.st->status, kStatNotSPD);
+        a.st->active[o] = 0;
+      } else {
+        alpha = a.st->rz[o] / pq;
+      }
+    }
+    a.st->alpha[o] = alpha;
+  }
+  __syncthreads();
+  if (tid == 0) a.st->ticket = 0u;
+}
+
+// ---------------------------------------------------------------------------
+// K2: p = D^-1 r + beta p, x += alpha p, r -= alpha q, partials (r,z), (r,r);
+// the last CTA updates masks, counts, beta and the graph's while condition.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_cg_upd(CGArgs<T> a, cudaGraphConditionalHandle cond) {
+  extern __shared__ double dsm[];
+  __shared__ T sal[kMaxN], sbe[kMaxN];
+  const int G4 = a.Np / 4;
+  const int nt = blockDim.x;
+  const int g = threadIdx.x % G4;
+  for (int o = threadIdx.x; o < a.Np; o += nt) {
+    sal[o] = (T)a.st->alpha[o];
+    sbe[o] = (T)a.st->beta[o];
+  }
+  __syncthreads();
+  const bool gact = (a.st->active[4 * g] | a.st->active[4 * g + 1] | a.st->active[4 * g + 2] |
+                     a.st->active[4 * g + 3]) != 0;
+  double acc[2][4] = {};
+  if (gact) {
+    const T al[4] = {sal[4 * g], sal[4 * g + 1], sal[4 * g + 2], sal[4 * g + 3]};
+    const T be[4] = {sbe[4 * g], sbe[4 * g + 1], sbe[4 * g + 2], sbe[4 * g + 3]};
+    const long long rowlen = (long long)(a.g.nx - 1) * G4;
+    const long long nrows = (long long)(a.g.ny - 1) * (a.g.nz - 1);
+    const long long total = rowlen * nrows;
+    for (long long i = (long long)blockIdx.x * nt + threadIdx.x; i < total; i += (long long)gridDim.x * nt) {
+      long long row = i / rowlen;
+      long long off = i - row * rowlen;
+      int y = (int)(row % (a.g.ny - 1)) + 1, z = (int)(row / (a.g.ny - 1)) + 1;
+      long long node = ((long long)z * a.g.Py + y) * a.g.Px + 1 + off / G4;
+      long long e = node * a.Np + 4 * g;
+      Vec4<T> x = lds4(a.x + e), r = lds4(a.r + e), p = lds4(a.p + e), q = lds4(a.q + e);
+      T di = a.dinv[node];
+      for (int c = 0; c < 4; ++c) {
+        p.v[c] = pnew<T>(di, r.v[c], be[c], p.v[c]);
+        x.v[c] = fmaT(al[c], p.v[c], x.v[c]);
+        r.v[c] = fmaT(-al[c], q.v[c], r.v[c]);
+        acc[0][c] += (double)(r.v[c] * (di * r.v[c]));
+        acc[1][c] += (double)r.v[c] * (double)r.v[c];
+      }
+      sts4(a.x + e, x);
+      sts4(a.r + e, r);
+      sts4(a.p + e, p);
+    }
+  }
+  double* red = dsm;
+  const int NTs = nt / G4;
+  const int j = threadIdx.x / G4;
+  for (int k = 0; k < 2; ++k)
+    for (int c = 0; c < 4; ++c) red[(k * NTs + j) * a.Np + 4 * g + c] = acc[k][c];
+  __syncthreads();
+  for (int t = threadIdx.x; t < 2 * a.Np; t += nt) {
+    int k = t / a.Np, o = t % a.Np;
+    double s = 0.0;
+    for (int jj = 0; jj < NTs; ++jj) s += red[(k * NTs + jj) * a.Np + o];
+    a.part[((long long)k * gridDim.x + blockIdx.x) * a.Np + o] = s;
+  }
+  if (!last_cta(&a.st->ticket)) return;
+  double* tot = dsm + 2 * a.Np * 33;
+  reduce_over_ctas<2>(a.part, gridDim.x, a.Np, dsm, tot);
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  const double tol = a.st->tol;
+  const int maxit = a.st->maxit;
+  for (int o = threadIdx.x; o < a.Np; o += nt) {
+    double beta = 0.0;
+    if (a.st->active[o]) {
+      double rz = tot[o], rr = tot[a.Np + o];
+      int it = a.st->iters[o] + 1;
+      a.st->iters[o] = it;
+      a.st->rr[o] = rr;
+      bool act = true;
+      if (!(isfinite(rz) && isfinite(rr))) {
+        atomicOr(&a.st->status, kStatNonFinite);
+        act = false;
+      } else if (rr <= tol * tol * a.st->bb[o]) {
+        act = false;
+      } else if (!(rz > 0.0)) {
+        atomicOr(&a.st->status, kStatNotSPD);
+        act = false;
+      } else if (it >= maxit) {
+        atomicOr(&a.st->status, kStatNotConverged);
+        act = false;
+      }
+      if (act) {
+        beta = rz / a.st->rz[o];
+        atomicAdd(&cnt, 1);
+      }
+      a.st->rz[o] = rz;
+      a.st->active[o] = act ? 1 : 0;
+    }
+    a.st->beta[o] = beta;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    a.st->n_active = cnt;
+    a.st->ticket = 0u;
+    if (a.in_graph) cudaGraphSetConditional(cond, cnt > 0 ? 1u : 0u);
+  }
+}
+
+template <typename T>
+void* k1_fn(int G4) {
+  switch (G4) {
+    case 1: return (void*)k_cg_q<T, 1>;
+    case 2: return (void*)k_cg_q<T, 2>;
+    case 3: return (void*)k_cg_q<T, 3>;
+    case 4: return (void*)k_cg_q<T, 4>;
+    case 5: return (void*)k_cg_q<T, 5>;
+    case 6: return (void*)k_cg_q<T, 6>;
+    case 7: return (void*)k_cg_q<T, 7>;
+    case 8: return (void*)k_cg_q<T, 8>;
+  }
+  return nullptr;
+}
+
+// Adds a kernel node whose arguments are copied from `args` (addresses of the values).
+cudaError_t add_kernel(cudaGraph_t gr, cudaGraphNode_t* node, const cudaGraphNode_t* deps, size_t nd, void* fn,
+                       dim3 grid, dim3 block, size_t smem, void** args) {
+  cudaKernelNodeParams p{};
+  p.func = fn;
+  p.gridDim = grid;
+  p.blockDim = block;
+  p.sharedMemBytes = (unsigned)smem;
+  p.kernelParams = args;
+  p.extra = nullptr;
+  return cudaGraphAddKernelNode(node, gr, deps, nd, &p);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+
+// Shared-memory footprint of K1 for a tile shape and orbital block width.
+template <typename T>
+void k1_layout(int Np, int bw, int TX, int TY, K1Geom* G) {
+  const size_t sz = sizeof(T);
+  G->TX = TX;
+  G->TY = TY;
+  const int HX = TX + 2, HY = TY + 2;
+  G->DX = TX + 4;  // row of D^-1 staged from x0-1: TX+2 values padded to a 16-byte multiple
+  size_t vec = (size_t)HX * HY * bw * sz;
+  size_t dv = (size_t)G->DX * HY * sz;
+  size_t wv = (size_t)27 * TX * TY * sz;
+  auto al = [](size_t v) { return (v + 127) / 128 * 128; };
+  G->off_p = (int)al(vec);
+  G->off_d = (int)(G->off_p + al(vec));
+  G->off_w = (int)(G->off_d + al(dv));
+  G->slot_bytes = (int)(G->off_w + al(wv));
+  G->tx_bytes = (uint32_t)(2 * vec + dv + wv);
+  // sacc[Np], then the per-segment block sums [kNT][bw], reused at the end for the
+  // cross-CTA totals [Np] and slices (at most max(threads, Np) values)
+  const size_t nthr = (size_t)kNT * (bw / 4);
+  const size_t fin = (size_t)Np + (nthr > (size_t)Np ? nthr : (size_t)Np);
+  const size_t blk = (size_t)kNT * bw;
+  size_t red = ((size_t)Np + (blk > fin ? blk : fin)) * sizeof(double);
+  G->smem = 128 + (size_t)kSlots * G->slot_bytes + red;
+}
+
+template <typename T>
+cudaError_t cg_plan_geometry(const Grid& g, int Np, int nsm, K1Geom* geo, int* bw_out) {
+  const int sz = (int)sizeof(T);
+  // static shared memory of K1 (beta, group masks, flags) and the opt-in limit
+  const size_t stat = (size_t)kMaxN * sz + 2 * (kMaxN / 4) * sizeof(int) + 64;
+  const size_t limit = 227 * 1024 - stat - 1024;
+  const int cap = 32;  // widest orbital block (G4 <= 8)
+  const int shapes[3][2] = {{16, 8}, {16, 4}, {8, 8}};  // TX*TY a multiple of kNT
+  K1Geom best{};
+  int best_bw = 0;
+  // fewest orbital blocks whose ring fits; the last block may be ragged (TMA fills
+  // orbitals >= Np with zeros and the kernel stores none of them)
+  for (int nob = (Np + cap - 1) / cap; nob <= Np / 4 && !best_bw; ++nob) {
+    int bw = (Np + nob - 1) / nob;
+    bw = (bw + 3) / 4 * 4;
+    if ((Np + bw - 1) / bw != nob) continue;
+    for (int si = 0; si < 3; ++si) {
+      K1Geom G{};
+      k1_layout<T>(Np, bw, shapes[si][0], shapes[si][1], &G);
+      if (G.smem <= limit) {
+        best = G;
+        best_bw = bw;
+        break;
+      }
+    }
+  }
+  if (!best_bw) return cudaErrorInvalidConfiguration;
+  K1Geom G = best;
+  const int bw = best_bw;
+  *bw_out = bw;
+  G.G4 = bw / 4;
+  G.ncx = (g.nx - 1 + G.TX - 1) / G.TX;
+  G.ncy = (g.ny - 1 + G.TY - 1) / G.TY;
+  const int nob = (Np + bw - 1) / bw;
+  int per_sm = 1;
+  void* f1 = k1_fn<T>(G.G4);
+  if (f1 && cudaFuncSetAttribute(f1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G.smem) == cudaSuccess) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f1, kNT * G.G4, G.smem) == cudaSuccess && nb > 0)
+      per_sm = nb;
+  }
+  if (per_sm > 4) per_sm = 4;
+  G.nob = nob;
+  // every CTA takes an equal share of the nob*ncx*ncy*(nz-1) column-planes, at least 4 of them
+  // (each run of planes stages 2 halo planes)
+  const long long want = (long long)nsm * per_sm;
+  const long long F = (long long)nob * G.ncx * G.ncy * (g.nz - 1);
+  long long grid = F / 4;
+  if (grid < 1) grid = 1;
+  if (grid > want) grid = want;
+  G.grid = (int)grid;
+  *geo = G;
+  return cudaSuccess;
+}
+
+// Tensor maps, kernel attributes, stream-kernel grids and shared-memory sizes.
+template <typename T>
+cudaError_t cg_prepare(CGPlan<T>* P) {
+  cudaError_t e;
+  const K1Geom& G = P->geo;
+  const CGArgs<T>& a = P->args;
+  const int bw = G.G4 * 4;
+  const CUtensorMapDataType ty = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+  const uint64_t sz = sizeof(T);
+  {
+    uint64_t dims[4] = {(uint64_t)a.Np, (uint64_t)a.g.Px, (uint64_t)a.g.Py, (uint64_t)a.g.Pz};
+    uint64_t str[3] = {a.Np * sz, (uint64_t)a.g.Px * a.Np * sz, (uint64_t)a.g.Py * a.g.Px * a.Np * sz};
+    uint32_t box[4] = {(uint32_t)bw, (uint32_t)(G.TX + 2), (uint32_t)(G.TY + 2), 1};
+    if ((e = encode_tiled(&P->mr, ty, 4, a.r, dims, str, box)) != cudaSuccess) return e;
+    if ((e = encode_tiled(&P->mp, ty, 4, a.p, dims, str, box)) != cudaSuccess) return e;
+  }
+  {
+    uint64_t dims[3] = {(uint64_t)P->dpitch, (uint64_t)a.g.Py, (uint64_t)a.g.Pz};
+    uint64_t str[2] = {(uint64_t)P->dpitch * sz, (uint64_t)P->dpitch * a.g.Py * sz};
+    uint32_t box[3] = {(uint32_t)G.DX, (uint32_t)(G.TY + 2), 1};
+    if ((e = encode_tiled(&P->md, ty, 3, (void*)P->dinv_tma, dims, str, box)) != cudaSuccess) return e;
+  }
+  {
+    uint64_t dims[4] = {(uint64_t)P->wpitch, (uint64_t)(a.g.ny - 1), 27, (uint64_t)a.g.Pz};
+    uint64_t str[3] = {(uint64_t)P->wpitch * sz, (uint64_t)P->wpitch * (a.g.ny - 1) * sz,
+                       (uint64_t)27 * P->wpitch * (a.g.ny - 1) * sz};
+    uint32_t box[4] = {(uint32_t)G.TX, (uint32_t)G.TY, 27, 1};
+    if ((e = encode_tiled(&P->mw, ty, 4, (void*)P->wcoef, dims, str, box)) != cudaSuccess) return e;
+  }
+  void* f1 = k1_fn<T>(G.G4);
+  if (!f1) return cudaErrorInvalidValue;
+  if ((e = cudaFuncSetAttribute(f1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G.smem)) != cudaSuccess)
+    return e;
+  // streaming kernels: threads a multiple of Np/4
+  const int G4f = a.Np / 4;
+  int nt = (256 / G4f) * G4f;
+  if (nt < G4f) nt = G4f;
+  P->nt_stream = nt;
+  long long work = (long long)(a.g.nx - 1) * (a.g.ny - 1) * (a.g.nz - 1) * G4f;
+  long long gs = (work + nt - 1) / nt;
+  long long cap = (long long)P->nsm * 4;
+  P->grid_stream = (int)(gs < cap ? gs : cap);
+  // block reduction [K][nt/G4f][Np], then the last CTA's slices (<= 32 per item) and totals
+  const int NTs = nt / G4f;
+  auto need = [&](int K) {
+    size_t a1 = (size_t)K * NTs * a.Np;
+    size_t a2 = (size_t)K * a.Np * 33;
+    return ((a1 > a2 ? a1 : a2) + (size_t)K * a.Np * 34) * sizeof(double);
+  };
+  P->smem_init = need(3);
+  P->smem_upd = need(2);
+  if (P->smem_init > 200 * 1024) return cudaErrorInvalidConfiguration;
+  if ((e = cudaFuncSetAttribute((void*)k_cg_init<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)P->smem_init)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute((void*)k_cg_upd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)P->smem_upd)) != cudaSuccess)
+    return e;
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t cg_build_graph(CGPlan<T>* P, cudaStream_t st, bool with_apply) {
+  (void)st;
+  cudaError_t e;
+  const K1Geom& G = P->geo;
+  CGArgs<T> a = P->args;
+  a.in_graph = 1;
+  void* f1 = k1_fn<T>(G.G4);
+  cudaGraph_t gr;
+  if ((e = cudaGraphCreate(&gr, 0)) != cudaSuccess) return e;
+  cudaGraphConditionalHandle cond;
+  if ((e = cudaGraphConditionalHandleCreate(&cond, gr, 1, cudaGraphCondAssignDefault)) != cudaSuccess) {
+    cudaGraphDestroy(gr);
+    return e;
+  }
+  cudaGraphNode_t n_apply = nullptr, n_init = nullptr, n_while = nullptr, n1 = nullptr, n2 = nullptr;
+  int x_zero = with_apply ? 0 : 1;
+  do {
+    if (with_apply && (e = P->add_apply(gr, &n_apply)) != cudaSuccess) break;
+    {
+      void* args[] = {&a, &x_zero, &cond};
+      if ((e = add_kernel(gr, &n_init, n_apply ? &n_apply : nullptr, n_apply ? 1 : 0, (void*)k_cg_init<T>,
+                          dim3(P->grid_stream), dim3(P->nt_stream), P->smem_init, args)) != cudaSuccess)
+        break;
+    }
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    if ((e = cudaGraphAddNode(&n_while, gr, &n_init, nullptr, 1, &cp)) != cudaSuccess) break;
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    {
+      K1Geom geo = G;
+      void* args[] = {&a, &geo, &P->mr, &P->mp, &P->md, &P->mw};
+      if ((e = add_kernel(body, &n1, nullptr, 0, f1, dim3(G.grid), dim3(kNT * G.G4), G.smem, args)) != cudaSuccess)
+        break;
+    }
+    {
+      void* args[] = {&a, &cond};
+      if ((e = add_kernel(body, &n2, &n1, 1, (void*)k_cg_upd<T>, dim3(P->grid_stream), dim3(P->nt_stream),
+                          P->smem_upd, args)) != cudaSuccess)
+        break;
+    }
+    cudaGraphExec_t ex;
+    if ((e = cudaGraphInstantiate(&ex, gr, 0)) != cudaSuccess) break;
+    if (with_apply) P->exec_warm = ex;
+    else P->exec_zero = ex;
+  } while (0);
+  cudaGraphDestroy(gr);
+  return e;
+}
+
+template <typename T>
+cudaError_t cg_launch_init(CGPlan<T>* P, cudaStream_t st, bool x_zero) {
+  CGArgs<T> a = P->args;
+  a.in_graph = 0;
+  k_cg_init<T><<<P->grid_stream, P->nt_stream, P->smem_init, st>>>(a, x_zero ? 1 : 0, 0);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t cg_launch_k1(CGPlan<T>* P, cudaStream_t st) {
+  CGArgs<T> a = P->args;
+  a.in_graph = 0;
+  K1Geom geo = P->geo;
+  void* args[] = {&a, &geo, &P->mr, &P->mp, &P->md, &P->mw};
+  return cudaLaunchKernel(k1_fn<T>(geo.G4), dim3(geo.grid), dim3(kNT * geo.G4), args, geo.smem, st);
+}
+
+template <typename T>
+cudaError_t cg_launch_k2(CGPlan<T>* P, cudaStream_t st) {
+  CGArgs<T> a = P->args;
+  a.in_graph = 0;
+  k_cg_upd<T><<<P->grid_stream, P->nt_stream, P->smem_upd, st>>>(a, 0);
+  return cudaGetLastError();
+}
+
+template cudaError_t cg_prepare<float>(CGPlan<float>*);
+template cudaError_t cg_prepare<double>(CGPlan<double>*);
+template cudaError_t cg_launch_init<float>(CGPlan<float>*, cudaStream_t, bool);
+template cudaError_t cg_launch_init<double>(CGPlan<double>*, cudaStream_t, bool);
+template cudaError_t cg_launch_k1<float>(CGPlan<float>*, cudaStream_t);
+template cudaError_t cg_launch_k1<double>(CGPlan<double>*, cudaStream_t);
+template cudaError_t cg_launch_k2<float>(CGPlan<float>*, cudaStream_t);
+template cudaError_t cg_launch_k2<double>(CGPlan<double>*, cudaStream_t);
+
+template cudaError_t cg_plan_geometry<float>(const Grid&, int, int, K1Geom*, int*);
+template cudaError_t cg_plan_geometry<double>(const Grid&, int, int, K1Geom*, int*);
+template cudaError_t cg_build_graph<float>(CGPlan<float>*, cudaStream_t, bool);
+template cudaError_t cg_build_graph<double>(CGPlan<double>*, cudaStream_t, bool);
+
+// ---------------------------------------------------------------------------
+// Tensor-map encoding through the driver entry point (no libcuda link).
+// ---------------------------------------------------------------------------
+typedef CUresult (*PFN_encodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+cudaError_t encode_tiled(CUtensorMap* map, CUtensorMapDataType type, int rank, void* base, const uint64_t* dims,
+                         const uint64_t* strides_bytes, const uint32_t* box) {
+  static PFN_encodeTiled fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !p) return cudaErrorNotSupported;
+    fn = reinterpret_cast<PFN_encodeTiled>(p);
+  }
+  cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  CUresult r = fn(map, type, (cuuint32_t)rank, base, reinterpret_cast<const cuuint64_t*>(dims),
+                  reinterpret_cast<const cuuint64_t*>(strides_bytes), reinterpret_cast<const cuuint32_t*>(box), es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+}  // namespace paro

@@ -1,0 +1,100 @@
+// Device state, arguments and host plan of the batched CG (cg.cu).
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <functional>
+
+#include "common.cuh"
+
+namespace paro {
+
+// Per-orbital CG scalars and controls, in device memory (one per handle).
+struct CGDevState {
+  double rz[kMaxN];     // (r, D^-1 r) of the current residual
+  double pq[kMaxN];     // (p, A p)
+  double alpha[kMaxN];  // step of the current iteration (set by K1)
+  double beta[kMaxN];   // direction update for the next K1 (set by K2)
+  double bb[kMaxN];     // ||b||^2
+  double rr[kMaxN];     // ||r||^2
+  int active[kMaxN];
+  int iters[kMaxN];
+  int skip[kMaxN];      // orbitals excluded from this solve
+  int n_active;
+  int status;           // OR of kStat* bits
+  double tol;           // stop orbital i when ||r_i|| <= tol ||b_i||
+  int maxit;
+  unsigned int ticket;  // last-CTA detection; every last CTA resets it
+  unsigned long long work;  // sum over K1 launches of interior nodes x orbitals processed
+};
+
+template <typename T>
+struct CGArgs {
+  Grid g;
+  int N, Np;
+  T *x, *b, *r, *p, *q;  // padded-grid vectors [node][Np]
+  const T* dinv;         // inverse diagonal, padded grid (pitch Px)
+  double* part;          // per-CTA partial sums
+  CGDevState* st;
+  int in_graph;          // kernels set the graph's while condition only inside a graph
+};
+
+// Geometry of the tiled operator kernel K1.
+struct K1Geom {
+  int TX, TY, DX;     // tile (x, y) of a z-marching column, staged row pitch of D^-1
+  int ncx, ncy, nob;  // columns per axis, orbital blocks of width 4*G4
+  int grid, G4;       // CTAs (each takes an equal share of the column-planes), float4 groups per block
+  int off_p, off_d, off_w, slot_bytes;  // byte offsets inside one ring slot
+  uint32_t tx_bytes;                    // TMA bytes per slot
+  size_t smem;                          // dynamic shared memory per CTA
+};
+
+template <typename T>
+struct CGPlan {
+  CGArgs<T> args{};
+  K1Geom geo{};
+  int nsm = 152;
+  int dpitch = 0;  // row pitch of dinv_tma (elements)
+  int wpitch = 0;  // row pitch of wcoef (elements)
+  const T* dinv_tma = nullptr;
+  const T* wcoef = nullptr;
+  alignas(64) CUtensorMap mr;
+  alignas(64) CUtensorMap mp;
+  alignas(64) CUtensorMap md;
+  alignas(64) CUtensorMap mw;
+  int grid_stream = 0, nt_stream = 0;
+  size_t smem_init = 0, smem_upd = 0;
+  cudaGraphExec_t exec_zero = nullptr, exec_warm = nullptr;
+  int graph_N = -1;  // N the graphs were built for
+  // adds q = A x (the warm-start apply) as a graph node
+  std::function<cudaError_t(cudaGraph_t, cudaGraphNode_t*)> add_apply;
+};
+
+template <typename T>
+cudaError_t cg_plan_geometry(const Grid& g, int Np, int nsm, K1Geom* geo, int* bw_out);
+// Tensor maps, kernel attributes and launch shapes (after args, pitches and pointers are set).
+template <typename T>
+cudaError_t cg_prepare(CGPlan<T>* P);
+// Encodes the tensor maps, sets kernel attributes and instantiates the graph
+// (warm start: with the apply node; else x0 = 0).
+template <typename T>
+cudaError_t cg_build_graph(CGPlan<T>* P, cudaStream_t st, bool with_apply);
+// Host-driven form of the same loop (no graph): init, then K1/K2 pairs with
+// CUDA events around every K1 launch.  *iters_done: K1 launches issued.
+template <typename T>
+cudaError_t cg_launch_init(CGPlan<T>* P, cudaStream_t st, bool x_zero);
+template <typename T>
+cudaError_t cg_launch_k1(CGPlan<T>* P, cudaStream_t st);
+template <typename T>
+cudaError_t cg_launch_k2(CGPlan<T>* P, cudaStream_t st);
+
+// Build the tiled-kernel operator arrays from the 27-weight SoA coefficients.
+template <typename T>
+cudaError_t launch_build_tma_operator(const Grid& g, const T* coef, const T* dinv, T* wcoef, int wpitch, T* dinv_tma,
+                                      int dpitch, cudaStream_t st);
+template <typename T>
+cudaError_t graph_add_apply(cudaGraph_t gr, cudaGraphNode_t* node, const Grid& g, int Np, const T* coef, const T* x,
+                            T* y);
+
+}  // namespace paro

@@ -25,6 +25,7 @@ constexpr int kMaxRedBlocks = 1216;  // 152 SMs x 8: grid cap of the reducing ke
 constexpr int kStatNotSPD = 1;
 constexpr int kStatNonFinite = 2;
 constexpr int kStatNotConverged = 4;
+constexpr int kStatTimeout = 8;
 
 struct Grid {
   int nx, ny, nz;      // cells
@@ -121,28 +122,6 @@ struct CGState {
   unsigned long long* work;  // cg_q adds (interior nodes) x (orbitals it processed) per launch
 };
 
-template <typename T>
-struct CGVectors {
-  T* x;
-  T* b;
-  T* r;
-  T* p[2];
-  T* q;
-  const T* coef;
-  const T* dinv;
-};
-
-int red_blocks(const Grid& g, int Np);
-
-template <typename T>
-cudaError_t launch_cg_init(const Grid& g, int N, int Np, const CGVectors<T>& v, const CGState& s, bool x_zero,
-                           double tol, int maxit, cudaStream_t st);
-// One CG iteration = launch_cg_q (p update, q = A p, (p, q)) then launch_cg_update.
-template <typename T>
-cudaError_t launch_cg_q(const Grid& g, int Np, const CGVectors<T>& v, const CGState& s, int parity, cudaStream_t st);
-template <typename T>
-cudaError_t launch_cg_update(const Grid& g, int Np, const CGVectors<T>& v, const CGState& s, int parity, double tol,
-                             int maxit, cudaStream_t st);
 // Mixed refinement: r64 = b64 - A64 x64 -> rhs32 (float); convergence flags in s.skip.
 cudaError_t launch_refine_residual(const Grid& g, int N, int Np, const double* coef64, const double* x64,
                                    const double* b64, float* rhs32, const CGState& s, double tol, cudaStream_t st);

@@ -8,6 +8,7 @@
 // M_{V+sigma} is integrated cell by cell with the 2x2x2 Gauss rule at which V is
 // given; the rule is exact for sigma * mass, so sigma folds into V.
 // The weights of a node are the 27 entries of its row of A.
+#include "cg.cuh"
 #include "common.cuh"
 
 namespace paro {
@@ -151,7 +152,78 @@ __global__ void k_unpack_f32(Grid g, int N, int Np, const float* __restrict__ sr
 
 inline unsigned nblk(long long work, int threads) { return (unsigned)((work + threads - 1) / threads); }
 
+// Operator weights keyed by input plane, for the z-marching tiled kernel:
+//   W[s][o][yi][xi] = weight (dx, dy, dz) of the row of node (x, y, t), t = s - dz,
+// with o = (dz+1)*9 + (dy+1)*3 + (dx+1), x = xi + 1, y = yi + 1: the weight that
+// multiplies the value at (x+dx, y+dy, s) in output row (x, y, t).  Zero where
+// (x, y, t) is not an interior node.  Row pitch wpitch >= nx-1 (a multiple of 4).
+template <typename T>
+__global__ void k_build_w(Grid g, const T* __restrict__ coef, T* __restrict__ W, int wpitch) {
+  long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long plane = (long long)(g.ny - 1) * wpitch;
+  long long total = (long long)g.Pz * 27 * plane;
+  if (n >= total) return;
+  int xi = (int)(n % wpitch);
+  long long r = n / wpitch;
+  int yi = (int)(r % (g.ny - 1));
+  r /= (g.ny - 1);
+  int o = (int)(r % 27);
+  int s = (int)(r / 27);
+  int dz = o / 9 - 1;
+  int t = s - dz, x = xi + 1, y = yi + 1;
+  T w = 0;
+  if (x <= g.nx - 1 && t >= 1 && t <= g.nz - 1) w = coef[(long long)o * g.G + ((long long)t * g.Py + y) * g.Px + x];
+  W[n] = w;
+}
+
+// D^-1 on the padded grid with row pitch dpitch (a multiple of 4): zero outside the interior.
+template <typename T>
+__global__ void k_build_dinv_tma(Grid g, const T* __restrict__ dinv, T* __restrict__ D, int dpitch) {
+  long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long total = (long long)g.Pz * g.Py * dpitch;
+  if (n >= total) return;
+  int x = (int)(n % dpitch);
+  long long r = n / dpitch;
+  D[n] = (x < g.Px) ? dinv[r * g.Px + x] : (T)0;
+}
+
 }  // namespace
+
+template <typename T>
+cudaError_t launch_build_tma_operator(const Grid& g, const T* coef, const T* dinv, T* wcoef, int wpitch, T* dinv_tma,
+                                      int dpitch, cudaStream_t st) {
+  long long nw = (long long)g.Pz * 27 * (g.ny - 1) * wpitch;
+  k_build_w<T><<<nblk(nw, 256), 256, 0, st>>>(g, coef, wcoef, wpitch);
+  long long nd = (long long)g.Pz * g.Py * dpitch;
+  k_build_dinv_tma<T><<<nblk(nd, 256), 256, 0, st>>>(g, dinv, dinv_tma, dpitch);
+  return cudaGetLastError();
+}
+template cudaError_t launch_build_tma_operator<float>(const Grid&, const float*, const float*, float*, int, float*, int,
+                                                      cudaStream_t);
+template cudaError_t launch_build_tma_operator<double>(const Grid&, const double*, const double*, double*, int,
+                                                       double*, int, cudaStream_t);
+
+template <typename T>
+cudaError_t graph_add_apply(cudaGraph_t gr, cudaGraphNode_t* node, const Grid& g, int Np, const T* coef, const T* x,
+                            T* y) {
+  Weights27 w{};
+  double csub = 0.0;
+  const double* scale = nullptr;
+  Grid gg = g;
+  int np = Np;
+  void* args[] = {&gg, &np, (void*)&coef, &w, &csub, (void*)&x, (void*)&y, (void*)&scale};
+  cudaKernelNodeParams p{};
+  p.func = (void*)k_apply<T, 0>;
+  p.gridDim = dim3(apply_blocks(g, Np));
+  p.blockDim = dim3(kRedThreads);
+  p.sharedMemBytes = 0;
+  p.kernelParams = args;
+  return cudaGraphAddKernelNode(node, gr, nullptr, 0, &p);
+}
+template cudaError_t graph_add_apply<float>(cudaGraph_t, cudaGraphNode_t*, const Grid&, int, const float*,
+                                            const float*, float*);
+template cudaError_t graph_add_apply<double>(cudaGraph_t, cudaGraphNode_t*, const Grid&, int, const double*,
+                                             const double*, double*);
 
 void mass_weights(const Grid& g, Weights27* mw) {
   for (int dz = -1; dz <= 1; ++dz)

@@ -173,6 +173,32 @@ def test_orbital_solve_mixed_refinement_reaches_fp64_tolerance(B):
     m.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_orbital_solve_many_orbital_blocks_ragged_mesh(B, prec):
+    # N = 41 orbitals (padded to 44): the tiled CG kernel splits them into several
+    # orbital blocks, the last one ragged; a non-cubic mesh leaves ragged x, y and z tiles
+    n, lo, hi = (19, 11, 9), (-4.0, -3.0, -2.5), (4.5, 2.0, 2.0)
+    rng = np.random.default_rng(4100)
+    x, y, z = W.gauss_point_coords(n, lo, hi)
+    Vq = np.ascontiguousarray((0.5 * (x ** 2 + y ** 2 + z ** 2)).ravel())
+    ops = O.assemble(O.Mesh(n, lo, hi), Vq, 0.5)
+    nI = (n[0] - 1) * (n[1] - 1) * (n[2] - 1)
+    U0 = rng.standard_normal((nI, 41))
+    rr = O.rayleigh_ritz(ops, U0)
+    ref = O.source_problems(ops, rr.U, rr.lam, 1e-12, 5000)
+    m = B.Mesh(n, lo, hi, B.PARO_FP64 if prec == "fp64" else B.PARO_MIXED)
+    Vd = dev(Vq)
+    m.set_potential(Vd, 0.5)
+    U = dev(rr.U)
+    X = torch.empty_like(U)
+    params = B.paro_default_params(solve_tol=1e-11, pcg_maxit=5000, inner_tol=1e-4)
+    rc, st = m.orbital_solve(rr.lam, U, X, params)
+    assert rc == 0, B.paro_last_error(m.h)
+    assert st.max_relres <= 1e-11
+    assert np.max(np.abs(host(X) - ref.X)) < 1e-8 * np.max(np.abs(ref.X))
+    m.close()
+
+
 @pytest.mark.parametrize("N", [1, 6, 11])
 def test_rayleigh_ritz_matches_oracle(B, N):
     p = W.harmonic(nc=10, L=5.0, N=N, seed=3100 + N)
