@@ -225,6 +225,51 @@ def test_harmonic_oscillator_levels_and_rate():
     assert 3.5 < ratio < 4.6, ratio
 
 
+def _separable_oscillator_spectrum(nc, L, k):
+    """Lowest k eigenvalues of the discrete Q1 harmonic oscillator from 1-D problems.
+
+    With V = (x^2 + y^2 + z^2)/2 sampled at the tensor 2-point Gauss points, the
+    potential mass matrix splits into (m2/2) x m x m + ... , where m2 is the 1-D
+    matrix of the Gauss sums of x^2 phi_i phi_j.  So H = K/2 + M_V = a x m x m +
+    m x a x m + m x m x a with a = k/2 + m2/2, and the generalized eigenvalues
+    of (H, m x m x m) are all sums mu_a + mu_b + mu_c of the 1-D ones of (a, m).
+    """
+    h = 2.0 * L / nc
+    t = np.array([(1 - 1 / math.sqrt(3)) / 2, (1 + 1 / math.sqrt(3)) / 2])
+    m2 = np.zeros((nc + 1, nc + 1))
+    for e in range(nc):
+        xq = -L + h * (e + t)
+        lq = np.stack([1 - t, t])  # basis values at the Gauss points
+        for a in range(2):
+            for b in range(2):
+                m2[e + a, e + b] += np.sum(0.5 * h * xq ** 2 * lq[a] * lq[b])
+    a1 = 0.5 * _k1(nc, h).toarray() + 0.5 * m2[1:nc, 1:nc]
+    mu = sla.eigh(a1, _m1(nc, h).toarray(), eigvals_only=True)
+    mu = np.sort(mu)[: k + 2]
+    sums = np.sort((mu[:, None, None] + mu[None, :, None] + mu[None, None, :]).ravel())
+    return sums[:k]
+
+
+def test_harmonic_oscillator_separable_spectrum_dense():
+    # the oracle's assembled 3-D operator against the 1-D separable construction
+    p = W.harmonic(nc=8, L=4.0, N=1, seed=1)
+    ops = O.assemble(O.Mesh(p.n, p.lo, p.hi), p.Vq, 0.0)
+    dense = sla.eigh(ops.H.toarray(), ops.M.toarray(), eigvals_only=True)
+    sep = _separable_oscillator_spectrum(8, 4.0, 30)
+    assert np.max(np.abs(dense[:30] - sep) / np.abs(sep)) < 1e-11
+
+
+@pytest.mark.parametrize("key,nc", [("harmonic_32_L8", 32), ("harmonic_64_L8", 64)])
+def test_stored_oscillator_spectra_match_separable_form(key, nc):
+    import json
+    import os
+
+    with open(os.path.join(os.path.dirname(__file__), "golden", "discrete_spectra.json")) as f:
+        gold = np.array(json.load(f)[key]["values"])
+    sep = _separable_oscillator_spectrum(nc, 8.0, len(gold))
+    assert np.max(np.abs(gold - sep)) < 1e-9
+
+
 def test_hydrogen_ground_state_trend():
     # -Z^2/(2 n^2): the lowest level approaches -1/2 as the mesh is refined
     vals = []
