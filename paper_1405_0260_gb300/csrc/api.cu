@@ -54,7 +54,7 @@ struct paro_mesh_s {
   int nsm = 152;
   CGDevState* cgst = nullptr;
   double* cgpart = nullptr;
-  int wpitch = 0, dpitch = 0;
+  int dpitch = 0;
   float *w32 = nullptr, *dt32 = nullptr;
   double *w64 = nullptr, *dt64 = nullptr;
   CGPlan<float>* plan32 = nullptr;
@@ -177,7 +177,6 @@ int make_plan(paro_mesh m, int Np, CGPlan<T>** out, T* x, T* b, T* r, T* p, T* q
   P->args.st = m->cgst;
   P->args.in_graph = 0;
   P->dpitch = m->dpitch;
-  P->wpitch = m->wpitch;
   P->dinv_tma = dinv_tma;
   P->wcoef = wcoef;
   int bw = 0;
@@ -573,7 +572,6 @@ int paro_mesh_create(paro_mesh* out, int nx, int ny, int nz, const double lo[3],
   g.hy = (hi[1] - lo[1]) / ny;
   g.hz = (hi[2] - lo[2]) / nz;
   mass_weights(g, &m->mw);
-  m->wpitch = (nx - 1 + 3) / 4 * 4;
   m->dpitch = (g.Px + 3) / 4 * 4;
   {
     int dev = 0, nsm = 0;
@@ -588,8 +586,8 @@ int paro_mesh_create(paro_mesh* out, int nx, int ny, int nz, const double lo[3],
       (rc = dalloc(m, &m->dscal, (size_t)S_COUNT * kMaxN)) ||
       (rc = dalloc(m, &m->dint, (size_t)I_COUNT * kMaxN + 8)) ||
       (rc = dalloc(m, &m->partial, (size_t)3 * kMaxRedBlocks * kMaxN)) || (rc = dalloc(m, &m->ticket, 4)) ||
-      (rc = dalloc(m, &m->cgst, 1)) || (rc = dalloc(m, &m->w32, (size_t)27 * g.Pz * (ny - 1) * m->wpitch)) ||
-      (rc = dalloc(m, &m->w64, (size_t)27 * g.Pz * (ny - 1) * m->wpitch)) ||
+      (rc = dalloc(m, &m->cgst, 1)) || (rc = dalloc(m, &m->w32, packed_weights_count(g))) ||
+      (rc = dalloc(m, &m->w64, packed_weights_count(g))) ||
       (rc = dalloc(m, &m->dt32, (size_t)g.Pz * g.Py * m->dpitch)) ||
       (rc = dalloc(m, &m->dt64, (size_t)g.Pz * g.Py * m->dpitch))) {
     g_create_err = m->err;
@@ -635,9 +633,9 @@ int paro_set_potential(paro_mesh m, const double* Vq, double sigma) {
   if (!Vq) return fail(m, PARO_ERR_ARG, "Vq is null");
   if (!std::isfinite(sigma)) return fail(m, PARO_ERR_ARG, "sigma must be finite");
   LAUNCH(1, launch_build_coef(m->g, Vq, sigma, m->coef64, m->coef32, m->dinv64, m->dinv32, m->st));
-  LAUNCH(2, launch_build_tma_operator<double>(m->g, m->coef64, m->dinv64, m->w64, m->wpitch, m->dt64, m->dpitch,
+  LAUNCH(2, launch_build_tma_operator<double>(m->g, m->coef64, m->dinv64, m->w64, m->dt64, m->dpitch,
                                                m->st));
-  LAUNCH(2, launch_build_tma_operator<float>(m->g, m->coef32, m->dinv32, m->w32, m->wpitch, m->dt32, m->dpitch,
+  LAUNCH(2, launch_build_tma_operator<float>(m->g, m->coef32, m->dinv32, m->w32, m->dt32, m->dpitch,
                                               m->st));
   m->sigma = sigma;
   m->have_pot = true;

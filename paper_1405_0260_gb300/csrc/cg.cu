@@ -32,8 +32,13 @@ namespace paro {
 
 namespace {
 
-constexpr int kNT = 64;  // node slots per pass in K1 (threads = kNT * G4)
+// K1 threads: geo.nthr node slots x G4 orbital groups; nthr = TX * TY / NPT.
+// Upper bound of the slots for the register budget of each instance:
+template <typename T, int NPT>
+constexpr int k1_max_slots() { return (sizeof(T) == 4 ? 128 : 64) / NPT; }
 constexpr int kSlots = 4;
+constexpr int kUpdThreads = 640;  // update kernel block (<= 102 registers a thread)
+constexpr int kWS = 28;  // packed operator weights per node (27 + one pad)
 
 template <typename T>
 struct Vec4 {
@@ -107,6 +112,35 @@ __device__ void reduce_over_ctas(const double* part, int G, int Np, double* sm, 
   __syncthreads();
 }
 
+// Fixed-order column sums of a [rows][cols] block of doubles in shared memory by
+// every thread of the CTA: thread t sums rows sl, sl+S, ... of column c (t = sl*cols + c),
+// then one thread per column adds the S slices in order.  tmp holds S*cols <= blockDim.x
+// values.  Returns with the sums in tmp[0 .. cols) (after a barrier).
+__device__ void block_colsum(const double* in, int rows, int cols, double* tmp) {
+  const int nt = blockDim.x;
+  int S = nt / cols;
+  if (S < 1) S = 1;
+  if (S > rows) S = rows;
+  for (int t = threadIdx.x; t < S * cols; t += nt) {
+    const int c = t % cols, sl = t / cols;
+    double a0 = 0, a1 = 0;
+    int r = sl;
+    for (; r + S < rows; r += 2 * S) {
+      a0 += in[r * cols + c];
+      a1 += in[(r + S) * cols + c];
+    }
+    if (r < rows) a0 += in[r * cols + c];
+    tmp[t] = a0 + a1;
+  }
+  __syncthreads();
+  double v = 0.0;
+  if (threadIdx.x < cols)
+    for (int sl = 0; sl < S; ++sl) v += tmp[sl * cols + threadIdx.x];
+  __syncthreads();
+  if (threadIdx.x < cols) tmp[threadIdx.x] = v;
+  __syncthreads();
+}
+
 // Writes this CTA's partials, takes a ticket; true in the last CTA.
 __device__ bool last_cta(unsigned int* ticket) {
   __shared__ bool am_last;
@@ -130,7 +164,7 @@ __global__ void __launch_bounds__(256) k_cg_init(CGArgs<T> a, int x_zero, cudaGr
   const int G4 = a.Np / 4;
   const int nt = blockDim.x;  // multiple of G4
   const int g = threadIdx.x % G4;
-  double acc[3][4] = {};
+  T acc[3][4] = {};
   const long long rowlen = (long long)(a.g.nx - 1) * G4;  // float4 groups per interior row
   const long long nrows = (long long)(a.g.ny - 1) * (a.g.nz - 1);
   const long long total = rowlen * nrows;
@@ -152,28 +186,27 @@ __global__ void __launch_bounds__(256) k_cg_init(CGArgs<T> a, int x_zero, cudaGr
     sts4(a.p + e, Vec4<T>{});
     T di = a.dinv[node];
     for (int c = 0; c < 4; ++c) {
-      acc[0][c] += (double)(r.v[c] * (di * r.v[c]));
-      acc[1][c] += (double)r.v[c] * (double)r.v[c];
-      acc[2][c] += (double)b.v[c] * (double)b.v[c];
+      acc[0][c] = fmaT(r.v[c], di * r.v[c], acc[0][c]);
+      acc[1][c] = fmaT(r.v[c], r.v[c], acc[1][c]);
+      acc[2][c] = fmaT(b.v[c], b.v[c], acc[2][c]);
     }
   }
-  // block reduce over threads of equal group
-  double* red = dsm;  // [nt/G4][Np] per k
+  // block reduce over threads of equal group: red[j][k*Np + o], then column sums
+  double* red = dsm;
   const int NTs = nt / G4;
   const int j = threadIdx.x / G4;
-  for (int k = 0; k < 3; ++k) {
-    for (int c = 0; c < 4; ++c) red[(k * NTs + j) * a.Np + 4 * g + c] = acc[k][c];
-  }
+  for (int k = 0; k < 3; ++k)
+    for (int c = 0; c < 4; ++c) red[j * 3 * a.Np + k * a.Np + 4 * g + c] = (double)acc[k][c];
   __syncthreads();
+  double* ctmp = red + (size_t)NTs * 3 * a.Np;
+  block_colsum(red, NTs, 3 * a.Np, ctmp);
   for (int t = threadIdx.x; t < 3 * a.Np; t += nt) {
-    int k = t / a.Np, o = t % a.Np;
-    double s = 0.0;
-    for (int jj = 0; jj < NTs; ++jj) s += red[(k * NTs + jj) * a.Np + o];
-    a.part[((long long)k * gridDim.x + blockIdx.x) * a.Np + o] = s;
+    const int k = t / a.Np, o = t % a.Np;
+    a.part[((long long)k * gridDim.x + blockIdx.x) * a.Np + o] = ctmp[t];
   }
   if (!last_cta(&a.st->ticket)) return;
-  // slices of the cross-CTA sum use dsm[0 .. 32*3*Np); totals follow
-  double* tot = dsm + 3 * a.Np * 33;
+  // slices of the cross-CTA sum (at most max(threads, 3 Np) values), then the totals
+  double* tot = dsm + (nt > 3 * a.Np ? nt : 3 * a.Np);
   reduce_over_ctas<3>(a.part, gridDim.x, a.Np, dsm, tot);
   __shared__ int cnt;
   if (threadIdx.x == 0) cnt = 0;
@@ -211,18 +244,22 @@ __global__ void __launch_bounds__(256) k_cg_init(CGArgs<T> a, int x_zero, cudaGr
 // ---------------------------------------------------------------------------
 // K1: tiled stencil.  q = A p_new, p_new = D^-1 r + beta p_old, partial (p, q)
 // ---------------------------------------------------------------------------
-template <typename T, int G4>
-__global__ void __launch_bounds__(kNT* G4) k_cg_q(CGArgs<T> a, K1Geom geo, const __grid_constant__ CUtensorMap mr,
+// Thread layout: thread (j, g) owns orbitals o0+4g .. o0+4g+3 of NPT vertically
+// adjacent tile nodes (tx, ty0 .. ty0+NPT-1), tx = j % TX, ty0 = NPT (j / TX);
+// TX * TY = nthr * NPT.  Per input plane it reads the (NPT+2) x 3 neighbourhood
+// column by column from shared memory and the 27 packed weights of each of its
+// nodes (kWS per node, 16-byte vector loads).
+template <typename T, int G4, int NPT>
+__global__ void __launch_bounds__(k1_max_slots<T, NPT>() * G4) k_cg_q(CGArgs<T> a, K1Geom geo, const __grid_constant__ CUtensorMap mr,
                                                   const __grid_constant__ CUtensorMap mp,
                                                   const __grid_constant__ CUtensorMap md,
                                                   const __grid_constant__ CUtensorMap mw) {
   constexpr int bw = 4 * G4;
   extern __shared__ __align__(128) unsigned char smem[];
-  const int TX = geo.TX, TY = geo.TY;
-  const int HX = TX + 2, HY = TY + 2;
+  const int TX = geo.TX;
+  const int HX = TX + 2, HY = geo.TY + 2;
   const int tid = threadIdx.x;
   const int g = tid % G4, j = tid / G4;
-  (void)HY;
   // shared layout: barriers, kSlots ring slots (r, p, D^-1, W), then reduction space
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
   unsigned char* base = smem + 128;
@@ -231,8 +268,8 @@ __global__ void __launch_bounds__(kNT* G4) k_cg_q(CGArgs<T> a, K1Geom geo, const
   auto slotD = [&](int s) { return reinterpret_cast<T*>(base + (size_t)s * geo.slot_bytes + geo.off_d); };
   auto slotW = [&](int s) { return reinterpret_cast<T*>(base + (size_t)s * geo.slot_bytes + geo.off_w); };
   double* sacc = reinterpret_cast<double*>(base + (size_t)kSlots * geo.slot_bytes);  // [Np]
-  double* sred = sacc + a.Np;                                                       // [kNT][bw]
-  __shared__ int abort_flag;
+  double* sred = sacc + a.Np;                                                       // [nthr][bw]
+  const int nthr = geo.nthr;
   __shared__ T sbeta[kMaxN];
   __shared__ int sact[kMaxN / 4];
   __shared__ int sblk[kMaxN / 4];
@@ -244,7 +281,6 @@ __global__ void __launch_bounds__(kNT* G4) k_cg_q(CGArgs<T> a, K1Geom geo, const
   const long long fbeg = F * blockIdx.x / gridDim.x;
   const long long fend = F * (blockIdx.x + 1) / gridDim.x;
   if (tid == 0) {
-    abort_flag = 0;
     for (int s = 0; s < kSlots; ++s) mbar_init(&bars[s], 1);
     fence_mbar_init();
     prefetch_tmap(&mr);
@@ -278,7 +314,7 @@ __global__ void __launch_bounds__(kNT* G4) k_cg_q(CGArgs<T> a, K1Geom geo, const
     const int ob = (int)(r / geo.ncy);
     o0 = ob * bw;
     x0 = 1 + tx * TX;
-    y0 = 1 + ty * TY;
+    y0 = 1 + ty * geo.TY;
     z0 = 1 + zl;
     z1 = 1 + zh;
   };
@@ -308,7 +344,7 @@ __global__ void __launch_bounds__(kNT* G4) k_cg_q(CGArgs<T> a, K1Geom geo, const
         tma_load_4d(slotR(slot), &mr, lo0, lx0 - 1, ly0 - 1, zin, &bars[slot]);
         tma_load_4d(slotP(slot), &mp, lo0, lx0 - 1, ly0 - 1, zin, &bars[slot]);
         tma_load_3d(slotD(slot), &md, lx0 - 1, ly0 - 1, zin, &bars[slot]);
-        tma_load_4d(slotW(slot), &mw, lx0 - 1, ly0 - 1, 0, zin, &bars[slot]);
+        tma_load_4d(slotW(slot), &mw, 0, lx0 - 1, ly0 - 1, zin, &bars[slot]);
         ++lstep;
         ++ls;
         return;
@@ -320,121 +356,165 @@ __global__ void __launch_bounds__(kNT* G4) k_cg_q(CGArgs<T> a, K1Geom geo, const
   if (tid == 0)
     for (int k = 0; k < kSlots; ++k) issue_next();
 
-  int cstep = 0;                    // consumer steps done
-  const int npt = (TX * TY) / kNT;  // nodes per thread per plane (1 or 2)
+  // this thread's nodes and its fixed shared-memory offsets (elements)
+  const int tx = j % TX, ty0 = NPT * (j / TX);
+  const int poff = (ty0 * HX + tx) * bw + 4 * g;  // halo node (tx-1, ty0-1) relative to the tile
+  const int woff = (ty0 * TX + tx) * kWS;         // packed weights of node (tx, ty0)
+  const int hstep = HX * bw;                      // one halo row
+  // halo nodes this thread updates p on (the same every plane): element offset of
+  // its group in the staged vectors and the offset of the node in the D^-1 tile
+  constexpr int kPnMax = 3;
+  int pn_h[kPnMax], pn_d[kPnMax], pn_cnt = 0;
+#pragma unroll
+  for (int i = 0; i < kPnMax; ++i) {
+    const int h = j + i * nthr;
+    pn_h[i] = 0;
+    pn_d[i] = 0;
+    if (h < HX * HY) {
+      const int hy = h / HX, hx = h - hy * HX;
+      pn_h[i] = h * bw + 4 * g;
+      pn_d[i] = hy * geo.DX + hx;
+      pn_cnt = i + 1;
+    }
+  }
+  const long long plane = (long long)a.g.Px * a.g.Py;
+
+  int cstep = 0;    // consumer steps done
+  int cur_o0 = -1;  // orbital block the dot partials below belong to
+  T dot[4] = {0, 0, 0, 0};
+  bool timed_out = false;
+  auto flush_dots = [&](int o0) {
+    // per-thread partial sums are in the kernel's precision (float64 arithmetic is
+    // ~1/56 of float32 on this GPU); the block and cross-CTA sums are float64
+#pragma unroll
+    for (int c = 0; c < 4; ++c) sred[j * bw + 4 * g + c] = (double)dot[c];
+    __syncthreads();
+    double* ctmp = sred + nthr * bw;
+    block_colsum(sred, nthr, bw, ctmp);
+    for (int o = tid; o < bw && o0 + o < a.Np; o += blockDim.x) sacc[o0 + o] += ctmp[o];
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < 4; ++c) dot[c] = 0;
+  };
+
   for (long long f = fbeg; f < fend;) {
     int o0, x0, y0, z0, z1;
     seg_at(f, o0, x0, y0, z0, z1);
     f += z1 - z0;
     if (!sblk[o0 / bw]) continue;
+    if (o0 != cur_o0) {
+      if (cur_o0 >= 0) flush_dots(cur_o0);
+      cur_o0 = o0;
+    }
     // a ragged last block: groups at orbitals >= Np are staged as zeros and never stored
     const bool gact = (o0 + 4 * g < a.Np) && sact[o0 / 4 + g] != 0;
-    const T be0 = gact ? sbeta[o0 + 4 * g] : T(0), be1 = gact ? sbeta[o0 + 4 * g + 1] : T(0),
-            be2 = gact ? sbeta[o0 + 4 * g + 2] : T(0), be3 = gact ? sbeta[o0 + 4 * g + 3] : T(0);
+    T be[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) be[c] = gact ? sbeta[o0 + 4 * g + c] : T(0);
+    // output node columns of this thread (-1: outside the interior)
+    long long col[NPT];
+#pragma unroll
+    for (int k = 0; k < NPT; ++k) {
+      const int x = x0 + tx, y = y0 + ty0 + k;
+      col[k] = (x <= a.g.nx - 1 && y <= a.g.ny - 1) ? (long long)y * a.g.Px + x : -1;
+    }
     // Rolling accumulators of the three output planes an input plane touches:
     // aD = output s-1 (completed at step s), aC = output s, aU = output s+1.
-    Vec4<T> aD[2], aC[2], aU[2], pcPrev[2], pcCur[2];
+    Vec4<T> aD[NPT], aC[NPT], aU[NPT], pcPrev[NPT], pcCur[NPT];
 #pragma unroll
-    for (int k = 0; k < 2; ++k) aD[k] = aC[k] = aU[k] = pcPrev[k] = pcCur[k] = Vec4<T>{};
-    double dot0 = 0, dot1 = 0, dot2 = 0, dot3 = 0;
+    for (int k = 0; k < NPT; ++k) aD[k] = aC[k] = aU[k] = pcPrev[k] = pcCur[k] = Vec4<T>{};
     for (int s = z0 - 1; s <= z1; ++s) {
       const int slot = cstep % kSlots;
       const uint32_t par = (cstep / kSlots) & 1;
-      if (!mbar_wait(&bars[slot], par)) abort_flag = 1;
-      __syncthreads();
-      if (abort_flag) goto bail;
+      const bool ok = mbar_wait(&bars[slot], par);
       if (gact) {
         // p_new = D^-1 r + beta p_old on tile + halo, in place
         const T* D = slotD(slot);
         T* P = slotP(slot);
         const T* R = slotR(slot);
-        for (int h = j; h < HX * HY; h += kNT) {
-          const int hy = h / HX, hx = h - hy * HX;
-          const T di = D[hy * geo.DX + hx];
-          Vec4<T> rv = lds4(R + h * bw + 4 * g);
-          Vec4<T> pv = lds4(P + h * bw + 4 * g);
-          pv.v[0] = pnew<T>(di, rv.v[0], be0, pv.v[0]);
-          pv.v[1] = pnew<T>(di, rv.v[1], be1, pv.v[1]);
-          pv.v[2] = pnew<T>(di, rv.v[2], be2, pv.v[2]);
-          pv.v[3] = pnew<T>(di, rv.v[3], be3, pv.v[3]);
-          sts4(P + h * bw + 4 * g, pv);
+#pragma unroll
+        for (int i = 0; i < kPnMax; ++i) {
+          if (i < pn_cnt) {
+            const T di = D[pn_d[i]];
+            const Vec4<T> rv = lds4(R + pn_h[i]);
+            Vec4<T> pv = lds4(P + pn_h[i]);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) pv.v[c] = pnew<T>(di, rv.v[c], be[c], pv.v[c]);
+            sts4(P + pn_h[i], pv);
+          }
         }
         // these generic-proxy writes precede the TMA write that later refills the slot
         fence_proxy_async_smem();
       }
-      __syncthreads();
+      if (__syncthreads_or(!ok)) {
+        timed_out = true;
+        goto bail;
+      }
+      // every thread is past step cstep-1: refill its slot
+      if (tid == 0 && cstep > 0) issue_next();
       if (gact) {
-        const T* P = slotP(slot);
-        const T* W = slotW(slot);
-        const int TXY = TX * TY;
+        const T* P = slotP(slot) + poff;
+        const T* Wn = slotW(slot) + woff;
+        Vec4<T> w[NPT][7];
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          if (k < npt) {
-            const int n = j + k * kNT;
-            const int ty = n / TX, tx = n - ty * TX;
+        for (int k = 0; k < NPT; ++k)
 #pragma unroll
-            for (int dy = -1; dy <= 1; ++dy) {
+          for (int q = 0; q < 7; ++q) w[k][q] = lds4(Wn + k * TX * kWS + 4 * q);
 #pragma unroll
-              for (int dx = -1; dx <= 1; ++dx) {
-                const int h = (ty + 1 + dy) * HX + (tx + 1 + dx);
-                const Vec4<T> v = lds4(P + h * bw + 4 * g);
-                const int o = (dy + 1) * 3 + (dx + 1);
-                const T wu = W[o * TXY + n];         // dz = -1 of output s+1
-                const T wc = W[(9 + o) * TXY + n];   // dz =  0 of output s
-                const T wd = W[(18 + o) * TXY + n];  // dz = +1 of output s-1
+        for (int cx = 0; cx < 3; ++cx) {
+          Vec4<T> v[NPT + 2];
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                  aU[k].v[c] = fmaT(wu, v.v[c], aU[k].v[c]);
-                  aC[k].v[c] = fmaT(wc, v.v[c], aC[k].v[c]);
-                  aD[k].v[c] = fmaT(wd, v.v[c], aD[k].v[c]);
-                }
-                if (dy == 0 && dx == 0) pcCur[k] = v;
+          for (int r = 0; r < NPT + 2; ++r) v[r] = lds4(P + r * hstep + cx * bw);
+#pragma unroll
+          for (int k = 0; k < NPT; ++k) {
+#pragma unroll
+            for (int cy = 0; cy < 3; ++cy) {
+              const int o = cy * 3 + cx;
+              const T wu = w[k][o / 4].v[o % 4];                // dz = -1 of output s+1
+              const T wc = w[k][(9 + o) / 4].v[(9 + o) % 4];    // dz =  0 of output s
+              const T wd = w[k][(18 + o) / 4].v[(18 + o) % 4];  // dz = +1 of output s-1
+              const Vec4<T>& pv = v[k + cy];
+#pragma unroll
+              for (int c = 0; c < 4; ++c) {
+                aU[k].v[c] = fmaT(wu, pv.v[c], aU[k].v[c]);
+                aC[k].v[c] = fmaT(wc, pv.v[c], aC[k].v[c]);
+                aD[k].v[c] = fmaT(wd, pv.v[c], aD[k].v[c]);
               }
+              if (cy == 1 && cx == 1) pcCur[k] = pv;
             }
-            // output s-1 is complete
-            const int tz = s - 1;
-            if (tz >= z0 && tz < z1) {
-              const int x = x0 + tx, y = y0 + ty;
-              if (x <= a.g.nx - 1 && y <= a.g.ny - 1) {
-                const long long node = ((long long)tz * a.g.Py + y) * a.g.Px + x;
-                dot0 += (double)(pcPrev[k].v[0] * aD[k].v[0]);
-                dot1 += (double)(pcPrev[k].v[1] * aD[k].v[1]);
-                dot2 += (double)(pcPrev[k].v[2] * aD[k].v[2]);
-                dot3 += (double)(pcPrev[k].v[3] * aD[k].v[3]);
-                sts4(a.q + node * a.Np + o0 + 4 * g, aD[k]);
-              }
-            }
-            aD[k] = aC[k];
-            aC[k] = aU[k];
-            aU[k] = Vec4<T>{};
-            pcPrev[k] = pcCur[k];
           }
         }
+        // output s-1 is complete
+        const int tz = s - 1;
+        if (tz >= z0 && tz < z1) {
+#pragma unroll
+          for (int k = 0; k < NPT; ++k) {
+            if (col[k] >= 0) {
+#pragma unroll
+              for (int c = 0; c < 4; ++c) dot[c] = fmaT(pcPrev[k].v[c], aD[k].v[c], dot[c]);
+              sts4(a.q + ((long long)tz * plane + col[k]) * a.Np + o0 + 4 * g, aD[k]);
+            }
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) {
+          aD[k] = aC[k];
+          aC[k] = aU[k];
+          aU[k] = Vec4<T>{};
+          pcPrev[k] = pcCur[k];
+        }
       }
-      __syncthreads();
       ++cstep;
-      if (tid == 0) issue_next();
     }
-    // per-segment block reduction of (p, q) into sacc[o0 .. o0+bw)
-    sred[j * bw + 4 * g + 0] = dot0;
-    sred[j * bw + 4 * g + 1] = dot1;
-    sred[j * bw + 4 * g + 2] = dot2;
-    sred[j * bw + 4 * g + 3] = dot3;
-    __syncthreads();
-    for (int o = tid; o < bw && o0 + o < a.Np; o += blockDim.x) {
-      double sum = 0.0;
-      for (int jj = 0; jj < kNT; ++jj) sum += sred[jj * bw + o];
-      sacc[o0 + o] += sum;
-    }
-    __syncthreads();
   }
+  if (cur_o0 >= 0) flush_dots(cur_o0);
 bail:
-  __syncthreads();
-  if (abort_flag) {
-    if (tid == 0) atomicOr(&a.st->status, kStatTimeout);
-    // wait (bounded) for copies still in flight before the CTA's shared memory goes away
-    if (tid == 0)
+  if (timed_out) {
+    if (tid == 0) {
+      atomicOr(&a.st->status, kStatTimeout);
+      // wait (bounded) for copies still in flight before the CTA's shared memory goes away
       for (int k = cstep; k < lstep; ++k) mbar_wait(&bars[k % kSlots], (k / kSlots) & 1);
+    }
     __syncthreads();
   }
   for (int o = tid; o < a.Np; o += blockDim.x) a.part[(long long)blockIdx.x * a.Np + o] = sacc[o];
@@ -474,7 +554,8 @@ bail:
 // the last CTA updates masks, counts, beta and the graph's while condition.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_cg_upd(CGArgs<T> a, cudaGraphConditionalHandle cond) {
+// Persistent: one CTA of up to kUpdThreads threads per SM, so the last CTA sums few partials.
+__global__ void __launch_bounds__(kUpdThreads, 1) k_cg_upd(CGArgs<T> a, cudaGraphConditionalHandle cond) {
   extern __shared__ double dsm[];
   __shared__ T sal[kMaxN], sbe[kMaxN];
   const int G4 = a.Np / 4;
@@ -487,47 +568,81 @@ __global__ void __launch_bounds__(256) k_cg_upd(CGArgs<T> a, cudaGraphConditiona
   __syncthreads();
   const bool gact = (a.st->active[4 * g] | a.st->active[4 * g + 1] | a.st->active[4 * g + 2] |
                      a.st->active[4 * g + 3]) != 0;
-  double acc[2][4] = {};
+  T acc[2][4] = {};
   if (gact) {
     const T al[4] = {sal[4 * g], sal[4 * g + 1], sal[4 * g + 2], sal[4 * g + 3]};
     const T be[4] = {sbe[4 * g], sbe[4 * g + 1], sbe[4 * g + 2], sbe[4 * g + 3]};
-    const long long rowlen = (long long)(a.g.nx - 1) * G4;
-    const long long nrows = (long long)(a.g.ny - 1) * (a.g.nz - 1);
-    const long long total = rowlen * nrows;
-    for (long long i = (long long)blockIdx.x * nt + threadIdx.x; i < total; i += (long long)gridDim.x * nt) {
-      long long row = i / rowlen;
-      long long off = i - row * rowlen;
-      int y = (int)(row % (a.g.ny - 1)) + 1, z = (int)(row / (a.g.ny - 1)) + 1;
-      long long node = ((long long)z * a.g.Py + y) * a.g.Px + 1 + off / G4;
-      long long e = node * a.Np + 4 * g;
-      Vec4<T> x = lds4(a.x + e), r = lds4(a.r + e), p = lds4(a.p + e), q = lds4(a.q + e);
-      T di = a.dinv[node];
-      for (int c = 0; c < 4; ++c) {
-        p.v[c] = pnew<T>(di, r.v[c], be[c], p.v[c]);
-        x.v[c] = fmaT(al[c], p.v[c], x.v[c]);
-        r.v[c] = fmaT(-al[c], q.v[c], r.v[c]);
-        acc[0][c] += (double)(r.v[c] * (di * r.v[c]));
-        acc[1][c] += (double)r.v[c] * (double)r.v[c];
+    // Nodes of planes z = 1 .. nz-1 of the padded grid, walked with a fixed stride,
+    // kU nodes per pass (all their loads issued before any use); the node
+    // coordinates advance incrementally and boundary nodes are skipped.
+    constexpr int kU = sizeof(T) == 4 ? 2 : 1;  // nodes in flight per thread
+    const int Px = a.g.Px, Py = a.g.Py;
+    const long long plane = (long long)Px * Py;
+    const long long nend = plane * a.g.nz;
+    const long long stride = (long long)gridDim.x * (nt / G4);
+    const int sx = (int)(stride % Px), sy = (int)((stride / Px) % Py);
+    long long node = plane + (long long)blockIdx.x * (nt / G4) + threadIdx.x / G4;
+    int x = (int)(node % Px), y = (int)((node / Px) % Py);
+    auto advance = [&](int& xx, int& yy) {
+      xx += sx;
+      int cy = 0;
+      if (xx >= Px) {
+        xx -= Px;
+        cy = 1;
       }
-      sts4(a.x + e, x);
-      sts4(a.r + e, r);
-      sts4(a.p + e, p);
+      yy += sy + cy;
+      if (yy >= Py) yy -= Py;
+    };
+    for (; node < nend; node += kU * stride) {
+      long long e[kU];
+      bool ok[kU];
+      Vec4<T> xv[kU], r[kU], p[kU], q[kU];
+      T di[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const long long nd = node + u * stride;
+        ok[u] = nd < nend && x > 0 && x < Px - 1 && y > 0 && y < Py - 1;
+        e[u] = nd * a.Np + 4 * g;
+        if (ok[u]) {
+          xv[u] = lds4(a.x + e[u]);
+          r[u] = lds4(a.r + e[u]);
+          p[u] = lds4(a.p + e[u]);
+          q[u] = lds4(a.q + e[u]);
+          di[u] = a.dinv[nd];
+        }
+        advance(x, y);
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        if (!ok[u]) continue;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          p[u].v[c] = pnew<T>(di[u], r[u].v[c], be[c], p[u].v[c]);
+          xv[u].v[c] = fmaT(al[c], p[u].v[c], xv[u].v[c]);
+          r[u].v[c] = fmaT(-al[c], q[u].v[c], r[u].v[c]);
+          acc[0][c] = fmaT(r[u].v[c], di[u] * r[u].v[c], acc[0][c]);
+          acc[1][c] = fmaT(r[u].v[c], r[u].v[c], acc[1][c]);
+        }
+        sts4(a.x + e[u], xv[u]);
+        sts4(a.r + e[u], r[u]);
+        sts4(a.p + e[u], p[u]);
+      }
     }
   }
-  double* red = dsm;
+  double* red = dsm;  // red[j][k*Np + o]
   const int NTs = nt / G4;
   const int j = threadIdx.x / G4;
   for (int k = 0; k < 2; ++k)
-    for (int c = 0; c < 4; ++c) red[(k * NTs + j) * a.Np + 4 * g + c] = acc[k][c];
+    for (int c = 0; c < 4; ++c) red[j * 2 * a.Np + k * a.Np + 4 * g + c] = (double)acc[k][c];
   __syncthreads();
+  double* ctmp = red + (size_t)NTs * 2 * a.Np;
+  block_colsum(red, NTs, 2 * a.Np, ctmp);
   for (int t = threadIdx.x; t < 2 * a.Np; t += nt) {
-    int k = t / a.Np, o = t % a.Np;
-    double s = 0.0;
-    for (int jj = 0; jj < NTs; ++jj) s += red[(k * NTs + jj) * a.Np + o];
-    a.part[((long long)k * gridDim.x + blockIdx.x) * a.Np + o] = s;
+    const int k = t / a.Np, o = t % a.Np;
+    a.part[((long long)k * gridDim.x + blockIdx.x) * a.Np + o] = ctmp[t];
   }
   if (!last_cta(&a.st->ticket)) return;
-  double* tot = dsm + 2 * a.Np * 33;
+  double* tot = dsm + (nt > 2 * a.Np ? nt : 2 * a.Np);
   reduce_over_ctas<2>(a.part, gridDim.x, a.Np, dsm, tot);
   __shared__ int cnt;
   if (threadIdx.x == 0) cnt = 0;
@@ -571,18 +686,29 @@ __global__ void __launch_bounds__(256) k_cg_upd(CGArgs<T> a, cudaGraphConditiona
   }
 }
 
-template <typename T>
-void* k1_fn(int G4) {
+template <typename T, int NPT>
+void* k1_fn_n(int G4) {
   switch (G4) {
-    case 1: return (void*)k_cg_q<T, 1>;
-    case 2: return (void*)k_cg_q<T, 2>;
-    case 3: return (void*)k_cg_q<T, 3>;
-    case 4: return (void*)k_cg_q<T, 4>;
-    case 5: return (void*)k_cg_q<T, 5>;
-    case 6: return (void*)k_cg_q<T, 6>;
-    case 7: return (void*)k_cg_q<T, 7>;
-    case 8: return (void*)k_cg_q<T, 8>;
+    case 1: return (void*)k_cg_q<T, 1, NPT>;
+    case 2: return (void*)k_cg_q<T, 2, NPT>;
+    case 3: return (void*)k_cg_q<T, 3, NPT>;
+    case 4: return (void*)k_cg_q<T, 4, NPT>;
+    case 5: return (void*)k_cg_q<T, 5, NPT>;
+    case 6: return (void*)k_cg_q<T, 6, NPT>;
+    case 7: return (void*)k_cg_q<T, 7, NPT>;
+    case 8: return (void*)k_cg_q<T, 8, NPT>;
   }
+  return nullptr;
+}
+
+// float: two nodes per thread on 16 x 8 tiles, one on the others; float64 one node
+// per thread (two would hold 112 weight registers)
+template <typename T>
+void* k1_fn(int G4, int npt) {
+  if constexpr (sizeof(T) == 4) {
+    if (npt == 2) return k1_fn_n<T, 2>(G4);
+  }
+  if (npt == 1) return k1_fn_n<T, 1>(G4);
   return nullptr;
 }
 
@@ -607,26 +733,28 @@ cudaError_t add_kernel(cudaGraph_t gr, cudaGraphNode_t* node, const cudaGraphNod
 
 // Shared-memory footprint of K1 for a tile shape and orbital block width.
 template <typename T>
-void k1_layout(int Np, int bw, int TX, int TY, K1Geom* G) {
+void k1_layout(int Np, int bw, int TX, int TY, int npt, K1Geom* G) {
   const size_t sz = sizeof(T);
   G->TX = TX;
   G->TY = TY;
+  G->npt = npt;
+  G->nthr = TX * TY / npt;
   const int HX = TX + 2, HY = TY + 2;
   G->DX = TX + 4;  // row of D^-1 staged from x0-1: TX+2 values padded to a 16-byte multiple
   size_t vec = (size_t)HX * HY * bw * sz;
   size_t dv = (size_t)G->DX * HY * sz;
-  size_t wv = (size_t)27 * TX * TY * sz;
+  size_t wv = (size_t)kWS * TX * TY * sz;
   auto al = [](size_t v) { return (v + 127) / 128 * 128; };
   G->off_p = (int)al(vec);
   G->off_d = (int)(G->off_p + al(vec));
   G->off_w = (int)(G->off_d + al(dv));
   G->slot_bytes = (int)(G->off_w + al(wv));
   G->tx_bytes = (uint32_t)(2 * vec + dv + wv);
-  // sacc[Np], then the per-segment block sums [kNT][bw], reused at the end for the
+  // sacc[Np], then the per-segment block sums [nthr][bw], reused at the end for the
   // cross-CTA totals [Np] and slices (at most max(threads, Np) values)
-  const size_t nthr = (size_t)kNT * (bw / 4);
+  const size_t nthr = (size_t)G->nthr * (bw / 4);
   const size_t fin = (size_t)Np + (nthr > (size_t)Np ? nthr : (size_t)Np);
-  const size_t blk = (size_t)kNT * bw;
+  const size_t blk = (size_t)G->nthr * bw + nthr;  // block sums and the column-sum slices
   size_t red = ((size_t)Np + (blk > fin ? blk : fin)) * sizeof(double);
   G->smem = 128 + (size_t)kSlots * G->slot_bytes + red;
 }
@@ -638,7 +766,11 @@ cudaError_t cg_plan_geometry(const Grid& g, int Np, int nsm, K1Geom* geo, int* b
   const size_t stat = (size_t)kMaxN * sz + 2 * (kMaxN / 4) * sizeof(int) + 64;
   const size_t limit = 227 * 1024 - stat - 1024;
   const int cap = 32;  // widest orbital block (G4 <= 8)
-  const int shapes[3][2] = {{16, 8}, {16, 4}, {8, 8}};  // TX*TY a multiple of kNT
+  // Tile shapes (TX, TY, nodes per thread).  float: 16 x 8 with one node per thread
+  // while the block has at most 20 orbitals (640 threads), else two; float64: 64-node
+  // tiles, one node per thread.  The p update of the halo takes at most 3 passes.
+  const int shapes[3][2] = {{16, 8}, {16, 4}, {8, 8}};
+  const int first_shape = sizeof(T) == 4 ? 0 : 1;
   K1Geom best{};
   int best_bw = 0;
   // fewest orbital blocks whose ring fits; the last block may be ragged (TMA fills
@@ -647,9 +779,13 @@ cudaError_t cg_plan_geometry(const Grid& g, int Np, int nsm, K1Geom* geo, int* b
     int bw = (Np + nob - 1) / nob;
     bw = (bw + 3) / 4 * 4;
     if ((Np + bw - 1) / bw != nob) continue;
-    for (int si = 0; si < 3; ++si) {
+    for (int si = first_shape; si < 3; ++si) {
+      const int TX = shapes[si][0], TY = shapes[si][1];
+      int npt = 1;
+      if (sizeof(T) == 4 && TX * TY == 128 && bw > 20) npt = 2;
+      if (TX * TY / npt > (sizeof(T) == 4 ? 128 : 64) / npt) continue;
       K1Geom G{};
-      k1_layout<T>(Np, bw, shapes[si][0], shapes[si][1], &G);
+      k1_layout<T>(Np, bw, TX, TY, npt, &G);
       if (G.smem <= limit) {
         best = G;
         best_bw = bw;
@@ -666,10 +802,10 @@ cudaError_t cg_plan_geometry(const Grid& g, int Np, int nsm, K1Geom* geo, int* b
   G.ncy = (g.ny - 1 + G.TY - 1) / G.TY;
   const int nob = (Np + bw - 1) / bw;
   int per_sm = 1;
-  void* f1 = k1_fn<T>(G.G4);
+  void* f1 = k1_fn<T>(G.G4, G.npt);
   if (f1 && cudaFuncSetAttribute(f1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G.smem) == cudaSuccess) {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f1, kNT * G.G4, G.smem) == cudaSuccess && nb > 0)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f1, G.nthr * G.G4, G.smem) == cudaSuccess && nb > 0)
       per_sm = nb;
   }
   if (per_sm > 4) per_sm = 4;
@@ -709,13 +845,14 @@ cudaError_t cg_prepare(CGPlan<T>* P) {
     if ((e = encode_tiled(&P->md, ty, 3, (void*)P->dinv_tma, dims, str, box)) != cudaSuccess) return e;
   }
   {
-    uint64_t dims[4] = {(uint64_t)P->wpitch, (uint64_t)(a.g.ny - 1), 27, (uint64_t)a.g.Pz};
-    uint64_t str[3] = {(uint64_t)P->wpitch * sz, (uint64_t)P->wpitch * (a.g.ny - 1) * sz,
-                       (uint64_t)27 * P->wpitch * (a.g.ny - 1) * sz};
-    uint32_t box[4] = {(uint32_t)G.TX, (uint32_t)G.TY, 27, 1};
+    // packed weights [Pz][ny-1][nx-1][kWS]
+    const uint64_t nxi = (uint64_t)(a.g.nx - 1), nyi = (uint64_t)(a.g.ny - 1);
+    uint64_t dims[4] = {(uint64_t)kWS, nxi, nyi, (uint64_t)a.g.Pz};
+    uint64_t str[3] = {(uint64_t)kWS * sz, (uint64_t)kWS * nxi * sz, (uint64_t)kWS * nxi * nyi * sz};
+    uint32_t box[4] = {(uint32_t)kWS, (uint32_t)G.TX, (uint32_t)G.TY, 1};
     if ((e = encode_tiled(&P->mw, ty, 4, (void*)P->wcoef, dims, str, box)) != cudaSuccess) return e;
   }
-  void* f1 = k1_fn<T>(G.G4);
+  void* f1 = k1_fn<T>(G.G4, G.npt);
   if (!f1) return cudaErrorInvalidValue;
   if ((e = cudaFuncSetAttribute(f1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G.smem)) != cudaSuccess)
     return e;
@@ -729,14 +866,21 @@ cudaError_t cg_prepare(CGPlan<T>* P) {
   long long cap = (long long)P->nsm * 4;
   P->grid_stream = (int)(gs < cap ? gs : cap);
   // block reduction [K][nt/G4f][Np], then the last CTA's slices (<= 32 per item) and totals
-  const int NTs = nt / G4f;
-  auto need = [&](int K) {
-    size_t a1 = (size_t)K * NTs * a.Np;
-    size_t a2 = (size_t)K * a.Np * 33;
-    return ((a1 > a2 ? a1 : a2) + (size_t)K * a.Np * 34) * sizeof(double);
+  // block sums [K][threads/G4][Np] = 4 K threads values; afterwards the last CTA's
+  // slices (at most max(threads, K Np)) and the K Np totals
+  auto need_for = [&](int K, int threads) {
+    const size_t blk = (size_t)4 * K * threads + threads;
+    const size_t sl = (size_t)(threads > K * a.Np ? threads : K * a.Np);
+    const size_t fin = sl + (size_t)K * a.Np;
+    return (blk > fin ? blk : fin) * sizeof(double);
   };
+  auto need = [&](int K) { return need_for(K, nt); };
   P->smem_init = need(3);
-  P->smem_upd = need(2);
+  // update kernel: one CTA per SM, the widest multiple of Np/4 threads up to kUpdThreads
+  P->nt_upd = (kUpdThreads / G4f) * G4f;
+  P->grid_upd = P->nsm;
+  P->smem_upd = need_for(2, P->nt_upd);
+  if (P->smem_upd > 200 * 1024) return cudaErrorInvalidConfiguration;
   if (P->smem_init > 200 * 1024) return cudaErrorInvalidConfiguration;
   if ((e = cudaFuncSetAttribute((void*)k_cg_init<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)P->smem_init)) != cudaSuccess)
@@ -754,7 +898,7 @@ cudaError_t cg_build_graph(CGPlan<T>* P, cudaStream_t st, bool with_apply) {
   const K1Geom& G = P->geo;
   CGArgs<T> a = P->args;
   a.in_graph = 1;
-  void* f1 = k1_fn<T>(G.G4);
+  void* f1 = k1_fn<T>(G.G4, G.npt);
   cudaGraph_t gr;
   if ((e = cudaGraphCreate(&gr, 0)) != cudaSuccess) return e;
   cudaGraphConditionalHandle cond;
@@ -782,12 +926,12 @@ cudaError_t cg_build_graph(CGPlan<T>* P, cudaStream_t st, bool with_apply) {
     {
       K1Geom geo = G;
       void* args[] = {&a, &geo, &P->mr, &P->mp, &P->md, &P->mw};
-      if ((e = add_kernel(body, &n1, nullptr, 0, f1, dim3(G.grid), dim3(kNT * G.G4), G.smem, args)) != cudaSuccess)
+      if ((e = add_kernel(body, &n1, nullptr, 0, f1, dim3(G.grid), dim3(G.nthr * G.G4), G.smem, args)) != cudaSuccess)
         break;
     }
     {
       void* args[] = {&a, &cond};
-      if ((e = add_kernel(body, &n2, &n1, 1, (void*)k_cg_upd<T>, dim3(P->grid_stream), dim3(P->nt_stream),
+      if ((e = add_kernel(body, &n2, &n1, 1, (void*)k_cg_upd<T>, dim3(P->grid_upd), dim3(P->nt_upd),
                           P->smem_upd, args)) != cudaSuccess)
         break;
     }
@@ -814,14 +958,14 @@ cudaError_t cg_launch_k1(CGPlan<T>* P, cudaStream_t st) {
   a.in_graph = 0;
   K1Geom geo = P->geo;
   void* args[] = {&a, &geo, &P->mr, &P->mp, &P->md, &P->mw};
-  return cudaLaunchKernel(k1_fn<T>(geo.G4), dim3(geo.grid), dim3(kNT * geo.G4), args, geo.smem, st);
+  return cudaLaunchKernel(k1_fn<T>(geo.G4, geo.npt), dim3(geo.grid), dim3(geo.nthr * geo.G4), args, geo.smem, st);
 }
 
 template <typename T>
 cudaError_t cg_launch_k2(CGPlan<T>* P, cudaStream_t st) {
   CGArgs<T> a = P->args;
   a.in_graph = 0;
-  k_cg_upd<T><<<P->grid_stream, P->nt_stream, P->smem_upd, st>>>(a, 0);
+  k_cg_upd<T><<<P->grid_upd, P->nt_upd, P->smem_upd, st>>>(a, 0);
   return cudaGetLastError();
 }
 

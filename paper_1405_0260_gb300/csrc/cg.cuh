@@ -45,6 +45,7 @@ struct K1Geom {
   int TX, TY, DX;     // tile (x, y) of a z-marching column, staged row pitch of D^-1
   int ncx, ncy, nob;  // columns per axis, orbital blocks of width 4*G4
   int grid, G4;       // CTAs (each takes an equal share of the column-planes), float4 groups per block
+  int npt, nthr;      // tile nodes per thread; node slots per CTA (TX * TY = nthr * npt)
   int off_p, off_d, off_w, slot_bytes;  // byte offsets inside one ring slot
   uint32_t tx_bytes;                    // TMA bytes per slot
   size_t smem;                          // dynamic shared memory per CTA
@@ -56,14 +57,14 @@ struct CGPlan {
   K1Geom geo{};
   int nsm = 152;
   int dpitch = 0;  // row pitch of dinv_tma (elements)
-  int wpitch = 0;  // row pitch of wcoef (elements)
   const T* dinv_tma = nullptr;
   const T* wcoef = nullptr;
   alignas(64) CUtensorMap mr;
   alignas(64) CUtensorMap mp;
   alignas(64) CUtensorMap md;
   alignas(64) CUtensorMap mw;
-  int grid_stream = 0, nt_stream = 0;
+  int grid_stream = 0, nt_stream = 0;  // init kernel
+  int grid_upd = 0, nt_upd = 0;        // update kernel
   size_t smem_init = 0, smem_upd = 0;
   cudaGraphExec_t exec_zero = nullptr, exec_warm = nullptr;
   int graph_N = -1;  // N the graphs were built for
@@ -89,10 +90,13 @@ cudaError_t cg_launch_k1(CGPlan<T>* P, cudaStream_t st);
 template <typename T>
 cudaError_t cg_launch_k2(CGPlan<T>* P, cudaStream_t st);
 
+// Packed operator weights per input plane, [Pz][ny-1][nx-1][kPackedW], for the tiled kernel.
+constexpr int kPackedW = 28;
+__host__ __device__ inline size_t packed_weights_count(const Grid& g) { return (size_t)kPackedW * g.Pz * (g.ny - 1) * (g.nx - 1); }
 // Build the tiled-kernel operator arrays from the 27-weight SoA coefficients.
 template <typename T>
-cudaError_t launch_build_tma_operator(const Grid& g, const T* coef, const T* dinv, T* wcoef, int wpitch, T* dinv_tma,
-                                      int dpitch, cudaStream_t st);
+cudaError_t launch_build_tma_operator(const Grid& g, const T* coef, const T* dinv, T* wcoef, T* dinv_tma, int dpitch,
+                                      cudaStream_t st);
 template <typename T>
 cudaError_t graph_add_apply(cudaGraph_t gr, cudaGraphNode_t* node, const Grid& g, int Np, const T* coef, const T* x,
                             T* y);

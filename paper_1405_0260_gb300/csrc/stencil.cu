@@ -152,27 +152,27 @@ __global__ void k_unpack_f32(Grid g, int N, int Np, const float* __restrict__ sr
 
 inline unsigned nblk(long long work, int threads) { return (unsigned)((work + threads - 1) / threads); }
 
-// Operator weights keyed by input plane, for the z-marching tiled kernel:
-//   W[s][o][yi][xi] = weight (dx, dy, dz) of the row of node (x, y, t), t = s - dz,
-// with o = (dz+1)*9 + (dy+1)*3 + (dx+1), x = xi + 1, y = yi + 1: the weight that
-// multiplies the value at (x+dx, y+dy, s) in output row (x, y, t).  Zero where
-// (x, y, t) is not an interior node.  Row pitch wpitch >= nx-1 (a multiple of 4).
+// Operator weights keyed by input plane, for the z-marching tiled kernel, packed
+// per output node:  W[s][yi][xi][o] = weight (dx, dy, dz) of the row of node
+// (x, y, t), t = s - dz, x = xi + 1, y = yi + 1, o = (dz+1)*9 + (dy+1)*3 + (dx+1):
+// the weight that multiplies the value at (x+dx, y+dy, s) in output row (x, y, t).
+// Zero where t is not an interior plane; entry o = 27 pads the node to kPackedW.
 template <typename T>
-__global__ void k_build_w(Grid g, const T* __restrict__ coef, T* __restrict__ W, int wpitch) {
-  long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  long long plane = (long long)(g.ny - 1) * wpitch;
-  long long total = (long long)g.Pz * 27 * plane;
+__global__ void k_build_w(Grid g, const T* __restrict__ coef, T* __restrict__ W) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long total = (long long)packed_weights_count(g);
   if (n >= total) return;
-  int xi = (int)(n % wpitch);
-  long long r = n / wpitch;
-  int yi = (int)(r % (g.ny - 1));
-  r /= (g.ny - 1);
-  int o = (int)(r % 27);
-  int s = (int)(r / 27);
-  int dz = o / 9 - 1;
-  int t = s - dz, x = xi + 1, y = yi + 1;
+  const int o = (int)(n % kPackedW);
+  long long r = n / kPackedW;
+  const int xi = (int)(r % (g.nx - 1));
+  r /= (g.nx - 1);
+  const int yi = (int)(r % (g.ny - 1));
+  const int s = (int)(r / (g.ny - 1));
   T w = 0;
-  if (x <= g.nx - 1 && t >= 1 && t <= g.nz - 1) w = coef[(long long)o * g.G + ((long long)t * g.Py + y) * g.Px + x];
+  if (o < 27) {
+    const int t = s - (o / 9 - 1), x = xi + 1, y = yi + 1;
+    if (t >= 1 && t <= g.nz - 1) w = coef[(long long)o * g.G + ((long long)t * g.Py + y) * g.Px + x];
+  }
   W[n] = w;
 }
 
@@ -190,18 +190,18 @@ __global__ void k_build_dinv_tma(Grid g, const T* __restrict__ dinv, T* __restri
 }  // namespace
 
 template <typename T>
-cudaError_t launch_build_tma_operator(const Grid& g, const T* coef, const T* dinv, T* wcoef, int wpitch, T* dinv_tma,
-                                      int dpitch, cudaStream_t st) {
-  long long nw = (long long)g.Pz * 27 * (g.ny - 1) * wpitch;
-  k_build_w<T><<<nblk(nw, 256), 256, 0, st>>>(g, coef, wcoef, wpitch);
+cudaError_t launch_build_tma_operator(const Grid& g, const T* coef, const T* dinv, T* wcoef, T* dinv_tma, int dpitch,
+                                      cudaStream_t st) {
+  long long nw = (long long)packed_weights_count(g);
+  k_build_w<T><<<nblk(nw, 256), 256, 0, st>>>(g, coef, wcoef);
   long long nd = (long long)g.Pz * g.Py * dpitch;
   k_build_dinv_tma<T><<<nblk(nd, 256), 256, 0, st>>>(g, dinv, dinv_tma, dpitch);
   return cudaGetLastError();
 }
-template cudaError_t launch_build_tma_operator<float>(const Grid&, const float*, const float*, float*, int, float*, int,
+template cudaError_t launch_build_tma_operator<float>(const Grid&, const float*, const float*, float*, float*, int,
                                                       cudaStream_t);
-template cudaError_t launch_build_tma_operator<double>(const Grid&, const double*, const double*, double*, int,
-                                                       double*, int, cudaStream_t);
+template cudaError_t launch_build_tma_operator<double>(const Grid&, const double*, const double*, double*, double*, int,
+                                                       cudaStream_t);
 
 template <typename T>
 cudaError_t graph_add_apply(cudaGraph_t gr, cudaGraphNode_t* node, const Grid& g, int Np, const T* coef, const T* x,
