@@ -67,6 +67,7 @@ typedef enum {
 /* Arithmetic type for paro_apply. */
 #define PARO_F64 0
 #define PARO_F32 1
+#define PARO_FF 2 /* float64 X, Y; float-float arithmetic (the mixed path's float64-accurate applies) */
 
 typedef struct paro_mesh_s* paro_mesh;
 

@@ -29,7 +29,7 @@ STATUS = {
 }
 PARO_FP64, PARO_MIXED = 0, 1
 PARO_OP_A, PARO_OP_H, PARO_OP_M = 0, 1, 2
-PARO_F64, PARO_F32 = 0, 1
+PARO_F64, PARO_F32, PARO_FF = 0, 1, 2
 
 
 class paro_params(C.Structure):
@@ -221,10 +221,15 @@ class Mesh:
         rc = paro_iterate(self.h, N, self._dev(U), lam, params, st, allow)
         return rc, lam, st
 
-    def apply(self, op, X, Y):
+    def apply(self, op, X, Y, float_float=False):
+        """Y = op X.  float32 tensors: float32 weights; float64 tensors: float64
+        arithmetic, or float-float arithmetic when float_float (PARO_MIXED handles)."""
         import torch
 
-        dt = PARO_F32 if X.dtype == torch.float32 else PARO_F64
+        if X.dtype == torch.float32:
+            dt = PARO_F32
+        else:
+            dt = PARO_FF if float_float else PARO_F64
         paro_apply(self.h, X.shape[1], op, dt, self._dev(X, X.dtype), self._dev(Y, X.dtype))
 
 

@@ -29,8 +29,13 @@ struct paro_mesh_s {
   Weights27 mw{};
   // workspace sized for Np_alloc orbitals
   int Np_alloc = 0;
-  double *u = nullptr, *x = nullptr, *b = nullptr, *r = nullptr, *p0 = nullptr, *p1 = nullptr, *q = nullptr;
-  float *b32 = nullptr, *x32 = nullptr, *r32 = nullptr, *p32a = nullptr, *p32b = nullptr, *q32 = nullptr;
+  double *u = nullptr, *x = nullptr, *b = nullptr, *r = nullptr, *p0 = nullptr, *q = nullptr;
+  float *b32 = nullptr, *x32 = nullptr, *r32 = nullptr, *p32a = nullptr, *q32 = nullptr;
+  // mixed mode: float-float (hi/lo) copies of a float64 input vector and of two
+  // operator images, [G][Np] each; float-float weights of A and H, [G][28] each
+  float *fxh = nullptr, *fxl = nullptr, *fah = nullptr, *fal = nullptr, *fbh = nullptr, *fbl = nullptr;
+  double* gpart_ff = nullptr;
+  float *wAh = nullptr, *wAl = nullptr, *wHh = nullptr, *wHl = nullptr;
   double *gpart = nullptr, *GA = nullptr, *GB = nullptr, *C = nullptr, *theta = nullptr, *eigwork = nullptr;
   double* dscal = nullptr;  // per-orbital double scalars
   int* dint = nullptr;      // per-orbital int scalars
@@ -207,8 +212,9 @@ int ensure_workspace(paro_mesh m, int Np) {
   if (Np == m->Np_alloc) return PARO_OK;
   free_plans(m);
   // release the previous vector workspace
-  void* olds[] = {m->u, m->x, m->b, m->r, m->p0, m->p1, m->q, m->b32, m->x32, m->r32, m->p32a, m->p32b, m->q32,
-                  m->gpart, m->GA, m->GB, m->C, m->theta, m->eigwork, m->cgpart};
+  void* olds[] = {m->u,    m->x,   m->b,   m->r,   m->p0,  m->q,     m->b32,    m->x32, m->r32,
+                  m->p32a, m->q32, m->fxh, m->fxl, m->fah, m->fal,   m->fbh,    m->fbl, m->gpart_ff,
+                  m->gpart, m->GA, m->GB,  m->C,   m->theta, m->eigwork, m->cgpart};
   CK(cudaStreamSynchronize(m->st));
   for (void* p : olds) dfree(m, p);
   size_t n = (size_t)m->g.G * Np;
@@ -217,15 +223,20 @@ int ensure_workspace(paro_mesh m, int Np) {
   TRY(dalloc(m, &m->b, n));
   TRY(dalloc(m, &m->r, n));
   TRY(dalloc(m, &m->p0, n));
-  TRY(dalloc(m, &m->p1, n));
   TRY(dalloc(m, &m->q, n));
   if (m->precision == PARO_MIXED) {
     TRY(dalloc(m, &m->b32, n));
     TRY(dalloc(m, &m->x32, n));
     TRY(dalloc(m, &m->r32, n));
     TRY(dalloc(m, &m->p32a, n));
-    TRY(dalloc(m, &m->p32b, n));
     TRY(dalloc(m, &m->q32, n));
+    TRY(dalloc(m, &m->fxh, n));
+    TRY(dalloc(m, &m->fxl, n));
+    TRY(dalloc(m, &m->fah, n));
+    TRY(dalloc(m, &m->fal, n));
+    TRY(dalloc(m, &m->fbh, n));
+    TRY(dalloc(m, &m->fbl, n));
+    if (Np <= 32) TRY(dalloc(m, &m->gpart_ff, gram_ff_partial_doubles(m->g, Np)));
   }
   TRY(dalloc(m, &m->gpart, gram_partial_doubles(m->g, Np)));
   TRY(dalloc(m, &m->GA, (size_t)Np * Np));
@@ -362,7 +373,13 @@ int solve_packed(paro_mesh m, int N, const double* lam, const paro_params& p, pa
   for (int i = 0; i < Np; ++i) m->h_dbl[i] = i < N ? lam[i] + m->sigma : 0.0;
   double* scale = m->dscal + S_SCALE * kMaxN;
   CK(cudaMemcpyAsync(scale, m->h_dbl, sizeof(double) * Np, cudaMemcpyHostToDevice, m->st));
-  LAUNCH(1, launch_apply_f64(g, Np, nullptr, &m->mw, 0.0, m->u, m->b, scale, m->st));
+  if (m->precision == PARO_MIXED) {
+    // float-float mass apply (float64 accuracy on the float32 pipes)
+    LAUNCH(1, launch_split_ff((long long)g.G * Np, m->u, m->fxh, m->fxl, m->st));
+    LAUNCH(1, launch_ff_apply(g, Np, nullptr, nullptr, &m->mw, m->fxh, m->fxl, scale, m->b, nullptr, nullptr, m->st));
+  } else {
+    LAUNCH(1, launch_apply_f64(g, Np, nullptr, &m->mw, 0.0, m->u, m->b, scale, m->st));
+  }
   CK(cudaMemcpyAsync(m->x, m->u, sizeof(double) * g.G * Np, cudaMemcpyDeviceToDevice, m->st));
   long long its = 0;
   int itmax = 0;
@@ -384,8 +401,11 @@ int solve_packed(paro_mesh m, int N, const double* lam, const paro_params& p, pa
     long long its32 = 0;
     int maxit_seen = 0;
     for (;;) {
-      // r = b - A x in float64; its float32 rounding is the correction right-hand side
-      LAUNCH(1, launch_refine_residual(g, N, Np, m->coef64, m->x, m->b, m->b32, rs, p.solve_tol, m->st));
+      // r = b - A x, float64-accurate (float-float arithmetic); its float32 rounding
+      // is the correction right-hand side
+      LAUNCH(1, launch_split_ff((long long)g.G * Np, m->x, m->fxh, m->fxl, m->st));
+      LAUNCH(1, launch_refine_residual_ff(g, N, Np, m->wAh, m->wAl, m->fxh, m->fxl, m->b, m->b32, rs, p.solve_tol,
+                                          m->st));
       if (st) st->stencil_applies += N;
       int open = 0;
       TRY(read_n_active(m, &open));
@@ -442,12 +462,28 @@ int solve_packed(paro_mesh m, int N, const double* lam, const paro_params& p, pa
 int rr_packed(paro_mesh m, int N, const double* src, double* dst, double* lam) {
   const int Np = m->Np_alloc;
   Grid& g = m->g;
-  LAUNCH(1, launch_apply_f64(g, Np, m->coef64, &m->mw, m->sigma, src, m->r, nullptr, m->st));  // H = A - sigma M
-  LAUNCH(1, launch_apply_f64(g, Np, nullptr, &m->mw, 0.0, src, m->q, nullptr, m->st));         // M
-  LAUNCH(2, launch_gram2(g, N, Np, src, m->r, m->q, m->gpart, nullptr, m->GA, m->GB, m->st));
+  const bool ff = m->precision == PARO_MIXED && m->gpart_ff != nullptr;
+  if (ff) {
+    // float-float: HX and MX as hi/lo arrays, both Grams and the rotation from the split X
+    LAUNCH(1, launch_split_ff((long long)g.G * Np, src, m->fxh, m->fxl, m->st));
+    LAUNCH(1, launch_ff_apply(g, Np, m->wHh, m->wHl, nullptr, m->fxh, m->fxl, nullptr, nullptr, m->fah, m->fal,
+                              m->st));
+    LAUNCH(1, launch_ff_apply(g, Np, nullptr, nullptr, &m->mw, m->fxh, m->fxl, nullptr, nullptr, m->fbh, m->fbl,
+                              m->st));
+    int nch = 0;
+    LAUNCH(1, launch_gram2_ff(g, Np, m->fxh, m->fxl, m->fah, m->fal, m->fbh, m->fbl, m->gpart_ff, &nch, m->st));
+    LAUNCH(1, launch_gram_reduce(Np, nch, m->gpart_ff, m->GA, m->GB, m->st));
+  } else {
+    LAUNCH(1, launch_apply_f64(g, Np, m->coef64, &m->mw, m->sigma, src, m->r, nullptr, m->st));  // H = A - sigma M
+    LAUNCH(1, launch_apply_f64(g, Np, nullptr, &m->mw, 0.0, src, m->q, nullptr, m->st));         // M
+    LAUNCH(2, launch_gram2(g, N, Np, src, m->r, m->q, m->gpart, nullptr, m->GA, m->GB, m->st));
+  }
   LAUNCH(1, launch_small_eig(N, m->GA, m->GB, m->eigwork, m->C, m->theta, &m->cgst->status, m->st));
   TRY(check_status(m, "rayleigh_ritz"));
-  LAUNCH(1, launch_rotate(g, N, Np, src, m->C, dst, m->st));
+  if (ff)
+    LAUNCH(1, launch_rotate_ff(g, N, Np, m->fxh, m->fxl, m->C, dst, m->st));
+  else
+    LAUNCH(1, launch_rotate(g, N, Np, src, m->C, dst, m->st));
   CK(cudaMemcpyAsync(m->h_dbl, m->theta, sizeof(double) * N, cudaMemcpyDeviceToHost, m->st));
   CK(cudaStreamSynchronize(m->st));
   for (int i = 0; i < N; ++i) lam[i] = m->h_dbl[i];
@@ -589,7 +625,10 @@ int paro_mesh_create(paro_mesh* out, int nx, int ny, int nz, const double lo[3],
       (rc = dalloc(m, &m->cgst, 1)) || (rc = dalloc(m, &m->w32, packed_weights_count(g))) ||
       (rc = dalloc(m, &m->w64, packed_weights_count(g))) ||
       (rc = dalloc(m, &m->dt32, (size_t)g.Pz * g.Py * m->dpitch)) ||
-      (rc = dalloc(m, &m->dt64, (size_t)g.Pz * g.Py * m->dpitch))) {
+      (rc = dalloc(m, &m->dt64, (size_t)g.Pz * g.Py * m->dpitch)) ||
+      (precision == PARO_MIXED &&
+       ((rc = dalloc(m, &m->wAh, (size_t)g.G * kPackedW)) || (rc = dalloc(m, &m->wAl, (size_t)g.G * kPackedW)) ||
+        (rc = dalloc(m, &m->wHh, (size_t)g.G * kPackedW)) || (rc = dalloc(m, &m->wHl, (size_t)g.G * kPackedW))))) {
     g_create_err = m->err;
     paro_mesh_destroy(m);
     return rc;
@@ -637,6 +676,8 @@ int paro_set_potential(paro_mesh m, const double* Vq, double sigma) {
                                                m->st));
   LAUNCH(2, launch_build_tma_operator<float>(m->g, m->coef32, m->dinv32, m->w32, m->dt32, m->dpitch,
                                               m->st));
+  if (m->precision == PARO_MIXED)
+    LAUNCH(1, launch_build_wff(m->g, m->coef64, m->mw, sigma, m->wAh, m->wAl, m->wHh, m->wHl, m->st));
   m->sigma = sigma;
   m->have_pot = true;
   return PARO_OK;
@@ -738,7 +779,9 @@ int paro_apply(paro_mesh m, int N, int op, int dtype, const void* X, void* Y) {
   TRY(check_common(m, N));
   if (!X || !Y || X == Y) return fail(m, PARO_ERR_ARG, "X, Y must be non-null and distinct");
   if (op < PARO_OP_A || op > PARO_OP_M) return fail(m, PARO_ERR_ARG, "unknown op");
-  if (dtype != PARO_F64 && dtype != PARO_F32) return fail(m, PARO_ERR_ARG, "unknown dtype");
+  if (dtype != PARO_F64 && dtype != PARO_F32 && dtype != PARO_FF) return fail(m, PARO_ERR_ARG, "unknown dtype");
+  if (dtype == PARO_FF && m->precision != PARO_MIXED)
+    return fail(m, PARO_ERR_ARG, "float-float apply needs a PARO_MIXED handle");
   if (dtype == PARO_F32 && op != PARO_OP_A) return fail(m, PARO_ERR_ARG, "float32 apply supports PARO_OP_A only");
   if (dtype == PARO_F32 && m->precision != PARO_MIXED)
     return fail(m, PARO_ERR_ARG, "float32 apply needs a PARO_MIXED handle");
@@ -749,6 +792,16 @@ int paro_apply(paro_mesh m, int N, int op, int dtype, const void* X, void* Y) {
     if (op == PARO_OP_A) LAUNCH(1, launch_apply_f64(m->g, Np, m->coef64, nullptr, 0.0, m->u, m->x, nullptr, m->st));
     else if (op == PARO_OP_H) LAUNCH(1, launch_apply_f64(m->g, Np, m->coef64, &m->mw, m->sigma, m->u, m->x, nullptr, m->st));
     else LAUNCH(1, launch_apply_f64(m->g, Np, nullptr, &m->mw, 0.0, m->u, m->x, nullptr, m->st));
+    LAUNCH(1, launch_unpack(m->g, N, Np, m->x, static_cast<double*>(Y), m->st));
+  } else if (dtype == PARO_FF) {
+    LAUNCH(1, launch_pack(m->g, N, Np, static_cast<const double*>(X), m->u, m->st));
+    LAUNCH(1, launch_split_ff((long long)m->g.G * Np, m->u, m->fxh, m->fxl, m->st));
+    if (op == PARO_OP_M)
+      LAUNCH(1, launch_ff_apply(m->g, Np, nullptr, nullptr, &m->mw, m->fxh, m->fxl, nullptr, m->x, nullptr, nullptr,
+                                m->st));
+    else
+      LAUNCH(1, launch_ff_apply(m->g, Np, op == PARO_OP_A ? m->wAh : m->wHh, op == PARO_OP_A ? m->wAl : m->wHl,
+                                nullptr, m->fxh, m->fxl, nullptr, m->x, nullptr, nullptr, m->st));
     LAUNCH(1, launch_unpack(m->g, N, Np, m->x, static_cast<double*>(Y), m->st));
   } else {
     LAUNCH(1, launch_pack_f32(m->g, N, Np, static_cast<const float*>(X), m->b32, m->st));

@@ -127,6 +127,25 @@ cudaError_t launch_refine_residual(const Grid& g, int N, int Np, const double* c
                                    const double* b64, float* rhs32, const CGState& s, double tol, cudaStream_t st);
 cudaError_t launch_refine_update(const Grid& g, int Np, double* x64, const float* d32, const int* skip,
                                  cudaStream_t st);
+// The same residual in float-float arithmetic (x split into hi/lo arrays, packed weights of A).
+cudaError_t launch_refine_residual_ff(const Grid& g, int N, int Np, const float* whi, const float* wlo,
+                                      const float* xhi, const float* xlo, const double* b64, float* rhs32,
+                                      const CGState& s, double tol, cudaStream_t st);
+
+// ff.cu: float64-accurate applies, Grams and rotation in float-float arithmetic
+cudaError_t launch_split_ff(long long n, const double* x, float* hi, float* lo, cudaStream_t st);
+cudaError_t launch_build_wff(const Grid& g, const double* coef64, const Weights27& mw, double sigma, float* ahi,
+                             float* alo, float* hhi, float* hlo, cudaStream_t st);
+// y = scale_o (W x): W the packed per-node weights (whi/wlo) or the constant weights cw
+cudaError_t launch_ff_apply(const Grid& g, int Np, const float* whi, const float* wlo, const Weights27* cw,
+                            const float* xhi, const float* xlo, const double* scale, double* y64, float* yhi,
+                            float* ylo, cudaStream_t st);
+size_t gram_ff_partial_doubles(const Grid& g, int Np);
+cudaError_t launch_gram2_ff(const Grid& g, int Np, const float* xh, const float* xl, const float* ah, const float* al,
+                            const float* bh, const float* bl, double* part, int* n_chunks, cudaStream_t st);
+cudaError_t launch_gram_reduce(int Np, int nch, const double* part, double* G1, double* G2, cudaStream_t st);
+cudaError_t launch_rotate_ff(const Grid& g, int N, int Np, const float* xh, const float* xl, const double* C,
+                             double* U, cudaStream_t st);
 
 // rr.cu
 cudaError_t launch_gram2(const Grid& g, int N, int Np, const double* X, const double* Y1, const double* Y2,

@@ -6,7 +6,9 @@
 // converged orbitals so the next correction solve skips them.
 #include <cmath>
 
+#include "cg.cuh"
 #include "common.cuh"
+#include "ff.cuh"
 
 namespace paro {
 
@@ -116,6 +118,86 @@ __global__ void __launch_bounds__(kRedThreads) k_refine_residual(Grid g, int N, 
   if (threadIdx.x == 0) *s.n_active = cnt;
 }
 
+// The same residual in float-float arithmetic (ff.cuh): x as hi/lo arrays, the
+// packed per-node float-float weights of A, b in float64 (split on load).
+__global__ void __launch_bounds__(kRedThreads) k_refine_residual_ff(Grid g, int N, int Np, const float* __restrict__ whi,
+                                                                    const float* __restrict__ wlo,
+                                                                    const float* __restrict__ xhi,
+                                                                    const float* __restrict__ xlo,
+                                                                    const double* __restrict__ b,
+                                                                    float* __restrict__ rhs, CGState s, double tol) {
+  __shared__ double sred[2 * kRedThreads * 4];
+  double* tot = sred;
+  __shared__ int cnt;
+  NodeMap nm = node_map(Np);
+  int grp = threadIdx.x % nm.groups;
+  int nl = threadIdx.x / nm.groups;
+  bool live = nl < nm.npb;
+  double acc[2][4] = {};
+  if (live) {
+    float arr[4] = {0, 0, 0, 0}, abb[4] = {0, 0, 0, 0};
+    for (int n = blockIdx.x * nm.npb + nl; n < g.nI; n += gridDim.x * nm.npb) {
+      long long gp = interior_to_padded(g, n);
+      float wh[28], wl[28];
+#pragma unroll
+      for (int q = 0; q < 7; ++q) {
+        const float4 a = reinterpret_cast<const float4*>(whi + gp * kPackedW)[q];
+        const float4 c = reinterpret_cast<const float4*>(wlo + gp * kPackedW)[q];
+        wh[4 * q] = a.x, wh[4 * q + 1] = a.y, wh[4 * q + 2] = a.z, wh[4 * q + 3] = a.w;
+        wl[4 * q] = c.x, wl[4 * q + 1] = c.y, wl[4 * q + 2] = c.z, wl[4 * q + 3] = c.w;
+      }
+      FF ax[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+#pragma unroll
+      for (int o = 0; o < 27; ++o) {
+        const int dz = o / 9 - 1, dy = (o / 3) % 3 - 1, dx = o % 3 - 1;
+        const long long nb = gp + ((long long)dz * g.Py + dy) * g.Px + dx;
+        const FF w{wh[o], wl[o]};
+        const float4 h = *reinterpret_cast<const float4*>(xhi + nb * Np + 4 * grp);
+        const float4 l = *reinterpret_cast<const float4*>(xlo + nb * Np + 4 * grp);
+        ff_mac(ax[0], FF{h.x, l.x}, w);
+        ff_mac(ax[1], FF{h.y, l.y}, w);
+        ff_mac(ax[2], FF{h.z, l.z}, w);
+        ff_mac(ax[3], FF{h.w, l.w}, w);
+      }
+      V4<double> bv = ld4v(b, gp, Np, grp);
+      const double bb[4] = {bv.a, bv.b, bv.c, bv.d};
+      float r[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        FF rc = ff_split(bb[c]);
+        ff_add(rc, ff_neg(ax[c]));
+        rc = ff_norm(rc);
+        r[c] = rc.hi;
+        arr[c] = fmaf(rc.hi, rc.hi, arr[c]);
+        const float bh = (float)bb[c];
+        abb[c] = fmaf(bh, bh, abb[c]);
+      }
+      if (rhs != nullptr) st4(rhs + gp * Np + 4 * grp, V4<float>{r[0], r[1], r[2], r[3]});
+    }
+    for (int c = 0; c < 4; ++c) {
+      acc[0][c] = arr[c];
+      acc[1][c] = abb[c];
+    }
+  }
+  if (!reduce_partials<2>(acc, Np, grp, nl, live, s.partial, s.ticket, sred, tot)) return;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  for (int o = threadIdx.x; o < Np; o += blockDim.x) {
+    double rr = tot[o], bb = tot[Np + o];
+    s.rr[o] = rr;
+    s.bb[o] = bb;
+    bool done = (o >= N) || rr <= tol * tol * bb;
+    if (o < N && !(isfinite(rr) && isfinite(bb))) {
+      atomicOr(s.status, kStatNonFinite);
+      done = true;
+    }
+    s.skip[o] = done ? 1 : 0;
+    if (!done) atomicAdd(&cnt, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *s.n_active = cnt;
+}
+
 __global__ void k_refine_update(Grid g, int Np, double* __restrict__ x, const float* __restrict__ d,
                                 const int* __restrict__ skip) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -138,6 +220,13 @@ int red_blocks(const Grid& g, int Np) {
 cudaError_t launch_refine_residual(const Grid& g, int N, int Np, const double* coef64, const double* x64,
                                    const double* b64, float* rhs32, const CGState& s, double tol, cudaStream_t st) {
   k_refine_residual<<<red_blocks(g, Np), kRedThreads, 0, st>>>(g, N, Np, coef64, x64, b64, rhs32, s, tol);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_refine_residual_ff(const Grid& g, int N, int Np, const float* whi, const float* wlo,
+                                      const float* xhi, const float* xlo, const double* b64, float* rhs32,
+                                      const CGState& s, double tol, cudaStream_t st) {
+  k_refine_residual_ff<<<red_blocks(g, Np), kRedThreads, 0, st>>>(g, N, Np, whi, wlo, xhi, xlo, b64, rhs32, s, tol);
   return cudaGetLastError();
 }
 

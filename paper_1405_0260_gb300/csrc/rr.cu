@@ -86,12 +86,15 @@ __device__ __forceinline__ void rr_pair(int m, int r, int k, int* p, int* q) {
 
 // One CTA: Cholesky of G_B, two triangular solves, parallel cyclic Jacobi on
 // S = L^-1 G_A L^-T, sort, back-substitution C = L^-T Q.  All matrices N x N
-// row-major (ld N) in `work` (4 N^2 doubles); inputs G_A, G_B and output C have
+// row-major (ld N), in dynamic shared memory when the launch provides 4 N^2
+// doubles of it (smem != 0), else in `work`; inputs G_A, G_B and output C have
 // ld Np, C zero-padded to Np x Np.
 __global__ void __launch_bounds__(1024) k_small_eig(int N, int Np, const double* __restrict__ GA,
                                                     const double* __restrict__ GB, double* __restrict__ work,
                                                     double* __restrict__ C, double* __restrict__ theta,
-                                                    int* __restrict__ status) {
+                                                    int* __restrict__ status, int smem) {
+  extern __shared__ double esm[];
+  if (smem) work = esm;
   __shared__ int fail;
   __shared__ double red[1024 / 32][2];
   __shared__ double cs[kMaxN / 2 + 1][2];
@@ -321,10 +324,27 @@ cudaError_t launch_gram2(const Grid& g, int N, int Np, const double* X, const do
   return cudaGetLastError();
 }
 
+cudaError_t launch_gram_reduce(int Np, int nch, const double* part, double* G1, double* G2, cudaStream_t st) {
+  long long work = 2LL * Np * Np;
+  k_gram_reduce<<<(unsigned)((work + 255) / 256), 256, 0, st>>>(Np, nch, part, G1, G2);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_small_eig(int N, const double* GA, const double* GB, double* work, double* C, double* theta,
                              int* status, cudaStream_t st) {
   int Np = (N + 3) / 4 * 4;
-  k_small_eig<<<1, 1024, 0, st>>>(N, Np, GA, GB, work, C, theta, status);
+  // threads: about one per rotation-pair row element, a multiple of 32
+  int nt = (N * N / 2 + 31) / 32 * 32;
+  if (nt < 64) nt = 64;
+  if (nt > 1024) nt = 1024;
+  const size_t smem = (size_t)4 * N * N * sizeof(double);
+  if (smem <= 160 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_small_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    if (e != cudaSuccess) return e;
+    k_small_eig<<<1, nt, smem, st>>>(N, Np, GA, GB, work, C, theta, status, 1);
+  } else {
+    k_small_eig<<<1, nt, 0, st>>>(N, Np, GA, GB, work, C, theta, status, 0);
+  }
   return cudaGetLastError();
 }
 
@@ -383,7 +403,7 @@ extern "C" int paro_small_eig_static(int N, const double* GA, const double* GB, 
   // The status word keeps the previous call's value: clear it.  The work
   // matrices are fully written by the kernel before they are read.
   if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return PARO_ERR_CUDA;
-  paro::k_small_eig<<<1, 1024, 0, st>>>(N, N, GA, GB, scratch, C, theta, status);
+  paro::k_small_eig<<<1, 1024, 0, st>>>(N, N, GA, GB, scratch, C, theta, status, 0);
   if (cudaGetLastError() != cudaSuccess) return PARO_ERR_CUDA;
   int h = 0;
   if (cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return PARO_ERR_CUDA;

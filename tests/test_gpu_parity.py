@@ -92,6 +92,30 @@ def test_apply_fp64_matches_assembled_operators(B, n, N):
     m.close()
 
 
+@pytest.mark.parametrize("n,N", APPLY_CASES)
+def test_apply_float_float_matches_assembled_operators(B, n, N):
+    # Float-float arithmetic (the mixed path's float64-accurate applies).  Bound:
+    # values and weights are split to ~48 bits (2^-48 relative); every product
+    # drops lo*lo and rounds its cross terms to float32 (2^-48 of |w x|); the lo
+    # accumulator rounds at 2^-24 of itself, itself <= 2^-24 of the sum; 27 terms
+    # and a handful of roundings each give |err| <= ~100 * 2^-48 * (|A| |x|).
+    lo, hi = (-1.5, -2.0, -1.0), (2.5, 1.0, 1.75)
+    rng = np.random.default_rng(300 + N)
+    nI = (n[0] - 1) * (n[1] - 1) * (n[2] - 1)
+    p = W.Problem("apply_ff", n, lo, hi, rough_potential(n, lo, hi, 11 + N), 0.7, rng.standard_normal((nI, N)), 0)
+    ops = oracle_ops(p)
+    m = make_mesh(B, p, B.PARO_MIXED)
+    X = dev(p.U0)
+    Y = torch.empty_like(X)
+    for op, A in ((B.PARO_OP_A, ops.A), (B.PARO_OP_H, ops.H), (B.PARO_OP_M, ops.M)):
+        m.apply(op, X, Y, float_float=True)
+        ref = A @ p.U0
+        bound = abs(A) @ np.abs(p.U0)
+        err = np.abs(host(Y) - ref)
+        assert np.all(err <= 100 * 2.0 ** -48 * bound + 1e-300), (op, (err / bound).max())
+    m.close()
+
+
 @pytest.mark.parametrize("n,N", APPLY_CASES[1:])
 def test_apply_fp32_matches_assembled_operator(B, n, N):
     lo, hi = (-2.0, -2.0, -2.0), (2.0, 2.0, 2.0)
@@ -221,6 +245,23 @@ def test_rayleigh_ritz_matches_oracle(B, N):
     lam2, _ = m.rayleigh_ritz(X, X)
     assert np.max(np.abs(lam2 - lam)) < 1e-13 * np.max(np.abs(lam))
     assert np.max(np.abs(host(X) - u)) < 1e-13 * np.max(np.abs(u))
+    m.close()
+
+
+@pytest.mark.parametrize("N", [3, 11, 20])
+def test_rayleigh_ritz_float_float_matches_oracle(B, N):
+    # mixed handles do Rayleigh-Ritz in float-float arithmetic (applies, Grams, rotation)
+    p = W.hydrogen(nc=11, L=6.0, N=N, seed=3300 + N, sigma=1.0)
+    ops = oracle_ops(p)
+    ref = O.rayleigh_ritz(ops, p.U0)
+    m = make_mesh(B, p, B.PARO_MIXED)
+    X = dev(p.U0)
+    U = torch.empty_like(X)
+    lam, st = m.rayleigh_ritz(X, U)
+    assert np.max(np.abs(lam - ref.lam) / np.abs(ref.lam)) < 1e-11
+    u = host(U)
+    assert np.max(np.abs(u.T @ (ops.M @ u) - np.eye(N))) < 1e-11
+    assert np.max(O.subspace_angles_M(ops.M, u, ref.U)) < 1e-7
     m.close()
 
 
