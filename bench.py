@@ -170,6 +170,7 @@ def run_ours(args, ws, rank, local):
     prof_ms = 0.0
     prof_n = 0
     prof_units = 0
+    prof_nodes = 0
     for i in range(max(1, min(args.steps, 3))):
         with torch.cuda.stream(stream):
             flush_l2(flush)
@@ -178,6 +179,7 @@ def run_ours(args, ws, rank, local):
         prof_ms += st.prof_ms
         prof_n += st.prof_launches
         prof_units += st.prof_dof_orb
+        prof_nodes += st.prof_node_passes
     if dist is not None:
         dist.barrier()
     ms = sum(a.elapsed_time(b) for a, b in ev)
@@ -189,16 +191,18 @@ def run_ours(args, ws, rank, local):
     units = nI * N * args.steps * ws
     value = units / (t_max * 1e-3)
 
-    # roofline of the CG operator kernel: per unit (node x orbital) it reads r and
-    # p_old and writes p_new and q (4 x 4 B in float32); per node and launch it
-    # needs the operator data once (8 float32 potential values per cell, about one
-    # cell per node, + the Jacobi diagonal: 36 B).
+    # roofline of the persistent CG kernel (the whole float32 CG loop of a correction
+    # solve in one cooperative launch).  Per unit (node x orbital) and iteration it
+    # reads r, p and writes q in the operator pass (12 B) and reads x, r, p, q and
+    # writes x, r, p in the update (28 B): 40 B.  Per node and orbital-block pass it
+    # reads the 27 float32 operator weights (108 B) and the Jacobi diagonal twice (8 B).
     peak, peak_kind = peaks()
     roof = None
     if prof_n > 0 and prof_ms > 0:
-        alg_bytes = 16.0 * prof_units + 36.0 * nI * prof_n
+        alg_bytes = 40.0 * prof_units + 116.0 * prof_nodes
         achieved = alg_bytes / (prof_ms * 1e-3) / 1e9
-        roof = {"kernel": "k_cg_q<float> (TMA-tiled: p = D^-1 r + beta p; q = A p; (p,q))", "bound": "hbm",
+        roof = {"kernel": "k_cg_q<float, LOOP> (persistent CG loop: TMA-tiled q = A p, update, grid barriers)",
+                "bound": "hbm",
                 "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": None,
                 "launches": prof_n, "avg_launch_us": round(1e3 * prof_ms / prof_n, 2),

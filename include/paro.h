@@ -82,8 +82,10 @@ typedef struct {
   int max_refine;     /* mixed: refinement sweeps per source problem (20) */
   int check_every;    /* CG iterations between host convergence checks (16) */
   int fixed_outer;    /* paro_iterate: if > 0, run exactly this many outer iterations (0) */
-  int profile;        /* if != 0, time every launch of the CG operator kernel (q = A p) with CUDA
-                         events on the handle's stream and report it in paro_stats.prof_* (0) */
+  int profile;        /* 1: time every launch of the CG kernel (the persistent CG loop, one launch per
+                         solve) with CUDA events on the handle's stream and report it in paro_stats.prof_*;
+                         2: the same for a host-driven loop that launches the operator pass and the
+                         update as separate kernels (timing the operator pass); 0: off (0) */
 } paro_params;
 
 /* Statistics of a call.  Counters and times (cg_iters*, ms_*, stencil_applies,
@@ -101,9 +103,10 @@ typedef struct {
   double ms_rr;                /* device time in Rayleigh-Ritz */
   long long stencil_applies;   /* orbital-operator applies (one orbital, one apply = 1) */
   long long kernel_launches;   /* CUDA kernels this library launched during the call */
-  long long prof_launches;     /* profile != 0: launches of the CG operator kernel that were timed */
+  long long prof_launches;     /* profile != 0: timed launches (see paro_params.profile) */
   double prof_ms;              /* profile != 0: their summed device time (ms) */
-  long long prof_dof_orb;      /* profile != 0: sum over those launches of n_interior x orbitals processed */
+  long long prof_dof_orb;      /* profile != 0: sum over their operator passes of n_interior x orbitals processed */
+  long long prof_node_passes;  /* profile != 0: sum over their operator passes of n_interior x orbital blocks */
 } paro_stats;
 
 void paro_default_params(paro_params* p);

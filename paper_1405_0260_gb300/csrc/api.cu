@@ -323,6 +323,22 @@ int run_cg(paro_mesh m, CGPlan<T>* P, int N, bool warm, double tol, int maxit, i
   ctl_int[0] = maxit;
   CK(cudaMemcpyAsync(&m->cgst->tol, m->h_ctl, sizeof(double), cudaMemcpyHostToDevice, m->st));
   CK(cudaMemcpyAsync(&m->cgst->maxit, ctl_int, sizeof(int), cudaMemcpyHostToDevice, m->st));
+  // float32: the whole loop in one cooperative launch (profile 1: CUDA events
+  // around it).  float64 keeps the graph (or host-driven) loop of two kernels per
+  // iteration, which runs its longer float64 passes with less synchronisation.
+  if (P->coop_ok && m->profile != 2 && sizeof(T) == 4) {
+    if (warm) LAUNCH(1, launch_apply_T(m, P));
+    LAUNCH(1, cg_launch_init<T>(P, m->st, !warm));
+    if (m->profile) CK(cudaEventRecord(m->pev[2 * m->pev_used], m->st));
+    LAUNCH(1, cg_launch_loop<T>(P, m->st));
+    if (m->profile) {
+      CK(cudaEventRecord(m->pev[2 * m->pev_used + 1], m->st));
+      m->pev_used++;
+    }
+    TRY(read_iters(m, N, it_sum, it_max));  // synchronises the stream
+    if (m->profile) TRY(drain_profile(m));
+    return PARO_OK;
+  }
   if (!m->profile) {
     // N is baked into the graph arguments: rebuild when it changes
     cudaGraphExec_t* ex = warm ? &P->exec_warm : &P->exec_zero;
@@ -536,19 +552,25 @@ struct CallScope {
         }
     }
     if (cudaMemsetAsync(&m->cgst->work, 0, sizeof(unsigned long long), m->st) != cudaSuccess) return;
-    m->profile = 1;
+    if (cudaMemsetAsync(&m->cgst->work_nodes, 0, sizeof(unsigned long long), m->st) != cudaSuccess) return;
+    m->profile = profile == 2 ? 2 : 1;
   }
   ~CallScope() {
     if (s) {
       s->kernel_launches += m->launches - l0;
       if (m->profile) {
-        unsigned long long w = 0;
+        unsigned long long w = 0, wn = 0;
         if (cudaMemcpyAsync(m->h_dbl, &m->cgst->work, sizeof(w), cudaMemcpyDeviceToHost, m->st) == cudaSuccess &&
-            cudaStreamSynchronize(m->st) == cudaSuccess)
+            cudaMemcpyAsync(m->h_dbl + 1, &m->cgst->work_nodes, sizeof(wn), cudaMemcpyDeviceToHost, m->st) ==
+                cudaSuccess &&
+            cudaStreamSynchronize(m->st) == cudaSuccess) {
           std::memcpy(&w, m->h_dbl, sizeof(w));
+          std::memcpy(&wn, m->h_dbl + 1, sizeof(wn));
+        }
         s->prof_launches += m->prof_launches;
         s->prof_ms += m->prof_ms;
         s->prof_dof_orb += (long long)w;
+        s->prof_node_passes += (long long)wn;
       }
     }
     m->profile = 0;

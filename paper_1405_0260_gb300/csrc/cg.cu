@@ -59,6 +59,22 @@ __device__ __forceinline__ Vec4<T> lds4(const T* p) {
   return r;
 }
 
+// 16-byte (float) or 32-byte (double) vector load through L2 only (data other
+// CTAs of the same launch wrote)
+template <typename T>
+__device__ __forceinline__ Vec4<T> ldcg4(const T* p) {
+  Vec4<T> r;
+  if constexpr (sizeof(T) == 4) {
+    const float4 a = __ldcg(reinterpret_cast<const float4*>(p));
+    r.v[0] = a.x, r.v[1] = a.y, r.v[2] = a.z, r.v[3] = a.w;
+  } else {
+    const double2 a = __ldcg(reinterpret_cast<const double2*>(p));
+    const double2 b = __ldcg(reinterpret_cast<const double2*>(p) + 1);
+    r.v[0] = a.x, r.v[1] = a.y, r.v[2] = b.x, r.v[3] = b.y;
+  }
+  return r;
+}
+
 template <typename T>
 __device__ __forceinline__ void sts4(T* p, const Vec4<T>& r) {
   if constexpr (sizeof(T) == 4) {
@@ -249,7 +265,52 @@ __global__ void __launch_bounds__(256) k_cg_init(CGArgs<T> a, int x_zero, cudaGr
 // TX * TY = nthr * NPT.  Per input plane it reads the (NPT+2) x 3 neighbourhood
 // column by column from shared memory and the 27 packed weights of each of its
 // nodes (kWS per node, 16-byte vector loads).
-template <typename T, int G4, int NPT>
+// Grid-wide barrier of the persistent CG kernel: CTAs add 1 to a counter the
+// host zeroes before the launch; barrier number k completes at k * gridDim.x.
+// All threads call it.  The wait is bounded: false after kGridSpinLimit polls.
+constexpr unsigned kGridSpinLimit = 1u << 25;
+__device__ bool grid_barrier(unsigned* count, unsigned target) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(count, 1u);
+    int ok = 0;
+    for (unsigned i = 0; i < kGridSpinLimit; ++i) {
+      unsigned v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
+      if (v >= target) {
+        ok = 1;
+        break;
+      }
+      __nanosleep(32);
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Orders this thread's earlier generic-proxy global writes before later
+// async-proxy (TMA) reads of the same memory, here or in other CTAs.
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// Thread layout: thread (j, g) owns orbitals o0+4g .. o0+4g+3 of NPT vertically
+// adjacent tile nodes (tx, ty0 .. ty0+NPT-1), tx = j % TX, ty0 = NPT (j / TX);
+// TX * TY = nthr * NPT.  Per input plane it reads the (NPT+2) x 3 neighbourhood
+// column by column from shared memory and the 27 packed weights of each of its
+// nodes (kWS per node, 16-byte vector loads).
+//
+// LOOP false: one operator pass (K1); the last CTA turns (p, q) into alpha.
+// LOOP true:  the whole CG loop in one cooperative launch (one CTA per SM, all
+// co-resident): per iteration the operator pass, a grid barrier, alpha from the
+// per-CTA partials (every CTA sums them in the same fixed order, so all hold
+// identical scalars), the update of the nodes this CTA produced q for, a second
+// barrier, then beta, masks and convergence.  CTA 0 writes the final state back.
+template <typename T, int G4, int NPT, bool LOOP>
 __global__ void __launch_bounds__(k1_max_slots<T, NPT>() * G4) k_cg_q(CGArgs<T> a, K1Geom geo, const __grid_constant__ CUtensorMap mr,
                                                   const __grid_constant__ CUtensorMap mp,
                                                   const __grid_constant__ CUtensorMap md,
@@ -260,6 +321,7 @@ __global__ void __launch_bounds__(k1_max_slots<T, NPT>() * G4) k_cg_q(CGArgs<T> 
   const int HX = TX + 2, HY = geo.TY + 2;
   const int tid = threadIdx.x;
   const int g = tid % G4, j = tid / G4;
+  const int Np = a.Np;
   // shared layout: barriers, kSlots ring slots (r, p, D^-1, W), then reduction space
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
   unsigned char* base = smem + 128;
@@ -267,12 +329,21 @@ __global__ void __launch_bounds__(k1_max_slots<T, NPT>() * G4) k_cg_q(CGArgs<T> 
   auto slotP = [&](int s) { return reinterpret_cast<T*>(base + (size_t)s * geo.slot_bytes + geo.off_p); };
   auto slotD = [&](int s) { return reinterpret_cast<T*>(base + (size_t)s * geo.slot_bytes + geo.off_d); };
   auto slotW = [&](int s) { return reinterpret_cast<T*>(base + (size_t)s * geo.slot_bytes + geo.off_w); };
-  double* sacc = reinterpret_cast<double*>(base + (size_t)kSlots * geo.slot_bytes);  // [Np]
-  double* sred = sacc + a.Np;                                                       // [nthr][bw]
+  double* sacc = reinterpret_cast<double*>(base + (size_t)kSlots * geo.slot_bytes);  // [2 Np]
+  // per-orbital CG state of the persistent loop (identical in every CTA)
+  double* st_rz = sacc + 2 * Np;
+  double* st_bb = st_rz + Np;
+  double* st_al = st_bb + Np;
+  double* st_be = st_al + Np;
+  int* st_act = reinterpret_cast<int*>(st_be + Np);
+  int* st_it = st_act + Np;
+  double* sred = reinterpret_cast<double*>(st_it + Np + (Np & 1));  // block sums [nthr][2 bw] and totals
   const int nthr = geo.nthr;
   __shared__ T sbeta[kMaxN];
+  __shared__ T salpha[kMaxN];
   __shared__ int sact[kMaxN / 4];
   __shared__ int sblk[kMaxN / 4];
+  __shared__ int s_nact;
 
   // Static split of the column-planes over the CTAs: f = ((ob*ncy + ty)*ncx + tx)*nzo + (z - 1),
   // CTA c takes [F c / G, F (c+1) / G) as runs of consecutive output planes of one column.
@@ -288,17 +359,13 @@ __global__ void __launch_bounds__(k1_max_slots<T, NPT>() * G4) k_cg_q(CGArgs<T> 
     prefetch_tmap(&md);
     prefetch_tmap(&mw);
   }
-  for (int o = tid; o < a.Np; o += blockDim.x) {
-    sacc[o] = 0.0;
-    sbeta[o] = (T)a.st->beta[o];
-  }
-  for (int q = tid; q < a.Np / 4; q += blockDim.x)
-    sact[q] = a.st->active[4 * q] | a.st->active[4 * q + 1] | a.st->active[4 * q + 2] | a.st->active[4 * q + 3];
-  __syncthreads();
-  for (int ob = tid; ob < geo.nob; ob += blockDim.x) {
-    int any = 0;
-    for (int q = ob * G4; q < ob * G4 + G4 && q < a.Np / 4; ++q) any |= sact[q];
-    sblk[ob] = any;
+  for (int o = tid; o < Np; o += blockDim.x) {
+    st_rz[o] = a.st->rz[o];
+    st_bb[o] = a.st->bb[o];
+    st_al[o] = 0.0;
+    st_be[o] = a.st->beta[o];
+    st_act[o] = a.st->active[o];
+    st_it[o] = a.st->iters[o];
   }
   __syncthreads();
 
@@ -353,8 +420,6 @@ __global__ void __launch_bounds__(k1_max_slots<T, NPT>() * G4) k_cg_q(CGArgs<T> 
       lhave = false;
     }
   };
-  if (tid == 0)
-    for (int k = 0; k < kSlots; ++k) issue_next();
 
   // this thread's nodes and its fixed shared-memory offsets (elements)
   const int tx = j % TX, ty0 = NPT * (j / TX);
@@ -379,174 +444,420 @@ __global__ void __launch_bounds__(k1_max_slots<T, NPT>() * G4) k_cg_q(CGArgs<T> 
   }
   const long long plane = (long long)a.g.Px * a.g.Py;
 
-  int cstep = 0;    // consumer steps done
-  int cur_o0 = -1;  // orbital block the dot partials below belong to
-  T dot[4] = {0, 0, 0, 0};
+  int cstep = 0;  // consumer steps done (the ring's phases run on across iterations)
   bool timed_out = false;
-  auto flush_dots = [&](int o0) {
-    // per-thread partial sums are in the kernel's precision (float64 arithmetic is
-    // ~1/56 of float32 on this GPU); the block and cross-CTA sums are float64
-#pragma unroll
-    for (int c = 0; c < 4; ++c) sred[j * bw + 4 * g + c] = (double)dot[c];
+  unsigned bar_no = 0;  // grid barriers passed
+
+  // Fixed-order per-orbital sums of the per-thread partials of one orbital block
+  // into sacc[k Np + o0 ..] (K values per orbital: sred is [nthr][K bw]).
+  auto flush_sums = [&](int o0, int K) {
     __syncthreads();
-    double* ctmp = sred + nthr * bw;
-    block_colsum(sred, nthr, bw, ctmp);
-    for (int o = tid; o < bw && o0 + o < a.Np; o += blockDim.x) sacc[o0 + o] += ctmp[o];
+    double* ctmp = sred + nthr * K * bw;
+    block_colsum(sred, nthr, K * bw, ctmp);
+    for (int t = tid; t < K * bw; t += blockDim.x) {
+      const int k = t / bw, o = t % bw;
+      if (o0 + o < Np) sacc[k * Np + o0 + o] += ctmp[t];
+    }
     __syncthreads();
+  };
+  auto flush1 = [&](int o0, const T (&v)[4]) {
 #pragma unroll
-    for (int c = 0; c < 4; ++c) dot[c] = 0;
+    for (int c = 0; c < 4; ++c) sred[j * bw + 4 * g + c] = (double)v[c];
+    flush_sums(o0, 1);
+  };
+  auto flush2 = [&](int o0, const T (&v)[8]) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) sred[j * 2 * bw + k * bw + 4 * g + c] = (double)v[k * 4 + c];
+    flush_sums(o0, 2);
   };
 
-  for (long long f = fbeg; f < fend;) {
-    int o0, x0, y0, z0, z1;
-    seg_at(f, o0, x0, y0, z0, z1);
-    f += z1 - z0;
-    if (!sblk[o0 / bw]) continue;
-    if (o0 != cur_o0) {
-      if (cur_o0 >= 0) flush_dots(cur_o0);
-      cur_o0 = o0;
-    }
-    // a ragged last block: groups at orbitals >= Np are staged as zeros and never stored
-    const bool gact = (o0 + 4 * g < a.Np) && sact[o0 / 4 + g] != 0;
-    T be[4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) be[c] = gact ? sbeta[o0 + 4 * g + c] : T(0);
-    // output node columns of this thread (-1: outside the interior)
-    long long col[NPT];
-#pragma unroll
-    for (int k = 0; k < NPT; ++k) {
-      const int x = x0 + tx, y = y0 + ty0 + k;
-      col[k] = (x <= a.g.nx - 1 && y <= a.g.ny - 1) ? (long long)y * a.g.Px + x : -1;
-    }
-    // Rolling accumulators of the three output planes an input plane touches:
-    // aD = output s-1 (completed at step s), aC = output s, aU = output s+1.
-    Vec4<T> aD[NPT], aC[NPT], aU[NPT], pcPrev[NPT], pcCur[NPT];
-#pragma unroll
-    for (int k = 0; k < NPT; ++k) aD[k] = aC[k] = aU[k] = pcPrev[k] = pcCur[k] = Vec4<T>{};
-    for (int s = z0 - 1; s <= z1; ++s) {
-      const int slot = cstep % kSlots;
-      const uint32_t par = (cstep / kSlots) & 1;
-      const bool ok = mbar_wait(&bars[slot], par);
-      if (gact) {
-        // p_new = D^-1 r + beta p_old on tile + halo, in place
-        const T* D = slotD(slot);
-        T* P = slotP(slot);
-        const T* R = slotR(slot);
-#pragma unroll
-        for (int i = 0; i < kPnMax; ++i) {
-          if (i < pn_cnt) {
-            const T di = D[pn_d[i]];
-            const Vec4<T> rv = lds4(R + pn_h[i]);
-            Vec4<T> pv = lds4(P + pn_h[i]);
-#pragma unroll
-            for (int c = 0; c < 4; ++c) pv.v[c] = pnew<T>(di, rv.v[c], be[c], pv.v[c]);
-            sts4(P + pn_h[i], pv);
-          }
-        }
-        // these generic-proxy writes precede the TMA write that later refills the slot
-        fence_proxy_async_smem();
-      }
-      if (__syncthreads_or(!ok)) {
-        timed_out = true;
-        goto bail;
-      }
-      // every thread is past step cstep-1: refill its slot
-      if (tid == 0 && cstep > 0) issue_next();
-      if (gact) {
-        const T* P = slotP(slot) + poff;
-        const T* Wn = slotW(slot) + woff;
-        Vec4<T> w[NPT][7];
-#pragma unroll
-        for (int k = 0; k < NPT; ++k)
-#pragma unroll
-          for (int q = 0; q < 7; ++q) w[k][q] = lds4(Wn + k * TX * kWS + 4 * q);
-#pragma unroll
-        for (int cx = 0; cx < 3; ++cx) {
-          Vec4<T> v[NPT + 2];
-#pragma unroll
-          for (int r = 0; r < NPT + 2; ++r) v[r] = lds4(P + r * hstep + cx * bw);
-#pragma unroll
-          for (int k = 0; k < NPT; ++k) {
-#pragma unroll
-            for (int cy = 0; cy < 3; ++cy) {
-              const int o = cy * 3 + cx;
-              const T wu = w[k][o / 4].v[o % 4];                // dz = -1 of output s+1
-              const T wc = w[k][(9 + o) / 4].v[(9 + o) % 4];    // dz =  0 of output s
-              const T wd = w[k][(18 + o) / 4].v[(18 + o) % 4];  // dz = +1 of output s-1
-              const Vec4<T>& pv = v[k + cy];
-#pragma unroll
-              for (int c = 0; c < 4; ++c) {
-                aU[k].v[c] = fmaT(wu, pv.v[c], aU[k].v[c]);
-                aC[k].v[c] = fmaT(wc, pv.v[c], aC[k].v[c]);
-                aD[k].v[c] = fmaT(wd, pv.v[c], aD[k].v[c]);
-              }
-              if (cy == 1 && cx == 1) pcCur[k] = pv;
-            }
-          }
-        }
-        // output s-1 is complete
-        const int tz = s - 1;
-        if (tz >= z0 && tz < z1) {
-#pragma unroll
-          for (int k = 0; k < NPT; ++k) {
-            if (col[k] >= 0) {
-#pragma unroll
-              for (int c = 0; c < 4; ++c) dot[c] = fmaT(pcPrev[k].v[c], aD[k].v[c], dot[c]);
-              sts4(a.q + ((long long)tz * plane + col[k]) * a.Np + o0 + 4 * g, aD[k]);
-            }
-          }
-        }
-#pragma unroll
-        for (int k = 0; k < NPT; ++k) {
-          aD[k] = aC[k];
-          aC[k] = aU[k];
-          aU[k] = Vec4<T>{};
-          pcPrev[k] = pcCur[k];
-        }
-      }
-      ++cstep;
-    }
-  }
-  if (cur_o0 >= 0) flush_dots(cur_o0);
-bail:
-  if (timed_out) {
+  // ---- operator pass: q = A p_new over this CTA's segments, (p_new, q) into sacc[0 .. Np) ----
+  auto phase_q = [&]() -> bool {
+    for (int o = tid; o < 2 * Np; o += blockDim.x) sacc[o] = 0.0;
+    lf = fbeg;
+    lhave = false;
+    // every issued copy was consumed by the previous pass: the ring starts empty
+    const int c_start = cstep;
     if (tid == 0) {
-      atomicOr(&a.st->status, kStatTimeout);
-      // wait (bounded) for copies still in flight before the CTA's shared memory goes away
-      for (int k = cstep; k < lstep; ++k) mbar_wait(&bars[k % kSlots], (k / kSlots) & 1);
+      fence_proxy_async_global();
+      for (int k = 0; k < kSlots; ++k) issue_next();
+    }
+    int cur_o0 = -1;
+    T dot[4] = {0, 0, 0, 0};
+    for (long long f = fbeg; f < fend;) {
+      int o0, x0, y0, z0, z1;
+      seg_at(f, o0, x0, y0, z0, z1);
+      f += z1 - z0;
+      if (!sblk[o0 / bw]) continue;
+      if (o0 != cur_o0) {
+        if (cur_o0 >= 0) {
+          flush1(cur_o0, dot);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) dot[c] = 0;
+        }
+        cur_o0 = o0;
+      }
+      // a ragged last block: groups at orbitals >= Np are staged as zeros and never stored
+      const bool gact = (o0 + 4 * g < Np) && sact[o0 / 4 + g] != 0;
+      T be[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) be[c] = gact ? sbeta[o0 + 4 * g + c] : T(0);
+      // output node columns of this thread (-1: outside the interior)
+      long long col[NPT];
+#pragma unroll
+      for (int k = 0; k < NPT; ++k) {
+        const int x = x0 + tx, y = y0 + ty0 + k;
+        col[k] = (x <= a.g.nx - 1 && y <= a.g.ny - 1) ? (long long)y * a.g.Px + x : -1;
+      }
+      // Rolling accumulators of the three output planes an input plane touches:
+      // aD = output s-1 (completed at step s), aC = output s, aU = output s+1.
+      Vec4<T> aD[NPT], aC[NPT], aU[NPT], pcPrev[NPT], pcCur[NPT];
+#pragma unroll
+      for (int k = 0; k < NPT; ++k) aD[k] = aC[k] = aU[k] = pcPrev[k] = pcCur[k] = Vec4<T>{};
+      for (int s = z0 - 1; s <= z1; ++s) {
+        const int slot = cstep % kSlots;
+        const uint32_t par = (cstep / kSlots) & 1;
+        const bool ok = mbar_wait(&bars[slot], par);
+        if (gact) {
+          // p_new = D^-1 r + beta p_old on tile + halo, in place
+          const T* D = slotD(slot);
+          T* P = slotP(slot);
+          const T* R = slotR(slot);
+#pragma unroll
+          for (int i = 0; i < kPnMax; ++i) {
+            if (i < pn_cnt) {
+              const T di = D[pn_d[i]];
+              const Vec4<T> rv = lds4(R + pn_h[i]);
+              Vec4<T> pv = lds4(P + pn_h[i]);
+#pragma unroll
+              for (int c = 0; c < 4; ++c) pv.v[c] = pnew<T>(di, rv.v[c], be[c], pv.v[c]);
+              sts4(P + pn_h[i], pv);
+            }
+          }
+          // these generic-proxy writes precede the TMA write that later refills the slot
+          fence_proxy_async_smem();
+        }
+        if (__syncthreads_or(!ok)) return false;
+        // every thread is past step cstep-1: refill its slot (not at the first step of
+        // the pass, whose predecessor's slot holds this pass's fourth copy)
+        if (tid == 0 && cstep > c_start) issue_next();
+        if (gact) {
+          const T* P = slotP(slot) + poff;
+          const T* Wn = slotW(slot) + woff;
+          Vec4<T> w[NPT][7];
+#pragma unroll
+          for (int k = 0; k < NPT; ++k)
+#pragma unroll
+            for (int q = 0; q < 7; ++q) w[k][q] = lds4(Wn + k * TX * kWS + 4 * q);
+#pragma unroll
+          for (int cx = 0; cx < 3; ++cx) {
+            Vec4<T> v[NPT + 2];
+#pragma unroll
+            for (int r = 0; r < NPT + 2; ++r) v[r] = lds4(P + r * hstep + cx * bw);
+#pragma unroll
+            for (int k = 0; k < NPT; ++k) {
+#pragma unroll
+              for (int cy = 0; cy < 3; ++cy) {
+                const int o = cy * 3 + cx;
+                const T wu = w[k][o / 4].v[o % 4];                // dz = -1 of output s+1
+                const T wc = w[k][(9 + o) / 4].v[(9 + o) % 4];    // dz =  0 of output s
+                const T wd = w[k][(18 + o) / 4].v[(18 + o) % 4];  // dz = +1 of output s-1
+                const Vec4<T>& pv = v[k + cy];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                  aU[k].v[c] = fmaT(wu, pv.v[c], aU[k].v[c]);
+                  aC[k].v[c] = fmaT(wc, pv.v[c], aC[k].v[c]);
+                  aD[k].v[c] = fmaT(wd, pv.v[c], aD[k].v[c]);
+                }
+                if (cy == 1 && cx == 1) pcCur[k] = pv;
+              }
+            }
+          }
+          // output s-1 is complete
+          const int tz = s - 1;
+          if (tz >= z0 && tz < z1) {
+#pragma unroll
+            for (int k = 0; k < NPT; ++k) {
+              if (col[k] >= 0) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) dot[c] = fmaT(pcPrev[k].v[c], aD[k].v[c], dot[c]);
+                sts4(a.q + ((long long)tz * plane + col[k]) * Np + o0 + 4 * g, aD[k]);
+              }
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < NPT; ++k) {
+            aD[k] = aC[k];
+            aC[k] = aU[k];
+            aU[k] = Vec4<T>{};
+            pcPrev[k] = pcCur[k];
+          }
+        }
+        ++cstep;
+      }
+    }
+    if (cur_o0 >= 0) flush1(cur_o0, dot);
+    return true;
+  };
+
+  // refresh the shared copies of the masks and beta from the per-orbital state
+  auto load_masks = [&]() {
+    for (int o = tid; o < Np; o += blockDim.x) sbeta[o] = (T)st_be[o];
+    for (int q = tid; q < Np / 4; q += blockDim.x)
+      sact[q] = st_act[4 * q] | st_act[4 * q + 1] | st_act[4 * q + 2] | st_act[4 * q + 3];
+    __syncthreads();
+    for (int ob = tid; ob < geo.nob; ob += blockDim.x) {
+      int any = 0;
+      for (int q = ob * G4; q < ob * G4 + G4 && q < Np / 4; ++q) any |= sact[q];
+      sblk[ob] = any;
     }
     __syncthreads();
-  }
-  for (int o = tid; o < a.Np; o += blockDim.x) a.part[(long long)blockIdx.x * a.Np + o] = sacc[o];
-  if (!last_cta(&a.st->ticket)) return;
-  double* tot = sred;
-  double* scratch = sred + a.Np;
-  reduce_over_ctas<1>(a.part, gridDim.x, a.Np, scratch, tot);
-  if (tid == 0) {
-    unsigned long long w = 0;
-    for (int q4 = 0; q4 < a.Np / 4; ++q4)
-      if (sact[q4]) w += 4ull * a.g.nI;
-    a.st->work += w;
-  }
-  for (int o = tid; o < a.Np; o += blockDim.x) {
-    double pq = tot[o];
-    a.st->pq[o] = pq;
-    double alpha = 0.0;
-    if (a.st->active[o]) {
-      if (!isfinite(pq)) {
-        atomicOr(&a.st->status, kStatNonFinite);
-        a.st->active[o] = 0;
-      } else if (!(pq > 0.0)) {
-        atomicOr(&a.st->status, kStatNotSPD);
-        a.st->active[o] = 0;
-      } else {
-        alpha = a.st->rz[o] / pq;
+  };
+
+  if constexpr (!LOOP) {
+    // ---- one operator pass (K1), then alpha in the last CTA ----
+    load_masks();
+    if (!phase_q()) timed_out = true;
+    if (timed_out) {
+      if (tid == 0) {
+        atomicOr(&a.st->status, kStatTimeout);
+        // wait (bounded) for copies still in flight before the CTA's shared memory goes away
+        for (int k = cstep; k < lstep; ++k) mbar_wait(&bars[k % kSlots], (k / kSlots) & 1);
       }
+      __syncthreads();
     }
-    a.st->alpha[o] = alpha;
+    for (int o = tid; o < Np; o += blockDim.x) a.part[(long long)blockIdx.x * Np + o] = sacc[o];
+    if (!last_cta(&a.st->ticket)) return;
+    double* tot = sred;
+    double* scratch = sred + Np;
+    reduce_over_ctas<1>(a.part, gridDim.x, Np, scratch, tot);
+    if (tid == 0) {
+      unsigned long long w = 0, wn = 0;
+      for (int q4 = 0; q4 < Np / 4; ++q4)
+        if (sact[q4]) w += 4ull * a.g.nI;
+      for (int ob = 0; ob < geo.nob; ++ob)
+        if (sblk[ob]) wn += (unsigned long long)a.g.nI;
+      a.st->work += w;
+      a.st->work_nodes += wn;
+    }
+    for (int o = tid; o < Np; o += blockDim.x) {
+      double pq = tot[o];
+      a.st->pq[o] = pq;
+      double alpha = 0.0;
+      if (a.st->active[o]) {
+        if (!isfinite(pq)) {
+          atomicOr(&a.st->status, kStatNonFinite);
+          a.st->active[o] = 0;
+        } else if (!(pq > 0.0)) {
+          atomicOr(&a.st->status, kStatNotSPD);
+          a.st->active[o] = 0;
+        } else {
+          alpha = a.st->rz[o] / pq;
+        }
+      }
+      a.st->alpha[o] = alpha;
+    }
+    __syncthreads();
+    if (tid == 0) a.st->ticket = 0u;
+  } else {
+    // ---- the whole CG loop ----
+    const double tol = a.st->tol;
+    const int maxit = a.st->maxit;
+    double* part1 = a.part;                                  // [G][Np]
+    double* part2 = a.part + (long long)gridDim.x * Np;      // [2][G][Np]
+    double* tot = sred;                                      // [2 Np] totals, then slices
+    double* scratch = sred + 2 * Np;
+    int status = 0;
+    for (;;) {
+      if (tid == 0) s_nact = 0;
+      __syncthreads();
+      for (int o = tid; o < Np; o += blockDim.x)
+        if (st_act[o]) atomicAdd(&s_nact, 1);
+      __syncthreads();
+      if (s_nact == 0) break;
+      load_masks();
+      if (blockIdx.x == 0 && tid == 0) {
+        unsigned long long w = 0, wn = 0;
+        for (int q4 = 0; q4 < Np / 4; ++q4)
+          if (sact[q4]) w += 4ull * a.g.nI;
+        for (int ob = 0; ob < geo.nob; ++ob)
+          if (sblk[ob]) wn += (unsigned long long)a.g.nI;
+        a.st->work += w;
+        a.st->work_nodes += wn;
+      }
+      // operator pass and the per-CTA partial (p, q)
+      if (!phase_q()) {
+        timed_out = true;
+        break;
+      }
+      for (int o = tid; o < Np; o += blockDim.x) part1[(long long)blockIdx.x * Np + o] = sacc[o];
+      if (!grid_barrier(&a.st->bar_count, ++bar_no * gridDim.x)) {
+        timed_out = true;
+        break;
+      }
+      // alpha (identical in every CTA)
+      reduce_over_ctas<1>(part1, gridDim.x, Np, scratch, tot);
+      for (int o = tid; o < Np; o += blockDim.x) {
+        const double pq = tot[o];
+        double alpha = 0.0;
+        if (st_act[o]) {
+          if (!isfinite(pq)) {
+            status |= kStatNonFinite;
+            st_act[o] = 0;
+          } else if (!(pq > 0.0)) {
+            status |= kStatNotSPD;
+            st_act[o] = 0;
+          } else {
+            alpha = st_rz[o] / pq;
+          }
+        }
+        st_al[o] = alpha;
+        salpha[o] = (T)alpha;
+      }
+      __syncthreads();
+      // update of this CTA's nodes: p = D^-1 r + beta p, x += alpha p, r -= alpha q
+      for (int o = tid; o < 2 * Np; o += blockDim.x) sacc[o] = 0.0;
+      __syncthreads();
+      {
+        int cur_o0 = -1;
+        T acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // (r, D^-1 r) x4, (r, r) x4
+        for (long long f = fbeg; f < fend;) {
+          int o0, x0, y0, z0, z1;
+          seg_at(f, o0, x0, y0, z0, z1);
+          f += z1 - z0;
+          if (!sblk[o0 / bw]) continue;
+          if (o0 != cur_o0) {
+            if (cur_o0 >= 0) {
+              flush2(cur_o0, acc);
+#pragma unroll
+              for (int c = 0; c < 8; ++c) acc[c] = 0;
+            }
+            cur_o0 = o0;
+          }
+          const bool gact = (o0 + 4 * g < Np) && sact[o0 / 4 + g] != 0;
+          if (!gact) continue;
+          T al[4], be[4];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            al[c] = salpha[o0 + 4 * g + c];
+            be[c] = sbeta[o0 + 4 * g + c];
+          }
+#pragma unroll
+          for (int k = 0; k < NPT; ++k) {
+            const int x = x0 + tx, y = y0 + ty0 + k;
+            if (x > a.g.nx - 1 || y > a.g.ny - 1) continue;
+            const long long colnode = (long long)y * a.g.Px + x;
+            int z = z0;
+            for (; z + 1 < z1; z += 2) {
+              const long long n0 = (long long)z * plane + colnode, n1 = n0 + plane;
+              const long long e0 = n0 * Np + o0 + 4 * g, e1 = n1 * Np + o0 + 4 * g;
+              Vec4<T> xv0 = ldcg4(a.x + e0), r0 = ldcg4(a.r + e0), p0 = ldcg4(a.p + e0), q0 = ldcg4(a.q + e0);
+              Vec4<T> xv1 = ldcg4(a.x + e1), r1 = ldcg4(a.r + e1), p1 = ldcg4(a.p + e1), q1 = ldcg4(a.q + e1);
+              const T d0 = __ldcg(a.dinv + n0), d1 = __ldcg(a.dinv + n1);
+#pragma unroll
+              for (int c = 0; c < 4; ++c) {
+                p0.v[c] = pnew<T>(d0, r0.v[c], be[c], p0.v[c]);
+                xv0.v[c] = fmaT(al[c], p0.v[c], xv0.v[c]);
+                r0.v[c] = fmaT(-al[c], q0.v[c], r0.v[c]);
+                acc[c] = fmaT(r0.v[c], d0 * r0.v[c], acc[c]);
+                acc[4 + c] = fmaT(r0.v[c], r0.v[c], acc[4 + c]);
+                p1.v[c] = pnew<T>(d1, r1.v[c], be[c], p1.v[c]);
+                xv1.v[c] = fmaT(al[c], p1.v[c], xv1.v[c]);
+                r1.v[c] = fmaT(-al[c], q1.v[c], r1.v[c]);
+                acc[c] = fmaT(r1.v[c], d1 * r1.v[c], acc[c]);
+                acc[4 + c] = fmaT(r1.v[c], r1.v[c], acc[4 + c]);
+              }
+              sts4(a.x + e0, xv0);
+              sts4(a.r + e0, r0);
+              sts4(a.p + e0, p0);
+              sts4(a.x + e1, xv1);
+              sts4(a.r + e1, r1);
+              sts4(a.p + e1, p1);
+            }
+            if (z < z1) {
+              const long long n0 = (long long)z * plane + colnode;
+              const long long e0 = n0 * Np + o0 + 4 * g;
+              Vec4<T> xv0 = ldcg4(a.x + e0), r0 = ldcg4(a.r + e0), p0 = ldcg4(a.p + e0), q0 = ldcg4(a.q + e0);
+              const T d0 = __ldcg(a.dinv + n0);
+#pragma unroll
+              for (int c = 0; c < 4; ++c) {
+                p0.v[c] = pnew<T>(d0, r0.v[c], be[c], p0.v[c]);
+                xv0.v[c] = fmaT(al[c], p0.v[c], xv0.v[c]);
+                r0.v[c] = fmaT(-al[c], q0.v[c], r0.v[c]);
+                acc[c] = fmaT(r0.v[c], d0 * r0.v[c], acc[c]);
+                acc[4 + c] = fmaT(r0.v[c], r0.v[c], acc[4 + c]);
+              }
+              sts4(a.x + e0, xv0);
+              sts4(a.r + e0, r0);
+              sts4(a.p + e0, p0);
+            }
+          }
+        }
+        if (cur_o0 >= 0) flush2(cur_o0, acc);
+      }
+      // the next operator pass reads r and p through the async proxy (TMA)
+      fence_proxy_async_global();
+      for (int o = tid; o < Np; o += blockDim.x) {
+        part2[(long long)blockIdx.x * Np + o] = sacc[o];
+        part2[((long long)gridDim.x + blockIdx.x) * Np + o] = sacc[Np + o];
+      }
+      if (!grid_barrier(&a.st->bar_count, ++bar_no * gridDim.x)) {
+        timed_out = true;
+        break;
+      }
+      // beta, masks, counts (identical in every CTA)
+      reduce_over_ctas<2>(part2, gridDim.x, Np, scratch, tot);
+      for (int o = tid; o < Np; o += blockDim.x) {
+        double beta = 0.0;
+        if (st_act[o]) {
+          const double rz = tot[o], rr = tot[Np + o];
+          const int it = st_it[o] + 1;
+          st_it[o] = it;
+          if (blockIdx.x == 0) a.st->rr[o] = rr;
+          bool act = true;
+          if (!(isfinite(rz) && isfinite(rr))) {
+            status |= kStatNonFinite;
+            act = false;
+          } else if (rr <= tol * tol * st_bb[o]) {
+            act = false;
+          } else if (!(rz > 0.0)) {
+            status |= kStatNotSPD;
+            act = false;
+          } else if (it >= maxit) {
+            status |= kStatNotConverged;
+            act = false;
+          }
+          if (act) beta = rz / st_rz[o];
+          st_rz[o] = rz;
+          st_act[o] = act ? 1 : 0;
+        }
+        st_be[o] = beta;
+      }
+      __syncthreads();
+    }
+    if (timed_out && tid == 0) {
+      atomicOr(&a.st->status, kStatTimeout);
+      for (int k = cstep; k < lstep; ++k) mbar_wait(&bars[k % kSlots], (k / kSlots) & 1);
+    }
+    if (status && blockIdx.x == 0) atomicOr(&a.st->status, status);
+    __syncthreads();
+    if (blockIdx.x == 0) {
+      if (tid == 0) s_nact = 0;
+      __syncthreads();
+      for (int o = tid; o < Np; o += blockDim.x) {
+        a.st->rz[o] = st_rz[o];
+        a.st->alpha[o] = st_al[o];
+        a.st->beta[o] = st_be[o];
+        a.st->active[o] = st_act[o];
+        a.st->iters[o] = st_it[o];
+        if (st_act[o]) atomicAdd(&s_nact, 1);
+      }
+      __syncthreads();
+      if (tid == 0) a.st->n_active = s_nact;
+    }
   }
-  __syncthreads();
-  if (tid == 0) a.st->ticket = 0u;
 }
 
 // ---------------------------------------------------------------------------
@@ -686,29 +997,29 @@ __global__ void __launch_bounds__(kUpdThreads, 1) k_cg_upd(CGArgs<T> a, cudaGrap
   }
 }
 
-template <typename T, int NPT>
+template <typename T, int NPT, bool LOOP>
 void* k1_fn_n(int G4) {
   switch (G4) {
-    case 1: return (void*)k_cg_q<T, 1, NPT>;
-    case 2: return (void*)k_cg_q<T, 2, NPT>;
-    case 3: return (void*)k_cg_q<T, 3, NPT>;
-    case 4: return (void*)k_cg_q<T, 4, NPT>;
-    case 5: return (void*)k_cg_q<T, 5, NPT>;
-    case 6: return (void*)k_cg_q<T, 6, NPT>;
-    case 7: return (void*)k_cg_q<T, 7, NPT>;
-    case 8: return (void*)k_cg_q<T, 8, NPT>;
+    case 1: return (void*)k_cg_q<T, 1, NPT, LOOP>;
+    case 2: return (void*)k_cg_q<T, 2, NPT, LOOP>;
+    case 3: return (void*)k_cg_q<T, 3, NPT, LOOP>;
+    case 4: return (void*)k_cg_q<T, 4, NPT, LOOP>;
+    case 5: return (void*)k_cg_q<T, 5, NPT, LOOP>;
+    case 6: return (void*)k_cg_q<T, 6, NPT, LOOP>;
+    case 7: return (void*)k_cg_q<T, 7, NPT, LOOP>;
+    case 8: return (void*)k_cg_q<T, 8, NPT, LOOP>;
   }
   return nullptr;
 }
 
 // float: two nodes per thread on 16 x 8 tiles, one on the others; float64 one node
-// per thread (two would hold 112 weight registers)
+// per thread (two would hold 112 weight registers).  loop: the persistent CG kernel.
 template <typename T>
-void* k1_fn(int G4, int npt) {
+void* k1_fn(int G4, int npt, bool loop = false) {
   if constexpr (sizeof(T) == 4) {
-    if (npt == 2) return k1_fn_n<T, 2>(G4);
+    if (npt == 2) return loop ? k1_fn_n<T, 2, true>(G4) : k1_fn_n<T, 2, false>(G4);
   }
-  if (npt == 1) return k1_fn_n<T, 1>(G4);
+  if (npt == 1) return loop ? k1_fn_n<T, 1, true>(G4) : k1_fn_n<T, 1, false>(G4);
   return nullptr;
 }
 
@@ -752,10 +1063,13 @@ void k1_layout(int Np, int bw, int TX, int TY, int npt, K1Geom* G) {
   G->tx_bytes = (uint32_t)(2 * vec + dv + wv);
   // sacc[Np], then the per-segment block sums [nthr][bw], reused at the end for the
   // cross-CTA totals [Np] and slices (at most max(threads, Np) values)
+  // sacc [2 Np], the persistent loop's per-orbital state (5 Np doubles), then the
+  // block sums [nthr][2 bw] with their column-sum slices, reused for the
+  // cross-CTA totals [2 Np] and slices (at most max(threads, 2 Np) values)
   const size_t nthr = (size_t)G->nthr * (bw / 4);
-  const size_t fin = (size_t)Np + (nthr > (size_t)Np ? nthr : (size_t)Np);
-  const size_t blk = (size_t)G->nthr * bw + nthr;  // block sums and the column-sum slices
-  size_t red = ((size_t)Np + (blk > fin ? blk : fin)) * sizeof(double);
+  const size_t fin = (size_t)2 * Np + (nthr > (size_t)2 * Np ? nthr : (size_t)2 * Np);
+  const size_t blk = (size_t)G->nthr * 2 * bw + nthr;
+  size_t red = ((size_t)7 * Np + (blk > fin ? blk : fin)) * sizeof(double);
   G->smem = 128 + (size_t)kSlots * G->slot_bytes + red;
 }
 
@@ -763,7 +1077,7 @@ template <typename T>
 cudaError_t cg_plan_geometry(const Grid& g, int Np, int nsm, K1Geom* geo, int* bw_out) {
   const int sz = (int)sizeof(T);
   // static shared memory of K1 (beta, group masks, flags) and the opt-in limit
-  const size_t stat = (size_t)kMaxN * sz + 2 * (kMaxN / 4) * sizeof(int) + 64;
+  const size_t stat = (size_t)2 * kMaxN * sz + 2 * (kMaxN / 4) * sizeof(int) + 64;
   const size_t limit = 227 * 1024 - stat - 1024;
   const int cap = 32;  // widest orbital block (G4 <= 8)
   // Tile shapes (TX, TY, nodes per thread).  float: 16 x 8 with one node per thread
@@ -801,14 +1115,18 @@ cudaError_t cg_plan_geometry(const Grid& g, int Np, int nsm, K1Geom* geo, int* b
   G.ncx = (g.nx - 1 + G.TX - 1) / G.TX;
   G.ncy = (g.ny - 1 + G.TY - 1) / G.TY;
   const int nob = (Np + bw - 1) / bw;
-  int per_sm = 1;
-  void* f1 = k1_fn<T>(G.G4, G.npt);
-  if (f1 && cudaFuncSetAttribute(f1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G.smem) == cudaSuccess) {
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f1, G.nthr * G.G4, G.smem) == cudaSuccess && nb > 0)
-      per_sm = nb;
+  // CTAs per SM: the smaller occupancy of the single-pass and the persistent
+  // kernels, so the persistent grid is always co-resident
+  int per_sm = 4;
+  for (int loop = 0; loop < 2; ++loop) {
+    void* f = k1_fn<T>(G.G4, G.npt, loop != 0);
+    int nb = 1;
+    if (f && cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G.smem) == cudaSuccess) {
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, G.nthr * G.G4, G.smem) != cudaSuccess || nb < 1)
+        nb = 1;
+    }
+    if (nb < per_sm) per_sm = nb;
   }
-  if (per_sm > 4) per_sm = 4;
   G.nob = nob;
   // every CTA takes an equal share of the nob*ncx*ncy*(nz-1) column-planes, at least 4 of them
   // (each run of planes stages 2 halo planes)
@@ -853,9 +1171,19 @@ cudaError_t cg_prepare(CGPlan<T>* P) {
     if ((e = encode_tiled(&P->mw, ty, 4, (void*)P->wcoef, dims, str, box)) != cudaSuccess) return e;
   }
   void* f1 = k1_fn<T>(G.G4, G.npt);
-  if (!f1) return cudaErrorInvalidValue;
+  void* fl = k1_fn<T>(G.G4, G.npt, true);
+  if (!f1 || !fl) return cudaErrorInvalidValue;
   if ((e = cudaFuncSetAttribute(f1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G.smem)) != cudaSuccess)
     return e;
+  if ((e = cudaFuncSetAttribute(fl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G.smem)) != cudaSuccess)
+    return e;
+  {
+    int nb = 0, dev = 0, coop = 0;
+    P->coop_ok = cudaGetDevice(&dev) == cudaSuccess &&
+                 cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
+                 cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fl, G.nthr * G.G4, G.smem) == cudaSuccess &&
+                 (long long)nb * P->nsm >= G.grid;
+  }
   // streaming kernels: threads a multiple of Np/4
   const int G4f = a.Np / 4;
   int nt = (256 / G4f) * G4f;
@@ -975,7 +1303,21 @@ template cudaError_t cg_launch_init<float>(CGPlan<float>*, cudaStream_t, bool);
 template cudaError_t cg_launch_init<double>(CGPlan<double>*, cudaStream_t, bool);
 template cudaError_t cg_launch_k1<float>(CGPlan<float>*, cudaStream_t);
 template cudaError_t cg_launch_k1<double>(CGPlan<double>*, cudaStream_t);
+template <typename T>
+cudaError_t cg_launch_loop(CGPlan<T>* P, cudaStream_t st) {
+  CGArgs<T> a = P->args;
+  a.in_graph = 0;
+  K1Geom geo = P->geo;
+  cudaError_t e = cudaMemsetAsync(&a.st->bar_count, 0, sizeof(unsigned int), st);
+  if (e != cudaSuccess) return e;
+  void* args[] = {&a, &geo, &P->mr, &P->mp, &P->md, &P->mw};
+  return cudaLaunchCooperativeKernel(k1_fn<T>(geo.G4, geo.npt, true), dim3(geo.grid), dim3(geo.nthr * geo.G4), args,
+                                     geo.smem, st);
+}
+
 template cudaError_t cg_launch_k2<float>(CGPlan<float>*, cudaStream_t);
+template cudaError_t cg_launch_loop<float>(CGPlan<float>*, cudaStream_t);
+template cudaError_t cg_launch_loop<double>(CGPlan<double>*, cudaStream_t);
 template cudaError_t cg_launch_k2<double>(CGPlan<double>*, cudaStream_t);
 
 template cudaError_t cg_plan_geometry<float>(const Grid&, int, int, K1Geom*, int*);

@@ -26,7 +26,9 @@ struct CGDevState {
   double tol;           // stop orbital i when ||r_i|| <= tol ||b_i||
   int maxit;
   unsigned int ticket;  // last-CTA detection; every last CTA resets it
-  unsigned long long work;  // sum over K1 launches of interior nodes x orbitals processed
+  unsigned long long work;  // sum over operator passes of interior nodes x orbitals processed
+  unsigned int bar_count;   // grid barrier counter of the persistent CG kernel (zeroed per launch)
+  unsigned long long work_nodes;  // sum over operator passes of interior nodes x orbital blocks processed
 };
 
 template <typename T>
@@ -68,6 +70,7 @@ struct CGPlan {
   size_t smem_init = 0, smem_upd = 0;
   cudaGraphExec_t exec_zero = nullptr, exec_warm = nullptr;
   int graph_N = -1;  // N the graphs were built for
+  bool coop_ok = false;  // the persistent CG kernel's grid can be co-resident
   // adds q = A x (the warm-start apply) as a graph node
   std::function<cudaError_t(cudaGraph_t, cudaGraphNode_t*)> add_apply;
 };
@@ -89,6 +92,10 @@ template <typename T>
 cudaError_t cg_launch_k1(CGPlan<T>* P, cudaStream_t st);
 template <typename T>
 cudaError_t cg_launch_k2(CGPlan<T>* P, cudaStream_t st);
+// The whole CG loop as one cooperative launch (after cg_launch_init); returns an
+// error (and launches nothing) if the grid cannot be co-resident.
+template <typename T>
+cudaError_t cg_launch_loop(CGPlan<T>* P, cudaStream_t st);
 
 // Packed operator weights per input plane, [Pz][ny-1][nx-1][kPackedW], for the tiled kernel.
 constexpr int kPackedW = 28;

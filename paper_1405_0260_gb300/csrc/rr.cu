@@ -64,16 +64,20 @@ __global__ void __launch_bounds__(256) k_gram2(long long G, int Np, const double
   (void)nch;
 }
 
+// One warp per Gram entry: lanes stride the chunks, then a butterfly of fixed
+// shape (deterministic).
 __global__ void k_gram_reduce(int Np, int nch, const double* __restrict__ part, double* __restrict__ G1,
                               double* __restrict__ G2) {
-  long long NN = (long long)Np * Np;
-  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long NN = (long long)Np * Np;
+  const long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  const int lane = threadIdx.x % 32;
   if (t >= 2 * NN) return;
-  int w = (int)(t / NN);
-  long long e = t % NN;
+  const int w = (int)(t / NN);
+  const long long e = t % NN;
   double s = 0.0;
-  for (int c = 0; c < nch; ++c) s += part[(2LL * c + w) * NN + e];
-  (w == 0 ? G1 : G2)[e] = s;
+  for (int c = lane; c < nch; c += 32) s += part[(2LL * c + w) * NN + e];
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if (lane == 0) (w == 0 ? G1 : G2)[e] = s;
 }
 
 // Round-robin ("circle") pairing of m = even indices: round r, slot k.
@@ -99,6 +103,7 @@ __global__ void __launch_bounds__(1024) k_small_eig(int N, int Np, const double*
   __shared__ double red[1024 / 32][2];
   __shared__ double cs[kMaxN / 2 + 1][2];
   __shared__ int pr[kMaxN / 2 + 1][2];
+  __shared__ double rdiag[kMaxN];
   const int tid = threadIdx.x, nt = blockDim.x;
   double* L = work;
   double* S = work + (long long)N * N;
@@ -121,8 +126,8 @@ __global__ void __launch_bounds__(1024) k_small_eig(int N, int Np, const double*
     }
     __syncthreads();
     if (fail) break;
-    double lkk = L[k * N + k];
-    for (int i = k + 1 + tid; i < N; i += nt) L[i * N + k] /= lkk;
+    const double rk = 1.0 / L[k * N + k];
+    for (int i = k + 1 + tid; i < N; i += nt) L[i * N + k] *= rk;
     __syncthreads();
     int m = N - k - 1;
     for (int t = tid; t < m * m; t += nt) {
@@ -139,13 +144,15 @@ __global__ void __launch_bounds__(1024) k_small_eig(int N, int Np, const double*
     int i = t / N, j = t % N;
     if (j > i) L[t] = 0.0;
   }
+  // reciprocals of the diagonal of L (float64 division is slow on this GPU)
+  for (int i = tid; i < N; i += nt) rdiag[i] = 1.0 / L[i * N + i];
   __syncthreads();
   // W = L^-1 S  (column j by thread j)
   for (int j = tid; j < N; j += nt)
     for (int i = 0; i < N; ++i) {
       double s = S[i * N + j];
       for (int k = 0; k < i; ++k) s -= L[i * N + k] * W[k * N + j];
-      W[i * N + j] = s / L[i * N + i];
+      W[i * N + j] = s * rdiag[i];
     }
   __syncthreads();
   // S = L^-1 W^T = L^-1 S L^-T
@@ -153,7 +160,7 @@ __global__ void __launch_bounds__(1024) k_small_eig(int N, int Np, const double*
     for (int i = 0; i < N; ++i) {
       double s = W[j * N + i];
       for (int k = 0; k < i; ++k) s -= L[i * N + k] * S[k * N + j];
-      S[i * N + j] = s / L[i * N + i];
+      S[i * N + j] = s * rdiag[i];
     }
   __syncthreads();
   for (int t = tid; t < N * N; t += nt) {
@@ -197,19 +204,31 @@ __global__ void __launch_bounds__(1024) k_small_eig(int N, int Np, const double*
     off = red[0][0];
     all = red[0][1];
     __syncthreads();
-    if (!(off > 1e-30 * all)) break;
+    // stop at the float64 rounding floor of the rotations: off-norm <= ~3e-15 N norm(S)
+    if (!(off > 1e-29 * (double)N * N * all)) break;
     for (int r = 0; r < m - 1; ++r) {
       for (int k = tid; k < half; k += nt) {
         int p, q;
         rr_pair(m, r, k, &p, &q);
         double c = 1.0, s = 0.0;
         if (q < N) {
-          double apq = S[p * N + q];
-          if (apq != 0.0) {
-            double tau = (S[q * N + q] - S[p * N + p]) / (2.0 * apq);
-            double t = (tau >= 0.0) ? 1.0 / (tau + sqrt(1.0 + tau * tau)) : -1.0 / (-tau + sqrt(1.0 + tau * tau));
-            c = 1.0 / sqrt(1.0 + t * t);
-            s = t * c;
+          // The rotation angle in float32 (float64 division and square root are
+          // long sequences on this GPU's float64 pipe), then (c, s) renormalised to
+          // c^2 + s^2 = 1 in float64 by two Newton steps for 1/sqrt(c^2 + s^2):
+          // the rotation is orthogonal to float64 precision and annihilates
+          // a_pq up to a float32-relative residue, which later sweeps remove.
+          const float fa = (float)S[p * N + q];
+          if (fa != 0.0f) {
+            const float tau = (float)(S[q * N + q] - S[p * N + p]) / (2.0f * fa);
+            const float rt = sqrtf(1.0f + tau * tau);
+            const float t = (tau >= 0.0f) ? 1.0f / (tau + rt) : -1.0f / (-tau + rt);
+            const float cf = rsqrtf(1.0f + t * t);
+            const double cd = cf, sd = (double)(t * cf);
+            const double nn = cd * cd + sd * sd;
+            double y = 1.5 - 0.5 * nn;
+            y = y * (1.5 - 0.5 * nn * y * y);
+            c = cd * y;
+            s = sd * y;
           }
         }
         cs[k][0] = c;
@@ -257,7 +276,7 @@ __global__ void __launch_bounds__(1024) k_small_eig(int N, int Np, const double*
     for (int i = N - 1; i >= 0; --i) {
       double s = V[i * N + j];
       for (int k = i + 1; k < N; ++k) s -= L[k * N + i] * C[(long long)k * Np + rank];
-      C[(long long)i * Np + rank] = s / L[i * N + i];
+      C[(long long)i * Np + rank] = s * rdiag[i];
     }
   }
   for (int t = tid; t < Np * Np; t += nt) {
@@ -318,14 +337,14 @@ cudaError_t launch_gram2(const Grid& g, int N, int Np, const double* X, const do
   gram_shape(g, Np, &nch, &chunk);
   int ntile = (Np + kTile - 1) / kTile;
   k_gram2<<<ntile * ntile * nch, 256, 0, st>>>(g.G, Np, X, Y1, Y2, part, nch, chunk);
-  long long work = 2LL * Np * Np;
+  long long work = 2LL * Np * Np * 32;
   k_gram_reduce<<<(unsigned)((work + 255) / 256), 256, 0, st>>>(Np, nch, part, G1, G2);
   if (n_chunks) *n_chunks = nch;
   return cudaGetLastError();
 }
 
 cudaError_t launch_gram_reduce(int Np, int nch, const double* part, double* G1, double* G2, cudaStream_t st) {
-  long long work = 2LL * Np * Np;
+  long long work = 2LL * Np * Np * 32;
   k_gram_reduce<<<(unsigned)((work + 255) / 256), 256, 0, st>>>(Np, nch, part, G1, G2);
   return cudaGetLastError();
 }
