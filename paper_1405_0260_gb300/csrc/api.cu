@@ -191,6 +191,11 @@ int make_plan(paro_mesh m, int Np, CGPlan<T>** out, T* x, T* b, T* r, T* p, T* q
     delete P;
     return fail(m, PARO_ERR_CUDA, std::string("CG plan: ") + cudaGetErrorString(e));
   }
+  if (std::getenv("PARO_PRINT_PLAN"))
+    std::fprintf(stderr, "paro CG plan (%s): tile %dx%d, %d node(s)/thread, block %d orbitals x %d, %d threads, grid %d, "
+                 "smem %zu B, persistent %d\n", sizeof(T) == 4 ? "float32" : "float64", P->geo.TX, P->geo.TY,
+                 P->geo.npt, P->geo.G4 * 4, P->geo.nob, P->geo.nthr * P->geo.G4, P->geo.grid, P->geo.smem,
+                 (int)P->coop_ok);
   Grid g = m->g;
   P->add_apply = [g, Np, coef, x, q](cudaGraph_t gr, cudaGraphNode_t* node) {
     return graph_add_apply<T>(gr, node, g, Np, coef, x, q);
@@ -390,9 +395,11 @@ int solve_packed(paro_mesh m, int N, const double* lam, const paro_params& p, pa
   double* scale = m->dscal + S_SCALE * kMaxN;
   CK(cudaMemcpyAsync(scale, m->h_dbl, sizeof(double) * Np, cudaMemcpyHostToDevice, m->st));
   if (m->precision == PARO_MIXED) {
-    // float-float mass apply (float64 accuracy on the float32 pipes)
+    // float-float mass apply (float64 accuracy on the float32 pipes); b stays as a
+    // hi/lo pair in fah/fal for the solve (the Rayleigh-Ritz step reuses them after)
     LAUNCH(1, launch_split_ff((long long)g.G * Np, m->u, m->fxh, m->fxl, m->st));
-    LAUNCH(1, launch_ff_apply(g, Np, nullptr, nullptr, &m->mw, m->fxh, m->fxl, scale, m->b, nullptr, nullptr, m->st));
+    LAUNCH(1, launch_ff_apply(g, Np, nullptr, nullptr, &m->mw, m->fxh, m->fxl, scale, nullptr, m->fah, m->fal,
+                              m->st));
   } else {
     LAUNCH(1, launch_apply_f64(g, Np, nullptr, &m->mw, 0.0, m->u, m->b, scale, m->st));
   }
@@ -420,8 +427,8 @@ int solve_packed(paro_mesh m, int N, const double* lam, const paro_params& p, pa
       // r = b - A x, float64-accurate (float-float arithmetic); its float32 rounding
       // is the correction right-hand side
       LAUNCH(1, launch_split_ff((long long)g.G * Np, m->x, m->fxh, m->fxl, m->st));
-      LAUNCH(1, launch_refine_residual_ff(g, N, Np, m->wAh, m->wAl, m->fxh, m->fxl, m->b, m->b32, rs, p.solve_tol,
-                                          m->st));
+      LAUNCH(1, launch_refine_residual_ff(g, N, Np, m->wAh, m->wAl, m->fxh, m->fxl, m->fah, m->fal, m->b32, rs,
+                                          p.solve_tol, m->st));
       if (st) st->stencil_applies += N;
       int open = 0;
       TRY(read_n_active(m, &open));

@@ -450,12 +450,12 @@ __global__ void __launch_bounds__(k1_max_slots<T, NPT>() * G4) k_cg_q(CGArgs<T> 
 
   // Fixed-order per-orbital sums of the per-thread partials of one orbital block
   // into sacc[k Np + o0 ..] (K values per orbital: sred is [nthr][K bw]).
-  auto flush_sums = [&](int o0, int K) {
+  auto flush_sums = [&](int o0, int K, int k0) {
     __syncthreads();
     double* ctmp = sred + nthr * K * bw;
     block_colsum(sred, nthr, K * bw, ctmp);
     for (int t = tid; t < K * bw; t += blockDim.x) {
-      const int k = t / bw, o = t % bw;
+      const int k = k0 + t / bw, o = t % bw;
       if (o0 + o < Np) sacc[k * Np + o0 + o] += ctmp[t];
     }
     __syncthreads();
@@ -463,14 +463,16 @@ __global__ void __launch_bounds__(k1_max_slots<T, NPT>() * G4) k_cg_q(CGArgs<T> 
   auto flush1 = [&](int o0, const T (&v)[4]) {
 #pragma unroll
     for (int c = 0; c < 4; ++c) sred[j * bw + 4 * g + c] = (double)v[c];
-    flush_sums(o0, 1);
+    flush_sums(o0, 1, 0);
   };
+  // two values per orbital, summed one after the other (keeps sred at [nthr][bw])
   auto flush2 = [&](int o0, const T (&v)[8]) {
 #pragma unroll
-    for (int k = 0; k < 2; ++k)
+    for (int k = 0; k < 2; ++k) {
 #pragma unroll
-      for (int c = 0; c < 4; ++c) sred[j * 2 * bw + k * bw + 4 * g + c] = (double)v[k * 4 + c];
-    flush_sums(o0, 2);
+      for (int c = 0; c < 4; ++c) sred[j * bw + 4 * g + c] = (double)v[k * 4 + c];
+      flush_sums(o0, 1, k);
+    }
   };
 
   // ---- operator pass: q = A p_new over this CTA's segments, (p_new, q) into sacc[0 .. Np) ----
@@ -1064,11 +1066,11 @@ void k1_layout(int Np, int bw, int TX, int TY, int npt, K1Geom* G) {
   // sacc[Np], then the per-segment block sums [nthr][bw], reused at the end for the
   // cross-CTA totals [Np] and slices (at most max(threads, Np) values)
   // sacc [2 Np], the persistent loop's per-orbital state (5 Np doubles), then the
-  // block sums [nthr][2 bw] with their column-sum slices, reused for the
+  // block sums [nthr][bw] with their column-sum slices, reused for the
   // cross-CTA totals [2 Np] and slices (at most max(threads, 2 Np) values)
   const size_t nthr = (size_t)G->nthr * (bw / 4);
   const size_t fin = (size_t)2 * Np + (nthr > (size_t)2 * Np ? nthr : (size_t)2 * Np);
-  const size_t blk = (size_t)G->nthr * 2 * bw + nthr;
+  const size_t blk = (size_t)G->nthr * bw + nthr;
   size_t red = ((size_t)7 * Np + (blk > fin ? blk : fin)) * sizeof(double);
   G->smem = 128 + (size_t)kSlots * G->slot_bytes + red;
 }

@@ -127,10 +127,10 @@ cudaError_t launch_refine_residual(const Grid& g, int N, int Np, const double* c
                                    const double* b64, float* rhs32, const CGState& s, double tol, cudaStream_t st);
 cudaError_t launch_refine_update(const Grid& g, int Np, double* x64, const float* d32, const int* skip,
                                  cudaStream_t st);
-// The same residual in float-float arithmetic (x split into hi/lo arrays, packed weights of A).
+// The same residual in float-float arithmetic (x and b as hi/lo arrays, packed weights of A).
 cudaError_t launch_refine_residual_ff(const Grid& g, int N, int Np, const float* whi, const float* wlo,
-                                      const float* xhi, const float* xlo, const double* b64, float* rhs32,
-                                      const CGState& s, double tol, cudaStream_t st);
+                                      const float* xhi, const float* xlo, const float* bhi, const float* blo,
+                                      float* rhs32, const CGState& s, double tol, cudaStream_t st);
 
 // ff.cu: float64-accurate applies, Grams and rotation in float-float arithmetic
 cudaError_t launch_split_ff(long long n, const double* x, float* hi, float* lo, cudaStream_t st);

@@ -118,13 +118,14 @@ __global__ void __launch_bounds__(kRedThreads) k_refine_residual(Grid g, int N, 
   if (threadIdx.x == 0) *s.n_active = cnt;
 }
 
-// The same residual in float-float arithmetic (ff.cuh): x as hi/lo arrays, the
-// packed per-node float-float weights of A, b in float64 (split on load).
+// The same residual in float-float arithmetic (ff.cuh): x and b as hi/lo arrays,
+// the packed per-node float-float weights of A.
 __global__ void __launch_bounds__(kRedThreads) k_refine_residual_ff(Grid g, int N, int Np, const float* __restrict__ whi,
                                                                     const float* __restrict__ wlo,
                                                                     const float* __restrict__ xhi,
                                                                     const float* __restrict__ xlo,
-                                                                    const double* __restrict__ b,
+                                                                    const float* __restrict__ bhi,
+                                                                    const float* __restrict__ blo,
                                                                     float* __restrict__ rhs, CGState s, double tol) {
   __shared__ double sred[2 * kRedThreads * 4];
   double* tot = sred;
@@ -159,18 +160,18 @@ __global__ void __launch_bounds__(kRedThreads) k_refine_residual_ff(Grid g, int 
         ff_mac(ax[2], FF{h.z, l.z}, w);
         ff_mac(ax[3], FF{h.w, l.w}, w);
       }
-      V4<double> bv = ld4v(b, gp, Np, grp);
-      const double bb[4] = {bv.a, bv.b, bv.c, bv.d};
+      const float4 bh4 = *reinterpret_cast<const float4*>(bhi + gp * Np + 4 * grp);
+      const float4 bl4 = *reinterpret_cast<const float4*>(blo + gp * Np + 4 * grp);
+      const float bh[4] = {bh4.x, bh4.y, bh4.z, bh4.w}, bl[4] = {bl4.x, bl4.y, bl4.z, bl4.w};
       float r[4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        FF rc = ff_split(bb[c]);
+        FF rc{bh[c], bl[c]};
         ff_add(rc, ff_neg(ax[c]));
         rc = ff_norm(rc);
         r[c] = rc.hi;
         arr[c] = fmaf(rc.hi, rc.hi, arr[c]);
-        const float bh = (float)bb[c];
-        abb[c] = fmaf(bh, bh, abb[c]);
+        abb[c] = fmaf(bh[c], bh[c], abb[c]);
       }
       if (rhs != nullptr) st4(rhs + gp * Np + 4 * grp, V4<float>{r[0], r[1], r[2], r[3]});
     }
@@ -224,9 +225,10 @@ cudaError_t launch_refine_residual(const Grid& g, int N, int Np, const double* c
 }
 
 cudaError_t launch_refine_residual_ff(const Grid& g, int N, int Np, const float* whi, const float* wlo,
-                                      const float* xhi, const float* xlo, const double* b64, float* rhs32,
-                                      const CGState& s, double tol, cudaStream_t st) {
-  k_refine_residual_ff<<<red_blocks(g, Np), kRedThreads, 0, st>>>(g, N, Np, whi, wlo, xhi, xlo, b64, rhs32, s, tol);
+                                      const float* xhi, const float* xlo, const float* bhi, const float* blo,
+                                      float* rhs32, const CGState& s, double tol, cudaStream_t st) {
+  k_refine_residual_ff<<<red_blocks(g, Np), kRedThreads, 0, st>>>(g, N, Np, whi, wlo, xhi, xlo, bhi, blo, rhs32, s,
+                                                                  tol);
   return cudaGetLastError();
 }
 
