@@ -191,17 +191,17 @@ def run_ours(args, ws, rank, local):
     units = nI * N * args.steps * ws
     value = units / (t_max * 1e-3)
 
-    # roofline of the persistent CG kernel (the whole float32 CG loop of a correction
-    # solve in one cooperative launch).  Per unit (node x orbital) and iteration it
-    # reads r, p and writes q in the operator pass (12 B) and reads x, r, p, q and
-    # writes x, r, p in the update (28 B): 40 B.  Per node and orbital-block pass it
-    # reads the 27 float32 operator weights (108 B) and the Jacobi diagonal twice (8 B).
+    # roofline of the single-reduction CG kernel (the whole float32 CG loop of a
+    # correction solve in one cooperative launch, one pass per iteration).  Per unit
+    # (node x orbital) and iteration it reads r, w, s (with halo, counted once) and
+    # x, p, and writes p, s, x, r, w: 10 x 4 B = 40 B.  Per node and orbital-block
+    # pass it reads the 27 float32 operator weights (108 B) and the Jacobi diagonal (4 B).
     peak, peak_kind = peaks()
     roof = None
     if prof_n > 0 and prof_ms > 0:
-        alg_bytes = 40.0 * prof_units + 116.0 * prof_nodes
+        alg_bytes = 40.0 * prof_units + 112.0 * prof_nodes
         achieved = alg_bytes / (prof_ms * 1e-3) / 1e9
-        roof = {"kernel": "k_cg_q<float, LOOP> (persistent CG loop: TMA-tiled q = A p, update, grid barriers)",
+        roof = {"kernel": "k_cg1<float> (single-reduction CG loop: TMA-tiled w = A D^-1 r with the vector updates, one grid barrier a pass)",
                 "bound": "hbm",
                 "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": None,

@@ -30,7 +30,8 @@ struct paro_mesh_s {
   // workspace sized for Np_alloc orbitals
   int Np_alloc = 0;
   double *u = nullptr, *x = nullptr, *b = nullptr, *r = nullptr, *p0 = nullptr, *q = nullptr;
-  float *b32 = nullptr, *x32 = nullptr, *r32 = nullptr, *p32a = nullptr, *q32 = nullptr;
+  float *b32 = nullptr, *x32 = nullptr, *r32 = nullptr, *p32a = nullptr, *q32 = nullptr, *s32 = nullptr;
+  float *r32b = nullptr, *q32b = nullptr, *s32b = nullptr;  // second buffer set of the single-reduction CG
   // mixed mode: float-float (hi/lo) copies of a float64 input vector and of two
   // operator images, [G][Np] each; float-float weights of A and H, [G][28] each
   float *fxh = nullptr, *fxl = nullptr, *fah = nullptr, *fal = nullptr, *fbh = nullptr, *fbl = nullptr;
@@ -166,7 +167,7 @@ void free_plans(paro_mesh m) {
 
 template <typename T>
 int make_plan(paro_mesh m, int Np, CGPlan<T>** out, T* x, T* b, T* r, T* p, T* q, const T* dinv, const T* dinv_tma,
-              const T* wcoef, const T* coef) {
+              const T* wcoef, const T* coef, T* s = nullptr, T* r2 = nullptr, T* q2 = nullptr, T* s2 = nullptr) {
   CGPlan<T>* P = new CGPlan<T>();
   P->nsm = m->nsm;
   P->args.g = m->g;
@@ -177,6 +178,10 @@ int make_plan(paro_mesh m, int Np, CGPlan<T>** out, T* x, T* b, T* r, T* p, T* q
   P->args.r = r;
   P->args.p = p;
   P->args.q = q;
+  P->args.s = s;
+  P->args.r2 = r2;
+  P->args.q2 = q2;
+  P->args.s2 = s2;
   P->args.dinv = dinv;
   P->args.part = m->cgpart;
   P->args.st = m->cgst;
@@ -187,6 +192,9 @@ int make_plan(paro_mesh m, int Np, CGPlan<T>** out, T* x, T* b, T* r, T* p, T* q
   int bw = 0;
   cudaError_t e = cg_plan_geometry<T>(m->g, Np, m->nsm, &P->geo, &bw);
   if (e == cudaSuccess) e = cg_prepare<T>(P);
+  if constexpr (sizeof(T) == 4) {
+    if (e == cudaSuccess) e = cg1_prepare(P);
+  }
   if (e != cudaSuccess) {
     delete P;
     return fail(m, PARO_ERR_CUDA, std::string("CG plan: ") + cudaGetErrorString(e));
@@ -196,6 +204,12 @@ int make_plan(paro_mesh m, int Np, CGPlan<T>** out, T* x, T* b, T* r, T* p, T* q
                  "smem %zu B, persistent %d\n", sizeof(T) == 4 ? "float32" : "float64", P->geo.TX, P->geo.TY,
                  P->geo.npt, P->geo.G4 * 4, P->geo.nob, P->geo.nthr * P->geo.G4, P->geo.grid, P->geo.smem,
                  (int)P->coop_ok);
+  if constexpr (sizeof(T) == 4) {
+    if (std::getenv("PARO_PRINT_PLAN"))
+      std::fprintf(stderr, "paro single-reduction CG plan: tile %dx%d, block %d orbitals x %d, %d threads, grid %d, "
+                   "smem %zu B, usable %d\n", P->geo1.TX, P->geo1.TY, P->geo1.G4 * 4, P->geo1.nob,
+                   P->geo1.nthr * P->geo1.G4, P->geo1.grid, P->geo1.smem, (int)P->cg1_ok);
+  }
   Grid g = m->g;
   P->add_apply = [g, Np, coef, x, q](cudaGraph_t gr, cudaGraphNode_t* node) {
     return graph_add_apply<T>(gr, node, g, Np, coef, x, q);
@@ -209,7 +223,7 @@ int make_plans(paro_mesh m, int Np) {
   TRY(make_plan<double>(m, Np, &m->plan64, m->x, m->b, m->r, m->p0, m->q, m->dinv64, m->dt64, m->w64, m->coef64));
   if (m->precision == PARO_MIXED)
     TRY(make_plan<float>(m, Np, &m->plan32, m->x32, m->b32, m->r32, m->p32a, m->q32, m->dinv32, m->dt32, m->w32,
-                         m->coef32));
+                         m->coef32, m->s32, m->r32b, m->q32b, m->s32b));
   return PARO_OK;
 }
 
@@ -218,7 +232,7 @@ int ensure_workspace(paro_mesh m, int Np) {
   free_plans(m);
   // release the previous vector workspace
   void* olds[] = {m->u,    m->x,   m->b,   m->r,   m->p0,  m->q,     m->b32,    m->x32, m->r32,
-                  m->p32a, m->q32, m->fxh, m->fxl, m->fah, m->fal,   m->fbh,    m->fbl, m->gpart_ff,
+                  m->p32a, m->q32, m->s32, m->r32b, m->q32b, m->s32b, m->fxh, m->fxl, m->fah, m->fal,   m->fbh,    m->fbl, m->gpart_ff,
                   m->gpart, m->GA, m->GB,  m->C,   m->theta, m->eigwork, m->cgpart};
   CK(cudaStreamSynchronize(m->st));
   for (void* p : olds) dfree(m, p);
@@ -235,6 +249,10 @@ int ensure_workspace(paro_mesh m, int Np) {
     TRY(dalloc(m, &m->r32, n));
     TRY(dalloc(m, &m->p32a, n));
     TRY(dalloc(m, &m->q32, n));
+    TRY(dalloc(m, &m->s32, n));
+    TRY(dalloc(m, &m->r32b, n));
+    TRY(dalloc(m, &m->q32b, n));
+    TRY(dalloc(m, &m->s32b, n));
     TRY(dalloc(m, &m->fxh, n));
     TRY(dalloc(m, &m->fxl, n));
     TRY(dalloc(m, &m->fah, n));
@@ -249,7 +267,8 @@ int ensure_workspace(paro_mesh m, int Np) {
   TRY(dalloc(m, &m->C, (size_t)Np * Np));
   TRY(dalloc(m, &m->theta, (size_t)Np));
   TRY(dalloc(m, &m->eigwork, (size_t)4 * Np * Np));
-  TRY(dalloc(m, &m->cgpart, (size_t)3 * 4 * m->nsm * Np));
+  // per-CTA partials: up to 4 CTAs per SM, 3 values per orbital, two buffers
+  TRY(dalloc(m, &m->cgpart, (size_t)2 * 3 * 4 * m->nsm * Np));
   m->Np_alloc = Np;
   TRY(make_plans(m, Np));
   return PARO_OK;
@@ -331,6 +350,22 @@ int run_cg(paro_mesh m, CGPlan<T>* P, int N, bool warm, double tol, int maxit, i
   // float32: the whole loop in one cooperative launch (profile 1: CUDA events
   // around it).  float64 keeps the graph (or host-driven) loop of two kernels per
   // iteration, which runs its longer float64 passes with less synchronisation.
+  if constexpr (sizeof(T) == 4) {
+    // float32: the single-reduction CG, one cooperative launch per correction solve
+    if (P->cg1_ok && m->profile != 2) {
+      if (warm) LAUNCH(1, launch_apply_T(m, P));
+      LAUNCH(1, cg_launch_init<T>(P, m->st, !warm));
+      if (m->profile) CK(cudaEventRecord(m->pev[2 * m->pev_used], m->st));
+      LAUNCH(1, cg_launch_cg1(P, m->st));
+      if (m->profile) {
+        CK(cudaEventRecord(m->pev[2 * m->pev_used + 1], m->st));
+        m->pev_used++;
+      }
+      TRY(read_iters(m, N, it_sum, it_max));  // synchronises the stream
+      if (m->profile) TRY(drain_profile(m));
+      return PARO_OK;
+    }
+  }
   if (P->coop_ok && m->profile != 2 && sizeof(T) == 4) {
     if (warm) LAUNCH(1, launch_apply_T(m, P));
     LAUNCH(1, cg_launch_init<T>(P, m->st, !warm));

@@ -23,6 +23,7 @@
 // (alpha, beta, masks, counts); K2's last CTA also sets the graph's while
 // condition.  All mbarrier waits are bounded.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include "cg.cuh"
@@ -200,6 +201,10 @@ __global__ void __launch_bounds__(256) k_cg_init(CGArgs<T> a, int x_zero, cudaGr
     }
     sts4(a.r + e, r);
     sts4(a.p + e, Vec4<T>{});
+    if (a.s != nullptr) {  // single-reduction CG: w = s = 0 before its first pass
+      sts4(a.q + e, Vec4<T>{});
+      sts4(a.s + e, Vec4<T>{});
+    }
     T di = a.dinv[node];
     for (int c = 0; c < 4; ++c) {
       acc[0][c] = fmaT(r.v[c], di * r.v[c], acc[0][c]);
@@ -863,6 +868,464 @@ __global__ void __launch_bounds__(k1_max_slots<T, NPT>() * G4) k_cg_q(CGArgs<T> 
 }
 
 // ---------------------------------------------------------------------------
+// Single-reduction CG for the float32 correction solves (the preconditioned
+// Chronopoulos-Gear recurrences, algebraically the same Jacobi PCG):
+//   u_i = D^-1 r_i, w_i = A u_i, gamma_i = (r_i, u_i), delta_i = (w_i, u_i)
+//   beta_i = gamma_i / gamma_{i-1}, alpha_i = gamma_i / (delta_i - beta_i gamma_i / alpha_{i-1})
+//   p_i = u_i + beta_i p_{i-1}, s_i = w_i + beta_i s_{i-1} (= A p_i)
+//   x_{i+1} = x_i + alpha_i p_i, r_{i+1} = r_i - alpha_i s_i
+// One pass per iteration, with alpha, beta of the previous reduction: TMA stages
+// r, w and s with a one-node halo; on tile + halo the pass forms
+// s <- w + beta s, r <- r - alpha s, u = D^-1 r; the stencil gives w = A u at the
+// tile; each thread updates p and x of its own node (plain loads) and stores
+// p, s, x, r, w; (r, u), (w, u), (r, r) go to one cross-CTA reduction behind one
+// grid barrier.  The first pass runs with alpha = beta = 0 and s = w = 0 (it
+// only forms w_0 and the first scalars).  One CTA per SM, cooperative launch.
+// ---------------------------------------------------------------------------
+constexpr int kSlots1 = 3;
+
+// r, w and s are read with their halo while the pass writes their new values, so
+// they alternate between two buffer sets by pass parity (tensor maps *0 over
+// a.r, a.q, a.s and *1 over a.r2, a.q2, a.s2); x and p are touched only at the
+// nodes a thread owns and are updated in place.
+template <int G4, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) k_cg1(CGArgs<float> a, K1Geom geo,
+                                                         const __grid_constant__ CUtensorMap mr0,
+                                                         const __grid_constant__ CUtensorMap mq0,
+                                                         const __grid_constant__ CUtensorMap ms0,
+                                                         const __grid_constant__ CUtensorMap mr1,
+                                                         const __grid_constant__ CUtensorMap mq1,
+                                                         const __grid_constant__ CUtensorMap ms1,
+                                                         const __grid_constant__ CUtensorMap md,
+                                                         const __grid_constant__ CUtensorMap mw) {
+  using T = float;
+  constexpr int bw = 4 * G4;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int TX = geo.TX, TY = geo.TY;
+  const int HX = TX + 2, HY = TY + 2;
+  const int tid = threadIdx.x;
+  const int g = tid % G4, j = tid / G4;
+  const int Np = a.Np;
+  const int nthr = geo.nthr;  // = TX * TY (one node per thread)
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+  unsigned char* base = smem + 128;
+  // slot layout: r | w | s (each [HY][HX][bw]) | D^-1 [HY][DX] | weights [TY][TX][kWS]
+  auto slotR = [&](int s) { return reinterpret_cast<T*>(base + (size_t)s * geo.slot_bytes); };
+  auto slotQ = [&](int s) { return reinterpret_cast<T*>(base + (size_t)s * geo.slot_bytes + geo.off_p); };
+  auto slotS = [&](int s) { return reinterpret_cast<T*>(base + (size_t)s * geo.slot_bytes + geo.off_s); };
+  auto slotD = [&](int s) { return reinterpret_cast<T*>(base + (size_t)s * geo.slot_bytes + geo.off_d); };
+  auto slotW = [&](int s) { return reinterpret_cast<T*>(base + (size_t)s * geo.slot_bytes + geo.off_w); };
+  double* sacc = reinterpret_cast<double*>(base + (size_t)kSlots1 * geo.slot_bytes);  // [3 Np]
+  double* st_gam = sacc + 3 * Np;  // gamma of the previous pass
+  double* st_bb = st_gam + Np;
+  double* st_al = st_bb + Np;      // alpha of the previous pass
+  double* st_be = st_al + Np;      // beta of the previous pass
+  int* st_act = reinterpret_cast<int*>(st_be + Np);
+  int* st_it = st_act + Np;
+  double* sred = reinterpret_cast<double*>(st_it + Np);  // [nthr][bw] block sums, then totals/slices
+  __shared__ T sbeta[kMaxN], salpha[kMaxN];
+  __shared__ int sact[kMaxN / 4], sblk[kMaxN / 4];
+  __shared__ int s_nact;
+
+  const int nzo = a.g.nz - 1;
+  const long long F = (long long)geo.nob * geo.ncy * geo.ncx * nzo;
+  const long long fbeg = F * blockIdx.x / gridDim.x;
+  const long long fend = F * (blockIdx.x + 1) / gridDim.x;
+  if (tid == 0) {
+    for (int s = 0; s < kSlots1; ++s) mbar_init(&bars[s], 1);
+    fence_mbar_init();
+    prefetch_tmap(&mr0);
+    prefetch_tmap(&mq0);
+    prefetch_tmap(&ms0);
+    prefetch_tmap(&mr1);
+    prefetch_tmap(&mq1);
+    prefetch_tmap(&ms1);
+    prefetch_tmap(&md);
+    prefetch_tmap(&mw);
+  }
+  // buffer set read by the current pass (0: a.r/a.q/a.s, 1: a.r2/a.q2/a.s2)
+  int rd = 0;
+  for (int o = tid; o < Np; o += blockDim.x) {
+    st_gam[o] = 0.0;
+    st_bb[o] = a.st->bb[o];
+    st_al[o] = 0.0;
+    st_be[o] = 0.0;
+    st_act[o] = a.st->active[o];
+    st_it[o] = 0;
+  }
+  __syncthreads();
+
+  auto seg_at = [&](long long f, int& o0, int& x0, int& y0, int& z0, int& z1) {
+    const long long col = f / nzo;
+    const int zl = (int)(f - col * nzo);
+    const long long rem = fend - f;
+    const int zh = (rem < (long long)(nzo - zl)) ? zl + (int)rem : nzo;
+    const int tx = (int)(col % geo.ncx);
+    const long long r = col / geo.ncx;
+    const int ty = (int)(r % geo.ncy);
+    const int ob = (int)(r / geo.ncy);
+    o0 = ob * bw;
+    x0 = 1 + tx * TX;
+    y0 = 1 + ty * TY;
+    z0 = 1 + zl;
+    z1 = 1 + zh;
+  };
+  const uint32_t slot_tx = geo.tx_bytes;
+  long long lf = fbeg;
+  int ls = 0, lz0 = 0, lz1 = 0, lo0 = 0, lx0 = 0, ly0 = 0;
+  bool lhave = false;
+  int lstep = 0;
+  auto issue_next = [&]() {
+    while (lf < fend) {
+      if (!lhave) {
+        seg_at(lf, lo0, lx0, ly0, lz0, lz1);
+        lhave = true;
+        ls = 0;
+        if (!sblk[lo0 / bw]) {
+          lf += lz1 - lz0;
+          lhave = false;
+          continue;
+        }
+      }
+      const int zin = lz0 - 1 + ls;
+      if (zin <= lz1) {
+        const int slot = lstep % kSlots1;
+        mbar_arrive_expect_tx(&bars[slot], slot_tx);
+        tma_load_4d(slotR(slot), rd ? &mr1 : &mr0, lo0, lx0 - 1, ly0 - 1, zin, &bars[slot]);
+        tma_load_4d(slotQ(slot), rd ? &mq1 : &mq0, lo0, lx0 - 1, ly0 - 1, zin, &bars[slot]);
+        tma_load_4d(slotS(slot), rd ? &ms1 : &ms0, lo0, lx0 - 1, ly0 - 1, zin, &bars[slot]);
+        tma_load_3d(slotD(slot), &md, lx0 - 1, ly0 - 1, zin, &bars[slot]);
+        tma_load_4d(slotW(slot), &mw, 0, lx0 - 1, ly0 - 1, zin, &bars[slot]);
+        ++lstep;
+        ++ls;
+        return;
+      }
+      lf += lz1 - lz0;
+      lhave = false;
+    }
+  };
+
+  // this thread's node (tx, ty) and halo positions: item 0 is its own node, item 1
+  // (threads j < ring size) a node of the halo ring
+  const int tx = j % TX, ty = j / TX;
+  const int hown = (ty + 1) * HX + (tx + 1);
+  const int nring = 2 * HX + 2 * TY;
+  int hring = -1;
+  if (j < nring) {
+    int hx, hy;
+    if (j < HX) {
+      hy = 0, hx = j;
+    } else if (j < 2 * HX) {
+      hy = HY - 1, hx = j - HX;
+    } else if (j < 2 * HX + TY) {
+      hy = 1 + (j - 2 * HX), hx = 0;
+    } else {
+      hy = 1 + (j - 2 * HX - TY), hx = HX - 1;
+    }
+    hring = hy * HX + hx;
+  }
+  const int poff = (ty * HX + tx) * bw + 4 * g;  // halo node (tx-1, ty-1)
+  const int woff = (ty * TX + tx) * kWS;
+  const int hstep = HX * bw;
+  const long long plane = (long long)a.g.Px * a.g.Py;
+
+  int cstep = 0;
+  bool timed_out = false;
+  unsigned bar_no = 0;
+
+  auto flush3 = [&](int o0, const T (&v)[12]) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) sred[j * bw + 4 * g + c] = (double)v[k * 4 + c];
+      __syncthreads();
+      double* ctmp = sred + nthr * bw;
+      block_colsum(sred, nthr, bw, ctmp);
+      for (int o = tid; o < bw; o += blockDim.x)
+        if (o0 + o < Np) sacc[k * Np + o0 + o] += ctmp[o];
+      __syncthreads();
+    }
+  };
+
+  // one pass: returns false on a timed-out wait
+  auto pass = [&]() -> bool {
+    for (int o = tid; o < 3 * Np; o += blockDim.x) sacc[o] = 0.0;
+    lf = fbeg;
+    lhave = false;
+    const int c_start = cstep;
+    if (tid == 0) {
+      fence_proxy_async_global();
+      for (int k = 0; k < kSlots1; ++k) issue_next();
+    }
+    int cur_o0 = -1;
+    T dots[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};  // (r,u) x4, (w,u) x4, (r,r) x4
+    for (long long f = fbeg; f < fend;) {
+      int o0, x0, y0, z0, z1;
+      seg_at(f, o0, x0, y0, z0, z1);
+      f += z1 - z0;
+      if (!sblk[o0 / bw]) continue;
+      if (o0 != cur_o0) {
+        if (cur_o0 >= 0) {
+          flush3(cur_o0, dots);
+#pragma unroll
+          for (int c = 0; c < 12; ++c) dots[c] = 0;
+        }
+        cur_o0 = o0;
+      }
+      const bool gact = (o0 + 4 * g < Np) && sact[o0 / 4 + g] != 0;
+      T al[4], be[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        al[c] = gact ? salpha[o0 + 4 * g + c] : T(0);
+        be[c] = gact ? sbeta[o0 + 4 * g + c] : T(0);
+      }
+      const int xg = x0 + tx, yg = y0 + ty;
+      const bool inside = xg <= a.g.nx - 1 && yg <= a.g.ny - 1;
+      const long long colnode = (long long)yg * a.g.Px + xg;
+      // own-node values of the previous input plane, used one step later
+      Vec4<T> pr_uold{}, pr_u{}, pr_x{}, pr_p{};
+      Vec4<T> aD{}, aC{}, aU{};
+      for (int s = z0 - 1; s <= z1; ++s) {
+        const int slot = cstep % kSlots1;
+        const uint32_t par = (cstep / kSlots1) & 1;
+        // own node's x and p of this plane (used at the next step)
+        const bool own_out = gact && inside && s >= z0 && s < z1;
+        const long long eown = ((long long)s * plane + colnode) * Np + o0 + 4 * g;
+        Vec4<T> cx_x{}, cx_p{};
+        if (own_out) {
+          cx_x = ldcg4(a.x + eown);
+          cx_p = ldcg4(a.p + eown);
+        }
+        // previous plane's own node: p_{i-1} = u_{i-1} + beta p_{i-2}, x_i = x_{i-1} + alpha p_{i-1}
+        const bool prev_out = gact && inside && s - 1 >= z0 && s - 1 < z1;
+        const long long eprev = eown - plane * Np;
+        if (prev_out) {
+          Vec4<T> pn, xn;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const T alc = salpha[o0 + 4 * g + c], bec = sbeta[o0 + 4 * g + c];
+            pn.v[c] = fmaT(bec, pr_p.v[c], pr_uold.v[c]);
+            xn.v[c] = fmaT(alc, pn.v[c], pr_x.v[c]);
+          }
+          sts4(a.p + eprev, pn);
+          sts4(a.x + eprev, xn);
+        }
+        const bool ok = mbar_wait(&bars[slot], par);
+        Vec4<T> cu_uold{}, cu_u{};
+        if (gact) {
+          T* R = slotR(slot);
+          const T* Q = slotQ(slot);
+          const T* S = slotS(slot);
+          const T* D = slotD(slot);
+          // own node: s <- w + beta s, r <- r - alpha s, u = D^-1 r (u replaces r in the
+          // slot); r and s are final here and stored at once, with (r, u) and (r, r)
+          {
+            const int hy = hown / HX, hx = hown - hy * HX;
+            const T d = D[hy * geo.DX + hx];
+            const int e = hown * bw + 4 * g;
+            const Vec4<T> rv = lds4(R + e), wv = lds4(Q + e), sv = lds4(S + e);
+            Vec4<T> sn, rn;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              sn.v[c] = fmaT(be[c], sv.v[c], wv.v[c]);
+              rn.v[c] = fmaT(-al[c], sn.v[c], rv.v[c]);
+              cu_u.v[c] = d * rn.v[c];
+              cu_uold.v[c] = d * rv.v[c];
+            }
+            sts4(R + e, cu_u);
+            if (own_out) {
+              sts4((rd ? a.r : a.r2) + eown, rn);
+              sts4((rd ? a.s : a.s2) + eown, sn);
+#pragma unroll
+              for (int c = 0; c < 4; ++c) {
+                dots[c] = fmaT(rn.v[c], cu_u.v[c], dots[c]);
+                dots[8 + c] = fmaT(rn.v[c], rn.v[c], dots[8 + c]);
+              }
+            }
+          }
+          if (hring >= 0) {
+            const int hy = hring / HX, hx = hring - hy * HX;
+            const T d = D[hy * geo.DX + hx];
+            const int e = hring * bw + 4 * g;
+            const Vec4<T> rv = lds4(R + e), wv = lds4(Q + e), sv = lds4(S + e);
+            Vec4<T> uv;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              const T sn = fmaT(be[c], sv.v[c], wv.v[c]);
+              uv.v[c] = d * fmaT(-al[c], sn, rv.v[c]);
+            }
+            sts4(R + e, uv);
+          }
+          fence_proxy_async_smem();
+        }
+        if (__syncthreads_or(!ok)) return false;
+        if (tid == 0 && cstep > c_start) issue_next();
+        if (gact) {
+          const T* U = slotR(slot) + poff;
+          const T* Wn = slotW(slot) + woff;
+          Vec4<T> w[7];
+#pragma unroll
+          for (int q = 0; q < 7; ++q) w[q] = lds4(Wn + 4 * q);
+#pragma unroll
+          for (int cxi = 0; cxi < 3; ++cxi) {
+            Vec4<T> v[3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) v[r] = lds4(U + r * hstep + cxi * bw);
+#pragma unroll
+            for (int cy = 0; cy < 3; ++cy) {
+              const int o = cy * 3 + cxi;
+              const T wu = w[o / 4].v[o % 4];
+              const T wc = w[(9 + o) / 4].v[(9 + o) % 4];
+              const T wd = w[(18 + o) / 4].v[(18 + o) % 4];
+#pragma unroll
+              for (int c = 0; c < 4; ++c) {
+                aU.v[c] = fmaT(wu, v[cy].v[c], aU.v[c]);
+                aC.v[c] = fmaT(wc, v[cy].v[c], aC.v[c]);
+                aD.v[c] = fmaT(wd, v[cy].v[c], aD.v[c]);
+              }
+            }
+          }
+          // output plane s-1 is complete: w_i and (w, u)
+          if (prev_out) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) dots[4 + c] = fmaT(aD.v[c], pr_u.v[c], dots[4 + c]);
+            sts4((rd ? a.q : a.q2) + eprev, aD);
+          }
+          aD = aC;
+          aC = aU;
+          aU = Vec4<T>{};
+        }
+        pr_uold = cu_uold;
+        pr_u = cu_u;
+        pr_x = cx_x;
+        pr_p = cx_p;
+        ++cstep;
+      }
+    }
+    if (cur_o0 >= 0) flush3(cur_o0, dots);
+    return true;
+  };
+
+  auto load_masks = [&]() {
+    for (int o = tid; o < Np; o += blockDim.x) {
+      sbeta[o] = (T)st_be[o];
+      salpha[o] = (T)st_al[o];
+    }
+    for (int q = tid; q < Np / 4; q += blockDim.x)
+      sact[q] = st_act[4 * q] | st_act[4 * q + 1] | st_act[4 * q + 2] | st_act[4 * q + 3];
+    __syncthreads();
+    for (int ob = tid; ob < geo.nob; ob += blockDim.x) {
+      int any = 0;
+      for (int q = ob * G4; q < ob * G4 + G4 && q < Np / 4; ++q) any |= sact[q];
+      sblk[ob] = any;
+    }
+    __syncthreads();
+  };
+
+  const double tol = a.st->tol;
+  const int maxit = a.st->maxit;
+  double* tot = sred;
+  double* scratch = sred + 3 * Np;
+  int status = 0;
+  for (int npass = 0;; ++npass) {
+    if (tid == 0) s_nact = 0;
+    __syncthreads();
+    for (int o = tid; o < Np; o += blockDim.x)
+      if (st_act[o]) atomicAdd(&s_nact, 1);
+    __syncthreads();
+    if (s_nact == 0) break;
+    load_masks();
+    if (blockIdx.x == 0 && tid == 0) {
+      unsigned long long wu = 0, wn = 0;
+      for (int q4 = 0; q4 < Np / 4; ++q4)
+        if (sact[q4]) wu += 4ull * a.g.nI;
+      for (int ob = 0; ob < geo.nob; ++ob)
+        if (sblk[ob]) wn += (unsigned long long)a.g.nI;
+      a.st->work += wu;
+      a.st->work_nodes += wn;
+    }
+    if (!pass()) {
+      timed_out = true;
+      break;
+    }
+    rd ^= 1;
+    // the next pass reads r, w and s through the async proxy (TMA)
+    fence_proxy_async_global();
+    // partials alternate between two buffers by pass parity: with one barrier per
+    // pass, a fast CTA writes pass i+1's partials while slower CTAs may still read
+    // pass i's (pass i+2 cannot start before every CTA has passed barrier i+1)
+    double* part = a.part + (long long)(npass & 1) * 3 * gridDim.x * Np;
+    for (int o = tid; o < Np; o += blockDim.x)
+      for (int k = 0; k < 3; ++k) part[((long long)k * gridDim.x + blockIdx.x) * Np + o] = sacc[k * Np + o];
+    if (!grid_barrier(&a.st->bar_count, ++bar_no * gridDim.x)) {
+      timed_out = true;
+      break;
+    }
+    reduce_over_ctas<3>(part, gridDim.x, Np, scratch, tot);
+    for (int o = tid; o < Np; o += blockDim.x) {
+      if (!st_act[o]) {
+        st_al[o] = 0.0;
+        st_be[o] = 0.0;
+        continue;
+      }
+      const double gam = tot[o], del = tot[Np + o], rr = tot[2 * Np + o];
+      bool act = true;
+      double alpha = 0.0, beta = 0.0;
+      if (npass > 0) {
+        const int it = st_it[o] + 1;  // x was updated in this pass
+        st_it[o] = it;
+        if (blockIdx.x == 0) a.st->rr[o] = rr;
+        if (!(isfinite(gam) && isfinite(del) && isfinite(rr))) {
+          status |= kStatNonFinite;
+          act = false;
+        } else if (rr <= tol * tol * st_bb[o]) {
+          act = false;
+        } else if (it >= maxit) {
+          status |= kStatNotConverged;
+          act = false;
+        }
+      } else if (!(isfinite(gam) && isfinite(del))) {
+        status |= kStatNonFinite;
+        act = false;
+      }
+      if (act) {
+        if (npass > 0) beta = gam / st_gam[o];
+        const double den = npass > 0 ? del - beta * gam / st_al[o] : del;  // = (p, A p)
+        if (!(gam > 0.0) || !(den > 0.0)) {
+          status |= kStatNotSPD;
+          act = false;
+          beta = 0.0;
+        } else {
+          alpha = gam / den;
+        }
+      }
+      st_gam[o] = gam;
+      st_al[o] = act ? alpha : 0.0;
+      st_be[o] = act ? beta : 0.0;
+      st_act[o] = act ? 1 : 0;
+    }
+    __syncthreads();
+  }
+  if (timed_out && tid == 0) {
+    atomicOr(&a.st->status, kStatTimeout);
+    for (int k = cstep; k < lstep; ++k) mbar_wait(&bars[k % kSlots1], (k / kSlots1) & 1);
+  }
+  if (status && blockIdx.x == 0) atomicOr(&a.st->status, status);
+  __syncthreads();
+  if (blockIdx.x == 0) {
+    if (tid == 0) s_nact = 0;
+    __syncthreads();
+    for (int o = tid; o < Np; o += blockDim.x) {
+      a.st->active[o] = st_act[o];
+      a.st->iters[o] = st_it[o];
+      if (st_act[o]) atomicAdd(&s_nact, 1);
+    }
+    __syncthreads();
+    if (tid == 0) a.st->n_active = s_nact;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // K2: p = D^-1 r + beta p, x += alpha p, r -= alpha q, partials (r,z), (r,r);
 // the last CTA updates masks, counts, beta and the graph's while condition.
 // ---------------------------------------------------------------------------
@@ -1297,6 +1760,163 @@ cudaError_t cg_launch_k2(CGPlan<T>* P, cudaStream_t st) {
   a.in_graph = 0;
   k_cg_upd<T><<<P->grid_upd, P->nt_upd, P->smem_upd, st>>>(a, 0);
   return cudaGetLastError();
+}
+
+
+// ---------------------------------------------------------------------------
+// Single-reduction CG: geometry, tensor maps, launch (float32 only)
+// ---------------------------------------------------------------------------
+// Instances by orbital groups; 64-node tiles, at most 512 threads (up to 128
+// registers a thread: a 128-node tile at 640 threads would spill at 96).
+template <int MAXT>
+void* cg1_fn_t(int G4) {
+  switch (G4) {
+    case 1: return (void*)k_cg1<1, MAXT>;
+    case 2: return (void*)k_cg1<2, MAXT>;
+    case 3: return (void*)k_cg1<3, MAXT>;
+    case 4: return (void*)k_cg1<4, MAXT>;
+    case 5: return (void*)k_cg1<5, MAXT>;
+    case 6: return (void*)k_cg1<6, MAXT>;
+    case 7: return (void*)k_cg1<7, MAXT>;
+    case 8: return (void*)k_cg1<8, MAXT>;
+  }
+  return nullptr;
+}
+void* cg1_fn(int G4, int nthr) { return nthr == 64 ? cg1_fn_t<512>(G4) : nullptr; }
+
+// Shared-memory footprint of the single-reduction kernel: 3 slots of r, w, s (with
+// halo), D^-1 and the packed weights; sacc [3 Np], the per-orbital state (5 Np
+// doubles), block sums [nthr][bw] with slices, reused for totals [3 Np] and slices.
+void cg1_layout(int Np, int bw, int TX, int TY, K1Geom* G) {
+  const size_t sz = sizeof(float);
+  G->TX = TX;
+  G->TY = TY;
+  G->npt = 1;
+  G->nthr = TX * TY;
+  const int HX = TX + 2, HY = TY + 2;
+  G->DX = TX + 4;
+  const size_t vec = (size_t)HX * HY * bw * sz;
+  const size_t dv = (size_t)G->DX * HY * sz;
+  const size_t wv = (size_t)kWS * TX * TY * sz;
+  auto al = [](size_t v) { return (v + 127) / 128 * 128; };
+  G->off_p = (int)al(vec);
+  G->off_s = (int)(G->off_p + al(vec));
+  G->off_d = (int)(G->off_s + al(vec));
+  G->off_w = (int)(G->off_d + al(dv));
+  G->slot_bytes = (int)(G->off_w + al(wv));
+  G->tx_bytes = (uint32_t)(3 * vec + dv + wv);
+  const size_t nthr = (size_t)G->nthr * (bw / 4);
+  const size_t fin = (size_t)3 * Np + (nthr > (size_t)3 * Np ? nthr : (size_t)3 * Np);
+  const size_t blk = (size_t)G->nthr * bw + nthr;
+  const size_t red = ((size_t)3 * Np + 5 * (size_t)Np + (blk > fin ? blk : fin)) * sizeof(double);
+  G->smem = 128 + (size_t)kSlots1 * G->slot_bytes + red;
+}
+
+cudaError_t cg1_plan_geometry(const Grid& g, int Np, int nsm, K1Geom* geo) {
+  const size_t stat = (size_t)2 * kMaxN * sizeof(float) + 2 * (kMaxN / 4) * sizeof(int) + 64;
+  const size_t limit = 227 * 1024 - stat - 1024;
+  // 64-node tiles (measured at 64^3 x 20: 62.7 us a pass on 16x4 tiles with 320
+  // threads, 86 us on 16x8 tiles with 640 threads, where registers spill)
+  const int shapes[2][2] = {{16, 4}, {8, 8}};
+  int first = 0;
+  if (const char* t = std::getenv("PARO_CG_TILE"))  // tuning switch: PARO_CG_TILE=8x8
+    if (std::strcmp(t, "8x8") == 0) first = 1;
+  K1Geom best{};
+  int best_bw = 0;
+  for (int nob = (Np + 31) / 32; nob <= Np / 4 && !best_bw; ++nob) {
+    int bw = (Np + nob - 1) / nob;
+    bw = (bw + 3) / 4 * 4;
+    if ((Np + bw - 1) / bw != nob) continue;
+    for (int si = first; si < 2; ++si) {
+      const int TX = shapes[si][0], TY = shapes[si][1];
+      if (TX * TY * (bw / 4) > 512) continue;
+      K1Geom G{};
+      cg1_layout(Np, bw, TX, TY, &G);
+      if (G.smem <= limit) {
+        best = G;
+        best_bw = bw;
+        break;
+      }
+    }
+  }
+  if (!best_bw) return cudaErrorInvalidConfiguration;
+  K1Geom G = best;
+  G.G4 = best_bw / 4;
+  G.ncx = (g.nx - 1 + G.TX - 1) / G.TX;
+  G.ncy = (g.ny - 1 + G.TY - 1) / G.TY;
+  G.nob = (Np + best_bw - 1) / best_bw;
+  void* f = cg1_fn(G.G4, G.nthr);
+  int per_sm = 1;
+  if (f && cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G.smem) == cudaSuccess) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, G.nthr * G.G4, G.smem) == cudaSuccess && nb > 0)
+      per_sm = nb;
+  }
+  const long long want = (long long)nsm * per_sm;
+  const long long F = (long long)G.nob * G.ncx * G.ncy * (g.nz - 1);
+  long long grid = F / 4;
+  if (grid < 1) grid = 1;
+  if (grid > want) grid = want;
+  G.grid = (int)grid;
+  *geo = G;
+  return cudaSuccess;
+}
+
+cudaError_t cg1_prepare(CGPlan<float>* P) {
+  cudaError_t e;
+  P->cg1_ok = false;
+  if (P->args.s == nullptr || P->args.r2 == nullptr || P->args.q2 == nullptr || P->args.s2 == nullptr)
+    return cudaSuccess;
+  if ((e = cg1_plan_geometry(P->args.g, P->args.Np, P->nsm, &P->geo1)) != cudaSuccess) return e;
+  const K1Geom& G = P->geo1;
+  const CGArgs<float>& a = P->args;
+  const int bw = G.G4 * 4;
+  const uint64_t sz = sizeof(float);
+  const CUtensorMapDataType ty = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  {
+    uint64_t dims[4] = {(uint64_t)a.Np, (uint64_t)a.g.Px, (uint64_t)a.g.Py, (uint64_t)a.g.Pz};
+    uint64_t str[3] = {a.Np * sz, (uint64_t)a.g.Px * a.Np * sz, (uint64_t)a.g.Py * a.g.Px * a.Np * sz};
+    uint32_t box[4] = {(uint32_t)bw, (uint32_t)(G.TX + 2), (uint32_t)(G.TY + 2), 1};
+    if ((e = encode_tiled(&P->m1r[0], ty, 4, a.r, dims, str, box)) != cudaSuccess) return e;
+    if ((e = encode_tiled(&P->m1q[0], ty, 4, a.q, dims, str, box)) != cudaSuccess) return e;
+    if ((e = encode_tiled(&P->m1s[0], ty, 4, a.s, dims, str, box)) != cudaSuccess) return e;
+    if ((e = encode_tiled(&P->m1r[1], ty, 4, a.r2, dims, str, box)) != cudaSuccess) return e;
+    if ((e = encode_tiled(&P->m1q[1], ty, 4, a.q2, dims, str, box)) != cudaSuccess) return e;
+    if ((e = encode_tiled(&P->m1s[1], ty, 4, a.s2, dims, str, box)) != cudaSuccess) return e;
+  }
+  {
+    uint64_t dims[3] = {(uint64_t)P->dpitch, (uint64_t)a.g.Py, (uint64_t)a.g.Pz};
+    uint64_t str[2] = {(uint64_t)P->dpitch * sz, (uint64_t)P->dpitch * a.g.Py * sz};
+    uint32_t box[3] = {(uint32_t)G.DX, (uint32_t)(G.TY + 2), 1};
+    if ((e = encode_tiled(&P->m1d, ty, 3, (void*)P->dinv_tma, dims, str, box)) != cudaSuccess) return e;
+  }
+  {
+    const uint64_t nxi = (uint64_t)(a.g.nx - 1), nyi = (uint64_t)(a.g.ny - 1);
+    uint64_t dims[4] = {(uint64_t)kWS, nxi, nyi, (uint64_t)a.g.Pz};
+    uint64_t str[3] = {(uint64_t)kWS * sz, (uint64_t)kWS * nxi * sz, (uint64_t)kWS * nxi * nyi * sz};
+    uint32_t box[4] = {(uint32_t)kWS, (uint32_t)G.TX, (uint32_t)G.TY, 1};
+    if ((e = encode_tiled(&P->m1w, ty, 4, (void*)P->wcoef, dims, str, box)) != cudaSuccess) return e;
+  }
+  void* f = cg1_fn(G.G4, G.nthr);
+  if (!f) return cudaErrorInvalidValue;
+  if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G.smem)) != cudaSuccess)
+    return e;
+  int nb = 0, dev = 0, coop = 0;
+  P->cg1_ok = cudaGetDevice(&dev) == cudaSuccess &&
+              cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
+              cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, G.nthr * G.G4, G.smem) == cudaSuccess &&
+              (long long)nb * P->nsm >= G.grid;
+  return cudaSuccess;
+}
+
+cudaError_t cg_launch_cg1(CGPlan<float>* P, cudaStream_t st) {
+  CGArgs<float> a = P->args;
+  a.in_graph = 0;
+  K1Geom geo = P->geo1;
+  cudaError_t e = cudaMemsetAsync(&a.st->bar_count, 0, sizeof(unsigned int), st);
+  if (e != cudaSuccess) return e;
+  void* args[] = {&a, &geo, &P->m1r[0], &P->m1q[0], &P->m1s[0], &P->m1r[1], &P->m1q[1], &P->m1s[1], &P->m1d, &P->m1w};
+  return cudaLaunchCooperativeKernel(cg1_fn(geo.G4, geo.nthr), dim3(geo.grid), dim3(geo.nthr * geo.G4), args, geo.smem, st);
 }
 
 template cudaError_t cg_prepare<float>(CGPlan<float>*);

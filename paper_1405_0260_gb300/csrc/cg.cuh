@@ -36,6 +36,8 @@ struct CGArgs {
   Grid g;
   int N, Np;
   T *x, *b, *r, *p, *q;  // padded-grid vectors [node][Np]
+  T* s;                  // single-reduction CG: s = A p (null in the two-reduction form); q holds w = A u
+  T *r2, *q2, *s2;       // single-reduction CG: the second buffer set of r, w, s
   const T* dinv;         // inverse diagonal, padded grid (pitch Px)
   double* part;          // per-CTA partial sums
   CGDevState* st;
@@ -48,7 +50,7 @@ struct K1Geom {
   int ncx, ncy, nob;  // columns per axis, orbital blocks of width 4*G4
   int grid, G4;       // CTAs (each takes an equal share of the column-planes), float4 groups per block
   int npt, nthr;      // tile nodes per thread; node slots per CTA (TX * TY = nthr * npt)
-  int off_p, off_d, off_w, slot_bytes;  // byte offsets inside one ring slot
+  int off_p, off_s, off_d, off_w, slot_bytes;  // byte offsets inside one ring slot
   uint32_t tx_bytes;                    // TMA bytes per slot
   size_t smem;                          // dynamic shared memory per CTA
 };
@@ -71,6 +73,14 @@ struct CGPlan {
   cudaGraphExec_t exec_zero = nullptr, exec_warm = nullptr;
   int graph_N = -1;  // N the graphs were built for
   bool coop_ok = false;  // the persistent CG kernel's grid can be co-resident
+  // single-reduction CG (float32): geometry, tensor maps of r, w (= q), s, D^-1, weights
+  K1Geom geo1{};
+  bool cg1_ok = false;
+  alignas(64) CUtensorMap m1r[2];
+  alignas(64) CUtensorMap m1q[2];
+  alignas(64) CUtensorMap m1s[2];
+  alignas(64) CUtensorMap m1d;
+  alignas(64) CUtensorMap m1w;
   // adds q = A x (the warm-start apply) as a graph node
   std::function<cudaError_t(cudaGraph_t, cudaGraphNode_t*)> add_apply;
 };
@@ -96,6 +106,9 @@ cudaError_t cg_launch_k2(CGPlan<T>* P, cudaStream_t st);
 // error (and launches nothing) if the grid cannot be co-resident.
 template <typename T>
 cudaError_t cg_launch_loop(CGPlan<T>* P, cudaStream_t st);
+// Single-reduction CG (float32): plan (after the tensor maps' pointers are set) and launch.
+cudaError_t cg1_prepare(CGPlan<float>* P);
+cudaError_t cg_launch_cg1(CGPlan<float>* P, cudaStream_t st);
 
 // Packed operator weights per input plane, [Pz][ny-1][nx-1][kPackedW], for the tiled kernel.
 constexpr int kPackedW = 28;
