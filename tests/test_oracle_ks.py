@@ -1,0 +1,100 @@
+"""Pins of the Kohn-Sham oracle (oracle/ks.py) against what the mathematics fixes (no GPU)."""
+import math
+
+import numpy as np
+from scipy.special import erf
+
+from oracle import ks as KS
+from oracle import paro as O
+from paper_1405_0260_gb300 import workloads as W
+
+
+def _gaussian_density(mesh, N_e, s, c=(0.0, 0.0, 0.0)):
+    X = O.gauss_points(mesh).reshape(-1, 3)
+    r2 = ((X - np.asarray(c)) ** 2).sum(1)
+    return N_e * (2 * np.pi * s * s) ** -1.5 * np.exp(-r2 / (2 * s * s)), np.sqrt(r2)
+
+
+def test_density_integrates_to_the_occupation_sum():
+    # M-orthonormal orbitals: int u_i u_j = delta_ij, and the 2-point Gauss rule
+    # integrates products of Q1 functions exactly, so int rho = sum_i f_i
+    p = W.harmonic(nc=7, L=4.0, N=5, seed=11)
+    ops = O.assemble(O.Mesh(p.n, p.lo, p.hi), p.Vq, 0.0)
+    U = O.rayleigh_ritz(ops, p.U0).U
+    occ = np.array([2.0, 2.0, 1.0, 0.5, 0.0])
+    rho = KS.density_gauss(ops.mesh, U, occ)
+    assert abs(KS.integrate(ops.mesh, rho) - occ.sum()) < 1e-12
+    assert np.all(rho >= 0.0)
+
+
+def test_density_of_a_trilinear_function_is_its_square():
+    # the Q1 interpolant of a trilinear function is the function itself: on cells
+    # that do not touch the boundary the Gauss-point values are exact
+    mesh = O.Mesh((6, 5, 7), (-1.0, -0.5, 0.0), (2.0, 2.0, 3.5))
+    f = lambda x, y, z: (0.3 + 1.1 * x) * (1.0 - 0.4 * y) * (0.2 + 0.7 * z)  # noqa: E731
+    xyz = mesh.interior_coords()
+    u = f(xyz[:, 0], xyz[:, 1], xyz[:, 2])[:, None]
+    rho = KS.density_gauss(mesh, u, np.array([1.0])).reshape(mesh.n[2], mesh.n[1], mesh.n[0], 8)
+    X = O.gauss_points(mesh).reshape(mesh.n[2], mesh.n[1], mesh.n[0], 8, 3)
+    inner = (slice(1, -1), slice(1, -1), slice(1, -1))
+    exact = f(X[inner][..., 0], X[inner][..., 1], X[inner][..., 2]) ** 2
+    assert np.max(np.abs(rho[inner] - exact)) < 1e-13
+
+
+def test_monopole_of_a_gaussian_charge():
+    mesh = O.Mesh((12, 12, 12), (-6.0, -6.0, -6.0), (6.0, 6.0, 6.0))
+    rho, _ = _gaussian_density(mesh, 3.0, 0.8, c=(0.4, -0.3, 0.2))
+    Q, xc = KS.monopole(mesh, rho)
+    assert abs(Q - 3.0) < 1e-3
+    assert np.max(np.abs(xc - np.array([0.4, -0.3, 0.2]))) < 1e-3
+
+
+def test_hartree_of_a_gaussian_charge_converges_at_second_order():
+    # -Delta V = 4 pi rho for a normalised Gaussian of width s: V = erf(r / (sqrt 2 s)) / r;
+    # on [-8, 8]^3 the monopole boundary data are exact to 1e-15
+    errs = []
+    for nc in (12, 24):
+        mesh = O.Mesh((nc, nc, nc), (-8.0, -8.0, -8.0), (8.0, 8.0, 8.0))
+        rho, r = _gaussian_density(mesh, 1.0, 1.0)
+        V = KS.hartree(mesh, rho).VH_q
+        exact = erf(r / math.sqrt(2.0)) / r
+        w = np.tile(O.element_matrices(mesh.h)[3], mesh.n[0] ** 3)
+        errs.append(math.sqrt(np.sum(w * (V - exact) ** 2) / np.sum(w * exact ** 2)))
+    assert errs[1] < 6e-3, errs  # h = 2s/3
+    assert 3.3 < errs[0] / errs[1] < 4.7, errs
+
+
+def test_slater_energy_of_a_gaussian_density():
+    # int rho^(4/3) of N (2 pi s^2)^(-3/2) exp(-r^2 / 2 s^2) is N^(4/3) (3/4)^(3/2) / (sqrt(2 pi) s)
+    N_e, s = 2.0, 1.2
+    mesh = O.Mesh((40, 40, 40), (-8.0, -8.0, -8.0), (8.0, 8.0, 8.0))
+    rho, _ = _gaussian_density(mesh, N_e, s)
+    exact = -0.75 * (3.0 / math.pi) ** (1.0 / 3.0) * N_e ** (4.0 / 3.0) * 0.75 ** 1.5 / (math.sqrt(2 * math.pi) * s)
+    assert abs(KS.slater_energy(mesh, rho) - exact) < 1e-3 * abs(exact)
+    # the potential is the derivative of the energy density: V_x = d e_x / d rho
+    r0 = np.array([0.05, 0.3, 1.7])
+    e = lambda t: -0.75 * (3.0 / math.pi) ** (1.0 / 3.0) * t ** (4.0 / 3.0)  # noqa: E731
+    num = (e(r0 * (1 + 1e-6)) - e(r0 * (1 - 1e-6))) / (2e-6 * r0)
+    assert np.max(np.abs(KS.slater_potential(r0) - num)) < 1e-8
+
+
+def test_occupations():
+    assert KS.occupations(6, 7).tolist() == [2, 2, 2, 1, 0, 0]
+    assert KS.occupations(3, 4).tolist() == [2, 2, 0]
+
+
+def test_scf_keeps_the_charge_and_becomes_self_consistent():
+    # two electrons on a softened nucleus Z = 2, two orbitals (one buffer)
+    nc, L = 9, 5.0
+    mesh = O.Mesh((nc, nc, nc), (-L, -L, -L), (L, L, L))
+    X = O.gauss_points(mesh).reshape(-1, 3)
+    Vext = -2.0 / np.sqrt((X ** 2).sum(1) + 0.25)
+    p = W.harmonic(nc=nc, L=L, N=2, seed=21)
+    occ = KS.occupations(2, 2)
+    res = KS.scf(mesh, Vext, p.U0, occ, sigma=3.0, tol=1e-9, max_outer=300)
+    assert res.outer < 300
+    assert max(abs(c - 2.0) for c in res.charge) < 1e-10
+    rho_out = KS.density_gauss(mesh, res.U, occ)
+    assert KS.integrate(mesh, np.abs(rho_out - res.rho_q)) < 1e-6
+    # bound state below the continuum of the box
+    assert res.lam[0] < 0.0
