@@ -158,6 +158,42 @@ int paro_iterate(paro_mesh m, int N, double* U, double* lambda, const paro_param
  * X, Y: device (n_interior x N), must not alias.  The kernel the CG iterations use. */
 int paro_apply(paro_mesh m, int N, int op, int dtype, const void* X, void* Y);
 
+/* ---------------------------------------------------------------------------
+ * Kohn-Sham (Section 2.2): fields at the 2x2x2 Gauss points of every cell,
+ * device float64 arrays of 8*nx*ny*nz values in the order of paro_set_potential.
+ * ------------------------------------------------------------------------- */
+
+/* Electron density rho(x_q) = sum_i occ_i u_i(x_q)^2 (eq. (2.6)'s rho with
+ * occupations).  U: device (n_interior x N) float64; occ: host[N]; rho_q: device,
+ * written.  Needs a potential set on the handle (its workspace). */
+int paro_density(paro_mesh m, int N, const double* U, const double* occ, double* rho_q);
+
+/* v_q = vext_q + V_H(rho) + V_x(rho) and/or vh_q = V_H(rho).  V_H solves
+ * -Delta V_H = 4 pi rho (the Poisson form of Section 2.2) with Q1 elements on the
+ * box, Dirichlet data Q/|x - x_c| (the monopole of rho: charge Q, centre x_c),
+ * by float64 Jacobi-PCG to p->solve_tol through the library's own stencil and CG
+ * (an internal handle whose operator is K/2).  V_x = -(3 rho/pi)^(1/3) (Slater
+ * exchange, the local-density approximation).  rho_q, vext_q: device in;
+ * v_q, vh_q: device out (either may be NULL, not both).  p may be NULL (defaults). */
+int paro_ks_potential(paro_mesh m, const double* rho_q, const double* vext_q, double* v_q, double* vh_q,
+                      const paro_params* p);
+
+/* Kohn-Sham ParO (Algorithm 3.1 with the Kohn-Sham potential): one
+ * Rayleigh-Ritz on span(U) with vext_q gives the first density rho_in; each
+ * outer iteration sets the potential vext + V_H(rho_in) + V_x(rho_in) with the
+ * handle's sigma (from the last paro_set_potential), solves the N source
+ * problems and does Rayleigh-Ritz with it, then mixes
+ * rho_in <- (1 - mix) rho_in + mix rho_out (rho_out: density of the new
+ * orbitals).  Stops when max_i |Delta lambda_i| < p->tol or after p->fixed_outer.
+ * occ: host[N] occupations; vext_q: device; U: device (n_interior x N) in/out;
+ * lambda: host[N] out.  The handle's potential is the last effective potential
+ * on return.  Errors as paro_iterate. */
+int paro_scf_iterate(paro_mesh m, int N, const double* occ, const double* vext_q, double mix, double* U,
+                     double* lambda, const paro_params* p, paro_stats* s);
+
+/* Copy the mixed density rho_in of the last paro_scf_iterate to rho_q (device). */
+int paro_ks_density_in(paro_mesh m, double* rho_q);
+
 /* Largest N accepted by paro_small_eig_static. */
 #define PARO_STATIC_EIG_MAX_N 128
 

@@ -82,10 +82,16 @@ def lib():
     L.paro_rayleigh_ritz.argtypes = [vp, ip, vp, vp, dp, C.POINTER(paro_stats)]
     L.paro_iterate.argtypes = [vp, ip, vp, dp, C.POINTER(paro_params), C.POINTER(paro_stats)]
     L.paro_apply.argtypes = [vp, ip, ip, ip, vp, vp]
+    L.paro_density.argtypes = [vp, ip, vp, dp, vp]
+    L.paro_ks_potential.argtypes = [vp, vp, vp, vp, vp, C.POINTER(paro_params)]
+    L.paro_scf_iterate.argtypes = [vp, ip, dp, vp, C.c_double, vp, dp, C.POINTER(paro_params),
+                                   C.POINTER(paro_stats)]
+    L.paro_ks_density_in.argtypes = [vp, vp]
     L.paro_last_error.argtypes = [vp]
     L.paro_last_error.restype = C.c_char_p
     for f in ("paro_mesh_create", "paro_mesh_destroy", "paro_set_potential", "paro_orbital_solve",
-              "paro_rayleigh_ritz", "paro_iterate", "paro_apply"):
+              "paro_rayleigh_ritz", "paro_iterate", "paro_apply", "paro_density", "paro_ks_potential",
+              "paro_scf_iterate", "paro_ks_density_in"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -232,6 +238,29 @@ class Mesh:
         else:
             dt = PARO_FF if float_float else PARO_F64
         paro_apply(self.h, X.shape[1], op, dt, self._dev(X, X.dtype), self._dev(Y, X.dtype))
+
+    # Kohn-Sham (fields at the Gauss points, float64 device tensors of 8*nx*ny*nz values)
+    def density(self, U, occ, rho):
+        occ = np.ascontiguousarray(occ, dtype=np.float64)
+        _check(lib().paro_density(self.h, U.shape[1], self._dev(U), _dptr(occ), self._dev(rho)), self.h)
+
+    def ks_potential(self, rho, vext, v=None, vh=None, params=None):
+        _check(lib().paro_ks_potential(self.h, self._dev(rho), self._dev(vext),
+                                        None if v is None else self._dev(v), None if vh is None else self._dev(vh),
+                                        C.byref(params) if params is not None else None), self.h)
+
+    def scf_iterate(self, U, occ, vext, mix=0.3, params=None, allow=()):
+        N = U.shape[1]
+        occ = np.ascontiguousarray(occ, dtype=np.float64)
+        lam = np.zeros(N)
+        st = paro_stats()
+        rc = lib().paro_scf_iterate(self.h, N, _dptr(occ), C.c_void_p(self._dev(vext)), float(mix),
+                                     C.c_void_p(self._dev(U)), _dptr(lam),
+                                     C.byref(params) if params is not None else None, C.byref(st))
+        return _check(rc, self.h, allow), lam, st
+
+    def ks_density_in(self, rho):
+        _check(lib().paro_ks_density_in(self.h, self._dev(rho)), self.h)
 
 
 def paro_small_eig_static(N, GA_ptr, GB_ptr, C_ptr, theta_ptr, stream=0):

@@ -65,6 +65,16 @@ struct paro_mesh_s {
   double *w64 = nullptr, *dt64 = nullptr;
   CGPlan<float>* plan32 = nullptr;
   CGPlan<double>* plan64 = nullptr;
+  // Kohn-Sham: box origin, the float64 handle of the Poisson operator K/2 (V = 0,
+  // sigma = 0) that solves for the Hartree potential, and Gauss-point fields
+  double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+  paro_mesh pois = nullptr;
+  double* ks_mom = nullptr;   // [Q, x_c, y_c, z_c]
+  double* ks_part = nullptr;  // block partials of the moments
+  double* ks_rho = nullptr;   // rho_in
+  double* ks_rho2 = nullptr;  // rho_out
+  double* ks_v = nullptr;     // the effective potential
+  double* ks_occ = nullptr;   // occupations [Np]
 };
 
 static std::string g_create_err;
@@ -619,6 +629,77 @@ struct CallScope {
   }
 };
 
+
+// ---------------------------------------------------------------------------
+// Kohn-Sham helpers
+// ---------------------------------------------------------------------------
+
+long long gauss_count(const Grid& g) { return (long long)g.nx * g.ny * g.nz * 8; }
+
+int ensure_ks(paro_mesh m) {
+  if (m->ks_rho) return PARO_OK;
+  const long long nq = gauss_count(m->g);
+  TRY(dalloc(m, &m->ks_mom, 4));
+  TRY(dalloc(m, &m->ks_part, (size_t)4 * moments_blocks()));
+  TRY(dalloc(m, &m->ks_rho, (size_t)nq));
+  TRY(dalloc(m, &m->ks_rho2, (size_t)nq));
+  TRY(dalloc(m, &m->ks_v, (size_t)nq));
+  TRY(dalloc(m, &m->ks_occ, (size_t)kMaxN));
+  return PARO_OK;
+}
+
+// The float64 handle of K/2 on the same mesh (V = 0, sigma = 0), for the Poisson solve.
+int ensure_poisson(paro_mesh m) {
+  if (m->pois) return PARO_OK;
+  paro_mesh c = nullptr;
+  int rc = paro_mesh_create(&c, m->g.nx, m->g.ny, m->g.nz, m->lo, m->hi, PARO_FP64, m->st);
+  if (rc != PARO_OK) return fail(m, rc, std::string("Poisson handle: ") + paro_last_error(nullptr));
+  m->pois = c;
+  double* zeros = nullptr;
+  TRY(dalloc(m, &zeros, (size_t)gauss_count(m->g)));  // zeroed on the stream
+  rc = paro_set_potential(c, zeros, 0.0);
+  if (rc != PARO_OK) return fail(m, rc, std::string("Poisson handle: ") + paro_last_error(c));
+  TRY(ensure_workspace(c, 4));
+  return PARO_OK;
+}
+
+// Hartree potential of rho (Gauss points): monopole, right-hand side, CG solve of
+// (K/2) w = 2 pi (rho, phi) - (K/2)_{I,boundary} g on the Poisson handle; the
+// solution is left in m->pois->x (padded, column 0).
+int hartree_solve(paro_mesh m, const double* rho, double tol, int maxit) {
+  TRY(ensure_ks(m));
+  TRY(ensure_poisson(m));
+  paro_mesh c = m->pois;
+  LAUNCH(2, launch_moments(m->g, m->lo, rho, m->ks_part, m->ks_mom, m->st));
+  CK(cudaMemsetAsync(c->b, 0, sizeof(double) * c->g.G * 4, m->st));
+  LAUNCH(1, launch_hartree_rhs(c->g, m->lo, rho, c->coef64, m->ks_mom, c->b, m->st));
+  CK(cudaMemsetAsync(c->cgst->skip, 0, sizeof(int) * kMaxN, m->st));
+  long long its = 0;
+  int itmax = 0;
+  int rc = run_cg<double>(c, c->plan64, 1, false, tol, maxit, 16, &its, &itmax);
+  if (rc != PARO_OK) return fail(m, rc, std::string("Hartree solve: ") + c->err);
+  rc = check_status(c, "Hartree solve");
+  if (rc != PARO_OK) return fail(m, rc, c->err);
+  m->launches += c->launches;
+  c->launches = 0;
+  return PARO_OK;
+}
+
+// v = V_ext + V_H(rho) + V_x(rho) at the Gauss points (vh: V_H alone, optional).
+int ks_potential(paro_mesh m, const double* rho, const double* vext, double* v, double* vh, double tol, int maxit) {
+  TRY(hartree_solve(m, rho, tol, maxit));
+  LAUNCH(1, launch_ks_potential(m->g, m->lo, m->pois->x, m->ks_mom, rho, vext, v, vh, m->st));
+  return PARO_OK;
+}
+
+int upload_occ(paro_mesh m, int N, const double* occ) {
+  TRY(ensure_ks(m));
+  for (int i = 0; i < N; ++i) m->h_dbl[i] = occ[i];
+  CK(cudaMemcpyAsync(m->ks_occ, m->h_dbl, sizeof(double) * N, cudaMemcpyHostToDevice, m->st));
+  CK(cudaStreamSynchronize(m->st));
+  return PARO_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -671,6 +752,10 @@ int paro_mesh_create(paro_mesh* out, int nx, int ny, int nz, const double lo[3],
   g.hx = (hi[0] - lo[0]) / nx;
   g.hy = (hi[1] - lo[1]) / ny;
   g.hz = (hi[2] - lo[2]) / nz;
+  for (int d = 0; d < 3; ++d) {
+    m->lo[d] = lo[d];
+    m->hi[d] = hi[d];
+  }
   mass_weights(g, &m->mw);
   m->dpitch = (g.Px + 3) / 4 * 4;
   {
@@ -717,6 +802,7 @@ int paro_mesh_create(paro_mesh* out, int nx, int ny, int nz, const double lo[3],
 int paro_mesh_destroy(paro_mesh m) {
   if (!m) return PARO_ERR_ARG;
   cudaStreamSynchronize(m->st);
+  if (m->pois) paro_mesh_destroy(m->pois);
   free_plans(m);
   for (void* p : m->allocs)
     if (p) cudaFree(p);
@@ -872,6 +958,99 @@ int paro_apply(paro_mesh m, int N, int op, int dtype, const void* X, void* Y) {
     LAUNCH(1, launch_apply_f32(m->g, Np, m->coef32, m->b32, m->q32, m->st));
     LAUNCH(1, launch_unpack_f32(m->g, N, Np, m->q32, static_cast<float*>(Y), m->st));
   }
+  CK(cudaStreamSynchronize(m->st));
+  return PARO_OK;
+}
+
+int paro_density(paro_mesh m, int N, const double* U, const double* occ, double* rho_q) {
+  TRY(check_common(m, N));
+  if (!U || !occ || !rho_q) return fail(m, PARO_ERR_ARG, "null pointer");
+  const int Np = (N + 3) / 4 * 4;
+  TRY(ensure_workspace(m, Np));
+  TRY(upload_occ(m, N, occ));
+  LAUNCH(1, launch_pack(m->g, N, Np, U, m->u, m->st));
+  LAUNCH(1, launch_density(m->g, N, Np, m->u, m->ks_occ, rho_q, m->st));
+  CK(cudaStreamSynchronize(m->st));
+  return PARO_OK;
+}
+
+int paro_ks_potential(paro_mesh m, const double* rho_q, const double* vext_q, double* v_q, double* vh_q,
+                      const paro_params* p) {
+  if (!m) return PARO_ERR_ARG;
+  if (!rho_q || !vext_q || (!v_q && !vh_q)) return fail(m, PARO_ERR_ARG, "null pointer");
+  paro_params pp;
+  if (p) pp = *p;
+  else paro_default_params(&pp);
+  TRY(ks_potential(m, rho_q, vext_q, v_q, vh_q, pp.solve_tol, pp.pcg_maxit));
+  CK(cudaStreamSynchronize(m->st));
+  return PARO_OK;
+}
+
+int paro_scf_iterate(paro_mesh m, int N, const double* occ, const double* vext_q, double mix, double* U,
+                     double* lambda, const paro_params* p, paro_stats* s) {
+  TRY(check_common(m, N));
+  if (!occ || !vext_q || !U || !lambda) return fail(m, PARO_ERR_ARG, "null pointer");
+  if (!(mix > 0.0 && mix <= 1.0)) return fail(m, PARO_ERR_ARG, "mix must be in (0, 1]");
+  paro_params pp;
+  if (p) pp = *p;
+  else paro_default_params(&pp);
+  const int Np = (N + 3) / 4 * 4;
+  TRY(ensure_workspace(m, Np));
+  TRY(ensure_ks(m));
+  TRY(upload_occ(m, N, occ));
+  CallScope cs(m, s, pp.profile);
+  const double sigma = m->sigma;
+  LAUNCH(1, launch_pack(m->g, N, Np, U, m->u, m->st));
+  // start: Rayleigh-Ritz on span(U) with V_ext alone; its density is the first rho_in
+  TRY(paro_set_potential(m, vext_q, sigma));
+  std::vector<double> lam(N), lam_new(N);
+  TRY(rr_packed(m, N, m->u, m->x, lam.data()));
+  CK(cudaMemcpyAsync(m->u, m->x, sizeof(double) * m->g.G * Np, cudaMemcpyDeviceToDevice, m->st));
+  LAUNCH(1, launch_density(m->g, N, Np, m->u, m->ks_occ, m->ks_rho, m->st));
+  const int limit = pp.fixed_outer > 0 ? pp.fixed_outer : pp.max_outer;
+  int outer = 0, rc = PARO_ERR_NOT_CONVERGED;
+  double dl = INFINITY;
+  while (outer < limit) {
+    // V from rho_in, used in both Step 3 and Step 4 of this iteration
+    TRY(ks_potential(m, m->ks_rho, vext_q, m->ks_v, nullptr, pp.solve_tol, pp.pcg_maxit));
+    TRY(paro_set_potential(m, m->ks_v, sigma));
+    {
+      Timer t(m, s ? &s->ms_solve : nullptr);
+      int r1 = solve_packed(m, N, lam.data(), pp, s);
+      if (r1 != PARO_OK) return r1;
+    }
+    {
+      Timer t(m, s ? &s->ms_rr : nullptr);
+      TRY(rr_packed(m, N, m->x, m->u, lam_new.data()));
+    }
+    LAUNCH(1, launch_density(m->g, N, Np, m->u, m->ks_occ, m->ks_rho2, m->st));
+    LAUNCH(1, launch_mix(gauss_count(m->g), mix, m->ks_rho, m->ks_rho2, m->st));
+    dl = 0.0;
+    for (int i = 0; i < N; ++i) dl = std::fmax(dl, std::fabs(lam_new[i] - lam[i]));
+    lam = lam_new;
+    ++outer;
+    if (pp.fixed_outer <= 0 && dl < pp.tol) {
+      rc = PARO_OK;
+      break;
+    }
+  }
+  if (pp.fixed_outer > 0) rc = PARO_OK;
+  if (s) {
+    s->outer_iters = outer;
+    s->max_dlambda = dl;
+  }
+  for (int i = 0; i < N; ++i) lambda[i] = lam[i];
+  LAUNCH(1, launch_unpack(m->g, N, Np, m->u, U, m->st));
+  CK(cudaStreamSynchronize(m->st));
+  if (rc != PARO_OK) m->err = "paro_scf_iterate: max_outer reached before tol";
+  return rc;
+}
+
+int paro_ks_density_in(paro_mesh m, double* rho_q) {
+  if (!m) return PARO_ERR_ARG;
+  if (!rho_q) return fail(m, PARO_ERR_ARG, "null pointer");
+  if (!m->ks_rho) return fail(m, PARO_ERR_STATE, "no Kohn-Sham run on this handle");
+  CK(cudaMemcpyAsync(rho_q, m->ks_rho, sizeof(double) * gauss_count(m->g), cudaMemcpyDeviceToDevice, m->st));
   CK(cudaStreamSynchronize(m->st));
   return PARO_OK;
 }

@@ -156,4 +156,17 @@ cudaError_t launch_small_eig(int N, const double* GA, const double* GB, double* 
 cudaError_t launch_rotate(const Grid& g, int N, int Np, const double* X, const double* C, double* U,
                           cudaStream_t st);
 
+// ks.cu: Kohn-Sham pieces (fields at the Gauss points)
+cudaError_t launch_density(const Grid& g, int N, int Np, const double* U, const double* occ, double* rho,
+                           cudaStream_t st);
+int moments_blocks();
+cudaError_t launch_moments(const Grid& g, const double lo[3], const double* rho, double* part, double* mom,
+                           cudaStream_t st);
+cudaError_t launch_hartree_rhs(const Grid& g, const double lo[3], const double* rho, const double* kcoef,
+                               const double* mom, double* rhs, cudaStream_t st);
+cudaError_t launch_ks_potential(const Grid& g, const double lo[3], const double* w, const double* mom,
+                                const double* rho, const double* vext, double* vout, double* vh_out,
+                                cudaStream_t st);
+cudaError_t launch_mix(long long n, double beta, double* rho_in, const double* rho_out, cudaStream_t st);
+
 }  // namespace paro

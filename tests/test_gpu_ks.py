@@ -1,0 +1,109 @@
+"""Parity of the Kohn-Sham kernels (through the C ABI) with the CPU oracle (oracle/ks.py).
+
+Tolerances: the density is a sum of squares of interpolated values (float64,
+relative 1e-13); the Hartree potential comes from CG to 1e-12 on both sides of a
+system whose condition number grows like h^-2 (relative 1e-9); the SCF loop is
+compared iterate by iterate for a fixed number of outer iterations (1e-9
+relative on the eigenvalues), and the mixed path at convergence (1e-6 Ha).
+"""
+import numpy as np
+import pytest
+
+from oracle import ks as KS
+from oracle import paro as O
+from paper_1405_0260_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1405_0260_gb300 import binding
+
+    binding.lib()
+    return binding
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def cluster(nc=10, L=5.0):
+    """Two softened nuclei (Z = 1 and 2: three electrons), four orbitals (occupations 2, 1, 0, 0)."""
+    mesh = O.Mesh((nc, nc, nc), (-L, -L, -L), (L, L, L))
+    X = O.gauss_points(mesh).reshape(-1, 3)
+    R = np.array([[0.6, -0.2, 0.1], [-0.7, 0.3, -0.2]])
+    Z = np.array([1.0, 2.0])
+    Vext = sum(-z / np.sqrt(((X - r) ** 2).sum(1) + 0.25) for z, r in zip(Z, R))
+    p = W.harmonic(nc=nc, L=L, N=4, seed=5100)
+    return mesh, np.ascontiguousarray(Vext), p.U0, KS.occupations(4, 3)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_density_matches_oracle(B, prec):
+    mesh, Vext, U0, occ = cluster(nc=9)
+    m = B.Mesh(mesh.n, mesh.lo, mesh.hi, B.PARO_FP64 if prec == "fp64" else B.PARO_MIXED)
+    vq = dev(Vext)
+    m.set_potential(vq, 3.0)
+    rho = torch.empty(8 * mesh.n[0] ** 3, dtype=torch.float64, device="cuda")
+    m.density(dev(U0), occ, rho)
+    ref = KS.density_gauss(mesh, U0, occ)
+    assert np.max(np.abs(host(rho) - ref)) < 1e-13 * np.max(ref)
+    m.close()
+
+
+def test_hartree_and_ks_potential_match_oracle(B):
+    mesh, Vext, U0, occ = cluster(nc=12, L=6.0)
+    ops = O.assemble(mesh, Vext, 3.0)
+    U = O.rayleigh_ritz(ops, U0).U
+    rho = KS.density_gauss(mesh, U, occ)
+    ref_h = KS.hartree(mesh, rho).VH_q
+    ref_v = Vext + ref_h + KS.slater_potential(rho)
+    m = B.Mesh(mesh.n, mesh.lo, mesh.hi, B.PARO_FP64)
+    vq = dev(Vext)
+    m.set_potential(vq, 3.0)
+    v = torch.empty_like(vq)
+    vh = torch.empty_like(vq)
+    m.ks_potential(dev(rho), vq, v, vh, B.paro_default_params(solve_tol=1e-13, pcg_maxit=20000))
+    assert np.max(np.abs(host(vh) - ref_h)) < 1e-9 * np.max(np.abs(ref_h))
+    assert np.max(np.abs(host(v) - ref_v)) < 1e-9 * np.max(np.abs(ref_v))
+    m.close()
+
+
+def test_scf_fp64_iterate_by_iterate(B):
+    mesh, Vext, U0, occ = cluster(nc=9)
+    ref = KS.scf(mesh, Vext, U0, occ, sigma=3.0, fixed_outer=4, pcg_tol=1e-12)
+    m = B.Mesh(mesh.n, mesh.lo, mesh.hi, B.PARO_FP64)
+    vq = dev(Vext)
+    m.set_potential(vq, 3.0)
+    U = dev(U0)
+    params = B.paro_default_params(fixed_outer=4, solve_tol=1e-12)
+    rc, lam, st = m.scf_iterate(U, occ, vq, 0.3, params)
+    assert rc == 0 and st.outer_iters == 4
+    assert np.max(np.abs(lam - ref.lam) / np.abs(ref.lam)) < 1e-9, (lam, ref.lam)
+    rho_in = torch.empty_like(vq)
+    m.ks_density_in(rho_in)
+    assert np.max(np.abs(host(rho_in) - ref.rho_q)) < 1e-8 * np.max(ref.rho_q)
+    m.close()
+
+
+def test_scf_mixed_converges_to_oracle(B):
+    mesh, Vext, U0, occ = cluster(nc=9)
+    ref = KS.scf(mesh, Vext, U0, occ, sigma=3.0, tol=1e-10, max_outer=400, pcg_tol=1e-12)
+    m = B.Mesh(mesh.n, mesh.lo, mesh.hi, B.PARO_MIXED)
+    vq = dev(Vext)
+    m.set_potential(vq, 3.0)
+    U = dev(U0)
+    rc, lam, st = m.scf_iterate(U, occ, vq, 0.3, B.paro_default_params(tol=1e-10, max_outer=400, solve_tol=1e-11))
+    assert rc == 0
+    assert np.max(np.abs(lam - ref.lam)) < 1e-6, (lam, ref.lam)
+    m.close()

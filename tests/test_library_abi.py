@@ -33,7 +33,8 @@ def lib():
 def test_header_declares_the_entry_points():
     names = declared_functions()
     for f in ("paro_mesh_create", "paro_mesh_destroy", "paro_set_potential", "paro_orbital_solve",
-              "paro_rayleigh_ritz", "paro_iterate", "paro_apply", "paro_last_error", "paro_default_params"):
+              "paro_rayleigh_ritz", "paro_iterate", "paro_apply", "paro_last_error", "paro_default_params",
+              "paro_density", "paro_ks_potential", "paro_scf_iterate", "paro_ks_density_in"):
         assert f in names
 
 
