@@ -107,6 +107,7 @@ typedef struct {
   double prof_ms;              /* profile != 0: their summed device time (ms) */
   long long prof_dof_orb;      /* profile != 0: sum over their operator passes of n_interior x orbitals processed */
   long long prof_node_passes;  /* profile != 0: sum over their operator passes of n_interior x orbital blocks */
+  int rr_tc_steps;             /* Rayleigh-Ritz steps whose Gram matrices ran on the tensor cores (mixed handles) */
 } paro_stats;
 
 void paro_default_params(paro_params* p);

@@ -48,7 +48,7 @@ class paro_stats(C.Structure):
         ("max_dlambda", C.c_double), ("ms_solve", C.c_double), ("ms_rr", C.c_double),
         ("stencil_applies", C.c_longlong), ("kernel_launches", C.c_longlong),
         ("prof_launches", C.c_longlong), ("prof_ms", C.c_double), ("prof_dof_orb", C.c_longlong),
-        ("prof_node_passes", C.c_longlong),
+        ("prof_node_passes", C.c_longlong), ("rr_tc_steps", C.c_int),
     ]
 
     def as_dict(self):

@@ -17,6 +17,7 @@ using namespace paro;
 
 struct paro_mesh_s {
   Grid g{};
+  long long rr_tc = 0;  // Rayleigh-Ritz steps with tensor-core Grams (for paro_stats)
   int precision = PARO_FP64;
   cudaStream_t st = nullptr;
   std::string err;
@@ -36,6 +37,7 @@ struct paro_mesh_s {
   // operator images, [G][Np] each; float-float weights of A and H, [G][28] each
   float *fxh = nullptr, *fxl = nullptr, *fah = nullptr, *fal = nullptr, *fbh = nullptr, *fbl = nullptr;
   double* gpart_ff = nullptr;
+  double* gpart_tc = nullptr;  // tensor-core Gram partials (32 < Np <= kTcMaxNp)
   float *wAh = nullptr, *wAl = nullptr, *wHh = nullptr, *wHl = nullptr;
   double *gpart = nullptr, *GA = nullptr, *GB = nullptr, *C = nullptr, *theta = nullptr, *eigwork = nullptr;
   double* dscal = nullptr;  // per-orbital double scalars
@@ -86,6 +88,7 @@ namespace {
     cudaError_t e_ = (call);                                                          \
     if (e_ != cudaSuccess) {                                                          \
       m->err = std::string(#call) + ": " + cudaGetErrorString(e_);                    \
+      (void)cudaGetLastError(); /* a non-sticky error must not surface in a later call */ \
       return e_ == cudaErrorMemoryAllocation ? PARO_ERR_OOM : PARO_ERR_CUDA;          \
     }                                                                                 \
   } while (0)
@@ -242,10 +245,13 @@ int ensure_workspace(paro_mesh m, int Np) {
   free_plans(m);
   // release the previous vector workspace
   void* olds[] = {m->u,    m->x,   m->b,   m->r,   m->p0,  m->q,     m->b32,    m->x32, m->r32,
-                  m->p32a, m->q32, m->s32, m->r32b, m->q32b, m->s32b, m->fxh, m->fxl, m->fah, m->fal,   m->fbh,    m->fbl, m->gpart_ff,
+                  m->p32a, m->q32, m->s32, m->r32b, m->q32b, m->s32b, m->fxh, m->fxl, m->fah, m->fal,   m->fbh,    m->fbl, m->gpart_ff, m->gpart_tc,
                   m->gpart, m->GA, m->GB,  m->C,   m->theta, m->eigwork, m->cgpart};
   CK(cudaStreamSynchronize(m->st));
   for (void* p : olds) dfree(m, p);
+  // the Gram workspaces below are allocated only for some Np: no stale pointers
+  m->gpart_ff = nullptr;
+  m->gpart_tc = nullptr;
   size_t n = (size_t)m->g.G * Np;
   TRY(dalloc(m, &m->u, n));
   TRY(dalloc(m, &m->x, n));
@@ -269,6 +275,7 @@ int ensure_workspace(paro_mesh m, int Np) {
     TRY(dalloc(m, &m->fal, n));
     TRY(dalloc(m, &m->fbh, n));
     TRY(dalloc(m, &m->fbl, n));
+    if (Np <= kTcMaxNp) TRY(dalloc(m, &m->gpart_tc, gram_tc_partial_doubles(m->g, Np)));
     if (Np <= 32) TRY(dalloc(m, &m->gpart_ff, gram_ff_partial_doubles(m->g, Np)));
   }
   TRY(dalloc(m, &m->gpart, gram_partial_doubles(m->g, Np)));
@@ -526,12 +533,51 @@ int solve_packed(paro_mesh m, int N, const double* lam, const paro_params& p, pa
   return check_status(m, "orbital_solve");
 }
 
+// Gram precision of one Rayleigh-Ritz step on a mixed handle.
+enum RRMode {
+  kRRFast,      // tensor-core Grams (~1e-9 of |x| |y|; float64 Grams where Np > kTcMaxNp)
+  kRRAccurate,  // float-float Grams (Np <= 32), float64 Grams otherwise
+  kRRFP64,      // float64 Grams and rotation
+};
+
+// The ParO loop of a mixed handle takes the fast Grams while the Ritz values
+// still move by more than this (relative to max(1, |lambda|_max)); below it the
+// tensor-core Grams' rounding would show in |delta lambda|, so the loop switches
+// to the accurate Grams for the last iterations.
+constexpr double kRRSwitchRel = 1e-6;
+
+RRMode next_rr_mode(paro_mesh m, RRMode cur, double dl, const std::vector<double>& lam) {
+  if (m->precision != PARO_MIXED || cur != kRRFast) return cur;
+  double scale = 1.0;
+  for (double v : lam) scale = std::fmax(scale, std::fabs(v));
+  return dl < kRRSwitchRel * scale ? kRRAccurate : kRRFast;
+}
+
 // Step 4 on packed buffers: src -> dst (Ritz vectors), lam (host, ascending).
-int rr_packed(paro_mesh m, int N, const double* src, double* dst, double* lam) {
+// kRRFP64 is used for the start on user guesses, whose overlap matrix can be
+// ill-conditioned far beyond what the mixed path's Grams resolve (their error is
+// amplified by cond(X^T M X)); inside the ParO loop X stays near M-orthonormal.
+int rr_packed(paro_mesh m, int N, const double* src, double* dst, double* lam, RRMode mode = kRRFast) {
   const int Np = m->Np_alloc;
   Grid& g = m->g;
-  const bool ff = m->precision == PARO_MIXED && m->gpart_ff != nullptr;
-  if (ff) {
+  const bool mixed = m->precision == PARO_MIXED;
+  const bool tc = mixed && mode == kRRFast && m->gpart_tc != nullptr;
+  const bool ff = mixed && mode == kRRAccurate && m->gpart_ff != nullptr;
+  if (tc) {
+    // float-float X, HX and MX; both Grams on the tensor cores from their hi parts
+    // (exact BF16 digit products, float-float across 128-node chunks)
+    LAUNCH(1, launch_split_ff((long long)g.G * Np, src, m->fxh, m->fxl, m->st));
+    LAUNCH(1, launch_ff_apply(g, Np, m->wHh, m->wHl, nullptr, m->fxh, m->fxl, nullptr, nullptr, m->fah, m->fal,
+                              m->st));
+    LAUNCH(1, launch_ff_apply(g, Np, nullptr, nullptr, &m->mw, m->fxh, m->fxl, nullptr, nullptr, m->fbh, m->fbl,
+                              m->st));
+    int nch = 0;
+    LAUNCH(1, launch_gram_tc(g, Np, m->fxh, m->fah, m->gpart_tc, &nch, &m->cgst->status, m->st));
+    LAUNCH(1, launch_gram_reduce1(Np, nch, m->gpart_tc, m->GA, m->st));
+    LAUNCH(1, launch_gram_tc(g, Np, m->fxh, m->fbh, m->gpart_tc, &nch, &m->cgst->status, m->st));
+    LAUNCH(1, launch_gram_reduce1(Np, nch, m->gpart_tc, m->GB, m->st));
+    ++m->rr_tc;
+  } else if (ff) {
     // float-float: HX and MX as hi/lo arrays, both Grams and the rotation from the split X
     LAUNCH(1, launch_split_ff((long long)g.G * Np, src, m->fxh, m->fxl, m->st));
     LAUNCH(1, launch_ff_apply(g, Np, m->wHh, m->wHl, nullptr, m->fxh, m->fxl, nullptr, nullptr, m->fah, m->fal,
@@ -548,7 +594,8 @@ int rr_packed(paro_mesh m, int N, const double* src, double* dst, double* lam) {
   }
   LAUNCH(1, launch_small_eig(N, m->GA, m->GB, m->eigwork, m->C, m->theta, &m->cgst->status, m->st));
   TRY(check_status(m, "rayleigh_ritz"));
-  if (ff)
+  // the float-float rotation stages C (hi/lo, 8 Np^2 bytes) in shared memory
+  if ((ff || tc) && Np <= kRotateFFMaxNp)
     LAUNCH(1, launch_rotate_ff(g, N, Np, m->fxh, m->fxl, m->C, dst, m->st));
   else
     LAUNCH(1, launch_rotate(g, N, Np, src, m->C, dst, m->st));
@@ -588,8 +635,8 @@ struct Timer {
 struct CallScope {
   paro_mesh m;
   paro_stats* s;
-  long long l0;
-  CallScope(paro_mesh mm, paro_stats* ss, int profile) : m(mm), s(ss), l0(mm->launches) {
+  long long l0, tc0;
+  CallScope(paro_mesh mm, paro_stats* ss, int profile) : m(mm), s(ss), l0(mm->launches), tc0(mm->rr_tc) {
     m->profile = 0;
     m->prof_launches = 0;
     m->prof_ms = 0.0;
@@ -610,6 +657,7 @@ struct CallScope {
   ~CallScope() {
     if (s) {
       s->kernel_launches += m->launches - l0;
+      s->rr_tc_steps += (int)(m->rr_tc - tc0);
       if (m->profile) {
         unsigned long long w = 0, wn = 0;
         if (cudaMemcpyAsync(m->h_dbl, &m->cgst->work, sizeof(w), cudaMemcpyDeviceToHost, m->st) == cudaSuccess &&
@@ -884,12 +932,13 @@ int paro_iterate(paro_mesh m, int N, double* U, double* lambda, const paro_param
   std::vector<double> lam(lambda, lambda + N), lam_new(N);
   if (std::isnan(lambda[0])) {
     Timer t(m, s ? &s->ms_rr : nullptr);
-    TRY(rr_packed(m, N, m->u, m->x, lam.data()));
+    TRY(rr_packed(m, N, m->u, m->x, lam.data(), kRRFP64));
     t.stop();
     // copy rather than swap: the CG plans hold the addresses of the workspace vectors
     CK(cudaMemcpyAsync(m->u, m->x, sizeof(double) * m->g.G * Np, cudaMemcpyDeviceToDevice, m->st));
   }
   const int nchk = (pp.n_check > 0 && pp.n_check < N) ? pp.n_check : N;
+  RRMode rr_mode = kRRFast;
   int outer = 0;
   int rc = PARO_ERR_NOT_CONVERGED;
   const int limit = pp.fixed_outer > 0 ? pp.fixed_outer : pp.max_outer;
@@ -902,11 +951,12 @@ int paro_iterate(paro_mesh m, int N, double* U, double* lambda, const paro_param
     }
     {
       Timer t(m, s ? &s->ms_rr : nullptr);
-      TRY(rr_packed(m, N, m->x, m->u, lam_new.data()));
+      TRY(rr_packed(m, N, m->x, m->u, lam_new.data(), rr_mode));
     }
     dl = 0.0;
     for (int i = 0; i < nchk; ++i) dl = std::fmax(dl, std::fabs(lam_new[i] - lam[i]));
     lam = lam_new;
+    rr_mode = next_rr_mode(m, rr_mode, dl, lam);
     ++outer;
     if (pp.fixed_outer <= 0 && dl < pp.tol) {
       rc = PARO_OK;
@@ -1004,12 +1054,13 @@ int paro_scf_iterate(paro_mesh m, int N, const double* occ, const double* vext_q
   // start: Rayleigh-Ritz on span(U) with V_ext alone; its density is the first rho_in
   TRY(paro_set_potential(m, vext_q, sigma));
   std::vector<double> lam(N), lam_new(N);
-  TRY(rr_packed(m, N, m->u, m->x, lam.data()));
+  TRY(rr_packed(m, N, m->u, m->x, lam.data(), kRRFP64));
   CK(cudaMemcpyAsync(m->u, m->x, sizeof(double) * m->g.G * Np, cudaMemcpyDeviceToDevice, m->st));
   LAUNCH(1, launch_density(m->g, N, Np, m->u, m->ks_occ, m->ks_rho, m->st));
   const int limit = pp.fixed_outer > 0 ? pp.fixed_outer : pp.max_outer;
   int outer = 0, rc = PARO_ERR_NOT_CONVERGED;
   double dl = INFINITY;
+  RRMode rr_mode = kRRFast;
   while (outer < limit) {
     // V from rho_in, used in both Step 3 and Step 4 of this iteration
     TRY(ks_potential(m, m->ks_rho, vext_q, m->ks_v, nullptr, pp.solve_tol, pp.pcg_maxit));
@@ -1021,13 +1072,14 @@ int paro_scf_iterate(paro_mesh m, int N, const double* occ, const double* vext_q
     }
     {
       Timer t(m, s ? &s->ms_rr : nullptr);
-      TRY(rr_packed(m, N, m->x, m->u, lam_new.data()));
+      TRY(rr_packed(m, N, m->x, m->u, lam_new.data(), rr_mode));
     }
     LAUNCH(1, launch_density(m->g, N, Np, m->u, m->ks_occ, m->ks_rho2, m->st));
     LAUNCH(1, launch_mix(gauss_count(m->g), mix, m->ks_rho, m->ks_rho2, m->st));
     dl = 0.0;
     for (int i = 0; i < N; ++i) dl = std::fmax(dl, std::fabs(lam_new[i] - lam[i]));
     lam = lam_new;
+    rr_mode = next_rr_mode(m, rr_mode, dl, lam);
     ++outer;
     if (pp.fixed_outer <= 0 && dl < pp.tol) {
       rc = PARO_OK;

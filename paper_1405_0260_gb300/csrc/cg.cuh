@@ -63,10 +63,10 @@ struct CGPlan {
   int dpitch = 0;  // row pitch of dinv_tma (elements)
   const T* dinv_tma = nullptr;
   const T* wcoef = nullptr;
-  alignas(64) CUtensorMap mr;
-  alignas(64) CUtensorMap mp;
-  alignas(64) CUtensorMap md;
-  alignas(64) CUtensorMap mw;
+  CUtensorMap mr;  // CUtensorMap carries its own 64-byte alignment
+  CUtensorMap mp;
+  CUtensorMap md;
+  CUtensorMap mw;
   int grid_stream = 0, nt_stream = 0;  // init kernel
   int grid_upd = 0, nt_upd = 0;        // update kernel
   size_t smem_init = 0, smem_upd = 0;
@@ -76,11 +76,11 @@ struct CGPlan {
   // single-reduction CG (float32): geometry, tensor maps of r, w (= q), s, D^-1, weights
   K1Geom geo1{};
   bool cg1_ok = false;
-  alignas(64) CUtensorMap m1r[2];
-  alignas(64) CUtensorMap m1q[2];
-  alignas(64) CUtensorMap m1s[2];
-  alignas(64) CUtensorMap m1d;
-  alignas(64) CUtensorMap m1w;
+  CUtensorMap m1r[2];
+  CUtensorMap m1q[2];
+  CUtensorMap m1s[2];
+  CUtensorMap m1d;
+  CUtensorMap m1w;
   // adds q = A x (the warm-start apply) as a graph node
   std::function<cudaError_t(cudaGraph_t, cudaGraphNode_t*)> add_apply;
 };

@@ -144,6 +144,14 @@ size_t gram_ff_partial_doubles(const Grid& g, int Np);
 cudaError_t launch_gram2_ff(const Grid& g, int Np, const float* xh, const float* xl, const float* ah, const float* al,
                             const float* bh, const float* bl, double* part, int* n_chunks, cudaStream_t st);
 cudaError_t launch_gram_reduce(int Np, int nch, const double* part, double* G1, double* G2, cudaStream_t st);
+cudaError_t launch_gram_reduce1(int Np, int nch, const double* part, double* Gm, cudaStream_t st);
+// gram_tc.cu: one Gram X^T Y on the tensor cores (exact BF16 digit products, Np <= kTcMaxNp),
+// from the hi parts of the float-float arrays; per-CTA partials
+constexpr int kTcMaxNp = 256;
+size_t gram_tc_partial_doubles(const Grid& g, int Np);
+cudaError_t launch_gram_tc(const Grid& g, int Np, const float* xh, const float* yh, double* part, int* n_chunks,
+                           int* status, cudaStream_t st);
+constexpr int kRotateFFMaxNp = 144;  // C as float-float in shared memory: 8 Np^2 bytes
 cudaError_t launch_rotate_ff(const Grid& g, int N, int Np, const float* xh, const float* xl, const double* C,
                              double* U, cudaStream_t st);
 

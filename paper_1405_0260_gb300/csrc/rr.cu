@@ -349,6 +349,24 @@ cudaError_t launch_gram_reduce(int Np, int nch, const double* part, double* G1, 
   return cudaGetLastError();
 }
 
+// One Gram from per-chunk partials part[nch][Np][Np]: one warp per entry.
+__global__ void k_gram_reduce1(int Np, int nch, const double* __restrict__ part, double* __restrict__ Gm) {
+  const long long NN = (long long)Np * Np;
+  const long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  const int lane = threadIdx.x % 32;
+  if (t >= NN) return;
+  double s = 0.0;
+  for (int c = lane; c < nch; c += 32) s += part[(long long)c * NN + t];
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if (lane == 0) Gm[t] = s;
+}
+
+cudaError_t launch_gram_reduce1(int Np, int nch, const double* part, double* Gm, cudaStream_t st) {
+  long long work = (long long)Np * Np * 32;
+  k_gram_reduce1<<<(unsigned)((work + 255) / 256), 256, 0, st>>>(Np, nch, part, Gm);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_small_eig(int N, const double* GA, const double* GB, double* work, double* C, double* theta,
                              int* status, cudaStream_t st) {
   int Np = (N + 3) / 4 * 4;
