@@ -206,7 +206,11 @@ def run_ours(args, ws, rank, local):
                 "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": None,
                 "launches": prof_n, "avg_launch_us": round(1e3 * prof_ms / prof_n, 2),
-                "alg_bytes_per_launch": round(alg_bytes / prof_n)}
+                "alg_bytes_per_launch": round(alg_bytes / prof_n),
+                # one orbital block (N <= 32): passes = node passes / interior nodes, and
+                # the share of (node, orbital) pairs still active in those passes
+                "passes_per_launch": round(prof_nodes / nI / prof_n, 2),
+                "active_fraction": round(prof_units / (prof_nodes * N), 4)}
 
     # end to end through the C ABI with host buffers
     Uh = torch.empty((nI, N), dtype=torch.float64, pin_memory=True)
