@@ -108,6 +108,7 @@ typedef struct {
   long long prof_dof_orb;      /* profile != 0: sum over their operator passes of n_interior x orbitals processed */
   long long prof_node_passes;  /* profile != 0: sum over their operator passes of n_interior x orbital blocks */
   int rr_tc_steps;             /* Rayleigh-Ritz steps whose Gram matrices ran on the tensor cores (mixed handles) */
+  long long poisson_cg_iters;  /* CG iterations of the Hartree (Poisson) solves of a Kohn-Sham call */
 } paro_stats;
 
 void paro_default_params(paro_params* p);
@@ -186,6 +187,9 @@ int paro_ks_potential(paro_mesh m, const double* rho_q, const double* vext_q, do
  * problems and does Rayleigh-Ritz with it, then mixes
  * rho_in <- (1 - mix) rho_in + mix rho_out (rho_out: density of the new
  * orbitals).  Stops when max_i |Delta lambda_i| < p->tol or after p->fixed_outer.
+ * The Hartree solve is warm-started from the previous one; PARO_FP64 handles
+ * solve it to p->solve_tol, PARO_MIXED handles to max(p->solve_tol,
+ * min(1e-4, 1e-2 x the previous iteration's max |Delta lambda|)).
  * occ: host[N] occupations; vext_q: device; U: device (n_interior x N) in/out;
  * lambda: host[N] out.  The handle's potential is the last effective potential
  * on return.  Errors as paro_iterate. */

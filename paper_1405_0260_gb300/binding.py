@@ -49,6 +49,7 @@ class paro_stats(C.Structure):
         ("stencil_applies", C.c_longlong), ("kernel_launches", C.c_longlong),
         ("prof_launches", C.c_longlong), ("prof_ms", C.c_double), ("prof_dof_orb", C.c_longlong),
         ("prof_node_passes", C.c_longlong), ("rr_tc_steps", C.c_int),
+        ("poisson_cg_iters", C.c_longlong),
     ]
 
     def as_dict(self):

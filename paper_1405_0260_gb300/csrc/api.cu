@@ -18,6 +18,7 @@ using namespace paro;
 struct paro_mesh_s {
   Grid g{};
   long long rr_tc = 0;  // Rayleigh-Ritz steps with tensor-core Grams (for paro_stats)
+  long long ks_pois_iters = 0;  // CG iterations of the Hartree solves (for paro_stats)
   int precision = PARO_FP64;
   cudaStream_t st = nullptr;
   std::string err;
@@ -439,6 +440,60 @@ int run_cg(paro_mesh m, CGPlan<T>* P, int N, bool warm, double tol, int maxit, i
 }
 
 // Step 3 on the packed buffers: u (current orbitals) -> x (source solutions).
+// Mixed-precision solve of A x = b for N columns: x (float64, padded) holds the
+// initial guess, b is given as a float-float pair in fah/fal.  Each sweep forms
+// r = b - A x in float-float arithmetic (float64-accurate), stops the columns with
+// |r| <= solve_tol |b|, solves A d = r to inner_tol with the float32 CG and adds d.
+int refine_solve(paro_mesh m, int N, const paro_params& p, paro_stats* st) {
+  const int Np = m->Np_alloc;
+  Grid& g = m->g;
+  CGState rs = cg_state(m, true);
+  int sweep = 0;
+  long long its32 = 0;
+  int maxit_seen = 0;
+  for (;;) {
+    // r = b - A x, float64-accurate (float-float arithmetic); its float32 rounding
+    // is the correction right-hand side
+    LAUNCH(1, launch_split_ff((long long)g.G * Np, m->x, m->fxh, m->fxl, m->st));
+    LAUNCH(1, launch_refine_residual_ff(g, N, Np, m->wAh, m->wAl, m->fxh, m->fxl, m->fah, m->fal, m->b32, rs,
+                                        p.solve_tol, m->st));
+    if (st) st->stencil_applies += N;
+    int open = 0;
+    TRY(read_n_active(m, &open));
+    if (open == 0) break;
+    if (sweep >= p.max_refine) {
+      if (st) st->refine_sweeps = sweep;
+      TRY(check_status(m, "orbital_solve"));
+      m->err = "mixed refinement: max_refine sweeps reached";
+      return PARO_ERR_NOT_CONVERGED;
+    }
+    long long i1 = 0;
+    int imx = 0;
+    TRY(run_cg<float>(m, m->plan32, N, false, p.inner_tol, p.pcg_maxit, p.check_every, &i1, &imx));
+    // an inner limit is not fatal: refinement carries on from the partial correction
+    int* stw = &m->cgst->status;
+    CK(cudaMemcpyAsync(m->h_int, stw, sizeof(int), cudaMemcpyDeviceToHost, m->st));
+    CK(cudaStreamSynchronize(m->st));
+    if (m->h_int[0] & kStatNotConverged) {
+      m->h_int[0] &= ~kStatNotConverged;
+      CK(cudaMemcpyAsync(stw, m->h_int, sizeof(int), cudaMemcpyHostToDevice, m->st));
+    }
+    TRY(check_status(m, "orbital_solve (float32 correction)"));
+    LAUNCH(1, launch_refine_update(g, Np, m->x, m->x32, m->cgst->skip, m->st));
+    its32 += i1;
+    if (imx > maxit_seen) maxit_seen = imx;
+    ++sweep;
+  }
+  if (st) {
+    st->cg_iters += its32;
+    st->cg_iters_f32 += its32;
+    st->cg_iters_max = maxit_seen;
+    st->refine_sweeps = sweep;
+    st->stencil_applies += its32;
+  }
+  return PARO_OK;
+}
+
 int solve_packed(paro_mesh m, int N, const double* lam, const paro_params& p, paro_stats* st) {
   const int Np = m->Np_alloc;
   Grid& g = m->g;
@@ -471,50 +526,7 @@ int solve_packed(paro_mesh m, int N, const double* lam, const paro_params& p, pa
     CGState rs = cg_state(m, true);
     LAUNCH(1, launch_refine_residual(g, N, Np, m->coef64, m->x, m->b, nullptr, rs, p.solve_tol, m->st));
   } else {
-    CGState rs = cg_state(m, true);
-    int sweep = 0;
-    long long its32 = 0;
-    int maxit_seen = 0;
-    for (;;) {
-      // r = b - A x, float64-accurate (float-float arithmetic); its float32 rounding
-      // is the correction right-hand side
-      LAUNCH(1, launch_split_ff((long long)g.G * Np, m->x, m->fxh, m->fxl, m->st));
-      LAUNCH(1, launch_refine_residual_ff(g, N, Np, m->wAh, m->wAl, m->fxh, m->fxl, m->fah, m->fal, m->b32, rs,
-                                          p.solve_tol, m->st));
-      if (st) st->stencil_applies += N;
-      int open = 0;
-      TRY(read_n_active(m, &open));
-      if (open == 0) break;
-      if (sweep >= p.max_refine) {
-        if (st) st->refine_sweeps = sweep;
-        TRY(check_status(m, "orbital_solve"));
-        m->err = "mixed refinement: max_refine sweeps reached";
-        return PARO_ERR_NOT_CONVERGED;
-      }
-      long long i1 = 0;
-      int imx = 0;
-      TRY(run_cg<float>(m, m->plan32, N, false, p.inner_tol, p.pcg_maxit, p.check_every, &i1, &imx));
-      // an inner limit is not fatal: refinement carries on from the partial correction
-      int* stw = &m->cgst->status;
-      CK(cudaMemcpyAsync(m->h_int, stw, sizeof(int), cudaMemcpyDeviceToHost, m->st));
-      CK(cudaStreamSynchronize(m->st));
-      if (m->h_int[0] & kStatNotConverged) {
-        m->h_int[0] &= ~kStatNotConverged;
-        CK(cudaMemcpyAsync(stw, m->h_int, sizeof(int), cudaMemcpyHostToDevice, m->st));
-      }
-      TRY(check_status(m, "orbital_solve (float32 correction)"));
-      LAUNCH(1, launch_refine_update(g, Np, m->x, m->x32, m->cgst->skip, m->st));
-      its32 += i1;
-      if (imx > maxit_seen) maxit_seen = imx;
-      ++sweep;
-    }
-    if (st) {
-      st->cg_iters += its32;
-      st->cg_iters_f32 += its32;
-      st->cg_iters_max = maxit_seen;
-      st->refine_sweeps = sweep;
-      st->stencil_applies += its32;
-    }
+    TRY(refine_solve(m, N, p, st));
   }
   if (st) {
     double* rr = m->dscal + S_RRR * kMaxN;
@@ -635,8 +647,9 @@ struct Timer {
 struct CallScope {
   paro_mesh m;
   paro_stats* s;
-  long long l0, tc0;
-  CallScope(paro_mesh mm, paro_stats* ss, int profile) : m(mm), s(ss), l0(mm->launches), tc0(mm->rr_tc) {
+  long long l0, tc0, pi0;
+  CallScope(paro_mesh mm, paro_stats* ss, int profile)
+      : m(mm), s(ss), l0(mm->launches), tc0(mm->rr_tc), pi0(mm->ks_pois_iters) {
     m->profile = 0;
     m->prof_launches = 0;
     m->prof_ms = 0.0;
@@ -658,6 +671,7 @@ struct CallScope {
     if (s) {
       s->kernel_launches += m->launches - l0;
       s->rr_tc_steps += (int)(m->rr_tc - tc0);
+      s->poisson_cg_iters += m->ks_pois_iters - pi0;
       if (m->profile) {
         unsigned long long w = 0, wn = 0;
         if (cudaMemcpyAsync(m->h_dbl, &m->cgst->work, sizeof(w), cudaMemcpyDeviceToHost, m->st) == cudaSuccess &&
@@ -700,21 +714,26 @@ int ensure_ks(paro_mesh m) {
 int ensure_poisson(paro_mesh m) {
   if (m->pois) return PARO_OK;
   paro_mesh c = nullptr;
-  int rc = paro_mesh_create(&c, m->g.nx, m->g.ny, m->g.nz, m->lo, m->hi, PARO_FP64, m->st);
+  // the Poisson problem takes the parent's precision: float32 CG in float-float
+  // refinement on mixed handles
+  int rc = paro_mesh_create(&c, m->g.nx, m->g.ny, m->g.nz, m->lo, m->hi, m->precision, m->st);
   if (rc != PARO_OK) return fail(m, rc, std::string("Poisson handle: ") + paro_last_error(nullptr));
   m->pois = c;
   double* zeros = nullptr;
   TRY(dalloc(m, &zeros, (size_t)gauss_count(m->g)));  // zeroed on the stream
   rc = paro_set_potential(c, zeros, 0.0);
   if (rc != PARO_OK) return fail(m, rc, std::string("Poisson handle: ") + paro_last_error(c));
-  TRY(ensure_workspace(c, 4));
+  TRY(ensure_workspace(c, 4));  // zeroed: the first solve starts from w = 0
   return PARO_OK;
 }
 
-// Hartree potential of rho (Gauss points): monopole, right-hand side, CG solve of
-// (K/2) w = 2 pi (rho, phi) - (K/2)_{I,boundary} g on the Poisson handle; the
-// solution is left in m->pois->x (padded, column 0).
-int hartree_solve(paro_mesh m, const double* rho, double tol, int maxit) {
+// Hartree potential of rho (Gauss points): monopole, right-hand side, solve of
+// (K/2) w = 2 pi (rho, phi) - (K/2)_{I,boundary} g on the Poisson handle, warm-
+// started from the previous solution (the density of an SCF loop changes little
+// from one iteration to the next); the solution is left in m->pois->x (padded,
+// column 0).  Mixed handles: float32 CG in float-float refinement to
+// pp.solve_tol; float64 handles: float64 CG.
+int hartree_solve(paro_mesh m, const double* rho, const paro_params& pp) {
   TRY(ensure_ks(m));
   TRY(ensure_poisson(m));
   paro_mesh c = m->pois;
@@ -722,9 +741,21 @@ int hartree_solve(paro_mesh m, const double* rho, double tol, int maxit) {
   CK(cudaMemsetAsync(c->b, 0, sizeof(double) * c->g.G * 4, m->st));
   LAUNCH(1, launch_hartree_rhs(c->g, m->lo, rho, c->coef64, m->ks_mom, c->b, m->st));
   CK(cudaMemsetAsync(c->cgst->skip, 0, sizeof(int) * kMaxN, m->st));
-  long long its = 0;
-  int itmax = 0;
-  int rc = run_cg<double>(c, c->plan64, 1, false, tol, maxit, 16, &its, &itmax);
+  int rc;
+  if (c->precision == PARO_MIXED) {
+    rc = launch_split_ff((long long)c->g.G * 4, c->b, c->fah, c->fal, m->st) == cudaSuccess ? PARO_OK : PARO_ERR_CUDA;
+    if (rc == PARO_OK) {
+      ++m->launches;
+      paro_stats ps{};
+      rc = refine_solve(c, 1, pp, &ps);
+      m->ks_pois_iters += ps.cg_iters;
+    }
+  } else {
+    long long its = 0;
+    int itmax = 0;
+    rc = run_cg<double>(c, c->plan64, 1, true, pp.solve_tol, pp.pcg_maxit, 16, &its, &itmax);
+    m->ks_pois_iters += its;
+  }
   if (rc != PARO_OK) return fail(m, rc, std::string("Hartree solve: ") + c->err);
   rc = check_status(c, "Hartree solve");
   if (rc != PARO_OK) return fail(m, rc, c->err);
@@ -734,8 +765,8 @@ int hartree_solve(paro_mesh m, const double* rho, double tol, int maxit) {
 }
 
 // v = V_ext + V_H(rho) + V_x(rho) at the Gauss points (vh: V_H alone, optional).
-int ks_potential(paro_mesh m, const double* rho, const double* vext, double* v, double* vh, double tol, int maxit) {
-  TRY(hartree_solve(m, rho, tol, maxit));
+int ks_potential(paro_mesh m, const double* rho, const double* vext, double* v, double* vh, const paro_params& pp) {
+  TRY(hartree_solve(m, rho, pp));
   LAUNCH(1, launch_ks_potential(m->g, m->lo, m->pois->x, m->ks_mom, rho, vext, v, vh, m->st));
   return PARO_OK;
 }
@@ -1031,7 +1062,7 @@ int paro_ks_potential(paro_mesh m, const double* rho_q, const double* vext_q, do
   paro_params pp;
   if (p) pp = *p;
   else paro_default_params(&pp);
-  TRY(ks_potential(m, rho_q, vext_q, v_q, vh_q, pp.solve_tol, pp.pcg_maxit));
+  TRY(ks_potential(m, rho_q, vext_q, v_q, vh_q, pp));
   CK(cudaStreamSynchronize(m->st));
   return PARO_OK;
 }
@@ -1062,8 +1093,14 @@ int paro_scf_iterate(paro_mesh m, int N, const double* occ, const double* vext_q
   double dl = INFINITY;
   RRMode rr_mode = kRRFast;
   while (outer < limit) {
-    // V from rho_in, used in both Step 3 and Step 4 of this iteration
-    TRY(ks_potential(m, m->ks_rho, vext_q, m->ks_v, nullptr, pp.solve_tol, pp.pcg_maxit));
+    // V from rho_in, used in both Step 3 and Step 4 of this iteration.  Mixed
+    // handles solve the Hartree problem only as accurately as the SCF state needs
+    // (the mixing corrects an early inexact potential): min(1e-4, 1e-2 |delta
+    // lambda| of the previous iteration), never below solve_tol; float64 handles
+    // solve to solve_tol every time.
+    paro_params ph = pp;
+    if (m->precision == PARO_MIXED) ph.solve_tol = std::fmax(pp.solve_tol, std::fmin(1e-4, 1e-2 * dl));
+    TRY(ks_potential(m, m->ks_rho, vext_q, m->ks_v, nullptr, ph));
     TRY(paro_set_potential(m, m->ks_v, sigma));
     {
       Timer t(m, s ? &s->ms_solve : nullptr);

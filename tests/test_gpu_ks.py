@@ -61,21 +61,28 @@ def test_density_matches_oracle(B, prec):
     m.close()
 
 
-def test_hartree_and_ks_potential_match_oracle(B):
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_hartree_and_ks_potential_match_oracle(B, prec):
+    # float64 CG, or float32 CG in float-float refinement (mixed handles); the
+    # second call starts from the first call's solution (warm start) and must
+    # land on the same potential for the changed density
     mesh, Vext, U0, occ = cluster(nc=12, L=6.0)
     ops = O.assemble(mesh, Vext, 3.0)
     U = O.rayleigh_ritz(ops, U0).U
     rho = KS.density_gauss(mesh, U, occ)
-    ref_h = KS.hartree(mesh, rho).VH_q
-    ref_v = Vext + ref_h + KS.slater_potential(rho)
-    m = B.Mesh(mesh.n, mesh.lo, mesh.hi, B.PARO_FP64)
+    rho2 = 0.8 * rho + 0.2 * KS.density_gauss(mesh, U[:, ::-1], occ)
+    m = B.Mesh(mesh.n, mesh.lo, mesh.hi, B.PARO_FP64 if prec == "fp64" else B.PARO_MIXED)
     vq = dev(Vext)
     m.set_potential(vq, 3.0)
     v = torch.empty_like(vq)
     vh = torch.empty_like(vq)
-    m.ks_potential(dev(rho), vq, v, vh, B.paro_default_params(solve_tol=1e-13, pcg_maxit=20000))
-    assert np.max(np.abs(host(vh) - ref_h)) < 1e-9 * np.max(np.abs(ref_h))
-    assert np.max(np.abs(host(v) - ref_v)) < 1e-9 * np.max(np.abs(ref_v))
+    params = B.paro_default_params(solve_tol=1e-13 if prec == "fp64" else 1e-12, pcg_maxit=20000)
+    for r in (rho, rho2):
+        ref_h = KS.hartree(mesh, r).VH_q
+        ref_v = Vext + ref_h + KS.slater_potential(r)
+        m.ks_potential(dev(r), vq, v, vh, params)
+        assert np.max(np.abs(host(vh) - ref_h)) < 1e-9 * np.max(np.abs(ref_h))
+        assert np.max(np.abs(host(v) - ref_v)) < 1e-9 * np.max(np.abs(ref_v))
     m.close()
 
 
