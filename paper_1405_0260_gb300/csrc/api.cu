@@ -317,6 +317,16 @@ int read_n_active(paro_mesh m, int* out) {
 }
 
 // Sum and max of the per-orbital CG counts of the last solve.
+// PARO_TRACE=1 in the environment: one line per CG solve on stderr with the
+// iteration count of every orbital (how unevenly the masked orbitals finish).
+bool trace_on() {
+  static const bool on = [] {
+    const char* t = std::getenv("PARO_TRACE");
+    return t != nullptr && t[0] == '1';
+  }();
+  return on;
+}
+
 int read_iters(paro_mesh m, int N, long long* sum, int* mx) {
   CK(cudaMemcpyAsync(m->h_int, m->cgst->iters, sizeof(int) * N, cudaMemcpyDeviceToHost, m->st));
   CK(cudaStreamSynchronize(m->st));
@@ -328,6 +338,11 @@ int read_iters(paro_mesh m, int N, long long* sum, int* mx) {
   }
   *sum = s;
   *mx = x;
+  if (trace_on()) {
+    std::fprintf(stderr, "paro-trace cg N=%d iters:", N);
+    for (int i = 0; i < N; ++i) std::fprintf(stderr, " %d", m->h_int[i]);
+    std::fprintf(stderr, "\n");
+  }
   return PARO_OK;
 }
 

@@ -45,6 +45,8 @@ struct CGArgs {
 };
 
 // Geometry of the tiled operator kernel K1.
+constexpr int kMaxGrid1 = 512;  // CTAs of the single-reduction CG kernel (split table size)
+
 struct K1Geom {
   int TX, TY, DX;     // tile (x, y) of a z-marching column, staged row pitch of D^-1
   int ncx, ncy, nob;  // columns per axis, orbital blocks of width 4*G4
@@ -53,6 +55,8 @@ struct K1Geom {
   int off_p, off_s, off_d, off_w, slot_bytes;  // byte offsets inside one ring slot
   uint32_t tx_bytes;                    // TMA bytes per slot
   size_t smem;                          // dynamic shared memory per CTA
+  // single-reduction kernel: CTA c takes the column-planes [split[c], split[c+1])
+  int split[kMaxGrid1 + 1];
 };
 
 template <typename T>
