@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -18,6 +19,7 @@ using namespace paro;
 struct paro_mesh_s {
   Grid g{};
   long long rr_tc = 0;  // Rayleigh-Ritz steps with tensor-core Grams (for paro_stats)
+  const char* tune_source = "default";  // how the float32 CG geometry was chosen
   long long ks_pois_iters = 0;  // CG iterations of the Hartree solves (for paro_stats)
   int precision = PARO_FP64;
   cudaStream_t st = nullptr;
@@ -179,6 +181,95 @@ void free_plans(paro_mesh m) {
   }
 }
 
+// Autotuner of the single-reduction CG geometry (tile shape, orbital block width).
+// PARO_AUTOTUNE=0 keeps the untuned default.  PARO_AUTOTUNE_CACHE=<file>: a JSON
+// object mapping "<device>|<nx>x<ny>x<nz>|Np<Np>" to [TX, TY, block width, us per
+// pass], read before and rewritten after a tuning run.
+struct TuneEntry {
+  int TX = 0, TY = 0, bw = 0;
+  double us = 0.0;
+};
+
+std::map<std::string, TuneEntry> tune_cache_read(const char* path) {
+  std::map<std::string, TuneEntry> out;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return out;
+  std::string txt;
+  char buf[4096];
+  size_t n;
+  while ((n = std::fread(buf, 1, sizeof buf, f)) > 0) txt.append(buf, n);
+  std::fclose(f);
+  size_t pos = 0;
+  while ((pos = txt.find('"', pos)) != std::string::npos) {
+    const size_t end = txt.find('"', pos + 1);
+    if (end == std::string::npos) break;
+    const size_t lb = txt.find('[', end), rb = lb == std::string::npos ? lb : txt.find(']', lb);
+    if (rb == std::string::npos) break;
+    TuneEntry e;
+    if (std::sscanf(txt.c_str() + lb + 1, " %d , %d , %d , %lf", &e.TX, &e.TY, &e.bw, &e.us) == 4)
+      out[txt.substr(pos + 1, end - pos - 1)] = e;
+    pos = rb + 1;
+  }
+  return out;
+}
+
+void tune_cache_write(const char* path, const std::map<std::string, TuneEntry>& c) {
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE* f = std::fopen(tmp.c_str(), "w");
+  if (!f) return;
+  std::fprintf(f, "{\n");
+  size_t i = 0;
+  for (const auto& kv : c)
+    std::fprintf(f, "  \"%s\": [%d, %d, %d, %.2f]%s\n", kv.first.c_str(), kv.second.TX, kv.second.TY, kv.second.bw,
+                 kv.second.us, ++i < c.size() ? "," : "");
+  std::fprintf(f, "}\n");
+  std::fclose(f);
+  std::rename(tmp.c_str(), path);
+}
+
+// Chooses the geometry of a float32 plan's single-reduction kernel: from the
+// cache, else by timing the candidates (cg1_autotune).
+int autotune_cg1(paro_mesh m, CGPlan<float>* P) {
+  const char* off = std::getenv("PARO_AUTOTUNE");
+  if ((off && off[0] == '0') || !P->cg1_ok) return PARO_OK;
+  std::vector<K1Geom> cand;
+  cg1_candidates(m->g, P->args.Np, m->nsm, &cand);
+  if (cand.size() < 2) return PARO_OK;
+  int dev = 0;
+  cudaDeviceProp prop{};
+  CK(cudaGetDevice(&dev));
+  CK(cudaGetDeviceProperties(&prop, dev));
+  const std::string key = std::string(prop.name) + "|" + std::to_string(m->g.nx) + "x" + std::to_string(m->g.ny) +
+                          "x" + std::to_string(m->g.nz) + "|Np" + std::to_string(P->args.Np);
+  const char* path = std::getenv("PARO_AUTOTUNE_CACHE");
+  std::map<std::string, TuneEntry> cache;
+  if (path) {
+    cache = tune_cache_read(path);
+    auto it = cache.find(key);
+    if (it != cache.end())
+      for (const K1Geom& G : cand)
+        if (G.TX == it->second.TX && G.TY == it->second.TY && G.G4 * 4 == it->second.bw) {
+          CK(cg1_prepare_geo(P, G));
+          m->tune_source = "cache";
+          return PARO_OK;
+        }
+  }
+  int chosen = -1, tried = 0;
+  float us = 0.f;
+  CK(cg1_autotune(P, m->st, 8, &chosen, &us, &tried));
+  m->tune_source = "timed";
+  if (chosen >= 0 && path) {
+    TuneEntry e;
+    e.TX = cand[chosen].TX;
+    e.TY = cand[chosen].TY;
+    e.bw = cand[chosen].G4 * 4;
+    e.us = us;
+    cache[key] = e;
+    tune_cache_write(path, cache);
+  }
+  return PARO_OK;
+}
+
 template <typename T>
 int make_plan(paro_mesh m, int Np, CGPlan<T>** out, T* x, T* b, T* r, T* p, T* q, const T* dinv, const T* dinv_tma,
               const T* wcoef, const T* coef, T* s = nullptr, T* r2 = nullptr, T* q2 = nullptr, T* s2 = nullptr) {
@@ -213,6 +304,14 @@ int make_plan(paro_mesh m, int Np, CGPlan<T>** out, T* x, T* b, T* r, T* p, T* q
     delete P;
     return fail(m, PARO_ERR_CUDA, std::string("CG plan: ") + cudaGetErrorString(e));
   }
+  if constexpr (sizeof(T) == 4) {
+    m->tune_source = "default";
+    const int rc = autotune_cg1(m, P);
+    if (rc != PARO_OK) {
+      delete P;
+      return rc;
+    }
+  }
   if (std::getenv("PARO_PRINT_PLAN"))
     std::fprintf(stderr, "paro CG plan (%s): tile %dx%d, %d node(s)/thread, block %d orbitals x %d, %d threads, grid %d, "
                  "smem %zu B, persistent %d\n", sizeof(T) == 4 ? "float32" : "float64", P->geo.TX, P->geo.TY,
@@ -221,8 +320,8 @@ int make_plan(paro_mesh m, int Np, CGPlan<T>** out, T* x, T* b, T* r, T* p, T* q
   if constexpr (sizeof(T) == 4) {
     if (std::getenv("PARO_PRINT_PLAN"))
       std::fprintf(stderr, "paro single-reduction CG plan: tile %dx%d, block %d orbitals x %d, %d threads, grid %d, "
-                   "smem %zu B, usable %d\n", P->geo1.TX, P->geo1.TY, P->geo1.G4 * 4, P->geo1.nob,
-                   P->geo1.nthr * P->geo1.G4, P->geo1.grid, P->geo1.smem, (int)P->cg1_ok);
+                   "smem %zu B, usable %d, geometry %s\n", P->geo1.TX, P->geo1.TY, P->geo1.G4 * 4, P->geo1.nob,
+                   P->geo1.nthr * P->geo1.G4, P->geo1.grid, P->geo1.smem, (int)P->cg1_ok, m->tune_source);
   }
   Grid g = m->g;
   P->add_apply = [g, Np, coef, x, q](cudaGraph_t gr, cudaGraphNode_t* node) {

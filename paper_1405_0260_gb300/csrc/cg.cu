@@ -25,6 +25,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <vector>
 
 #include "cg.cuh"
 #include "tma.cuh"
@@ -1671,7 +1672,9 @@ cudaError_t cg_prepare(CGPlan<T>* P) {
   // block sums [K][threads/G4][Np] = 4 K threads values; afterwards the last CTA's
   // slices (at most max(threads, K Np)) and the K Np totals
   auto need_for = [&](int K, int threads) {
-    const size_t blk = (size_t)4 * K * threads + threads;
+    // block sums, then block_colsum's slices: max(threads, K Np) values
+    const size_t cs = (size_t)(threads > K * a.Np ? threads : K * a.Np);
+    const size_t blk = (size_t)4 * K * threads + cs;
     const size_t sl = (size_t)(threads > K * a.Np ? threads : K * a.Np);
     const size_t fin = sl + (size_t)K * a.Np;
     return (blk > fin ? blk : fin) * sizeof(double);
@@ -1853,64 +1856,77 @@ void balanced_split(long long F, int nzo, int grid, int* out) {
   greedy(lo, out);
 }
 
-cudaError_t cg1_plan_geometry(const Grid& g, int Np, int nsm, K1Geom* geo) {
+// Completes a geometry for orbital blocks of width bw: block and column counts,
+// the grid (one CTA per SM times what the occupancy allows, capped by the work)
+// and the balanced split.
+static void cg1_finish(const Grid& g, int Np, int nsm, int bw, K1Geom* G) {
+  G->G4 = bw / 4;
+  G->ncx = (g.nx - 1 + G->TX - 1) / G->TX;
+  G->ncy = (g.ny - 1 + G->TY - 1) / G->TY;
+  G->nob = (Np + bw - 1) / bw;
+  void* f = cg1_fn(G->G4, G->nthr);
+  int per_sm = 1;
+  if (f && cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G->smem) == cudaSuccess) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, G->nthr * G->G4, G->smem) == cudaSuccess && nb > 0)
+      per_sm = nb;
+  }
+  (void)cudaGetLastError();
+  long long want = (long long)nsm * per_sm;
+  if (want > kMaxGrid1) want = kMaxGrid1;
+  const long long F = (long long)G->nob * G->ncx * G->ncy * (g.nz - 1);
+  long long grid = F / 4;
+  if (grid < 1) grid = 1;
+  if (grid > want) grid = want;
+  G->grid = (int)grid;
+  balanced_split(F, g.nz - 1, G->grid, G->split);
+}
+
+void cg1_candidates(const Grid& g, int Np, int nsm, std::vector<K1Geom>* out) {
+  out->clear();
   const size_t stat = (size_t)2 * kMaxN * sizeof(float) + 2 * (kMaxN / 4) * sizeof(int) + 64;
   const size_t limit = 227 * 1024 - stat - 1024;
-  // 64-node tiles (measured at 64^3 x 20: 62.7 us a pass on 16x4 tiles with 320
-  // threads, 86 us on 16x8 tiles with 640 threads, where registers spill)
+  // 64-node tiles, one node per thread (measured at 64^3 x 20: 62.7 us a pass on
+  // 16x4 tiles with 320 threads, 86 us on 16x8 tiles with 640 threads, where
+  // registers spill); orbital blocks from the widest down, the three widest
+  // feasible widths at most
   const int shapes[2][2] = {{16, 4}, {8, 8}};
-  int first = 0;
-  if (const char* t = std::getenv("PARO_CG_TILE"))  // tuning switch: PARO_CG_TILE=8x8
-    if (std::strcmp(t, "8x8") == 0) first = 1;
-  K1Geom best{};
-  int best_bw = 0;
-  for (int nob = (Np + 31) / 32; nob <= Np / 4 && !best_bw; ++nob) {
+  int widths = 0;
+  for (int nob = (Np + 31) / 32; nob <= Np / 4 && widths < 3; ++nob) {
     int bw = (Np + nob - 1) / nob;
     bw = (bw + 3) / 4 * 4;
     if ((Np + bw - 1) / bw != nob) continue;
-    for (int si = first; si < 2; ++si) {
+    bool any = false;
+    for (int si = 0; si < 2; ++si) {
       const int TX = shapes[si][0], TY = shapes[si][1];
       if (TX * TY * (bw / 4) > 512) continue;
       K1Geom G{};
       cg1_layout(Np, bw, TX, TY, &G);
-      if (G.smem <= limit) {
-        best = G;
-        best_bw = bw;
-        break;
-      }
+      if (G.smem > limit) continue;
+      cg1_finish(g, Np, nsm, bw, &G);
+      out->push_back(G);
+      any = true;
     }
+    if (any) ++widths;
   }
-  if (!best_bw) return cudaErrorInvalidConfiguration;
-  K1Geom G = best;
-  G.G4 = best_bw / 4;
-  G.ncx = (g.nx - 1 + G.TX - 1) / G.TX;
-  G.ncy = (g.ny - 1 + G.TY - 1) / G.TY;
-  G.nob = (Np + best_bw - 1) / best_bw;
-  void* f = cg1_fn(G.G4, G.nthr);
-  int per_sm = 1;
-  if (f && cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G.smem) == cudaSuccess) {
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, G.nthr * G.G4, G.smem) == cudaSuccess && nb > 0)
-      per_sm = nb;
-  }
-  long long want = (long long)nsm * per_sm;
-  if (want > kMaxGrid1) want = kMaxGrid1;
-  const long long F = (long long)G.nob * G.ncx * G.ncy * (g.nz - 1);
-  long long grid = F / 4;
-  if (grid < 1) grid = 1;
-  if (grid > want) grid = want;
-  G.grid = (int)grid;
-  balanced_split(F, g.nz - 1, G.grid, G.split);
-  *geo = G;
-  return cudaSuccess;
 }
 
 cudaError_t cg1_prepare(CGPlan<float>* P) {
+  P->cg1_ok = false;
+  if (P->args.s == nullptr || P->args.r2 == nullptr || P->args.q2 == nullptr || P->args.s2 == nullptr)
+    return cudaSuccess;
+  std::vector<K1Geom> c;
+  cg1_candidates(P->args.g, P->args.Np, P->nsm, &c);
+  if (c.empty()) return cudaErrorInvalidConfiguration;
+  return cg1_prepare_geo(P, c[0]);
+}
+
+cudaError_t cg1_prepare_geo(CGPlan<float>* P, const K1Geom& geo) {
   cudaError_t e;
   P->cg1_ok = false;
   if (P->args.s == nullptr || P->args.r2 == nullptr || P->args.q2 == nullptr || P->args.s2 == nullptr)
     return cudaSuccess;
-  if ((e = cg1_plan_geometry(P->args.g, P->args.Np, P->nsm, &P->geo1)) != cudaSuccess) return e;
+  P->geo1 = geo;
   const K1Geom& G = P->geo1;
   const CGArgs<float>& a = P->args;
   const int bw = G.G4 * 4;
@@ -1960,6 +1976,78 @@ cudaError_t cg_launch_cg1(CGPlan<float>* P, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   void* args[] = {&a, &geo, &P->m1r[0], &P->m1q[0], &P->m1s[0], &P->m1r[1], &P->m1q[1], &P->m1s[1], &P->m1d, &P->m1w};
   return cudaLaunchCooperativeKernel(cg1_fn(geo.G4, geo.nthr), dim3(geo.grid), dim3(geo.nthr * geo.G4), args, geo.smem, st);
+}
+
+namespace {
+// b = 1 at the interior nodes of every column (boundary rows stay zero)
+__global__ void k_fill_interior(Grid g, int Np, float* b) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)g.nI * Np) return;
+  const long long gp = interior_to_padded(g, (int)(t / Np));
+  b[gp * Np + t % Np] = 1.0f;
+}
+}  // namespace
+
+cudaError_t cg1_autotune(CGPlan<float>* P, cudaStream_t st, int passes, int* chosen, float* best_us, int* tried) {
+  std::vector<K1Geom> cand;
+  cg1_candidates(P->args.g, P->args.Np, P->nsm, &cand);
+  *chosen = -1;
+  *tried = 0;
+  *best_us = 0.f;
+  if (cand.empty()) return cudaErrorInvalidConfiguration;
+  CGArgs<float>& a = P->args;
+  const int Nsave = a.N;
+  a.N = a.Np;
+  // inputs: b = 1, x = 0; tol = 0 so that no orbital converges, maxit = passes
+  cudaError_t e = cudaMemsetAsync(a.b, 0, sizeof(float) * a.g.G * a.Np, st);
+  const long long n = (long long)a.g.nI * a.Np;
+  if (e == cudaSuccess) {
+    k_fill_interior<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a.g, a.Np, a.b);
+    e = cudaGetLastError();
+  }
+  const double tol0 = 0.0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&a.st->tol, &tol0, sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&a.st->maxit, &passes, sizeof(int), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.st->skip, 0, sizeof(int) * kMaxN, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  float best = 0.f;
+  for (size_t i = 0; i < cand.size() && e == cudaSuccess; ++i) {
+    if (cg1_prepare_geo(P, cand[i]) != cudaSuccess || !P->cg1_ok) {
+      (void)cudaGetLastError();
+      continue;
+    }
+    float ms = 0.f;
+    bool ok = cudaMemsetAsync(&a.st->status, 0, sizeof(int), st) == cudaSuccess;
+    for (int rep = 0; rep < 2 && ok; ++rep) {  // the second run is timed
+      ok = cg_launch_init<float>(P, st, true) == cudaSuccess && cudaEventRecord(e0, st) == cudaSuccess &&
+           cg_launch_cg1(P, st) == cudaSuccess && cudaEventRecord(e1, st) == cudaSuccess &&
+           cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+    }
+    int status = 0;
+    ok = ok && cudaMemcpy(&status, &a.st->status, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess &&
+         (status & (kStatTimeout | kStatNonFinite | kStatNotSPD)) == 0;
+    if (!ok) {
+      (void)cudaGetLastError();
+      continue;
+    }
+    ++*tried;
+    if (*chosen < 0 || ms < best) {
+      best = ms;
+      *chosen = (int)i;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  a.N = Nsave;
+  const int zero = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&a.st->status, &zero, sizeof(int), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e;
+  if (*chosen < 0) return cg1_prepare_geo(P, cand[0]);
+  *best_us = 1e3f * best / passes;
+  return cg1_prepare_geo(P, cand[*chosen]);
 }
 
 template cudaError_t cg_prepare<float>(CGPlan<float>*);

@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <functional>
+#include <vector>
 
 #include "common.cuh"
 
@@ -111,8 +112,17 @@ cudaError_t cg_launch_k2(CGPlan<T>* P, cudaStream_t st);
 template <typename T>
 cudaError_t cg_launch_loop(CGPlan<T>* P, cudaStream_t st);
 // Single-reduction CG (float32): plan (after the tensor maps' pointers are set) and launch.
-cudaError_t cg1_prepare(CGPlan<float>* P);
+// The feasible geometries for (mesh, Np), widest orbital blocks first; the first
+// is the untuned default.
+void cg1_candidates(const Grid& g, int Np, int nsm, std::vector<K1Geom>* out);
+cudaError_t cg1_prepare(CGPlan<float>* P);                           // the default geometry
+cudaError_t cg1_prepare_geo(CGPlan<float>* P, const K1Geom& geo);     // a given geometry
 cudaError_t cg_launch_cg1(CGPlan<float>* P, cudaStream_t st);
+// Autotuner: times `passes` CG passes of every candidate on the plan's own
+// operator and workspace (b = 1, x = 0, tol = 0; overwrites b, x and the CG
+// state) and prepares the fastest; *chosen: its index in cg1_candidates (-1 if
+// none ran), *best_us: its time per pass, *tried: candidates timed.
+cudaError_t cg1_autotune(CGPlan<float>* P, cudaStream_t st, int passes, int* chosen, float* best_us, int* tried);
 
 // Packed operator weights per input plane, [Pz][ny-1][nx-1][kPackedW], for the tiled kernel.
 constexpr int kPackedW = 28;

@@ -223,6 +223,24 @@ def test_orbital_solve_many_orbital_blocks_ragged_mesh(B, prec):
     m.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_orbital_solve_wide_blocks(B, prec):
+    # N = 90 (Np = 92): three orbital blocks of the tiled CG, the last one ragged,
+    # and reductions over 3 Np > the streaming kernels' thread count
+    p = W.harmonic(nc=10, L=5.0, N=90, seed=4200, sigma=1.0)
+    ops = oracle_ops(p)
+    rr = O.rayleigh_ritz(ops, p.U0)
+    ref = O.source_problems(ops, rr.U, rr.lam, 1e-12, 5000)
+    m = make_mesh(B, p, B.PARO_FP64 if prec == "fp64" else B.PARO_MIXED)
+    U = dev(rr.U)
+    X = torch.empty_like(U)
+    rc, st = m.orbital_solve(rr.lam, U, X, B.paro_default_params(solve_tol=1e-11, pcg_maxit=5000))
+    assert rc == 0, B.paro_last_error(m.h)
+    assert st.max_relres <= 1e-11
+    assert np.max(np.abs(host(X) - ref.X)) < 1e-8 * np.max(np.abs(ref.X))
+    m.close()
+
+
 @pytest.mark.parametrize("N", [1, 6, 11])
 def test_rayleigh_ritz_matches_oracle(B, N):
     p = W.harmonic(nc=10, L=5.0, N=N, seed=3100 + N)
