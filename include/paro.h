@@ -237,6 +237,30 @@ int paro_small_eig_static(int N, const double* GA, const double* GB, double* C, 
  * the last paro_mesh_create failure.  The string lives until the next call. */
 const char* paro_last_error(paro_mesh m);
 
+/* Interior node count (nx-1)(ny-1)(nz-1) of a handle (PARO_ERR_ARG on NULL). */
+long long paro_interior_nodes(paro_mesh m);
+
+/* Batches of independent systems (meshes, orbital counts and potentials of
+ * their own): paro_batch_iterate runs paro_iterate on every system from a pool
+ * of n_workers host threads, the largest system (interior nodes x N) first.
+ * Give every handle its own CUDA stream (paro_mesh_create's cuda_stream): the
+ * kernels of different systems then overlap on the GPU and the host-side waits
+ * of one system hide behind the others' work; handles that share a stream stay
+ * correct, only serialised.  A handle may appear in one entry of a batch. */
+typedef struct paro_batch_s* paro_batch;
+int paro_batch_create(paro_batch* out, int n_workers); /* 1 <= n_workers <= 256 */
+/* Registers system (m, N, U, lambda, p) and returns its index (>= 0), or an
+ * error status.  U: device (n_interior x N) in/out; lambda: host[N] in/out (NaN
+ * in lambda[0]: initial Rayleigh-Ritz, as paro_iterate); p is copied (NULL:
+ * defaults).  U and lambda must stay valid until paro_batch_iterate returns. */
+int paro_batch_add(paro_batch b, paro_mesh m, int N, double* U, double* lambda, const paro_params* p);
+int paro_batch_size(paro_batch b);
+/* Iterates every system to its tolerance (paro_iterate).  rc: host[size] out,
+ * every system's status; stats: host[size] out or NULL.  Returns PARO_OK if all
+ * converged, else the status of the first failing system in index order. */
+int paro_batch_iterate(paro_batch b, int* rc, paro_stats* stats);
+int paro_batch_destroy(paro_batch b); /* the handles are not destroyed */
+
 #ifdef __cplusplus
 }
 #endif

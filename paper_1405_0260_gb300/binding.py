@@ -90,9 +90,17 @@ def lib():
     L.paro_ks_density_in.argtypes = [vp, vp]
     L.paro_last_error.argtypes = [vp]
     L.paro_last_error.restype = C.c_char_p
+    L.paro_interior_nodes.argtypes = [vp]
+    L.paro_interior_nodes.restype = C.c_longlong
+    L.paro_batch_create.argtypes = [C.POINTER(vp), ip]
+    L.paro_batch_add.argtypes = [vp, vp, ip, vp, dp, C.POINTER(paro_params)]
+    L.paro_batch_size.argtypes = [vp]
+    L.paro_batch_iterate.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(paro_stats)]
+    L.paro_batch_destroy.argtypes = [vp]
     for f in ("paro_mesh_create", "paro_mesh_destroy", "paro_set_potential", "paro_orbital_solve",
               "paro_rayleigh_ritz", "paro_iterate", "paro_apply", "paro_density", "paro_ks_potential",
-              "paro_scf_iterate", "paro_ks_density_in"):
+              "paro_scf_iterate", "paro_ks_density_in", "paro_batch_create", "paro_batch_add", "paro_batch_size",
+              "paro_batch_iterate", "paro_batch_destroy"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -262,6 +270,51 @@ class Mesh:
 
     def ks_density_in(self, rho):
         _check(lib().paro_ks_density_in(self.h, self._dev(rho)), self.h)
+
+
+class Batch:
+    """Independent systems advanced by paro_batch_iterate from a pool of host threads.
+
+    add(mesh, U, lam=None, params=None): U a CUDA float64 tensor (n_interior x N)
+    on the mesh's stream, updated in place; lam None starts with a Rayleigh-Ritz.
+    iterate() returns the per-system status codes, eigenvalues and statistics.
+    """
+
+    def __init__(self, workers=4):
+        h = C.c_void_p()
+        rc = lib().paro_batch_create(C.byref(h), int(workers))
+        if rc != PARO_OK:
+            raise ParoError(rc, "paro_batch_create")
+        self.h = h
+        self.items = []
+
+    def add(self, mesh, U, lam=None, params=None):
+        N = U.shape[1]
+        lam = np.full(N, np.nan) if lam is None else np.ascontiguousarray(lam, dtype=np.float64).copy()
+        idx = lib().paro_batch_add(self.h, mesh.h, N, C.c_void_p(mesh._dev(U)), _dptr(lam),
+                                   C.byref(params) if params is not None else None)
+        if idx < 0:
+            raise ParoError(idx, "paro_batch_add")
+        self.items.append((mesh, U, lam, params))  # keeps U, lam and params alive
+        return idx
+
+    def iterate(self):
+        n = len(self.items)
+        rc = (C.c_int * max(n, 1))()
+        st = (paro_stats * max(n, 1))()
+        lib().paro_batch_iterate(self.h, rc, st)
+        return [int(rc[i]) for i in range(n)], [it[2] for it in self.items], [st[i] for i in range(n)]
+
+    def close(self):
+        if self.h is not None:
+            lib().paro_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def paro_small_eig_static(N, GA_ptr, GB_ptr, C_ptr, theta_ptr, stream=0):

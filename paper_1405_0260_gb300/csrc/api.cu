@@ -1258,6 +1258,8 @@ int paro_ks_density_in(paro_mesh m, double* rho_q) {
   return PARO_OK;
 }
 
+long long paro_interior_nodes(paro_mesh m) { return m ? (long long)m->g.nI : (long long)PARO_ERR_ARG; }
+
 const char* paro_last_error(paro_mesh m) {
   if (!m) return g_create_err.c_str();
   return m->err.c_str();

@@ -1596,7 +1596,7 @@ cudaError_t cg_plan_geometry(const Grid& g, int Np, int nsm, K1Geom* geo, int* b
   for (int loop = 0; loop < 2; ++loop) {
     void* f = k1_fn<T>(G.G4, G.npt, loop != 0);
     int nb = 1;
-    if (f && cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G.smem) == cudaSuccess) {
+    if (f && allow_max_dyn_smem(f) == cudaSuccess) {
       if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, G.nthr * G.G4, G.smem) != cudaSuccess || nb < 1)
         nb = 1;
     }
@@ -1648,10 +1648,8 @@ cudaError_t cg_prepare(CGPlan<T>* P) {
   void* f1 = k1_fn<T>(G.G4, G.npt);
   void* fl = k1_fn<T>(G.G4, G.npt, true);
   if (!f1 || !fl) return cudaErrorInvalidValue;
-  if ((e = cudaFuncSetAttribute(f1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G.smem)) != cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute(fl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G.smem)) != cudaSuccess)
-    return e;
+  if ((e = allow_max_dyn_smem(f1)) != cudaSuccess) return e;
+  if ((e = allow_max_dyn_smem(fl)) != cudaSuccess) return e;
   {
     int nb = 0, dev = 0, coop = 0;
     P->coop_ok = cudaGetDevice(&dev) == cudaSuccess &&
@@ -1687,12 +1685,8 @@ cudaError_t cg_prepare(CGPlan<T>* P) {
   P->smem_upd = need_for(2, P->nt_upd);
   if (P->smem_upd > 200 * 1024) return cudaErrorInvalidConfiguration;
   if (P->smem_init > 200 * 1024) return cudaErrorInvalidConfiguration;
-  if ((e = cudaFuncSetAttribute((void*)k_cg_init<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)P->smem_init)) != cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute((void*)k_cg_upd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)P->smem_upd)) != cudaSuccess)
-    return e;
+  if ((e = allow_max_dyn_smem((const void*)k_cg_init<T>)) != cudaSuccess) return e;
+  if ((e = allow_max_dyn_smem((const void*)k_cg_upd<T>)) != cudaSuccess) return e;
   return cudaSuccess;
 }
 
@@ -1866,7 +1860,7 @@ static void cg1_finish(const Grid& g, int Np, int nsm, int bw, K1Geom* G) {
   G->nob = (Np + bw - 1) / bw;
   void* f = cg1_fn(G->G4, G->nthr);
   int per_sm = 1;
-  if (f && cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G->smem) == cudaSuccess) {
+  if (f && allow_max_dyn_smem(f) == cudaSuccess) {
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, G->nthr * G->G4, G->smem) == cudaSuccess && nb > 0)
       per_sm = nb;
@@ -1958,8 +1952,7 @@ cudaError_t cg1_prepare_geo(CGPlan<float>* P, const K1Geom& geo) {
   }
   void* f = cg1_fn(G.G4, G.nthr);
   if (!f) return cudaErrorInvalidValue;
-  if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G.smem)) != cudaSuccess)
-    return e;
+  if ((e = allow_max_dyn_smem(f)) != cudaSuccess) return e;
   int nb = 0, dev = 0, coop = 0;
   P->cg1_ok = cudaGetDevice(&dev) == cudaSuccess &&
               cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&

@@ -82,6 +82,13 @@ __device__ __forceinline__ long long interior_to_padded(const Grid& g, int n) {
   return ((long long)k * g.Py + j) * g.Px + i;
 }
 
+// Allows a kernel the device's largest dynamic shared memory (its opt-in maximum
+// less the kernel's static shared memory), once per kernel and never lowered.
+// Handles used from several host threads at once would otherwise race: a launch
+// size set by one thread could lower the limit under another thread's launch.
+// The limit is only a cap; occupancy follows the size a launch requests.
+cudaError_t allow_max_dyn_smem(const void* f);
+
 // ---------------------------------------------------------------------------
 // Host-side launch wrappers (defined in stencil.cu, pcg.cu, rr.cu)
 // ---------------------------------------------------------------------------

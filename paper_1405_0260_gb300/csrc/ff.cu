@@ -305,7 +305,7 @@ cudaError_t launch_rotate_ff(const Grid& g, int N, int Np, const float* xh, cons
                              double* U, cudaStream_t st) {
   const size_t smem = (size_t)2 * Np * Np * sizeof(float);
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_rotate_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_max_dyn_smem((const void*)k_rotate_ff);
     if (e != cudaSuccess) return e;
   }
   k_rotate_ff<<<apply_grid(g, Np), kRedThreads, smem, st>>>(g, N, Np, xh, xl, C, U);

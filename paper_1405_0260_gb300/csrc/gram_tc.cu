@@ -370,7 +370,7 @@ template <int NCOL>
 cudaError_t launch_tc(long long G, int Np, int xr0, int na, int yc0, int nb, const float* xh, const float* yh,
                       double* part, long long chunk, int nch, int* status, cudaStream_t st) {
   const size_t smem = (size_t)tc_smem_bytes<NCOL>();
-  cudaError_t e = cudaFuncSetAttribute(k_gram_tc<NCOL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_dyn_smem((const void*)k_gram_tc<NCOL>);
   if (e != cudaSuccess) return e;
   k_gram_tc<NCOL><<<nch, kTcThreads, smem, st>>>(G, Np, xr0, na, yc0, nb, xh, yh, part, chunk, status);
   return cudaGetLastError();

@@ -376,7 +376,7 @@ cudaError_t launch_small_eig(int N, const double* GA, const double* GB, double* 
   if (nt > 1024) nt = 1024;
   const size_t smem = (size_t)4 * N * N * sizeof(double);
   if (smem <= 160 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_small_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    cudaError_t e = allow_max_dyn_smem((const void*)k_small_eig);
     if (e != cudaSuccess) return e;
     k_small_eig<<<1, nt, smem, st>>>(N, Np, GA, GB, work, C, theta, status, 1);
   } else {

@@ -9,6 +9,8 @@
 // given; the rule is exact for sigma * mass, so sigma folds into V.
 // The weights of a node are the 27 entries of its row of A.
 #include "cg.cuh"
+#include <mutex>
+#include <set>
 #include "common.cuh"
 
 namespace paro {
@@ -273,6 +275,22 @@ cudaError_t launch_pack_f32(const Grid& g, int N, int Np, const float* src, floa
 cudaError_t launch_unpack_f32(const Grid& g, int N, int Np, const float* src, float* dst, cudaStream_t st) {
   k_unpack_f32<<<nblk((long long)g.nI * N, 256), 256, 0, st>>>(g, N, Np, src, dst);
   return cudaGetLastError();
+}
+
+cudaError_t allow_max_dyn_smem(const void* f) {
+  static std::mutex mu;
+  static std::set<const void*> done;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count(f)) return cudaSuccess;
+  int dev = 0, optin = 0;
+  cudaFuncAttributes fa{};
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, f);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+  if (e == cudaSuccess) done.insert(f);
+  return e;
 }
 
 }  // namespace paro
