@@ -176,3 +176,28 @@ def random_block(n, N, seed):
     rng = np.random.default_rng(seed)
     nx, ny, nz = n
     return rng.standard_normal(((nx - 1) * (ny - 1) * (nz - 1), N))
+
+
+def batch_systems(count=64, seed=4000, L=10.0, meshes=(32, 48, 64, 96), n_range=(4, 48), n_nuclei=(1, 6),
+                  zmax=3, box=4.0, min_sep=1.5, tol=1e-7):
+    """Independent fixed-potential systems for batched runs.
+
+    Each system: 1-6 softened-Coulomb nuclei (Z ~ U{1..zmax}) uniform in
+    [-box, box]^3, pairwise >= min_sep apart, on [-L, L]^3 with nc drawn from
+    meshes and N ~ U{n_range}; Gaussian initial orbitals.  sigma is left to the
+    caller (it must make H + sigma M SPD).
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        nc = int(rng.choice(meshes))
+        N = int(rng.integers(n_range[0], n_range[1] + 1))
+        M = int(rng.integers(n_nuclei[0], n_nuclei[1] + 1))
+        nuc = place_nuclei(rng, M, zmax, box, min_sep)
+        n = (nc, nc, nc)
+        lo, hi = (-L, -L, -L), (L, L, L)
+        V = softened_coulomb(n, lo, hi, nuc)
+        U0 = gaussian_orbitals(n, lo, hi, N, rng)
+        out.append(Problem(f"batch{k}-{nc}^3-{M}nuc-N{N}", n, lo, hi, V, 0.0, U0, tol, nuc))
+    return out
+
