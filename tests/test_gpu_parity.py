@@ -414,3 +414,42 @@ def test_errors_are_reported_not_raised_on_device(B):
         m2.rayleigh_ritz(U, X)
     assert e.value.code == -8  # no potential yet
     m2.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_256_orbitals_solve_and_rayleigh_ritz(B, prec):
+    # the widest orbital count of the large workload on a small mesh: 8 CG orbital
+    # blocks, tensor-core Grams in 2 x 4 blocks (mixed), the float64 rotation
+    # (Np > the float-float rotation's shared memory), the small eigensolve at
+    # N = 256 with its work matrices in global memory
+    N = 256
+    p = W.harmonic(nc=12, L=6.0, N=N, seed=4300, sigma=1.0)
+    ops = oracle_ops(p)
+    rng = np.random.default_rng(4301)
+    # an M-orthonormal block of random vectors (256 Gaussians on 1331 unknowns are
+    # numerically dependent)
+    Gr = rng.standard_normal((p.n_interior, N))
+    Lc = np.linalg.cholesky(Gr.T @ (ops.M @ Gr))
+    U0 = np.linalg.solve(Lc, Gr.T).T
+    m = make_mesh(B, p, B.PARO_FP64 if prec == "fp64" else B.PARO_MIXED)
+    # Step 3 on the Ritz vectors of the guesses
+    lam0 = np.linspace(1.5, 8.0, N)
+    ref = O.source_problems(ops, U0, lam0, 1e-12, 5000)
+    U = dev(U0)
+    X = torch.empty_like(U)
+    rc, st = m.orbital_solve(lam0, U, X, B.paro_default_params(solve_tol=1e-11, pcg_maxit=5000))
+    assert rc == 0 and st.max_relres <= 1e-11
+    assert np.max(np.abs(host(X) - ref.X)) < 1e-8 * np.max(np.abs(ref.X))
+    # Step 4 on a near-orthonormal block
+    X0 = U0 + 1e-2 * np.max(np.abs(U0)) * rng.standard_normal(U0.shape)
+    rr = O.rayleigh_ritz(ops, X0)
+    Xd = dev(X0)
+    Ud = torch.empty_like(Xd)
+    lam, st = m.rayleigh_ritz(Xd, Ud)
+    scale = np.max(np.abs(rr.lam))
+    tol = 1e-10 if prec == "fp64" else 3e-8
+    assert np.max(np.abs(lam - rr.lam)) < tol * scale, np.max(np.abs(lam - rr.lam)) / scale
+    u = host(Ud)
+    assert np.max(np.abs(u.T @ (ops.M @ u) - np.eye(N))) < (1e-10 if prec == "fp64" else 1e-6)
+    assert st.rr_tc_steps == (1 if prec == "mixed" else 0)
+    m.close()
