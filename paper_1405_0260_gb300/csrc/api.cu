@@ -720,8 +720,9 @@ int rr_packed(paro_mesh m, int N, const double* src, double* dst, double* lam, R
   }
   LAUNCH(1, launch_small_eig(N, m->GA, m->GB, m->eigwork, m->C, m->theta, &m->cgst->status, m->st));
   TRY(check_status(m, "rayleigh_ritz"));
-  // the float-float rotation stages C (hi/lo, 8 Np^2 bytes) in shared memory
-  if ((ff || tc) && Np <= kRotateFFMaxNp)
+  // float-float rotation from the split X (C staged in shared memory whole, or in
+  // column blocks above kRotateFFMaxNp)
+  if (ff || tc)
     LAUNCH(1, launch_rotate_ff(g, N, Np, m->fxh, m->fxl, m->C, dst, m->st));
   else
     LAUNCH(1, launch_rotate(g, N, Np, src, m->C, dst, m->st));

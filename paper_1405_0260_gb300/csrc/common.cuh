@@ -158,7 +158,7 @@ constexpr int kTcMaxNp = 256;
 size_t gram_tc_partial_doubles(const Grid& g, int Np);
 cudaError_t launch_gram_tc(const Grid& g, int Np, const float* xh, const float* yh, double* part, int* n_chunks,
                            int* status, cudaStream_t st);
-constexpr int kRotateFFMaxNp = 144;  // C as float-float in shared memory: 8 Np^2 bytes
+constexpr int kRotateFFMaxNp = 144;  // whole C as float-float in shared memory (8 Np^2 bytes); column blocks above
 cudaError_t launch_rotate_ff(const Grid& g, int N, int Np, const float* xh, const float* xl, const double* C,
                              double* U, cudaStream_t st);
 

@@ -234,6 +234,52 @@ __global__ void __launch_bounds__(kRedThreads) k_rotate_ff(Grid g, int N, int Np
   }
 }
 
+// U = X C for any Np (float-float): CTA y takes output columns [64 y, 64 y + 64);
+// C's rows pass through shared memory 64 at a time as hi/lo [64][64]; a thread
+// owns 4 output columns of one node (16 threads a node, 16 nodes a pass).
+constexpr int kRotCB = 64, kRotKC = 64;
+__global__ void __launch_bounds__(256) k_rotate_ff_cols(Grid g, int N, int Np, const float* __restrict__ xh,
+                                                         const float* __restrict__ xl, const double* __restrict__ C,
+                                                         double* __restrict__ U) {
+  __shared__ float ch[kRotKC][kRotCB], cl[kRotKC][kRotCB];
+  const int b0 = blockIdx.y * kRotCB;
+  const int grp = threadIdx.x % (kRotCB / 4);  // 4 columns each
+  const int nl = threadIdx.x / (kRotCB / 4);   // 16 nodes a pass
+  const int npb = blockDim.x / (kRotCB / 4);
+  const int b = b0 + 4 * grp;
+  for (int n0 = blockIdx.x * npb; n0 < g.nI; n0 += gridDim.x * npb) {
+    const int n = n0 + nl;
+    const long long gp = n < g.nI ? interior_to_padded(g, n) : 0;
+    FF acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    for (int a0 = 0; a0 < N; a0 += kRotKC) {
+      __syncthreads();  // the previous chunk's C is no longer read
+      for (int t = threadIdx.x; t < kRotKC * kRotCB; t += blockDim.x) {
+        const int r = t / kRotCB, c = t % kRotCB;
+        const int a = a0 + r, bb = b0 + c;
+        const FF f = (a < N && bb < Np) ? ff_split(C[(long long)a * Np + bb]) : FF{0.f, 0.f};
+        ch[r][c] = f.hi;
+        cl[r][c] = f.lo;
+      }
+      __syncthreads();
+      const int na = N - a0 < kRotKC ? N - a0 : kRotKC;
+      if (n < g.nI && b < Np)
+        for (int r = 0; r < na; ++r) {
+          const long long e = gp * Np + a0 + r;
+          const FF xa{xh[e], xl[e]};
+          const float4 h = *reinterpret_cast<const float4*>(&ch[r][4 * grp]);
+          const float4 l = *reinterpret_cast<const float4*>(&cl[r][4 * grp]);
+          ff_mac(acc[0], xa, FF{h.x, l.x});
+          ff_mac(acc[1], xa, FF{h.y, l.y});
+          ff_mac(acc[2], xa, FF{h.z, l.z});
+          ff_mac(acc[3], xa, FF{h.w, l.w});
+        }
+    }
+    if (n < g.nI && b < Np)
+      st4(U + gp * Np + b, V4<double>{ff_to_double(ff_norm(acc[0])), ff_to_double(ff_norm(acc[1])),
+                                      ff_to_double(ff_norm(acc[2])), ff_to_double(ff_norm(acc[3]))});
+  }
+}
+
 int apply_grid(const Grid& g, int Np) {
   const NodeMap nm = node_map(Np);
   const long long need = (g.nI + nm.npb - 1) / nm.npb;
@@ -303,6 +349,15 @@ cudaError_t launch_gram2_ff(const Grid& g, int Np, const float* xh, const float*
 
 cudaError_t launch_rotate_ff(const Grid& g, int N, int Np, const float* xh, const float* xl, const double* C,
                              double* U, cudaStream_t st) {
+  if (Np > kRotateFFMaxNp) {
+    // column blocks of 64 outputs, C through shared memory 64 rows at a time
+    const int ncb = (Np + kRotCB - 1) / kRotCB;
+    long long nb = ((long long)g.nI + 15) / 16;
+    const long long cap = 152LL * 8 / ncb + 1;
+    dim3 grid((unsigned)(nb < cap ? nb : cap), (unsigned)ncb);
+    k_rotate_ff_cols<<<grid, 256, 0, st>>>(g, N, Np, xh, xl, C, U);
+    return cudaGetLastError();
+  }
   const size_t smem = (size_t)2 * Np * Np * sizeof(float);
   if (smem > 48 * 1024) {
     cudaError_t e = allow_max_dyn_smem((const void*)k_rotate_ff);

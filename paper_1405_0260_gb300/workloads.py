@@ -201,3 +201,17 @@ def batch_systems(count=64, seed=4000, L=10.0, meshes=(32, 48, 64, 96), n_range=
         out.append(Problem(f"batch{k}-{nc}^3-{M}nuc-N{N}", n, lo, hi, V, 0.0, U0, tol, nuc))
     return out
 
+
+def large_cluster(nc=192, L=20.0, n_nuclei=40, zmax=4, box=14.0, min_sep=1.8, N=256, seed=5000, tol=1e-7):
+    """The large fixed-potential workload: 40 softened-Coulomb nuclei (Z ~ U{1..4})
+    uniform in [-14, 14]^3 at least 1.8 bohr apart, cube [-20, 20]^3, nc^3 cells,
+    N orbitals.  Initial block: seeded standard normal values (N seeded Gaussians
+    on this mesh would be numerically dependent); sigma is left to the caller."""
+    rng = np.random.default_rng(seed)
+    nuc = place_nuclei(rng, n_nuclei, zmax, box, min_sep)
+    n = (nc, nc, nc)
+    lo, hi = (-L, -L, -L), (L, L, L)
+    V = softened_coulomb(n, lo, hi, nuc)
+    U0 = rng.standard_normal(((nc - 1) ** 3, N))
+    return Problem(f"large-{nc}^3-{n_nuclei}nuc-N{N}", n, lo, hi, V, 0.0, U0, tol, nuc)
+
