@@ -59,6 +59,14 @@ def problem(rank):
     return W.harmonic(nc=NC, L=L, N=NORB, seed=2000 + rank, sigma=SIGMA)
 
 
+# DRAM traffic of the CG kernel from one ncu capture of this workload's geometry
+# (dram__bytes_read.sum + dram__bytes_write.sum = 2.208 GB over the 9 passes of the
+# autotuner's all-active timing run, profiles/k_cg1_harmonic64_N20.md).  Scaled to a
+# launch by its passes; an upper bound, since converged orbitals skip their own
+# loads and stores.
+K_CG1_TRAFFIC_PER_PASS = 2.208e9 / 9
+
+
 def peaks():
     try:
         with open(PEAKS) as f:
@@ -204,7 +212,9 @@ def run_ours(args, ws, rank, local):
         roof = {"kernel": "k_cg1<float> (single-reduction CG loop: TMA-tiled w = A D^-1 r with the vector updates, one grid barrier a pass)",
                 "bound": "hbm",
                 "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": None,
+                "frac": round(achieved / peak, 4),
+                "traffic": round(K_CG1_TRAFFIC_PER_PASS * prof_nodes / nI / prof_n),
+                "traffic_note": "ncu DRAM bytes a pass of an all-active launch x passes a launch (upper bound)",
                 "launches": prof_n, "avg_launch_us": round(1e3 * prof_ms / prof_n, 2),
                 "alg_bytes_per_launch": round(alg_bytes / prof_n),
                 # one orbital block (N <= 32): passes = node passes / interior nodes, and
