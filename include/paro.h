@@ -186,7 +186,9 @@ int paro_ks_potential(paro_mesh m, const double* rho_q, const double* vext_q, do
  * handle's sigma (from the last paro_set_potential), solves the N source
  * problems and does Rayleigh-Ritz with it, then mixes
  * rho_in <- (1 - mix) rho_in + mix rho_out (rho_out: density of the new
- * orbitals).  Stops when max_i |Delta lambda_i| < p->tol or after p->fixed_outer.
+ * orbitals).  Stops when max |Delta lambda_i| over the lowest p->n_check
+ * orbitals (0: all; Algorithm 3.2 tests the occupied ones and carries the rest
+ * as a buffer) is below p->tol, or after p->fixed_outer.
  * The Hartree solve is warm-started from the previous one; PARO_FP64 handles
  * solve it to p->solve_tol, PARO_MIXED handles to max(p->solve_tol,
  * min(1e-4, 1e-2 x the previous iteration's max |Delta lambda|)).
@@ -195,6 +197,16 @@ int paro_ks_potential(paro_mesh m, const double* rho_q, const double* vext_q, do
  * on return.  Errors as paro_iterate. */
 int paro_scf_iterate(paro_mesh m, int N, const double* occ, const double* vext_q, double mix, double* U,
                      double* lambda, const paro_params* p, paro_stats* s);
+
+/* Kohn-Sham electronic energy of the orbitals U (device, n_interior x N) with
+ * occupations occ and eigenvalues lambda (host[N] each), in the band-energy form
+ *     E = sum_i f_i lambda_i - 1/2 int rho V_H - int rho V_x + E_x,
+ * rho = sum_i f_i u_i^2, V_H by a Hartree solve (p->solve_tol), Slater exchange;
+ * at self-consistency this is the Kohn-Sham energy functional (the nuclei's
+ * mutual repulsion not included).  *energy: host out.  Leaves the handle's SCF
+ * density (rho_in) untouched. */
+int paro_ks_energy(paro_mesh m, int N, const double* occ, const double* lambda, const double* U,
+                   const paro_params* p, double* energy);
 
 /* Copy the mixed density rho_in of the last paro_scf_iterate to rho_q (device). */
 int paro_ks_density_in(paro_mesh m, double* rho_q);

@@ -29,7 +29,8 @@ M-orthonormal orbitals (exact with the Gauss rule); the density of a trilinear
 function equals its square at the Gauss points; the Hartree potential of a
 Gaussian charge approaches Q erf(r / (sqrt 2 s)) / r at O(h^2); the Slater
 energy of a Gaussian density matches its closed-form integral; SCF keeps the
-charge and reaches self-consistency.
+charge and reaches self-consistency; at self-consistency the band-energy form of
+the total energy equals its direct definition.
 """
 from __future__ import annotations
 
@@ -174,6 +175,27 @@ def effective_potential(mesh: P.Mesh, Vext_q: np.ndarray, rho_q: np.ndarray) -> 
     return np.asarray(Vext_q) + hartree(mesh, rho_q).VH_q + slater_potential(rho_q)
 
 
+def total_energy(mesh: P.Mesh, lam: np.ndarray, occ: np.ndarray, rho_q: np.ndarray) -> float:
+    """Kohn-Sham electronic energy in the band-energy form:
+        E = sum_i f_i lambda_i - 1/2 int rho V_H[rho] - int rho V_x[rho] + E_x[rho]
+    (the eigenvalue sum counts the Hartree energy twice and holds int rho V_x in
+    place of E_x).  The nuclei's mutual repulsion is not included."""
+    VH = hartree(mesh, rho_q).VH_q
+    return float(np.dot(np.asarray(occ, dtype=np.float64), np.asarray(lam, dtype=np.float64))
+                 - 0.5 * integrate(mesh, rho_q * VH) - integrate(mesh, rho_q * slater_potential(rho_q))
+                 + slater_energy(mesh, rho_q))
+
+
+def direct_energy(mesh: P.Mesh, Vext_q: np.ndarray, U: np.ndarray, occ: np.ndarray) -> float:
+    """The same energy from its definition, for the density of the orbitals U:
+        E = sum_i f_i (u_i, (K/2 + M_Vext) u_i) + 1/2 int rho V_H[rho] + E_x[rho]."""
+    ops = P.assemble(mesh, Vext_q, 0.0)
+    occ = np.asarray(occ, dtype=np.float64)
+    rho = density_gauss(mesh, U, occ)
+    one = float(np.einsum("i,ni,ni->", occ, U, ops.H @ U))
+    return one + 0.5 * integrate(mesh, rho * hartree(mesh, rho).VH_q) + slater_energy(mesh, rho)
+
+
 # ---------------------------------------------------------------------------
 # SCF: Algorithm 3.1 with the Kohn-Sham potential and linear mixing
 # ---------------------------------------------------------------------------
@@ -191,14 +213,16 @@ class SCFResult:
 
 def scf(mesh: P.Mesh, Vext_q: np.ndarray, U0: np.ndarray, occ: np.ndarray, sigma: float, mix: float = 0.3,
         tol: float = 1e-8, max_outer: int = 200, pcg_tol: float = 1e-12, pcg_maxit: int = 5000,
-        fixed_outer: int | None = None) -> SCFResult:
+        fixed_outer: int | None = None, n_check: int | None = None) -> SCFResult:
     """Kohn-Sham ParO.
 
     Start: one Rayleigh-Ritz on span(U0) with V_ext alone gives orbitals whose
     density is the first rho_in.  Each outer iteration builds V from rho_in,
     solves the N shifted source problems (Step 3) and does Rayleigh-Ritz
     (Step 4) with that potential, then mixes rho_in with the density of the new
-    orbitals.  Stops when max |Delta lambda| < tol, or after fixed_outer.
+    orbitals.  Stops when max |Delta lambda| < tol over the lowest n_check
+    orbitals (all by default; Algorithm 3.2 tests the occupied ones and carries
+    the others as a buffer), or after fixed_outer.
     """
     ops0 = P.assemble(mesh, Vext_q, sigma)
     rr = P.rayleigh_ritz(ops0, U0)
@@ -212,7 +236,8 @@ def scf(mesh: P.Mesh, Vext_q: np.ndarray, U0: np.ndarray, occ: np.ndarray, sigma
         ops = P.assemble(mesh, V, sigma)
         sol = P.source_problems(ops, U, lam, pcg_tol, pcg_maxit)
         rr = P.rayleigh_ritz(ops, sol.X)
-        dl = np.max(np.abs(rr.lam - lam))
+        k = len(lam) if n_check is None else n_check
+        dl = np.max(np.abs(rr.lam[:k] - lam[:k]))
         U, lam = rr.U, rr.lam
         rho_out = density_gauss(mesh, U, occ)
         rho_in = (1.0 - mix) * rho_in + mix * rho_out

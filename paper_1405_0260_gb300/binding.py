@@ -88,6 +88,7 @@ def lib():
     L.paro_scf_iterate.argtypes = [vp, ip, dp, vp, C.c_double, vp, dp, C.POINTER(paro_params),
                                    C.POINTER(paro_stats)]
     L.paro_ks_density_in.argtypes = [vp, vp]
+    L.paro_ks_energy.argtypes = [vp, ip, dp, dp, vp, C.POINTER(paro_params), dp]
     L.paro_last_error.argtypes = [vp]
     L.paro_last_error.restype = C.c_char_p
     L.paro_interior_nodes.argtypes = [vp]
@@ -99,7 +100,7 @@ def lib():
     L.paro_batch_destroy.argtypes = [vp]
     for f in ("paro_mesh_create", "paro_mesh_destroy", "paro_set_potential", "paro_orbital_solve",
               "paro_rayleigh_ritz", "paro_iterate", "paro_apply", "paro_density", "paro_ks_potential",
-              "paro_scf_iterate", "paro_ks_density_in", "paro_batch_create", "paro_batch_add", "paro_batch_size",
+              "paro_scf_iterate", "paro_ks_density_in", "paro_ks_energy", "paro_batch_create", "paro_batch_add", "paro_batch_size",
               "paro_batch_iterate", "paro_batch_destroy"):
         getattr(L, f).restype = C.c_int
     _lib = L
@@ -267,6 +268,16 @@ class Mesh:
                                      C.c_void_p(self._dev(U)), _dptr(lam),
                                      C.byref(params) if params is not None else None, C.byref(st))
         return _check(rc, self.h, allow), lam, st
+
+    def ks_energy(self, U, occ, lam, params=None):
+        """Kohn-Sham electronic energy (band-energy form) of the orbitals U."""
+        N = U.shape[1]
+        occ = np.ascontiguousarray(occ, dtype=np.float64)
+        lam = np.ascontiguousarray(lam, dtype=np.float64)
+        e = np.zeros(1)
+        _check(lib().paro_ks_energy(self.h, N, _dptr(occ), _dptr(lam), C.c_void_p(self._dev(U)),
+                                    C.byref(params) if params is not None else None, _dptr(e)), self.h)
+        return float(e[0])
 
     def ks_density_in(self, rho):
         _check(lib().paro_ks_density_in(self.h, self._dev(rho)), self.h)

@@ -80,6 +80,8 @@ struct paro_mesh_s {
   double* ks_rho2 = nullptr;  // rho_out
   double* ks_v = nullptr;     // the effective potential
   double* ks_occ = nullptr;   // occupations [Np]
+  double* ks_vh = nullptr;    // V_H of the energy evaluation (Gauss points)
+  double* ks_energy = nullptr;  // [int rho V_H, int rho V_x, E_x]
 };
 
 static std::string g_create_err;
@@ -822,6 +824,8 @@ int ensure_ks(paro_mesh m) {
   TRY(dalloc(m, &m->ks_rho2, (size_t)nq));
   TRY(dalloc(m, &m->ks_v, (size_t)nq));
   TRY(dalloc(m, &m->ks_occ, (size_t)kMaxN));
+  TRY(dalloc(m, &m->ks_vh, (size_t)nq));
+  TRY(dalloc(m, &m->ks_energy, 3));
   return PARO_OK;
 }
 
@@ -1204,6 +1208,7 @@ int paro_scf_iterate(paro_mesh m, int N, const double* occ, const double* vext_q
   CK(cudaMemcpyAsync(m->u, m->x, sizeof(double) * m->g.G * Np, cudaMemcpyDeviceToDevice, m->st));
   LAUNCH(1, launch_density(m->g, N, Np, m->u, m->ks_occ, m->ks_rho, m->st));
   const int limit = pp.fixed_outer > 0 ? pp.fixed_outer : pp.max_outer;
+  const int nchk = (pp.n_check > 0 && pp.n_check < N) ? pp.n_check : N;  // Algorithm 3.2: occupied only
   int outer = 0, rc = PARO_ERR_NOT_CONVERGED;
   double dl = INFINITY;
   RRMode rr_mode = kRRFast;
@@ -1229,7 +1234,7 @@ int paro_scf_iterate(paro_mesh m, int N, const double* occ, const double* vext_q
     LAUNCH(1, launch_density(m->g, N, Np, m->u, m->ks_occ, m->ks_rho2, m->st));
     LAUNCH(1, launch_mix(gauss_count(m->g), mix, m->ks_rho, m->ks_rho2, m->st));
     dl = 0.0;
-    for (int i = 0; i < N; ++i) dl = std::fmax(dl, std::fabs(lam_new[i] - lam[i]));
+    for (int i = 0; i < nchk; ++i) dl = std::fmax(dl, std::fabs(lam_new[i] - lam[i]));
     lam = lam_new;
     rr_mode = next_rr_mode(m, rr_mode, dl, lam);
     ++outer;
@@ -1248,6 +1253,31 @@ int paro_scf_iterate(paro_mesh m, int N, const double* occ, const double* vext_q
   CK(cudaStreamSynchronize(m->st));
   if (rc != PARO_OK) m->err = "paro_scf_iterate: max_outer reached before tol";
   return rc;
+}
+
+int paro_ks_energy(paro_mesh m, int N, const double* occ, const double* lambda, const double* U,
+                   const paro_params* p, double* energy) {
+  TRY(check_common(m, N));
+  if (!occ || !lambda || !U || !energy) return fail(m, PARO_ERR_ARG, "null pointer");
+  paro_params pp;
+  if (p) pp = *p;
+  else paro_default_params(&pp);
+  const int Np = (N + 3) / 4 * 4;
+  TRY(ensure_workspace(m, Np));
+  TRY(ensure_ks(m));
+  TRY(upload_occ(m, N, occ));
+  CallScope cs(m, nullptr, 0);
+  // rho of the given orbitals (in the rho_out buffer: rho_in of an SCF run is kept)
+  LAUNCH(1, launch_pack(m->g, N, Np, U, m->u, m->st));
+  LAUNCH(1, launch_density(m->g, N, Np, m->u, m->ks_occ, m->ks_rho2, m->st));
+  TRY(ks_potential(m, m->ks_rho2, nullptr, nullptr, m->ks_vh, pp));
+  LAUNCH(2, launch_energy_terms(m->g, m->ks_rho2, m->ks_vh, m->ks_part, m->ks_energy, m->st));
+  CK(cudaMemcpyAsync(m->h_dbl, m->ks_energy, sizeof(double) * 3, cudaMemcpyDeviceToHost, m->st));
+  CK(cudaStreamSynchronize(m->st));
+  double band = 0.0;
+  for (int i = 0; i < N; ++i) band += occ[i] * lambda[i];
+  *energy = band - 0.5 * m->h_dbl[0] - m->h_dbl[1] + m->h_dbl[2];
+  return PARO_OK;
 }
 
 int paro_ks_density_in(paro_mesh m, double* rho_q) {

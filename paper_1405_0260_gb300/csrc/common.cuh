@@ -182,6 +182,9 @@ cudaError_t launch_hartree_rhs(const Grid& g, const double lo[3], const double* 
 cudaError_t launch_ks_potential(const Grid& g, const double lo[3], const double* w, const double* mom,
                                 const double* rho, const double* vext, double* vout, double* vh_out,
                                 cudaStream_t st);
+// out[0..2] = int rho V_H, int rho V_x, E_x (Slater) over the Gauss points; part: moments_blocks() x 3
+cudaError_t launch_energy_terms(const Grid& g, const double* rho, const double* vh, double* part, double* out,
+                                cudaStream_t st);
 cudaError_t launch_mix(long long n, double beta, double* rho_in, const double* rho_out, cudaStream_t st);
 
 }  // namespace paro

@@ -159,6 +159,41 @@ __global__ void k_ks_potential(Grid g, double lox, double loy, double loz, const
   if (vout) vout[t] = vext[t] + vh + vx;
 }
 
+// Per-block partial sums over the Gauss points (weight w = hx hy hz / 8) of
+// w rho V_H, w rho V_x and w e_x(rho), Slater: V_x = -(3 rho / pi)^(1/3),
+// e_x = 3/4 rho V_x.
+__global__ void k_energy_terms(Grid g, const double* __restrict__ rho, const double* __restrict__ vh,
+                               double* __restrict__ part) {
+  __shared__ double sm[3][256];
+  const long long n = (long long)g.nx * g.ny * g.nz * 8;
+  const double w = g.hx * g.hy * g.hz / 8.0;
+  double a[3] = {0, 0, 0};
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const double r = rho[t] > 0.0 ? rho[t] : 0.0;
+    const double vx = -cbrt(3.0 * r / M_PI);
+    a[0] += w * r * vh[t];
+    a[1] += w * r * vx;
+    a[2] += w * 0.75 * r * vx;
+  }
+  for (int k = 0; k < 3; ++k) sm[k][threadIdx.x] = a[k];
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int k = 0; k < 3; ++k) sm[k][threadIdx.x] += sm[k][threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x < 3) part[blockIdx.x * 3 + threadIdx.x] = sm[threadIdx.x][0];
+}
+
+// Fixed-order sum of the block partials: out[0..2].
+__global__ void k_energy_final(int nblocks, const double* __restrict__ part, double* __restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double a[3] = {0, 0, 0};
+  for (int b = 0; b < nblocks; ++b)
+    for (int k = 0; k < 3; ++k) a[k] += part[b * 3 + k];
+  for (int k = 0; k < 3; ++k) out[k] = a[k];
+}
+
 // rho_in <- (1 - beta) rho_in + beta rho_out
 __global__ void k_mix(long long n, double beta, double* __restrict__ rho_in, const double* __restrict__ rho_out) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -195,6 +230,14 @@ cudaError_t launch_ks_potential(const Grid& g, const double lo[3], const double*
                                 cudaStream_t st) {
   const long long n = (long long)g.nx * g.ny * g.nz * 8;
   k_ks_potential<<<nblk(n, 256), 256, 0, st>>>(g, lo[0], lo[1], lo[2], w, mom, rho, vext, vout, vh_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_energy_terms(const Grid& g, const double* rho, const double* vh, double* part, double* out,
+                                cudaStream_t st) {
+  const int nb = moments_blocks();
+  k_energy_terms<<<nb, 256, 0, st>>>(g, rho, vh, part);
+  k_energy_final<<<1, 32, 0, st>>>(nb, part, out);
   return cudaGetLastError();
 }
 

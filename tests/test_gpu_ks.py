@@ -114,3 +114,39 @@ def test_scf_mixed_converges_to_oracle(B):
     assert rc == 0
     assert np.max(np.abs(lam - ref.lam)) < 1e-6, (lam, ref.lam)
     m.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_ks_energy_matches_oracle(B, prec):
+    # the band-energy form for given orbitals and eigenvalues: density, Hartree
+    # solve and the three Gauss-point integrals against the oracle
+    mesh, Vext, U0, occ = cluster(nc=9)
+    ops = O.assemble(mesh, Vext, 3.0)
+    rr = O.rayleigh_ritz(ops, U0)
+    ref = KS.total_energy(mesh, rr.lam, occ, KS.density_gauss(mesh, rr.U, occ))
+    m = B.Mesh(mesh.n, mesh.lo, mesh.hi, B.PARO_FP64 if prec == "fp64" else B.PARO_MIXED)
+    vq = dev(Vext)
+    m.set_potential(vq, 3.0)
+    e = m.ks_energy(dev(rr.U), occ, rr.lam,
+                    B.paro_default_params(solve_tol=1e-13 if prec == "fp64" else 1e-12, pcg_maxit=20000))
+    assert abs(e - ref) < 1e-9 * abs(ref), (e, ref)
+    m.close()
+
+
+def test_scf_with_buffer_orbitals_reaches_the_oracle_energy(B):
+    # Algorithm 3.2: four orbitals, the occupied two tested for convergence; the
+    # energy at convergence against the oracle's direct definition
+    mesh, Vext, U0, occ = cluster(nc=9)
+    ref = KS.scf(mesh, Vext, U0, occ, sigma=3.0, tol=1e-10, max_outer=400, pcg_tol=1e-12, n_check=2)
+    e_ref = KS.direct_energy(mesh, Vext, ref.U, occ)
+    m = B.Mesh(mesh.n, mesh.lo, mesh.hi, B.PARO_MIXED)
+    vq = dev(Vext)
+    m.set_potential(vq, 3.0)
+    U = dev(U0)
+    params = B.paro_default_params(tol=1e-10, max_outer=400, solve_tol=1e-11, n_check=2)
+    rc, lam, st = m.scf_iterate(U, occ, vq, 0.3, params)
+    assert rc == 0
+    assert np.max(np.abs(lam[:2] - ref.lam[:2])) < 1e-6, (lam, ref.lam)
+    e = m.ks_energy(U, occ, lam, B.paro_default_params(solve_tol=1e-12))
+    assert abs(e - e_ref) < 1e-6 * abs(e_ref), (e, e_ref)
+    m.close()

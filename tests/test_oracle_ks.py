@@ -98,3 +98,23 @@ def test_scf_keeps_the_charge_and_becomes_self_consistent():
     assert KS.integrate(mesh, np.abs(rho_out - res.rho_q)) < 1e-6
     # bound state below the continuum of the box
     assert res.lam[0] < 0.0
+
+
+def test_total_energy_band_form_equals_direct_definition_at_self_consistency():
+    # sum f_i lambda_i double counts the Hartree energy and holds int rho V_x: the
+    # band-energy form subtracts both; at self-consistency (rho_in = rho of the
+    # orbitals whose eigenvalues were summed) it equals the functional itself
+    nc, L = 9, 5.0
+    mesh = O.Mesh((nc, nc, nc), (-L, -L, -L), (L, L, L))
+    X = O.gauss_points(mesh).reshape(-1, 3)
+    Vext = -2.0 / np.sqrt((X ** 2).sum(1) + 0.25)
+    p = W.harmonic(nc=nc, L=L, N=3, seed=22)
+    occ = KS.occupations(3, 2)
+    res = KS.scf(mesh, Vext, p.U0, occ, sigma=3.0, tol=1e-11, max_outer=400, n_check=1)
+    rho = KS.density_gauss(mesh, res.U, occ)
+    e_band = KS.total_energy(mesh, res.lam, occ, rho)
+    e_direct = KS.direct_energy(mesh, Vext, res.U, occ)
+    assert abs(e_band - e_direct) < 1e-7 * abs(e_direct), (e_band, e_direct)
+    # away from self-consistency the two differ (the pin has teeth)
+    rho_off = 0.5 * rho
+    assert abs(KS.total_energy(mesh, res.lam, occ, rho_off) - e_direct) > 1e-3
