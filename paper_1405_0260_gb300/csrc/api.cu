@@ -720,7 +720,8 @@ int rr_packed(paro_mesh m, int N, const double* src, double* dst, double* lam, R
     LAUNCH(1, launch_apply_f64(g, Np, nullptr, &m->mw, 0.0, src, m->q, nullptr, m->st));         // M
     LAUNCH(2, launch_gram2(g, N, Np, src, m->r, m->q, m->gpart, nullptr, m->GA, m->GB, m->st));
   }
-  LAUNCH(1, launch_small_eig(N, m->GA, m->GB, m->eigwork, m->C, m->theta, &m->cgst->status, m->st));
+  LAUNCH(1, launch_small_eig(N, m->GA, m->GB, m->eigwork, m->C, m->theta, &m->cgst->status, m->st,
+                             &m->cgst->bar_count));
   TRY(check_status(m, "rayleigh_ritz"));
   // float-float rotation from the split X (C staged in shared memory whole, or in
   // column blocks above kRotateFFMaxNp)

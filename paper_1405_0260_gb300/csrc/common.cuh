@@ -166,8 +166,11 @@ cudaError_t launch_rotate_ff(const Grid& g, int N, int Np, const float* xh, cons
 cudaError_t launch_gram2(const Grid& g, int N, int Np, const double* X, const double* Y1, const double* Y2,
                          double* part, int* n_chunks, double* G1, double* G2, cudaStream_t st);
 size_t gram_partial_doubles(const Grid& g, int Np);
+// N > kEigGridMinN with a barrier counter (bar, device): the whole-GPU form;
+// else one CTA.  C (Np x Np) needs room for N + 2 x 128 + 1 doubles of scratch.
+constexpr int kEigGridMinN = 64;
 cudaError_t launch_small_eig(int N, const double* GA, const double* GB, double* work, double* C, double* theta,
-                             int* status, cudaStream_t st);
+                             int* status, cudaStream_t st, unsigned* bar = nullptr);
 cudaError_t launch_rotate(const Grid& g, int N, int Np, const double* X, const double* C, double* U,
                           cudaStream_t st);
 

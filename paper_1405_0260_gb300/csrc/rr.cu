@@ -367,9 +367,279 @@ cudaError_t launch_gram_reduce1(int Np, int nch, const double* part, double* Gm,
   return cudaGetLastError();
 }
 
+namespace {
+
+// Grid-wide barrier of the multi-CTA eigensolve: CTAs add 1 to a counter the
+// host zeroes before the launch; barrier k completes at k * gridDim.x.  Bounded:
+// false after kEigSpinLimit polls.
+constexpr unsigned kEigSpinLimit = 1u << 24;
+__device__ bool eig_barrier(unsigned* count, unsigned target) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(count, 1u);
+    int ok = 0;
+    for (unsigned i = 0; i < kEigSpinLimit; ++i) {
+      unsigned v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
+      if (v >= target) {
+        ok = 1;
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// The small generalized eigensolve of k_small_eig for larger N on the whole GPU
+// (cooperative launch): the same steps and the same cyclic Jacobi ordering, but
+// every Jacobi round's rotations are spread over all CTAs with three grid
+// barriers a round (angles, rows, columns).  Cholesky in CTA 0; the triangular
+// solves and the back-substitution one warp per column.  work: L, S, V, W
+// (N x N each, ld N); C (Np x Np) doubles as scratch until its final write:
+// [0, 2 half) rotation (c, s), [2 half, 2 half + 2 grid) the sweep's partial
+// norms, then a failure flag.
+__global__ void __launch_bounds__(256) k_small_eig_grid(int N, int Np, const double* __restrict__ GA,
+                                                        const double* __restrict__ GB, double* __restrict__ work,
+                                                        double* __restrict__ C, double* __restrict__ theta,
+                                                        int* __restrict__ status, unsigned* __restrict__ bar) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const long long gt = (long long)blockIdx.x * nt + tid, gs = (long long)gridDim.x * nt;
+  const int lane = tid % 32;
+  const int gw = (int)(gt / 32), nw = (int)(gs / 32);
+  const long long NN = (long long)N * N;
+  double* L = work;
+  double* S = work + NN;
+  double* V = work + 2 * NN;
+  double* W = work + 3 * NN;
+  const int m = (N % 2 == 0) ? N : N + 1;
+  const int half = m / 2;
+  double* cs = C;                   // [half][2]
+  double* part = C + 2 * half;      // [grid][2]
+  double* flag = part + 2 * gridDim.x;
+  double* rdiag = W;                // after the triangular solves: W holds 1 / L[i][i] in its first row
+  __shared__ double red[256 / 32][2];
+  __shared__ int s_fail;
+  unsigned bno = 0;
+  auto sync = [&]() -> bool {
+    if (!eig_barrier(bar, ++bno * gridDim.x)) {
+      if (tid == 0) atomicOr(status, kStatTimeout);
+      return false;
+    }
+    return true;
+  };
+  // copy and symmetrise
+  for (long long t = gt; t < NN; t += gs) {
+    const int i = (int)(t / N), j = (int)(t % N);
+    L[t] = 0.5 * (GB[(long long)i * Np + j] + GB[(long long)j * Np + i]);
+    S[t] = 0.5 * (GA[(long long)i * Np + j] + GA[(long long)j * Np + i]);
+    V[t] = (i == j) ? 1.0 : 0.0;
+  }
+  if (gt == 0) flag[0] = 0.0;
+  if (!sync()) return;
+  // Cholesky (right-looking, lower triangle) in CTA 0
+  if (blockIdx.x == 0) {
+    if (tid == 0) s_fail = 0;
+    __syncthreads();
+    for (int k = 0; k < N; ++k) {
+      if (tid == 0) {
+        const double d = L[(long long)k * N + k];
+        if (!(d > 0.0) || !isfinite(d)) s_fail = 1;
+        else L[(long long)k * N + k] = sqrt(d);
+      }
+      __syncthreads();
+      if (s_fail) break;
+      const double rk = 1.0 / L[(long long)k * N + k];
+      for (int i = k + 1 + tid; i < N; i += nt) L[(long long)i * N + k] *= rk;
+      __syncthreads();
+      const int r = N - k - 1;
+      for (long long t = tid; t < (long long)r * r; t += nt) {
+        const int i = k + 1 + (int)(t / r), j = k + 1 + (int)(t % r);
+        if (j <= i) L[(long long)i * N + j] -= L[(long long)i * N + k] * L[(long long)j * N + k];
+      }
+      __syncthreads();
+    }
+    if (s_fail && tid == 0) {
+      flag[0] = 1.0;
+      atomicOr(status, kStatNotSPD);
+    }
+  }
+  if (!sync()) return;
+  if (flag[0] != 0.0) return;
+  for (long long t = gt; t < NN; t += gs) {
+    const int i = (int)(t / N), j = (int)(t % N);
+    if (j > i) L[t] = 0.0;
+  }
+  if (!sync()) return;
+  // W = L^-1 S, then S = L^-1 W^T: one warp per column, the lanes split each row's dot product
+  for (int pass = 0; pass < 2; ++pass) {
+    const double* Rin = pass == 0 ? S : W;
+    double* Rout = pass == 0 ? W : S;
+    for (int j = gw; j < N; j += nw) {
+      for (int i = 0; i < N; ++i) {
+        double acc = 0.0;
+        for (int k = lane; k < i; k += 32) acc += L[(long long)i * N + k] * Rout[(long long)k * N + j];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) {
+          const double b = pass == 0 ? Rin[(long long)i * N + j] : Rin[(long long)j * N + i];
+          Rout[(long long)i * N + j] = (b - acc) / L[(long long)i * N + i];
+        }
+        __syncwarp();
+      }
+    }
+    if (!sync()) return;
+  }
+  // symmetrise S, keep 1 / L[i][i] in W's first row (W is free now)
+  for (long long t = gt; t < NN; t += gs) {
+    const int i = (int)(t / N), j = (int)(t % N);
+    if (j > i) {
+      const double a = 0.5 * (S[t] + S[(long long)j * N + i]);
+      S[t] = a;
+      S[(long long)j * N + i] = a;
+    }
+  }
+  for (long long i = gt; i < N; i += gs) rdiag[i] = 1.0 / L[i * N + i];
+  if (!sync()) return;
+  // parallel cyclic Jacobi
+  for (int sweep = 0; sweep < 40 && N > 1; ++sweep) {
+    double off = 0.0, all = 0.0;
+    for (long long t = gt; t < NN; t += gs) {
+      const double v = S[t];
+      all += v * v;
+      if (t / N != t % N) off += v * v;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      all += __shfl_xor_sync(0xffffffffu, all, o);
+    }
+    if (lane == 0) {
+      red[tid / 32][0] = off;
+      red[tid / 32][1] = all;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double a = 0.0, b = 0.0;
+      for (int w = 0; w < nt / 32; ++w) {
+        a += red[w][0];
+        b += red[w][1];
+      }
+      part[2 * blockIdx.x] = a;
+      part[2 * blockIdx.x + 1] = b;
+    }
+    if (!sync()) return;
+    // every CTA sums the partials in the same order: the same decision everywhere
+    off = 0.0;
+    all = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) {
+      off += part[2 * b];
+      all += part[2 * b + 1];
+    }
+    if (!(off > 1e-29 * (double)N * N * all)) break;
+    for (int r = 0; r < m - 1; ++r) {
+      for (long long k = gt; k < half; k += gs) {
+        int p, q;
+        rr_pair(m, r, (int)k, &p, &q);
+        double c = 1.0, s = 0.0;
+        if (q < N) {
+          // angle in float32, (c, s) renormalised in float64 (as k_small_eig)
+          const float fa = (float)S[(long long)p * N + q];
+          if (fa != 0.0f) {
+            const float tau = (float)(S[(long long)q * N + q] - S[(long long)p * N + p]) / (2.0f * fa);
+            const float rt = sqrtf(1.0f + tau * tau);
+            const float t = (tau >= 0.0f) ? 1.0f / (tau + rt) : -1.0f / (-tau + rt);
+            const float cf = rsqrtf(1.0f + t * t);
+            const double cd = cf, sd = (double)(t * cf);
+            const double nn = cd * cd + sd * sd;
+            double y = 1.5 - 0.5 * nn;
+            y = y * (1.5 - 0.5 * nn * y * y);
+            c = cd * y;
+            s = sd * y;
+          }
+        }
+        cs[2 * k] = c;
+        cs[2 * k + 1] = s;
+      }
+      if (!sync()) return;
+      // rows p, q of S <- J^T S
+      for (long long t = gt; t < (long long)half * N; t += gs) {
+        const int k = (int)(t / N), col = (int)(t % N);
+        int p, q;
+        rr_pair(m, r, k, &p, &q);
+        if (q >= N) continue;
+        const double c = cs[2 * k], s = cs[2 * k + 1];
+        const double sp = S[(long long)p * N + col], sq = S[(long long)q * N + col];
+        S[(long long)p * N + col] = c * sp - s * sq;
+        S[(long long)q * N + col] = s * sp + c * sq;
+      }
+      if (!sync()) return;
+      // columns p, q of S <- S J; V <- V J
+      for (long long t = gt; t < (long long)half * N; t += gs) {
+        const int k = (int)(t / N), row = (int)(t % N);
+        int p, q;
+        rr_pair(m, r, k, &p, &q);
+        if (q >= N) continue;
+        const double c = cs[2 * k], s = cs[2 * k + 1];
+        const double sp = S[(long long)row * N + p], sq = S[(long long)row * N + q];
+        S[(long long)row * N + p] = c * sp - s * sq;
+        S[(long long)row * N + q] = s * sp + c * sq;
+        const double vp = V[(long long)row * N + p], vq = V[(long long)row * N + q];
+        V[(long long)row * N + p] = c * vp - s * vq;
+        V[(long long)row * N + q] = s * vp + c * vq;
+      }
+      if (!sync()) return;
+    }
+  }
+  // every CTA has read the sweep's partial norms (C's scratch) before C is written
+  if (!sync()) return;
+  // sort by ascending Ritz value (ties by index); back-substitution C = L^-T V, one
+  // warp per column
+  for (int j = gw; j < N; j += nw) {
+    const double tj = S[(long long)j * N + j];
+    int rank = 0;
+    for (int i = lane; i < N; i += 32) {
+      const double ti = S[(long long)i * N + i];
+      if (ti < tj || (ti == tj && i < j)) ++rank;
+    }
+    for (int o = 16; o > 0; o >>= 1) rank += __shfl_xor_sync(0xffffffffu, rank, o);
+    if (lane == 0) theta[rank] = tj;
+    for (int i = N - 1; i >= 0; --i) {
+      double acc = 0.0;
+      for (int k = i + 1 + lane; k < N; k += 32) acc += L[(long long)k * N + i] * C[(long long)k * Np + rank];
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) C[(long long)i * Np + rank] = (V[(long long)i * N + j] - acc) * rdiag[i];
+      __syncwarp();
+    }
+  }
+  for (long long t = gt; t < (long long)Np * Np; t += gs) {
+    const int i = (int)(t / Np), j = (int)(t % Np);
+    if (i >= N || j >= N) C[t] = 0.0;
+  }
+}
+
+}  // namespace
+
 cudaError_t launch_small_eig(int N, const double* GA, const double* GB, double* work, double* C, double* theta,
-                             int* status, cudaStream_t st) {
+                             int* status, cudaStream_t st, unsigned* bar) {
   int Np = (N + 3) / 4 * 4;
+  if (bar != nullptr && N > kEigGridMinN) {
+    // the whole GPU: a cooperative grid of up to 128 CTAs (co-resident by construction)
+    int dev = 0, nsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int half = (N + 1) / 2;
+    int grid = half < nsm ? half : nsm;
+    if (grid > 128) grid = 128;
+    if ((e = cudaMemsetAsync(bar, 0, sizeof(unsigned), st)) != cudaSuccess) return e;
+    int n = N, np = Np;
+    void* args[] = {&n, &np, (void*)&GA, (void*)&GB, &work, &C, &theta, &status, &bar};
+    return cudaLaunchCooperativeKernel((const void*)k_small_eig_grid, dim3(grid), dim3(256), args, 0, st);
+  }
   // threads: about one per rotation-pair row element, a multiple of 32
   int nt = (N * N / 2 + 31) / 32 * 32;
   if (nt < 64) nt = 64;
