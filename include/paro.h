@@ -86,6 +86,12 @@ typedef struct {
                          solve) with CUDA events on the handle's stream and report it in paro_stats.prof_*;
                          2: the same for a host-driven loop that launches the operator pass and the
                          update as separate kernels (timing the operator pass); 0: off (0) */
+  int n_clusters;     /* paro_iterate: > 0 separates the Rayleigh-Ritz step of the outer iterations by
+                         eigenvalue clusters (Section 3): orbitals come in n_clusters consecutive groups
+                         of cluster_size[k] (ascending; the sizes add up to N); each group is made
+                         M-orthogonal to the groups before it and gets its own small eigenproblem, and
+                         the Ritz values are sorted within each group.  0: one problem of size N (0) */
+  const int* cluster_size; /* host[n_clusters], read during the call (NULL) */
 } paro_params;
 
 /* Statistics of a call.  Counters and times (cg_iters*, ms_*, stencil_applies,

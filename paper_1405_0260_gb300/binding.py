@@ -37,8 +37,18 @@ class paro_params(C.Structure):
         ("tol", C.c_double), ("max_outer", C.c_int), ("n_check", C.c_int),
         ("solve_tol", C.c_double), ("pcg_maxit", C.c_int), ("inner_tol", C.c_double),
         ("max_refine", C.c_int), ("check_every", C.c_int), ("fixed_outer", C.c_int),
-        ("profile", C.c_int),
+        ("profile", C.c_int), ("n_clusters", C.c_int), ("cluster_size", C.POINTER(C.c_int)),
     ]
+
+    def set_clusters(self, sizes):
+        """Cluster-separated Rayleigh-Ritz with these consecutive group sizes (None: off)."""
+        if not sizes:
+            self.n_clusters, self.cluster_size, self._sizes = 0, None, None
+            return self
+        self._sizes = (C.c_int * len(sizes))(*[int(q) for q in sizes])  # kept alive with the params
+        self.n_clusters = len(sizes)
+        self.cluster_size = C.cast(self._sizes, C.POINTER(C.c_int))
+        return self
 
 
 class paro_stats(C.Structure):

@@ -19,6 +19,7 @@ using namespace paro;
 struct paro_mesh_s {
   Grid g{};
   long long rr_tc = 0;  // Rayleigh-Ritz steps with tensor-core Grams (for paro_stats)
+  int* clus = nullptr;  // cluster ids of the cluster-separated Rayleigh-Ritz (device, kMaxN)
   const char* tune_source = "default";  // how the float32 CG geometry was chosen
   long long ks_pois_iters = 0;  // CG iterations of the Hartree solves (for paro_stats)
   int precision = PARO_FP64;
@@ -685,7 +686,8 @@ RRMode next_rr_mode(paro_mesh m, RRMode cur, double dl, const std::vector<double
 // kRRFP64 is used for the start on user guesses, whose overlap matrix can be
 // ill-conditioned far beyond what the mixed path's Grams resolve (their error is
 // amplified by cond(X^T M X)); inside the ParO loop X stays near M-orthonormal.
-int rr_packed(paro_mesh m, int N, const double* src, double* dst, double* lam, RRMode mode = kRRFast) {
+int rr_packed(paro_mesh m, int N, const double* src, double* dst, double* lam, RRMode mode = kRRFast,
+              const int* clus = nullptr) {
   const int Np = m->Np_alloc;
   Grid& g = m->g;
   const bool mixed = m->precision == PARO_MIXED;
@@ -721,7 +723,7 @@ int rr_packed(paro_mesh m, int N, const double* src, double* dst, double* lam, R
     LAUNCH(2, launch_gram2(g, N, Np, src, m->r, m->q, m->gpart, nullptr, m->GA, m->GB, m->st));
   }
   LAUNCH(1, launch_small_eig(N, m->GA, m->GB, m->eigwork, m->C, m->theta, &m->cgst->status, m->st,
-                             &m->cgst->bar_count));
+                             &m->cgst->bar_count, clus));
   TRY(check_status(m, "rayleigh_ritz"));
   // float-float rotation from the split X (C staged in shared memory whole, or in
   // column blocks above kRotateFFMaxNp)
@@ -914,6 +916,9 @@ void paro_default_params(paro_params* p) {
   p->max_refine = 20;
   p->check_every = 16;
   p->fixed_outer = 0;
+  p->profile = 0;
+  p->n_clusters = 0;
+  p->cluster_size = nullptr;
 }
 
 int paro_mesh_create(paro_mesh* out, int nx, int ny, int nz, const double lo[3], const double hi[3], int precision,
@@ -1090,6 +1095,23 @@ int paro_iterate(paro_mesh m, int N, double* U, double* lambda, const paro_param
   }
   const int nchk = (pp.n_check > 0 && pp.n_check < N) ? pp.n_check : N;
   RRMode rr_mode = kRRFast;
+  const int* clus = nullptr;
+  if (pp.n_clusters > 0) {
+    if (!pp.cluster_size) return fail(m, PARO_ERR_ARG, "cluster_size is NULL");
+    int total = 0;
+    for (int k = 0; k < pp.n_clusters; ++k) {
+      if (pp.cluster_size[k] < 1) return fail(m, PARO_ERR_ARG, "cluster sizes must be positive");
+      total += pp.cluster_size[k];
+    }
+    if (total != N) return fail(m, PARO_ERR_ARG, "cluster sizes must add up to N");
+    if (!m->clus) TRY(dalloc(m, &m->clus, (size_t)kMaxN));
+    int* ids = m->h_int;  // pinned host staging
+    for (int k = 0, o = 0; k < pp.n_clusters; ++k)
+      for (int j = 0; j < pp.cluster_size[k]; ++j) ids[o++] = k;
+    CK(cudaMemcpyAsync(m->clus, ids, sizeof(int) * N, cudaMemcpyHostToDevice, m->st));
+    CK(cudaStreamSynchronize(m->st));
+    clus = m->clus;
+  }
   int outer = 0;
   int rc = PARO_ERR_NOT_CONVERGED;
   const int limit = pp.fixed_outer > 0 ? pp.fixed_outer : pp.max_outer;
@@ -1102,7 +1124,7 @@ int paro_iterate(paro_mesh m, int N, double* U, double* lambda, const paro_param
     }
     {
       Timer t(m, s ? &s->ms_rr : nullptr);
-      TRY(rr_packed(m, N, m->x, m->u, lam_new.data(), rr_mode));
+      TRY(rr_packed(m, N, m->x, m->u, lam_new.data(), rr_mode, clus));
     }
     dl = 0.0;
     for (int i = 0; i < nchk; ++i) dl = std::fmax(dl, std::fabs(lam_new[i] - lam[i]));

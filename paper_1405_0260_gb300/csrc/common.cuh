@@ -169,8 +169,10 @@ size_t gram_partial_doubles(const Grid& g, int Np);
 // N > kEigGridMinN with a barrier counter (bar, device): the whole-GPU form;
 // else one CTA.  C (Np x Np) needs room for N + 2 x 128 + 1 doubles of scratch.
 constexpr int kEigGridMinN = 64;
+// clus (device, N cluster ids ascending, optional): cluster-separated form, the
+// eigenproblem of each cluster's diagonal block alone, sorted within clusters.
 cudaError_t launch_small_eig(int N, const double* GA, const double* GB, double* work, double* C, double* theta,
-                             int* status, cudaStream_t st, unsigned* bar = nullptr);
+                             int* status, cudaStream_t st, unsigned* bar = nullptr, const int* clus = nullptr);
 cudaError_t launch_rotate(const Grid& g, int N, int Np, const double* X, const double* C, double* U,
                           cudaStream_t st);
 

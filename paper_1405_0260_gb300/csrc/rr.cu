@@ -96,7 +96,8 @@ __device__ __forceinline__ void rr_pair(int m, int r, int k, int* p, int* q) {
 __global__ void __launch_bounds__(1024) k_small_eig(int N, int Np, const double* __restrict__ GA,
                                                     const double* __restrict__ GB, double* __restrict__ work,
                                                     double* __restrict__ C, double* __restrict__ theta,
-                                                    int* __restrict__ status, int smem) {
+                                                    int* __restrict__ status, int smem,
+                                                    const int* __restrict__ clus) {
   extern __shared__ double esm[];
   if (smem) work = esm;
   __shared__ int fail;
@@ -167,6 +168,7 @@ __global__ void __launch_bounds__(1024) k_small_eig(int N, int Np, const double*
     int i = t / N, j = t % N;
     if (j > i) {
       double a = 0.5 * (S[i * N + j] + S[j * N + i]);
+      if (clus != nullptr && clus[i] != clus[j]) a = 0.0;  // cluster-separated: diagonal blocks only
       S[i * N + j] = a;
       S[j * N + i] = a;
     }
@@ -270,7 +272,11 @@ __global__ void __launch_bounds__(1024) k_small_eig(int N, int Np, const double*
     int rank = 0;
     for (int i = 0; i < N; ++i) {
       double ti = S[i * N + i];
-      if (ti < tj || (ti == tj && i < j)) ++rank;
+      if (clus != nullptr && clus[i] != clus[j]) {
+        if (clus[i] < clus[j]) ++rank;  // every orbital of an earlier cluster comes first
+      } else if (ti < tj || (ti == tj && i < j)) {
+        ++rank;
+      }
     }
     theta[rank] = tj;
     for (int i = N - 1; i >= 0; --i) {
@@ -407,7 +413,8 @@ __device__ bool eig_barrier(unsigned* count, unsigned target) {
 __global__ void __launch_bounds__(256) k_small_eig_grid(int N, int Np, const double* __restrict__ GA,
                                                         const double* __restrict__ GB, double* __restrict__ work,
                                                         double* __restrict__ C, double* __restrict__ theta,
-                                                        int* __restrict__ status, unsigned* __restrict__ bar) {
+                                                        int* __restrict__ status, unsigned* __restrict__ bar,
+                                                        const int* __restrict__ clus) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const long long gt = (long long)blockIdx.x * nt + tid, gs = (long long)gridDim.x * nt;
   const int lane = tid % 32;
@@ -498,7 +505,8 @@ __global__ void __launch_bounds__(256) k_small_eig_grid(int N, int Np, const dou
   for (long long t = gt; t < NN; t += gs) {
     const int i = (int)(t / N), j = (int)(t % N);
     if (j > i) {
-      const double a = 0.5 * (S[t] + S[(long long)j * N + i]);
+      double a = 0.5 * (S[t] + S[(long long)j * N + i]);
+      if (clus != nullptr && clus[i] != clus[j]) a = 0.0;  // cluster-separated: diagonal blocks only
       S[t] = a;
       S[(long long)j * N + i] = a;
     }
@@ -603,7 +611,11 @@ __global__ void __launch_bounds__(256) k_small_eig_grid(int N, int Np, const dou
     int rank = 0;
     for (int i = lane; i < N; i += 32) {
       const double ti = S[(long long)i * N + i];
-      if (ti < tj || (ti == tj && i < j)) ++rank;
+      if (clus != nullptr && clus[i] != clus[j]) {
+        if (clus[i] < clus[j]) ++rank;  // every orbital of an earlier cluster comes first
+      } else if (ti < tj || (ti == tj && i < j)) {
+        ++rank;
+      }
     }
     for (int o = 16; o > 0; o >>= 1) rank += __shfl_xor_sync(0xffffffffu, rank, o);
     if (lane == 0) theta[rank] = tj;
@@ -624,7 +636,7 @@ __global__ void __launch_bounds__(256) k_small_eig_grid(int N, int Np, const dou
 }  // namespace
 
 cudaError_t launch_small_eig(int N, const double* GA, const double* GB, double* work, double* C, double* theta,
-                             int* status, cudaStream_t st, unsigned* bar) {
+                             int* status, cudaStream_t st, unsigned* bar, const int* clus) {
   int Np = (N + 3) / 4 * 4;
   if (bar != nullptr && N > kEigGridMinN) {
     // the whole GPU: a cooperative grid of up to 128 CTAs (co-resident by construction)
@@ -637,7 +649,7 @@ cudaError_t launch_small_eig(int N, const double* GA, const double* GB, double* 
     if (grid > 128) grid = 128;
     if ((e = cudaMemsetAsync(bar, 0, sizeof(unsigned), st)) != cudaSuccess) return e;
     int n = N, np = Np;
-    void* args[] = {&n, &np, (void*)&GA, (void*)&GB, &work, &C, &theta, &status, &bar};
+    void* args[] = {&n, &np, (void*)&GA, (void*)&GB, &work, &C, &theta, &status, &bar, (void*)&clus};
     return cudaLaunchCooperativeKernel((const void*)k_small_eig_grid, dim3(grid), dim3(256), args, 0, st);
   }
   // threads: about one per rotation-pair row element, a multiple of 32
@@ -648,9 +660,9 @@ cudaError_t launch_small_eig(int N, const double* GA, const double* GB, double* 
   if (smem <= 160 * 1024) {
     cudaError_t e = allow_max_dyn_smem((const void*)k_small_eig);
     if (e != cudaSuccess) return e;
-    k_small_eig<<<1, nt, smem, st>>>(N, Np, GA, GB, work, C, theta, status, 1);
+    k_small_eig<<<1, nt, smem, st>>>(N, Np, GA, GB, work, C, theta, status, 1, clus);
   } else {
-    k_small_eig<<<1, nt, 0, st>>>(N, Np, GA, GB, work, C, theta, status, 0);
+    k_small_eig<<<1, nt, 0, st>>>(N, Np, GA, GB, work, C, theta, status, 0, clus);
   }
   return cudaGetLastError();
 }
@@ -710,7 +722,7 @@ extern "C" int paro_small_eig_static(int N, const double* GA, const double* GB, 
   // The status word keeps the previous call's value: clear it.  The work
   // matrices are fully written by the kernel before they are read.
   if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return PARO_ERR_CUDA;
-  paro::k_small_eig<<<1, 1024, 0, st>>>(N, N, GA, GB, scratch, C, theta, status, 0);
+  paro::k_small_eig<<<1, 1024, 0, st>>>(N, N, GA, GB, scratch, C, theta, status, 0, nullptr);
   if (cudaGetLastError() != cudaSuccess) return PARO_ERR_CUDA;
   int h = 0;
   if (cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return PARO_ERR_CUDA;

@@ -299,3 +299,47 @@ def test_subspace_angles_of_known_rotation():
         W = np.stack([np.eye(5)[:, 0], math.cos(t) * np.eye(5)[:, 1] + math.sin(t) * np.eye(5)[:, 2]], axis=1)
         ang = O.subspace_angles_M(M, U, W)
         assert abs(ang[0]) < 1e-15 and abs(ang[1] - t) < 1e-6 * t
+
+
+def test_cluster_separated_rayleigh_ritz_nested_spans_and_block_ritz_conditions():
+    # eigenvalue separation (Section 3) with block Gram-Schmidt: the first k clusters'
+    # Ritz vectors span exactly the first k clusters' columns of X, all of them are
+    # M-orthonormal, and the Ritz conditions hold inside each block (not across)
+    p = W.harmonic(nc=8, L=5.0, N=7, seed=31, sigma=0.0)
+    ops = O.assemble(O.Mesh(p.n, p.lo, p.hi), p.Vq, 0.0)
+    X = O.rayleigh_ritz(ops, p.U0).U + 0.05 * np.random.default_rng(32).standard_normal((p.n_interior, 7))
+    sizes = [1, 3, 3]
+    rr = O.rayleigh_ritz_clusters(ops, X, sizes)
+    assert np.max(np.abs(rr.U.T @ (ops.M @ rr.U) - np.eye(7))) < 1e-12
+    o = 0
+    for q in sizes:
+        assert np.max(O.subspace_angles_M(ops.M, rr.U[:, :o + q], X[:, :o + q])) < 1e-10
+        U = rr.U[:, o:o + q]
+        assert np.max(np.abs(U.T @ (ops.H @ U) - np.diag(rr.lam[o:o + q]))) < 1e-11 * np.max(np.abs(rr.lam))
+        o += q
+    # across blocks H is not diagonalised: the separation leaves the coupling in place
+    assert np.max(np.abs(rr.U[:, :1].T @ (ops.H @ rr.U[:, 1:4]))) > 1e-6
+    # a single cluster is the full problem
+    full = O.rayleigh_ritz(ops, X)
+    one = O.rayleigh_ritz_clusters(ops, X, [7])
+    assert np.max(np.abs(full.lam - one.lam)) < 1e-12 * np.max(np.abs(full.lam))
+
+
+def test_cluster_separated_paro_reaches_the_box_spectrum():
+    # well-posed initial data (each cluster's guesses near its own eigenspace): ParO with
+    # one Rayleigh-Ritz problem per degenerate shell {1}, {3} converges to the closed form
+    n, L = (8, 8, 8), (1.0, 1.0, 1.0)
+    mesh = _mesh(n, L)
+    ops = O.assemble(mesh, np.zeros(8 * 512), 0.5)
+    xyz = mesh.interior_coords()
+
+    def mode(a, b, c):
+        return (np.sin(a * math.pi * (xyz[:, 0] + 1) / 2) * np.sin(b * math.pi * (xyz[:, 1] + 1) / 2)
+                * np.sin(c * math.pi * (xyz[:, 2] + 1) / 2))
+
+    exact = np.stack([mode(1, 1, 1), mode(2, 1, 1), mode(1, 2, 1), mode(1, 1, 2)], axis=1)
+    rng = np.random.default_rng(33)
+    U0 = exact + 0.05 * rng.standard_normal(exact.shape)
+    res = O.paro(ops, U0, tol=1e-12, max_outer=400, pcg_tol=1e-13, clusters=[1, 3])
+    ref = _box_spectrum(n, mesh.h)[:4]
+    assert np.max(np.abs(res.lam - ref) / ref) < 1e-9
