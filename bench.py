@@ -484,6 +484,59 @@ def run_large(args):
     m.close()
 
 
+def run_ks(args):
+    """The Kohn-Sham cluster (8 softened nuclei, 128^3 cells, mixed precision):
+    SCF ParO with linear mixing 0.3, stopped at max |delta lambda| < 1e-6 over the
+    occupied orbitals (the 8 extra orbitals are the Algorithm 3.2 buffer) or after
+    --ks-max-outer SCF iterations, then the total energy (not the headline line).
+    Reports the time per SCF iteration and the state reached."""
+    import math
+
+    import torch
+
+    from oracle import ks as KS  # occupations only (a two-line rule), no method arithmetic
+    from paper_1405_0260_gb300 import binding as B
+    from paper_1405_0260_gb300 import workloads as W
+
+    p = W.cluster(nc=args.ks_nc)
+    N = p.U0.shape[1]
+    n_el = int(round(float(p.nuclei[:, 3].sum())))
+    occ = KS.occupations(N, n_el)
+    m = B.Mesh(p.n, p.lo, p.hi, B.PARO_MIXED)
+    vq = torch.from_numpy(np.ascontiguousarray(p.Vq)).cuda()
+    m.set_potential(vq, 0.0)
+    X = torch.from_numpy(np.ascontiguousarray(p.U0)).cuda()
+    # shift: first a safe one (min V bounds the spectrum from below) for a few ParO
+    # iterations on V_ext alone, then 1 - theta_1 rounded up (theta_1 their lowest Ritz
+    # value, an upper bound close to lambda_1).  The Hartree potential of 16 electrons
+    # raises the spectrum by more than Slater exchange lowers it; a shift that still
+    # leaves H + sigma M indefinite ends the solve with PARO_ERR_NOT_SPD.  A large shift
+    # slows every source-problem step ((lambda_i + s)/(lambda_N+1 + s) -> 1).
+    safe = math.ceil((0.5 - float(np.min(p.Vq))) / 0.5) * 0.5
+    m.set_potential(vq, safe)
+    U = X.clone()
+    _, lam0, _ = m.iterate(U, None, B.paro_default_params(tol=1e-2, max_outer=100, solve_tol=1e-8), allow=(-4,))
+    sigma = math.ceil((1.0 - lam0[0]) / 0.5) * 0.5
+    m.set_potential(vq, sigma)
+    params = B.paro_default_params(tol=1e-6, max_outer=args.ks_max_outer, solve_tol=1e-10, n_check=p.n_occ)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc, lam, st = m.scf_iterate(U, occ, vq, args.ks_mix, params, allow=(-4,))
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    energy = m.ks_energy(U, occ, lam, B.paro_default_params(solve_tol=1e-10))
+    line = {"metric": "Kohn-Sham SCF ParO to max |delta lambda| < 1e-6 Ha on the occupied orbitals (mixed)",
+            "workload": f"{len(p.nuclei)} softened nuclei, [-12,12]^3, {p.n[0]}^3 cells ({p.n_interior} dofs), "
+                        f"{n_el} electrons, N={N} ({p.n_occ} occupied + buffer), sigma={sigma}, mixing {args.ks_mix}",
+            "converged": rc == 0, "outer_iters": st.outer_iters, "seconds": dt,
+            "ms_per_outer": 1e3 * dt / max(st.outer_iters, 1), "max_dlambda": st.max_dlambda,
+            "poisson_cg_iters": st.poisson_cg_iters, "cg_iters_f32": st.cg_iters_f32,
+            "rr_tc_steps": st.rr_tc_steps, "energy_ha": energy,
+            "lambda_occupied": [float(v) for v in lam[:p.n_occ]], "data": "synthetic (seeded nuclei)"}
+    print(json.dumps(line), flush=True)
+    m.close()
+
+
 def collections_count(values):
     out = {}
     for v in values:
@@ -499,9 +552,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--skip-cpu", action="store_true", help="omit the cpu_baseline leg")
     ap.add_argument("--skip-converge", action="store_true", help="omit the time-to-converge leg")
-    ap.add_argument("--workload", default="harmonic64", choices=["harmonic64", "batch", "large"],
+    ap.add_argument("--workload", default="harmonic64", choices=["harmonic64", "batch", "large", "ks"],
                     help="batch: independent systems (meshes 32-96^3, N 4-48) through paro_batch_iterate; "
-                         "large: 192^3 cells, N = 256")
+                         "large: 192^3 cells, N = 256; ks: the Kohn-Sham cluster SCF to convergence")
+    ap.add_argument("--ks-nc", type=int, default=128, help="ks workload: cells per axis")
+    ap.add_argument("--ks-max-outer", type=int, default=1500, help="ks workload: SCF iteration limit")
+    ap.add_argument("--ks-mix", type=float, default=0.3, help="ks workload: linear density mixing")
     ap.add_argument("--large-nc", type=int, default=192, help="large workload: cells per axis")
     ap.add_argument("--systems", type=int, default=64, help="batch workload: number of systems")
     ap.add_argument("--workers", type=int, default=8, help="batch workload: host worker threads")
@@ -509,9 +565,9 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
     ws, rank, local = dist_env()
-    if args.workload in ("batch", "large"):
+    if args.workload in ("batch", "large", "ks"):
         if rank == 0 and args.impl == "ours":
-            (run_batch if args.workload == "batch" else run_large)(args)
+            {"batch": run_batch, "large": run_large, "ks": run_ks}[args.workload](args)
         return
     if args.impl == "reference":
         run_reference(args, ws, rank)
