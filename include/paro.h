@@ -69,6 +69,10 @@ typedef enum {
 #define PARO_F32 1
 #define PARO_FF 2 /* float64 X, Y; float-float arithmetic (the mixed path's float64-accurate applies) */
 
+/* Preconditioner of the float32 correction solves (paro_params.precond). */
+#define PARO_PRECOND_JACOBI 0 /* Jacobi (D^-1), fused into the single-reduction CG kernel */
+#define PARO_PRECOND_MG 1     /* one geometric-multigrid V-cycle (see paro_mg_vcycle); PARO_MIXED handles */
+
 typedef struct paro_mesh_s* paro_mesh;
 
 /* Solver controls.  paro_default_params fills the defaults noted here. */
@@ -92,6 +96,12 @@ typedef struct {
                          M-orthogonal to the groups before it and gets its own small eigenproblem, and
                          the Ritz values are sorted within each group.  0: one problem of size N (0) */
   const int* cluster_size; /* host[n_clusters], read during the call (NULL) */
+  int precond;        /* PARO_PRECOND_JACOBI or PARO_PRECOND_MG: the preconditioner of the float32
+                         correction solves of a PARO_MIXED handle, the Hartree solves included
+                         (Section 3: each source problem solved by a parallel multigrid method).
+                         PARO_PRECOND_MG on a PARO_FP64 handle: PARO_ERR_ARG (PARO_PRECOND_JACOBI) */
+  int mg_nu;          /* multigrid: damped-Jacobi sweeps before and after the coarse correction, 1..8 (1) */
+  int mg_coarse_sweeps; /* multigrid: sweeps on the coarsest level, 1..64 (4) */
 } paro_params;
 
 /* Statistics of a call.  Counters and times (cg_iters*, ms_*, stencil_applies,
@@ -160,6 +170,18 @@ int paro_rayleigh_ritz(paro_mesh m, int N, const double* X, double* U_out, doubl
  * lambda[0] to start with one Rayleigh-Ritz step on span(U); out: Ritz values.
  * Stops on max |delta lambda| < tol (or after fixed_outer iterations). */
 int paro_iterate(paro_mesh m, int N, double* U, double* lambda, const paro_params* p, paro_stats* s);
+
+/* Z = B R: one V(mg_nu, mg_nu) cycle of the geometric multigrid preconditioner of
+ * A = K/2 + M_{V+sigma} (the handle's current operator), float32, all N columns at
+ * once (Section 3, two-level parallelisation).  Hierarchy: the cell counts are halved
+ * while all three are even and >= 4; prolongation P = trilinear interpolation (the
+ * coarse Q1 basis in the fine one); coarse operators A_c = P^T A P (Galerkin, built
+ * in float64); damped Jacobi x <- x + w D^-1 (b - A x), w = min(1, 4/(3 rho)) with
+ * rho = max_i sum_j |A_ij| / A_ii; mg_coarse_sweeps sweeps on the coarsest level; the
+ * first sweep of every level starts from x = 0.  B is symmetric positive definite.
+ * R, Z: device (n_interior x N) float32, must not alias.  PARO_MIXED handles only.
+ * p: mg_nu and mg_coarse_sweeps are read (NULL: defaults). */
+int paro_mg_vcycle(paro_mesh m, int N, const float* R, float* Z, const paro_params* p);
 
 /* Y = op X for a block of N orbitals (op: PARO_OP_A/H/M), in float64 (dtype
  * PARO_F64: X, Y double) or float32 (PARO_F32: X, Y float, float32 weights).

@@ -30,6 +30,7 @@ STATUS = {
 PARO_FP64, PARO_MIXED = 0, 1
 PARO_OP_A, PARO_OP_H, PARO_OP_M = 0, 1, 2
 PARO_F64, PARO_F32, PARO_FF = 0, 1, 2
+PARO_PRECOND_JACOBI, PARO_PRECOND_MG = 0, 1
 
 
 class paro_params(C.Structure):
@@ -38,6 +39,7 @@ class paro_params(C.Structure):
         ("solve_tol", C.c_double), ("pcg_maxit", C.c_int), ("inner_tol", C.c_double),
         ("max_refine", C.c_int), ("check_every", C.c_int), ("fixed_outer", C.c_int),
         ("profile", C.c_int), ("n_clusters", C.c_int), ("cluster_size", C.POINTER(C.c_int)),
+        ("precond", C.c_int), ("mg_nu", C.c_int), ("mg_coarse_sweeps", C.c_int),
     ]
 
     def set_clusters(self, sizes):
@@ -93,6 +95,7 @@ def lib():
     L.paro_rayleigh_ritz.argtypes = [vp, ip, vp, vp, dp, C.POINTER(paro_stats)]
     L.paro_iterate.argtypes = [vp, ip, vp, dp, C.POINTER(paro_params), C.POINTER(paro_stats)]
     L.paro_apply.argtypes = [vp, ip, ip, ip, vp, vp]
+    L.paro_mg_vcycle.argtypes = [vp, ip, vp, vp, C.POINTER(paro_params)]
     L.paro_density.argtypes = [vp, ip, vp, dp, vp]
     L.paro_ks_potential.argtypes = [vp, vp, vp, vp, vp, C.POINTER(paro_params)]
     L.paro_scf_iterate.argtypes = [vp, ip, dp, vp, C.c_double, vp, dp, C.POINTER(paro_params),
@@ -109,7 +112,7 @@ def lib():
     L.paro_batch_iterate.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(paro_stats)]
     L.paro_batch_destroy.argtypes = [vp]
     for f in ("paro_mesh_create", "paro_mesh_destroy", "paro_set_potential", "paro_orbital_solve",
-              "paro_rayleigh_ritz", "paro_iterate", "paro_apply", "paro_density", "paro_ks_potential",
+              "paro_rayleigh_ritz", "paro_iterate", "paro_apply", "paro_mg_vcycle", "paro_density", "paro_ks_potential",
               "paro_scf_iterate", "paro_ks_density_in", "paro_ks_energy", "paro_batch_create", "paro_batch_add", "paro_batch_size",
               "paro_batch_iterate", "paro_batch_destroy"):
         getattr(L, f).restype = C.c_int
@@ -258,6 +261,13 @@ class Mesh:
         else:
             dt = PARO_FF if float_float else PARO_F64
         paro_apply(self.h, X.shape[1], op, dt, self._dev(X, X.dtype), self._dev(Y, X.dtype))
+
+    def mg_vcycle(self, R, Z, params=None):
+        """Z = B R, one multigrid V-cycle (float32 tensors, PARO_MIXED handles)."""
+        import torch
+
+        _check(lib().paro_mg_vcycle(self.h, R.shape[1], self._dev(R, torch.float32), self._dev(Z, torch.float32),
+                                    C.byref(params) if params is not None else None), self.h)
 
     # Kohn-Sham (fields at the Gauss points, float64 device tensors of 8*nx*ny*nz values)
     def density(self, U, occ, rho):

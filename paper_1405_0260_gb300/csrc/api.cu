@@ -12,6 +12,7 @@
 
 #include "../../include/paro.h"
 #include "cg.cuh"
+#include "mg.cuh"
 #include "common.cuh"
 
 using namespace paro;
@@ -83,6 +84,9 @@ struct paro_mesh_s {
   double* ks_occ = nullptr;   // occupations [Np]
   double* ks_vh = nullptr;    // V_H of the energy evaluation (Gauss points)
   double* ks_energy = nullptr;  // [int rho V_H, int rho V_x, E_x]
+  // multigrid preconditioner of the float32 correction solves (built on first use,
+  // coefficients rebuilt after every new potential)
+  MGHier mg;
 };
 
 static std::string g_create_err;
@@ -556,12 +560,118 @@ int run_cg(paro_mesh m, CGPlan<T>* P, int N, bool warm, double tol, int maxit, i
   return PARO_OK;
 }
 
+// Multigrid hierarchy for Np-wide level vectors: grids and storage on first use
+// (again when Np changes), Galerkin coefficients and Jacobi weights whenever the
+// operator changed since the last build.
+int ensure_mg(paro_mesh m, int Np) {
+  MGHier& h = m->mg;
+  if (h.nlev == 0 || h.Np != Np) {
+    CK(cudaStreamSynchronize(m->st));
+    for (int l = 1; l < h.nlev; ++l) {
+      MGLevel& L = h.lev[l];
+      void* olds[] = {L.coef64, L.coef32, L.dinv32, L.b, L.t, L.x, L.y};
+      for (void* o : olds) dfree(m, o);
+      L = MGLevel{};
+    }
+    Grid gs[kMaxMGLevels];
+    const int nc = mg_plan_levels(m->g, gs, kMaxMGLevels);
+    h.lev[0] = MGLevel{};
+    h.lev[0].g = m->g;
+    for (int l = 1; l <= nc; ++l) {
+      MGLevel& L = h.lev[l];
+      L.g = gs[l - 1];
+      const size_t G = (size_t)L.g.G;
+      TRY(dalloc(m, &L.coef64, 27 * G));
+      TRY(dalloc(m, &L.coef32, 27 * G));
+      TRY(dalloc(m, &L.dinv32, G));
+      TRY(dalloc(m, &L.b, G * Np));
+      TRY(dalloc(m, &L.t, G * Np));
+      TRY(dalloc(m, &L.x, G * Np));
+      TRY(dalloc(m, &L.y, G * Np));
+    }
+    if (!h.rho_bits) TRY(dalloc(m, &h.rho_bits, kMaxMGLevels));
+    h.nlev = nc + 1;
+    h.Np = Np;
+    h.built = false;
+  }
+  MGLevel& F = h.lev[0];
+  F.coef64 = m->coef64;
+  F.coef32 = m->coef32;
+  F.dinv32 = m->dinv32;
+  if (h.built) return PARO_OK;
+  CK(cudaMemsetAsync(h.rho_bits, 0, sizeof(unsigned long long) * kMaxMGLevels, m->st));
+  for (int l = 0; l < h.nlev; ++l) {
+    if (l > 0)
+      LAUNCH(1, launch_mg_galerkin(h.lev[l - 1].g, h.lev[l].g, h.lev[l - 1].coef64, h.lev[l].coef64,
+                                   h.lev[l].coef32, h.lev[l].dinv32, m->st));
+    LAUNCH(1, launch_mg_rho(h.lev[l].g, h.lev[l].coef64, h.rho_bits + l, m->st));
+  }
+  static_assert(kMaxMGLevels * sizeof(unsigned long long) <= kMaxN * sizeof(double), "h_dbl staging");
+  CK(cudaMemcpyAsync(m->h_dbl, h.rho_bits, sizeof(unsigned long long) * h.nlev, cudaMemcpyDeviceToHost, m->st));
+  CK(cudaStreamSynchronize(m->st));
+  for (int l = 0; l < h.nlev; ++l) {
+    const double rho = m->h_dbl[l];  // the bit pattern of the bound, a positive double
+    if (!(rho > 0.0) || !std::isfinite(rho)) return fail(m, PARO_ERR_NOT_SPD, "multigrid: non-positive diagonal");
+    h.lev[l].rho = rho;
+    h.lev[l].omega = (float)std::fmin(1.0, 4.0 / (3.0 * rho));
+  }
+  h.built = true;
+  return PARO_OK;
+}
+
+// One MG-preconditioned float32 CG solve A x = b from x = 0 on the plan P (x, b,
+// r, p, s, w = q; u = r2; V-cycle scratch s2, q2), per-orbital masks as in the
+// Jacobi CG; the host tests the active count every check_every iterations.
+int run_mg(paro_mesh m, CGPlan<float>* P, int N, double tol, int maxit, int check_every, int nu, int nu_c,
+           long long* it_sum, int* it_max) {
+  P->args.N = N;
+  TRY(ensure_mg(m, P->args.Np));
+  m->h_ctl[0] = tol;
+  int* ctl_int = reinterpret_cast<int*>(m->h_ctl + 1);
+  ctl_int[0] = maxit;
+  CK(cudaMemcpyAsync(&m->cgst->tol, m->h_ctl, sizeof(double), cudaMemcpyHostToDevice, m->st));
+  CK(cudaMemcpyAsync(&m->cgst->maxit, ctl_int, sizeof(int), cudaMemcpyHostToDevice, m->st));
+  LAUNCH(1, cg_launch_init<float>(P, m->st, true));
+  int nact = 0;
+  TRY(read_n_active(m, &nact));
+  int done = 0;
+  while (nact > 0 && done < maxit) {
+    int k = check_every;
+    if (k > maxit - done) k = maxit - done;
+    for (int i = 0; i < k; ++i) {
+      long long nl = 0;
+      CK(mg_vcycle(m->mg, P->args.Np, P->args.r, P->args.r2, P->args.s2, P->args.q2, m->cgst->active, nu, nu_c,
+                   m->st, &nl));
+      m->launches += nl;
+      LAUNCH(1, mg_launch_wdots(P, m->coef32, m->st));
+      LAUNCH(1, mg_launch_update(P, m->st));
+    }
+    done += k;
+    TRY(read_n_active(m, &nact));
+  }
+  TRY(read_iters(m, N, it_sum, it_max));
+  return PARO_OK;
+}
+
+int check_precond(paro_mesh m, const paro_params& p) {
+  if (p.precond != PARO_PRECOND_JACOBI && p.precond != PARO_PRECOND_MG)
+    return fail(m, PARO_ERR_ARG, "unknown preconditioner");
+  if (p.precond == PARO_PRECOND_MG) {
+    if (m->precision != PARO_MIXED)
+      return fail(m, PARO_ERR_ARG, "the multigrid preconditioner runs in the float32 solves of a PARO_MIXED handle");
+    if (p.mg_nu < 1 || p.mg_nu > 8 || p.mg_coarse_sweeps < 1 || p.mg_coarse_sweeps > 64)
+      return fail(m, PARO_ERR_ARG, "mg_nu must be in [1, 8] and mg_coarse_sweeps in [1, 64]");
+  }
+  return PARO_OK;
+}
+
 // Step 3 on the packed buffers: u (current orbitals) -> x (source solutions).
 // Mixed-precision solve of A x = b for N columns: x (float64, padded) holds the
 // initial guess, b is given as a float-float pair in fah/fal.  Each sweep forms
 // r = b - A x in float-float arithmetic (float64-accurate), stops the columns with
 // |r| <= solve_tol |b|, solves A d = r to inner_tol with the float32 CG and adds d.
 int refine_solve(paro_mesh m, int N, const paro_params& p, paro_stats* st) {
+  TRY(check_precond(m, p));
   const int Np = m->Np_alloc;
   Grid& g = m->g;
   CGState rs = cg_state(m, true);
@@ -586,7 +696,10 @@ int refine_solve(paro_mesh m, int N, const paro_params& p, paro_stats* st) {
     }
     long long i1 = 0;
     int imx = 0;
-    TRY(run_cg<float>(m, m->plan32, N, false, p.inner_tol, p.pcg_maxit, p.check_every, &i1, &imx));
+    if (p.precond == PARO_PRECOND_MG)
+      TRY(run_mg(m, m->plan32, N, p.inner_tol, p.pcg_maxit, p.check_every, p.mg_nu, p.mg_coarse_sweeps, &i1, &imx));
+    else
+      TRY(run_cg<float>(m, m->plan32, N, false, p.inner_tol, p.pcg_maxit, p.check_every, &i1, &imx));
     // an inner limit is not fatal: refinement carries on from the partial correction
     int* stw = &m->cgst->status;
     CK(cudaMemcpyAsync(m->h_int, stw, sizeof(int), cudaMemcpyDeviceToHost, m->st));
@@ -630,6 +743,7 @@ int solve_packed(paro_mesh m, int N, const double* lam, const paro_params& p, pa
   CK(cudaMemcpyAsync(m->x, m->u, sizeof(double) * g.G * Np, cudaMemcpyDeviceToDevice, m->st));
   long long its = 0;
   int itmax = 0;
+  TRY(check_precond(m, p));
   if (m->precision == PARO_FP64) {
     CK(cudaMemsetAsync(m->cgst->skip, 0, sizeof(int) * kMaxN, m->st));
     TRY(run_cg<double>(m, m->plan64, N, true, p.solve_tol, p.pcg_maxit, p.check_every, &its, &itmax));
@@ -856,6 +970,7 @@ int ensure_poisson(paro_mesh m) {
 // column 0).  Mixed handles: float32 CG in float-float refinement to
 // pp.solve_tol; float64 handles: float64 CG.
 int hartree_solve(paro_mesh m, const double* rho, const paro_params& pp) {
+  TRY(check_precond(m, pp));
   TRY(ensure_ks(m));
   TRY(ensure_poisson(m));
   paro_mesh c = m->pois;
@@ -919,6 +1034,9 @@ void paro_default_params(paro_params* p) {
   p->profile = 0;
   p->n_clusters = 0;
   p->cluster_size = nullptr;
+  p->precond = PARO_PRECOND_JACOBI;
+  p->mg_nu = 1;
+  p->mg_coarse_sweeps = 4;
 }
 
 int paro_mesh_create(paro_mesh* out, int nx, int ny, int nz, const double lo[3], const double hi[3], int precision,
@@ -1034,6 +1152,7 @@ int paro_set_potential(paro_mesh m, const double* Vq, double sigma) {
     LAUNCH(1, launch_build_wff(m->g, m->coef64, m->mw, sigma, m->wAh, m->wAl, m->wHh, m->wHl, m->st));
   m->sigma = sigma;
   m->have_pot = true;
+  m->mg.built = false;
   return PARO_OK;
 }
 
@@ -1181,6 +1300,27 @@ int paro_apply(paro_mesh m, int N, int op, int dtype, const void* X, void* Y) {
     LAUNCH(1, launch_apply_f32(m->g, Np, m->coef32, m->b32, m->q32, m->st));
     LAUNCH(1, launch_unpack_f32(m->g, N, Np, m->q32, static_cast<float*>(Y), m->st));
   }
+  CK(cudaStreamSynchronize(m->st));
+  return PARO_OK;
+}
+
+int paro_mg_vcycle(paro_mesh m, int N, const float* R, float* Z, const paro_params* p) {
+  TRY(check_common(m, N));
+  if (!R || !Z || (const void*)R == (const void*)Z) return fail(m, PARO_ERR_ARG, "R, Z must be non-null and distinct");
+  paro_params pp;
+  if (p) pp = *p;
+  else paro_default_params(&pp);
+  pp.precond = PARO_PRECOND_MG;
+  TRY(check_precond(m, pp));
+  const int Np = (N + 3) / 4 * 4;
+  TRY(ensure_workspace(m, Np));
+  TRY(ensure_mg(m, Np));
+  CGArgs<float>& a = m->plan32->args;
+  LAUNCH(1, launch_pack_f32(m->g, N, Np, R, a.r, m->st));
+  long long nl = 0;
+  CK(mg_vcycle(m->mg, Np, a.r, a.r2, a.s2, a.q2, nullptr, pp.mg_nu, pp.mg_coarse_sweeps, m->st, &nl));
+  m->launches += nl;
+  LAUNCH(1, launch_unpack_f32(m->g, N, Np, a.r2, Z, m->st));
   CK(cudaStreamSynchronize(m->st));
   return PARO_OK;
 }
