@@ -279,6 +279,8 @@ def time_to_converge(B, torch, p, stream, max_outer=400):
     for name, prec, params in (
         ("mixed", B.PARO_MIXED, B.paro_default_params(fixed_outer=1, solve_tol=1e-10, inner_tol=1e-4)),
         ("fp64", B.PARO_FP64, B.paro_default_params(fixed_outer=1, solve_tol=1e-10)),
+        ("mixed_mg", B.PARO_MIXED, B.paro_default_params(fixed_outer=1, solve_tol=1e-10, inner_tol=1e-4,
+                                                         precond=B.PARO_PRECOND_MG)),
     ):
         m = B.Mesh(p.n, p.lo, p.hi, prec, stream=stream)
         with torch.cuda.stream(stream):
@@ -306,6 +308,8 @@ def time_to_converge(B, torch, p, stream, max_outer=400):
         m.close()
     if out["mixed"]["reached"] and out["fp64"]["reached"]:
         out["speedup_mixed_vs_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    if out["mixed_mg"]["reached"] and out["fp64"]["reached"]:
+        out["speedup_mixed_mg_vs_fp64"] = out["fp64"]["seconds"] / out["mixed_mg"]["seconds"]
     return out
 
 
@@ -373,7 +377,8 @@ def run_batch(args):
 
     systems = W.batch_systems(count=args.systems)
     units = sum(p.n_interior * p.N for p in systems) * args.steps
-    params = B.paro_default_params(fixed_outer=args.steps, solve_tol=1e-10)
+    params = B.paro_default_params(fixed_outer=args.steps, solve_tol=1e-10,
+                                   precond=B.PARO_PRECOND_MG if args.precond == "mg" else B.PARO_PRECOND_JACOBI)
     # sigma per system: 1 - (lowest initial Ritz value), rounded up to 0.5 Ha, but at
     # least 0.5 - min V: the Ritz value of poor guesses can sit far above lambda_1,
     # while min V (Gauss points) bounds the spectrum from below (K/2 >= 0), so
@@ -425,7 +430,7 @@ def run_batch(args):
     t_fp64 = loop(B.PARO_FP64)
     sizes = collections_count(p.n[0] for p in systems)
     line = {"metric": "batched ParO throughput, independent systems (mixed batch vs float64 per-system loop)",
-            "unit": UNIT, "systems": len(systems), "outer_iters_per_system": args.steps,
+            "unit": UNIT, "systems": len(systems), "precond": args.precond, "outer_iters_per_system": args.steps,
             "mesh_counts": sizes, "N_range": [min(p.N for p in systems), max(p.N for p in systems)],
             "mixed_batch": {"value": units / t_mixed, "seconds": t_mixed, "workers": args.workers,
                             "ok": sum(1 for rc in rcs if rc == 0),
@@ -460,11 +465,12 @@ def run_large(args):
     U = torch.from_numpy(p.U0).cuda()
     p.U0 = None  # release the host copy
     t0 = time.perf_counter()
-    rc, lam, st0 = m.iterate(U, None, B.paro_default_params(fixed_outer=1, solve_tol=1e-10))
+    pc = B.PARO_PRECOND_MG if args.precond == "mg" else B.PARO_PRECOND_JACOBI
+    rc, lam, st0 = m.iterate(U, None, B.paro_default_params(fixed_outer=1, solve_tol=1e-10, precond=pc))
     torch.cuda.synchronize()
     t_first = time.perf_counter() - t0
     free1, _ = torch.cuda.mem_get_info()
-    params = B.paro_default_params(fixed_outer=args.steps, solve_tol=1e-10)
+    params = B.paro_default_params(fixed_outer=args.steps, solve_tol=1e-10, precond=pc)
     t0 = time.perf_counter()
     rc, lam, st = m.iterate(U, lam, params)
     torch.cuda.synchronize()
@@ -473,7 +479,7 @@ def run_large(args):
     line = {"metric": "ParO outer iterations on the large workload (mixed precision)", "unit": UNIT,
             "value": units / dt, "seconds_per_outer": dt / args.steps, "outer_iters": args.steps,
             "workload": f"{len(p.nuclei)} softened-Coulomb nuclei, [-20,20]^3, {p.n[0]}^3 cells "
-                        f"({nI} dofs), N={N}, sigma={sigma}",
+                        f"({nI} dofs), N={N}, sigma={sigma}", "precond": args.precond,
             "device_memory_gb": round((free0 - free1) / 1e9, 1), "device_total_gb": round(total / 1e9, 1),
             "first_call_s": round(t_first, 2), "generate_s": round(t_gen, 1),
             "stats": {"cg_iters_f32": st.cg_iters_f32, "cg_iters_max": st.cg_iters_max,
@@ -518,20 +524,45 @@ def run_ks(args):
     _, lam0, _ = m.iterate(U, None, B.paro_default_params(tol=1e-2, max_outer=100, solve_tol=1e-8), allow=(-4,))
     sigma = math.ceil((1.0 - lam0[0]) / 0.5) * 0.5
     m.set_potential(vq, sigma)
-    params = B.paro_default_params(tol=1e-6, max_outer=args.ks_max_outer, solve_tol=1e-10, n_check=p.n_occ)
+    pc = B.PARO_PRECOND_MG if args.precond == "mg" else B.PARO_PRECOND_JACOBI
+    params = B.paro_default_params(tol=1e-6, max_outer=args.ks_max_outer, solve_tol=1e-10, n_check=p.n_occ,
+                                   precond=pc)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     rc, lam, st = m.scf_iterate(U, occ, vq, args.ks_mix, params, allow=(-4,))
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     energy = m.ks_energy(U, occ, lam, B.paro_default_params(solve_tol=1e-10))
+    # the pieces of one SCF iteration outside the source problems and Rayleigh-Ritz,
+    # each timed alone (device time, 3 calls): the potential set-up (operator
+    # weights), the density, and the Kohn-Sham potential (Hartree solve + Slater)
+    rho = torch.empty_like(vq)
+    veff = torch.empty_like(vq)
+    m.density(U, occ, rho)
+    m.ks_potential(rho, vq, veff, None, params)
+
+    def dev_ms(fn, reps=3):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        b.synchronize()
+        return a.elapsed_time(b) / reps
+
+    pieces = {"set_potential_ms": dev_ms(lambda: m.set_potential(veff, sigma)),
+              "density_ms": dev_ms(lambda: m.density(U, occ, rho)),
+              "ks_potential_warm_ms": dev_ms(lambda: m.ks_potential(rho, vq, veff, None, params))}
     line = {"metric": "Kohn-Sham SCF ParO to max |delta lambda| < 1e-6 Ha on the occupied orbitals (mixed)",
             "workload": f"{len(p.nuclei)} softened nuclei, [-12,12]^3, {p.n[0]}^3 cells ({p.n_interior} dofs), "
                         f"{n_el} electrons, N={N} ({p.n_occ} occupied + buffer), sigma={sigma}, mixing {args.ks_mix}",
             "converged": rc == 0, "outer_iters": st.outer_iters, "seconds": dt,
             "ms_per_outer": 1e3 * dt / max(st.outer_iters, 1), "max_dlambda": st.max_dlambda,
             "poisson_cg_iters": st.poisson_cg_iters, "cg_iters_f32": st.cg_iters_f32,
-            "rr_tc_steps": st.rr_tc_steps, "energy_ha": energy,
+            "rr_tc_steps": st.rr_tc_steps, "energy_ha": energy, "precond": args.precond,
+            "ms_orbital_solves": st.ms_solve, "ms_rayleigh_ritz": st.ms_rr,
+            "ms_hartree_density_potential": 1e3 * dt - st.ms_solve - st.ms_rr, "pieces": pieces,
             "lambda_occupied": [float(v) for v in lam[:p.n_occ]], "data": "synthetic (seeded nuclei)"}
     print(json.dumps(line), flush=True)
     m.close()
@@ -558,6 +589,8 @@ def main():
     ap.add_argument("--ks-nc", type=int, default=128, help="ks workload: cells per axis")
     ap.add_argument("--ks-max-outer", type=int, default=1500, help="ks workload: SCF iteration limit")
     ap.add_argument("--ks-mix", type=float, default=0.3, help="ks workload: linear density mixing")
+    ap.add_argument("--precond", default="jacobi", choices=["jacobi", "mg"],
+                    help="ks, large, batch workloads: preconditioner of the float32 correction solves")
     ap.add_argument("--large-nc", type=int, default=192, help="large workload: cells per axis")
     ap.add_argument("--systems", type=int, default=64, help="batch workload: number of systems")
     ap.add_argument("--workers", type=int, default=8, help="batch workload: host worker threads")

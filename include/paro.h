@@ -72,6 +72,8 @@ typedef enum {
 /* Preconditioner of the float32 correction solves (paro_params.precond). */
 #define PARO_PRECOND_JACOBI 0 /* Jacobi (D^-1), fused into the single-reduction CG kernel */
 #define PARO_PRECOND_MG 1     /* one geometric-multigrid V-cycle (see paro_mg_vcycle); PARO_MIXED handles */
+#define PARO_PRECOND_AUTO -1  /* hartree_precond only: multigrid on PARO_MIXED handles whose mesh coarsens at
+                                 least twice, else Jacobi */
 
 typedef struct paro_mesh_s* paro_mesh;
 
@@ -97,11 +99,13 @@ typedef struct {
                          the Ritz values are sorted within each group.  0: one problem of size N (0) */
   const int* cluster_size; /* host[n_clusters], read during the call (NULL) */
   int precond;        /* PARO_PRECOND_JACOBI or PARO_PRECOND_MG: the preconditioner of the float32
-                         correction solves of a PARO_MIXED handle, the Hartree solves included
+                         correction solves of the N source problems on a PARO_MIXED handle
                          (Section 3: each source problem solved by a parallel multigrid method).
                          PARO_PRECOND_MG on a PARO_FP64 handle: PARO_ERR_ARG (PARO_PRECOND_JACOBI) */
   int mg_nu;          /* multigrid: damped-Jacobi sweeps before and after the coarse correction, 1..8 (1) */
   int mg_coarse_sweeps; /* multigrid: sweeps on the coarsest level, 1..64 (4) */
+  int hartree_precond; /* preconditioner of the Hartree (Poisson) solves of the Kohn-Sham calls:
+                          PARO_PRECOND_AUTO, PARO_PRECOND_JACOBI or PARO_PRECOND_MG (PARO_PRECOND_AUTO) */
 } paro_params;
 
 /* Statistics of a call.  Counters and times (cg_iters*, ms_*, stencil_applies,

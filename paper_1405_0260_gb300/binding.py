@@ -30,7 +30,7 @@ STATUS = {
 PARO_FP64, PARO_MIXED = 0, 1
 PARO_OP_A, PARO_OP_H, PARO_OP_M = 0, 1, 2
 PARO_F64, PARO_F32, PARO_FF = 0, 1, 2
-PARO_PRECOND_JACOBI, PARO_PRECOND_MG = 0, 1
+PARO_PRECOND_AUTO, PARO_PRECOND_JACOBI, PARO_PRECOND_MG = -1, 0, 1
 
 
 class paro_params(C.Structure):
@@ -39,7 +39,7 @@ class paro_params(C.Structure):
         ("solve_tol", C.c_double), ("pcg_maxit", C.c_int), ("inner_tol", C.c_double),
         ("max_refine", C.c_int), ("check_every", C.c_int), ("fixed_outer", C.c_int),
         ("profile", C.c_int), ("n_clusters", C.c_int), ("cluster_size", C.POINTER(C.c_int)),
-        ("precond", C.c_int), ("mg_nu", C.c_int), ("mg_coarse_sweeps", C.c_int),
+        ("precond", C.c_int), ("mg_nu", C.c_int), ("mg_coarse_sweeps", C.c_int), ("hartree_precond", C.c_int),
     ]
 
     def set_clusters(self, sizes):

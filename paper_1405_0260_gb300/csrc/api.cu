@@ -969,11 +969,22 @@ int ensure_poisson(paro_mesh m) {
 // from one iteration to the next); the solution is left in m->pois->x (padded,
 // column 0).  Mixed handles: float32 CG in float-float refinement to
 // pp.solve_tol; float64 handles: float64 CG.
-int hartree_solve(paro_mesh m, const double* rho, const paro_params& pp) {
-  TRY(check_precond(m, pp));
+int hartree_solve(paro_mesh m, const double* rho, const paro_params& p) {
+  if (p.hartree_precond < PARO_PRECOND_AUTO || p.hartree_precond > PARO_PRECOND_MG)
+    return fail(m, PARO_ERR_ARG, "unknown Hartree preconditioner");
   TRY(ensure_ks(m));
   TRY(ensure_poisson(m));
   paro_mesh c = m->pois;
+  // the Poisson problem is where multigrid pays most (Jacobi-PCG iterations grow
+  // like 1/h there, without a mass term to bound them)
+  paro_params pp = p;
+  pp.precond = p.hartree_precond;
+  if (pp.precond == PARO_PRECOND_AUTO) {
+    Grid gs[kMaxMGLevels];
+    pp.precond = (c->precision == PARO_MIXED && mg_plan_levels(c->g, gs, kMaxMGLevels) >= 2) ? PARO_PRECOND_MG
+                                                                                                : PARO_PRECOND_JACOBI;
+  }
+  TRY(check_precond(m, pp));
   LAUNCH(2, launch_moments(m->g, m->lo, rho, m->ks_part, m->ks_mom, m->st));
   CK(cudaMemsetAsync(c->b, 0, sizeof(double) * c->g.G * 4, m->st));
   LAUNCH(1, launch_hartree_rhs(c->g, m->lo, rho, c->coef64, m->ks_mom, c->b, m->st));
@@ -1037,6 +1048,7 @@ void paro_default_params(paro_params* p) {
   p->precond = PARO_PRECOND_JACOBI;
   p->mg_nu = 1;
   p->mg_coarse_sweeps = 4;
+  p->hartree_precond = PARO_PRECOND_AUTO;
 }
 
 int paro_mesh_create(paro_mesh* out, int nx, int ny, int nz, const double lo[3], const double hi[3], int precision,

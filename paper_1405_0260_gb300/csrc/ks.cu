@@ -7,6 +7,7 @@
 #include <cmath>
 
 #include "common.cuh"
+#include "q1.cuh"
 
 namespace paro {
 
@@ -14,42 +15,58 @@ namespace {
 
 inline unsigned nblk(long long work, int threads) { return (unsigned)((work + threads - 1) / threads); }
 
-// Trilinear basis at the Gauss point: local node a = ax + 2 ay + 4 az, point
-// q = qx + 2 qy + 4 qz, 1-D values l0 = (1 + 1/sqrt3)/2 at the near node, l1 = (1 - 1/sqrt3)/2.
-__device__ __forceinline__ double basis_at(int a, int q) {
-  const double g0 = 0.5 + 0.5 / 1.7320508075688772935;  // node value at the nearer Gauss point
-  const double g1 = 0.5 - 0.5 / 1.7320508075688772935;
-  const double bx = ((a & 1) == (q & 1)) ? g0 : g1;
-  const double by = (((a >> 1) & 1) == ((q >> 1) & 1)) ? g0 : g1;
-  const double bz = (((a >> 2) & 1) == ((q >> 2) & 1)) ? g0 : g1;
-  return bx * by * bz;
+// sum_q r[q] phi_a(x_q) for one corner a of the cell, axis by axis
+__device__ __forceinline__ double project1(const double* r, int a) {
+  const int ax = a & 1, ay = (a >> 1) & 1, az = (a >> 2) & 1;
+  double s = 0.0;
+#pragma unroll
+  for (int qz = 0; qz < 2; ++qz) {
+    double t = 0.0;
+#pragma unroll
+    for (int qy = 0; qy < 2; ++qy) {
+      const double* rr = r + 4 * qz + 2 * qy;
+      t += gq(ay, qy) * (gq(ax, 0) * rr[0] + gq(ax, 1) * rr[1]);
+    }
+    s += gq(az, qz) * t;
+  }
+  return s;
 }
 
-// rho_q = sum_i f_i (sum_a phi_a(x_q) u_i(a))^2, one thread per (cell, Gauss point).
-// U in the padded layout [node][Np] (boundary rows zero).
-__global__ void k_density(Grid g, int N, int Np, const double* __restrict__ U, const double* __restrict__ occ,
-                          double* __restrict__ rho) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+// rho_q = sum_i f_i (sum_a phi_a(x_q) u_i(a))^2, one thread per cell (its 8 Gauss
+// points), orbitals two at a time (16-byte loads of the 8 corner rows).
+// U in the padded layout [node][Np] (boundary rows zero, Np even).
+__global__ void __launch_bounds__(128) k_density(Grid g, int N, int Np, const double* __restrict__ U,
+                                                 const double* __restrict__ occ, double* __restrict__ rho) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long ncell = (long long)g.nx * g.ny * g.nz;
-  if (t >= ncell * 8) return;
-  const long long c = t / 8;
-  const int q = (int)(t % 8);
+  if (c >= ncell) return;
   const int cx = (int)(c % g.nx), cy = (int)((c / g.nx) % g.ny), cz = (int)(c / ((long long)g.nx * g.ny));
-  double phi[8];
   long long node[8];
 #pragma unroll
-  for (int a = 0; a < 8; ++a) {
-    phi[a] = basis_at(a, q);
+  for (int a = 0; a < 8; ++a)
     node[a] = ((long long)(cz + ((a >> 2) & 1)) * g.Py + (cy + ((a >> 1) & 1))) * g.Px + (cx + (a & 1));
-  }
-  double s = 0.0;
-  for (int i = 0; i < N; ++i) {
-    double v = 0.0;
+  double s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int i = 0; i < N; i += 2) {
+    double c0[8], c1[8], v[8];
 #pragma unroll
-    for (int a = 0; a < 8; ++a) v += phi[a] * U[node[a] * Np + i];
-    s += occ[i] * v * v;
+    for (int a = 0; a < 8; ++a) {
+      const double2 u = __ldg(reinterpret_cast<const double2*>(U + node[a] * Np + i));
+      c0[a] = u.x;
+      c1[a] = u.y;
+    }
+    const double f0 = occ[i];
+    interp8(c0, v);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s[q] += f0 * v[q] * v[q];
+    if (i + 1 < N) {
+      const double f1 = occ[i + 1];
+      interp8(c1, v);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) s[q] += f1 * v[q] * v[q];
+    }
   }
-  rho[t] = s;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) rho[c * 8 + q] = s[q];
 }
 
 // Per-block partial sums of (w rho, w rho x, w rho y, w rho z) over the Gauss points.
@@ -117,7 +134,7 @@ __global__ void k_hartree_rhs(Grid g, double lox, double loy, double loz, const 
       for (int ex = 0; ex < 2; ++ex) {
         const long long c = ((long long)(iz - 1 + ez) * g.ny + (iy - 1 + ey)) * g.nx + (ix - 1 + ex);
         const int a = (1 - ex) + 2 * (1 - ey) + 4 * (1 - ez);
-        for (int q = 0; q < 8; ++q) b += w * rho[c * 8 + q] * basis_at(a, q);
+        b += w * project1(rho + c * 8, a);
       }
   double bnd = 0.0;
   for (int o = 0; o < 27; ++o) {
@@ -132,31 +149,33 @@ __global__ void k_hartree_rhs(Grid g, double lox, double loy, double loz, const 
 
 // V_q = V_ext + V_H + V_x at the Gauss points: V_H interpolated from the nodal
 // solution (interior: w, padded layout with Np = 4; boundary: the monopole).
-__global__ void k_ks_potential(Grid g, double lox, double loy, double loz, const double* __restrict__ w,
-                               const double* __restrict__ mom, const double* __restrict__ rho,
-                               const double* __restrict__ vext, double* __restrict__ vout,
-                               double* __restrict__ vh_out) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(128) k_ks_potential(Grid g, double lox, double loy, double loz,
+                                                      const double* __restrict__ w, const double* __restrict__ mom,
+                                                      const double* __restrict__ rho,
+                                                      const double* __restrict__ vext, double* __restrict__ vout,
+                                                      double* __restrict__ vh_out) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long ncell = (long long)g.nx * g.ny * g.nz;
-  if (t >= ncell * 8) return;
-  const long long c = t / 8;
-  const int q = (int)(t % 8);
+  if (c >= ncell) return;
   const int cx = (int)(c % g.nx), cy = (int)((c / g.nx) % g.ny), cz = (int)(c / ((long long)g.nx * g.ny));
-  double vh = 0.0;
+  double cv[8], vh[8];
 #pragma unroll
   for (int a = 0; a < 8; ++a) {
     const int jx = cx + (a & 1), jy = cy + ((a >> 1) & 1), jz = cz + ((a >> 2) & 1);
-    double v;
     if (jx == 0 || jx == g.nx || jy == 0 || jy == g.ny || jz == 0 || jz == g.nz)
-      v = monopole_at(mom, lox + jx * g.hx, loy + jy * g.hy, loz + jz * g.hz);
+      cv[a] = monopole_at(mom, lox + jx * g.hx, loy + jy * g.hy, loz + jz * g.hz);
     else
-      v = w[(((long long)jz * g.Py + jy) * g.Px + jx) * 4];
-    vh += basis_at(a, q) * v;
+      cv[a] = w[(((long long)jz * g.Py + jy) * g.Px + jx) * 4];
   }
-  const double r = rho[t] > 0.0 ? rho[t] : 0.0;
-  const double vx = -cbrt(3.0 * r / M_PI);  // Slater exchange
-  if (vh_out) vh_out[t] = vh;
-  if (vout) vout[t] = vext[t] + vh + vx;
+  interp8(cv, vh);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const long long t = c * 8 + q;
+    const double r = rho[t] > 0.0 ? rho[t] : 0.0;
+    const double vx = -cbrt(3.0 * r / M_PI);  // Slater exchange
+    if (vh_out) vh_out[t] = vh[q];
+    if (vout) vout[t] = vext[t] + vh[q] + vx;
+  }
 }
 
 // Per-block partial sums over the Gauss points (weight w = hx hy hz / 8) of
@@ -204,8 +223,7 @@ __global__ void k_mix(long long n, double beta, double* __restrict__ rho_in, con
 
 cudaError_t launch_density(const Grid& g, int N, int Np, const double* U, const double* occ, double* rho,
                            cudaStream_t st) {
-  const long long n = (long long)g.nx * g.ny * g.nz * 8;
-  k_density<<<nblk(n, 256), 256, 0, st>>>(g, N, Np, U, occ, rho);
+  k_density<<<nblk((long long)g.nx * g.ny * g.nz, 128), 128, 0, st>>>(g, N, Np, U, occ, rho);
   return cudaGetLastError();
 }
 
@@ -228,8 +246,8 @@ cudaError_t launch_hartree_rhs(const Grid& g, const double lo[3], const double* 
 cudaError_t launch_ks_potential(const Grid& g, const double lo[3], const double* w, const double* mom,
                                 const double* rho, const double* vext, double* vout, double* vh_out,
                                 cudaStream_t st) {
-  const long long n = (long long)g.nx * g.ny * g.nz * 8;
-  k_ks_potential<<<nblk(n, 256), 256, 0, st>>>(g, lo[0], lo[1], lo[2], w, mom, rho, vext, vout, vh_out);
+  k_ks_potential<<<nblk((long long)g.nx * g.ny * g.nz, 128), 128, 0, st>>>(g, lo[0], lo[1], lo[2], w, mom, rho,
+                                                                           vext, vout, vh_out);
   return cudaGetLastError();
 }
 

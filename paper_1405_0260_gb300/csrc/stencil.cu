@@ -12,6 +12,7 @@
 #include <mutex>
 #include <set>
 #include "common.cuh"
+#include "q1.cuh"
 
 namespace paro {
 
@@ -20,15 +21,15 @@ namespace {
 __host__ __device__ inline double k1(int d, double h) { return d == 0 ? 2.0 / h : -1.0 / h; }
 __host__ __device__ inline double m1(int d, double h) { return d == 0 ? 4.0 * h / 6.0 : h / 6.0; }
 
-// Gauss abscissae on [0, 1] and the two linear shape functions.
-__device__ inline double gauss_xi(int q) {
-  const double s = 0.57735026918962576451;  // 1/sqrt(3)
-  return q == 0 ? 0.5 * (1.0 - s) : 0.5 * (1.0 + s);
-}
-__device__ inline double shape1(int a, double xi) { return a == 0 ? 1.0 - xi : xi; }
-
 __global__ void k_build_coef(Grid g, const double* __restrict__ Vq, double sigma, double* __restrict__ coef64,
                              float* __restrict__ coef32, double* __restrict__ dinv64, float* __restrict__ dinv32) {
+  // phi_a(x_q) on the reference cell, [a][q] with a = ax + 2 ay + 4 az, q likewise
+  __shared__ double sa[64];
+  for (int t = threadIdx.x; t < 64; t += blockDim.x) {
+    const int a = t >> 3, q = t & 7;
+    sa[t] = gq(a & 1, q & 1) * gq((a >> 1) & 1, (q >> 1) & 1) * gq((a >> 2) & 1, (q >> 2) & 1);
+  }
+  __syncthreads();
   int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= g.nI) return;
   int ix = g.nx - 1, iy = g.ny - 1;
@@ -53,23 +54,20 @@ __global__ void k_build_coef(Grid g, const double* __restrict__ Vq, double sigma
       for (int cx = 0; cx < 2; ++cx) {
         int ex = i - 1 + cx, ey = j - 1 + cy, ez = k - 1 + cz;
         long long cell = ((long long)ez * g.ny + ey) * g.nx + ex;
-        const double* v = Vq + cell * 8;
-        int ax = 1 - cx, ay = 1 - cy, az = 1 - cz;
-        for (int bz = 0; bz < 2; ++bz)
-          for (int by = 0; by < 2; ++by)
-            for (int bx = 0; bx < 2; ++bx) {
-              double acc = 0.0;
-              for (int qz = 0; qz < 2; ++qz)
-                for (int qy = 0; qy < 2; ++qy)
-                  for (int qx = 0; qx < 2; ++qx) {
-                    double px = shape1(ax, gauss_xi(qx)) * shape1(bx, gauss_xi(qx));
-                    double py = shape1(ay, gauss_xi(qy)) * shape1(by, gauss_xi(qy));
-                    double pz = shape1(az, gauss_xi(qz)) * shape1(bz, gauss_xi(qz));
-                    acc += (v[qz * 4 + qy * 2 + qx] + sigma) * px * py * pz;
-                  }
-              int o = (bz - az + 1) * 9 + (by - ay + 1) * 3 + (bx - ax + 1);
-              w[o] += wq * acc;
-            }
+        // row a of the cell's potential matrix: sum_q (V_q + sigma) phi_a(x_q) phi_b(x_q)
+        // for the 8 corners b, i.e. the values (V + sigma) phi_a at the Gauss points
+        // projected on the corners (the transpose of interp8, which has the same form)
+        const int ax = 1 - cx, ay = 1 - cy, az = 1 - cz;
+        const double* s_a = sa + (ax + 2 * ay + 4 * az) * 8;
+        double ua[8], row[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) ua[q] = (Vq[cell * 8 + q] + sigma) * s_a[q];
+        interp8(ua, row);
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+          const int bx = b & 1, by = (b >> 1) & 1, bz = (b >> 2) & 1;
+          w[(bz - az + 1) * 9 + (by - ay + 1) * 3 + (bx - ax + 1)] += wq * row[b];
+        }
       }
   for (int o = 0; o < 27; ++o) {
     coef64[(long long)o * g.G + gp] = w[o];

@@ -145,14 +145,16 @@ def test_mg_hartree_matches_oracle(B):
     occ = KS.occupations(4, 3)
     rho = KS.density_gauss(mesh, O.rayleigh_ritz(O.assemble(mesh, Vext, 3.0), p.U0).U, occ)
     ref = KS.hartree(mesh, rho).VH_q
-    m = B.Mesh(mesh.n, mesh.lo, mesh.hi, B.PARO_MIXED)
     vq = dev(Vext)
-    m.set_potential(vq, 3.0)
-    v = torch.empty_like(vq)
-    vh = torch.empty_like(vq)
-    m.ks_potential(dev(rho), vq, v, vh, B.paro_default_params(solve_tol=1e-12, precond=B.PARO_PRECOND_MG))
-    assert np.max(np.abs(host(vh) - ref)) < 1e-9 * np.max(np.abs(ref))
-    m.close()
+    for hp in (B.PARO_PRECOND_MG, B.PARO_PRECOND_JACOBI, B.PARO_PRECOND_AUTO):
+        # a fresh handle each time: the Hartree solve starts from the previous solution
+        m = B.Mesh(mesh.n, mesh.lo, mesh.hi, B.PARO_MIXED)
+        m.set_potential(vq, 3.0)
+        v = torch.empty_like(vq)
+        vh = torch.empty_like(vq)
+        m.ks_potential(dev(rho), vq, v, vh, B.paro_default_params(solve_tol=1e-12, hartree_precond=hp))
+        assert np.max(np.abs(host(vh) - ref)) < 1e-9 * np.max(np.abs(ref)), hp
+        m.close()
 
 
 def test_mg_needs_a_mixed_handle_and_valid_sweeps(B):
@@ -164,6 +166,9 @@ def test_mg_needs_a_mixed_handle_and_valid_sweeps(B):
     X = torch.empty_like(U)
     with pytest.raises(B.ParoError):
         m.orbital_solve(np.ones(4), U, X, B.paro_default_params(precond=B.PARO_PRECOND_MG))
+    rho = torch.full_like(vq, 0.01)
+    with pytest.raises(B.ParoError):
+        m.ks_potential(rho, vq, torch.empty_like(vq), None, B.paro_default_params(hartree_precond=B.PARO_PRECOND_MG))
     m.close()
     m = B.Mesh(p.n, p.lo, p.hi, B.PARO_MIXED)
     m.set_potential(vq, p.sigma)

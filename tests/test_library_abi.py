@@ -49,6 +49,7 @@ def test_default_params_and_null_handle_errors(lib):
     p = B.paro_default_params()
     assert p.tol == 1e-10 and p.solve_tol == 1e-12 and p.max_outer == 500 and p.profile == 0
     assert p.precond == B.PARO_PRECOND_JACOBI and p.mg_nu == 1 and p.mg_coarse_sweeps == 4
+    assert p.hartree_precond == B.PARO_PRECOND_AUTO
     # argument errors are caught before any CUDA call
     h = ctypes.c_void_p()
     lo = (ctypes.c_double * 3)(-1, -1, -1)
@@ -73,7 +74,7 @@ def test_ctypes_structs_match_c_layout(lib):
 int main(void) {
   printf("%zu %zu\n", sizeof(paro_params), sizeof(paro_stats));
   printf("%zu %zu %zu %zu\n", offsetof(paro_params, profile), offsetof(paro_stats, prof_ms),
-         offsetof(paro_stats, prof_dof_orb), offsetof(paro_params, mg_coarse_sweeps));
+         offsetof(paro_stats, prof_dof_orb), offsetof(paro_params, hartree_precond));
   return 0;
 }
 '''
@@ -89,4 +90,4 @@ int main(void) {
     assert sizes[2] == B.paro_params.profile.offset
     assert sizes[3] == B.paro_stats.prof_ms.offset
     assert sizes[4] == B.paro_stats.prof_dof_orb.offset
-    assert sizes[5] == B.paro_params.mg_coarse_sweeps.offset
+    assert sizes[5] == B.paro_params.hartree_precond.offset
