@@ -151,7 +151,7 @@ def run_ours(args, ws, rank, local):
     lam, _ = m.rayleigh_ritz(U, X)
     U.copy_(X)
     torch.cuda.synchronize()
-    params = B.paro_default_params(fixed_outer=1, solve_tol=1e-10, inner_tol=1e-4)
+    params = B.paro_default_params(fixed_outer=1, solve_tol=1e-10, inner_tol=args.inner_tol)
     for _ in range(args.warmup):
         _, lam, _ = m.iterate(U, lam, params)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
@@ -174,7 +174,7 @@ def run_ours(args, ws, rank, local):
         wall = time.perf_counter() - t0
     # Second timed region, same workload: the CG loop launched from the host
     # (no graph) with CUDA events around every launch of the operator kernel.
-    prof = B.paro_default_params(fixed_outer=1, solve_tol=1e-10, inner_tol=1e-4, profile=1)
+    prof = B.paro_default_params(fixed_outer=1, solve_tol=1e-10, inner_tol=args.inner_tol, profile=1)
     prof_ms = 0.0
     prof_n = 0
     prof_units = 0
@@ -246,7 +246,7 @@ def run_ours(args, ws, rank, local):
 
     ttc = None
     if not args.skip_converge and rank == 0:
-        ttc = time_to_converge(B, torch, p, stream)
+        ttc = time_to_converge(B, torch, p, stream, args.inner_tol)
     cpu = None
     if rank == 0 and ws == 1 and not args.skip_cpu:
         cpu = cpu_baseline(p)
@@ -259,7 +259,8 @@ def run_ours(args, ws, rank, local):
             "data": "synthetic (seeded Gaussian initial orbitals, analytic potential)",
             "config": {"workload": WORKLOAD, "precision": "mixed", "parallelism": f"replicas x{ws}",
                        "l2": "flushed (256 MiB write) between steps, outside the timed events",
-                       "step": "one ParO outer iteration (source problems to 1e-10 + Rayleigh-Ritz)"},
+                       "step": "one ParO outer iteration (source problems to 1e-10 + Rayleigh-Ritz)",
+                       "inner_tol": args.inner_tol},
             "e2e": e2e, "gpu_launches": launches, "roofline": roof, "clocks": clk.summary(),
             "cpu_baseline": cpu, "time_to_converge": ttc, "wall_s_timed_region": wall,
         }
@@ -268,7 +269,7 @@ def run_ours(args, ws, rank, local):
         dist.destroy_process_group()
 
 
-def time_to_converge(B, torch, p, stream, max_outer=400):
+def time_to_converge(B, torch, p, stream, inner_tol, max_outer=400):
     """Device time from the initial guess until max |lambda - lambda_discrete| < 1e-6 Ha."""
     try:
         with open(GOLD) as f:
@@ -277,9 +278,9 @@ def time_to_converge(B, torch, p, stream, max_outer=400):
         return {"error": f"no discrete reference values: {e}"}
     out = {"target": "max_i |lambda_i - lambda_i(discrete, shift-invert Lanczos)| < 1e-6 Ha"}
     for name, prec, params in (
-        ("mixed", B.PARO_MIXED, B.paro_default_params(fixed_outer=1, solve_tol=1e-10, inner_tol=1e-4)),
+        ("mixed", B.PARO_MIXED, B.paro_default_params(fixed_outer=1, solve_tol=1e-10, inner_tol=inner_tol)),
         ("fp64", B.PARO_FP64, B.paro_default_params(fixed_outer=1, solve_tol=1e-10)),
-        ("mixed_mg", B.PARO_MIXED, B.paro_default_params(fixed_outer=1, solve_tol=1e-10, inner_tol=1e-4,
+        ("mixed_mg", B.PARO_MIXED, B.paro_default_params(fixed_outer=1, solve_tol=1e-10, inner_tol=inner_tol,
                                                          precond=B.PARO_PRECOND_MG)),
     ):
         m = B.Mesh(p.n, p.lo, p.hi, prec, stream=stream)
@@ -589,6 +590,9 @@ def main():
     ap.add_argument("--ks-nc", type=int, default=128, help="ks workload: cells per axis")
     ap.add_argument("--ks-max-outer", type=int, default=1500, help="ks workload: SCF iteration limit")
     ap.add_argument("--ks-mix", type=float, default=0.3, help="ks workload: linear density mixing")
+    ap.add_argument("--inner-tol", type=float, default=0.0,
+                    help="mixed path: relative tolerance of each float32 correction solve "
+                         "(0: the library's choice, sqrt(solve_tol) = 1e-5 here)")
     ap.add_argument("--precond", default="jacobi", choices=["jacobi", "mg"],
                     help="ks, large, batch workloads: preconditioner of the float32 correction solves")
     ap.add_argument("--large-nc", type=int, default=192, help="large workload: cells per axis")

@@ -84,7 +84,8 @@ typedef struct {
   int n_check;        /* paro_iterate: test only the lowest n_check values; 0 = all N (0) */
   double solve_tol;   /* source problem: stop orbital i when ||b_i - A x_i||_2 <= solve_tol ||b_i||_2 (1e-12) */
   int pcg_maxit;      /* CG iteration limit per solve (FP64 mode) or per correction solve (mixed) (5000) */
-  double inner_tol;   /* mixed: relative tolerance of each float32 correction solve (1e-4) */
+  double inner_tol;   /* mixed: relative tolerance of each float32 correction solve; <= 0: sqrt(solve_tol)
+                         clamped to [1e-6, 1e-3], so that two refinement sweeps reach solve_tol (0) */
   int max_refine;     /* mixed: refinement sweeps per source problem (20) */
   int check_every;    /* CG iterations between host convergence checks (16) */
   int fixed_outer;    /* paro_iterate: if > 0, run exactly this many outer iterations (0) */

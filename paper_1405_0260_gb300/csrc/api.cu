@@ -672,6 +672,9 @@ int check_precond(paro_mesh m, const paro_params& p) {
 // |r| <= solve_tol |b|, solves A d = r to inner_tol with the float32 CG and adds d.
 int refine_solve(paro_mesh m, int N, const paro_params& p, paro_stats* st) {
   TRY(check_precond(m, p));
+  // inner tolerance: given, or sqrt(solve_tol) so that two sweeps reach solve_tol
+  // (clamped to what float32 CG reliably attains and to a useful minimum)
+  const double itol = p.inner_tol > 0.0 ? p.inner_tol : std::fmin(1e-3, std::fmax(1e-6, std::sqrt(p.solve_tol)));
   const int Np = m->Np_alloc;
   Grid& g = m->g;
   CGState rs = cg_state(m, true);
@@ -697,9 +700,9 @@ int refine_solve(paro_mesh m, int N, const paro_params& p, paro_stats* st) {
     long long i1 = 0;
     int imx = 0;
     if (p.precond == PARO_PRECOND_MG)
-      TRY(run_mg(m, m->plan32, N, p.inner_tol, p.pcg_maxit, p.check_every, p.mg_nu, p.mg_coarse_sweeps, &i1, &imx));
+      TRY(run_mg(m, m->plan32, N, itol, p.pcg_maxit, p.check_every, p.mg_nu, p.mg_coarse_sweeps, &i1, &imx));
     else
-      TRY(run_cg<float>(m, m->plan32, N, false, p.inner_tol, p.pcg_maxit, p.check_every, &i1, &imx));
+      TRY(run_cg<float>(m, m->plan32, N, false, itol, p.pcg_maxit, p.check_every, &i1, &imx));
     // an inner limit is not fatal: refinement carries on from the partial correction
     int* stw = &m->cgst->status;
     CK(cudaMemcpyAsync(m->h_int, stw, sizeof(int), cudaMemcpyDeviceToHost, m->st));
@@ -1038,7 +1041,7 @@ void paro_default_params(paro_params* p) {
   p->n_check = 0;
   p->solve_tol = 1e-12;
   p->pcg_maxit = 5000;
-  p->inner_tol = 1e-4;
+  p->inner_tol = 0.0;
   p->max_refine = 20;
   p->check_every = 16;
   p->fixed_outer = 0;
