@@ -239,11 +239,14 @@ __global__ void __launch_bounds__(1024) k_small_eig(int N, int Np, const double*
         pr[k][1] = q;
       }
       __syncthreads();
-      // rows p, q of S <- J^T S
+      // rows p, q of S <- J^T S (cluster-separated: S and V stay block diagonal, so
+      // only pairs within a cluster rotate, and only that cluster's entries:
+      // O(sum q_k^3) work a sweep instead of O(N^3))
       for (int t = tid; t < half * N; t += nt) {
         int k = t / N, col = t % N;
         int p = pr[k][0], q = pr[k][1];
         if (q >= N) continue;
+        if (clus != nullptr && (clus[p] != clus[q] || clus[col] != clus[p])) continue;
         double c = cs[k][0], s = cs[k][1];
         double sp = S[p * N + col], sq = S[q * N + col];
         S[p * N + col] = c * sp - s * sq;
@@ -255,6 +258,7 @@ __global__ void __launch_bounds__(1024) k_small_eig(int N, int Np, const double*
         int k = t / N, row = t % N;
         int p = pr[k][0], q = pr[k][1];
         if (q >= N) continue;
+        if (clus != nullptr && (clus[p] != clus[q] || clus[row] != clus[p])) continue;
         double c = cs[k][0], s = cs[k][1];
         double sp = S[row * N + p], sq = S[row * N + q];
         S[row * N + p] = c * sp - s * sq;
@@ -379,6 +383,8 @@ namespace {
 // host zeroes before the launch; barrier k completes at k * gridDim.x.  Bounded:
 // false after kEigSpinLimit polls.
 constexpr unsigned kEigSpinLimit = 1u << 24;
+// cluster-separated eigensolves: clusters up to this size are diagonalised one per CTA
+constexpr int kEigClusterCtaMaxQ = 128;
 __device__ bool eig_barrier(unsigned* count, unsigned target) {
   __shared__ int s_ok;
   __syncthreads();
@@ -514,92 +520,203 @@ __global__ void __launch_bounds__(256) k_small_eig_grid(int N, int Np, const dou
   for (long long i = gt; i < N; i += gs) rdiag[i] = 1.0 / L[i * N + i];
   if (!sync()) return;
   // parallel cyclic Jacobi
-  for (int sweep = 0; sweep < 40 && N > 1; ++sweep) {
-    double off = 0.0, all = 0.0;
-    for (long long t = gt; t < NN; t += gs) {
-      const double v = S[t];
-      all += v * v;
-      if (t / N != t % N) off += v * v;
+  // clusters are consecutive index ranges with ids 0, 1, ... in order; the largest
+  // decides the form of the Jacobi phase (every CTA computes the same)
+  int qmax = 0;
+  if (clus != nullptr)
+    for (int i = 0, run = 0; i < N; ++i) {
+      run = (i > 0 && clus[i] == clus[i - 1]) ? run + 1 : 1;
+      qmax = run > qmax ? run : qmax;
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      off += __shfl_xor_sync(0xffffffffu, off, o);
-      all += __shfl_xor_sync(0xffffffffu, all, o);
-    }
-    if (lane == 0) {
-      red[tid / 32][0] = off;
-      red[tid / 32][1] = all;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      double a = 0.0, b = 0.0;
-      for (int w = 0; w < nt / 32; ++w) {
-        a += red[w][0];
-        b += red[w][1];
-      }
-      part[2 * blockIdx.x] = a;
-      part[2 * blockIdx.x + 1] = b;
-    }
-    if (!sync()) return;
-    // every CTA sums the partials in the same order: the same decision everywhere
-    off = 0.0;
-    all = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) {
-      off += part[2 * b];
-      all += part[2 * b + 1];
-    }
-    if (!(off > 1e-29 * (double)N * N * all)) break;
-    for (int r = 0; r < m - 1; ++r) {
-      for (long long k = gt; k < half; k += gs) {
-        int p, q;
-        rr_pair(m, r, (int)k, &p, &q);
-        double c = 1.0, s = 0.0;
-        if (q < N) {
-          // angle in float32, (c, s) renormalised in float64 (as k_small_eig)
-          const float fa = (float)S[(long long)p * N + q];
-          if (fa != 0.0f) {
-            const float tau = (float)(S[(long long)q * N + q] - S[(long long)p * N + p]) / (2.0f * fa);
-            const float rt = sqrtf(1.0f + tau * tau);
-            const float t = (tau >= 0.0f) ? 1.0f / (tau + rt) : -1.0f / (-tau + rt);
-            const float cf = rsqrtf(1.0f + t * t);
-            const double cd = cf, sd = (double)(t * cf);
-            const double nn = cd * cd + sd * sd;
-            double y = 1.5 - 0.5 * nn;
-            y = y * (1.5 - 0.5 * nn * y * y);
-            c = cd * y;
-            s = sd * y;
-          }
+  if (clus != nullptr && qmax <= kEigClusterCtaMaxQ) {
+    // Cluster-separated (Section 3): S is block diagonal, so every cluster is its own
+    // eigenproblem.  CTA b diagonalises clusters b, b + grid, ... alone, with CTA
+    // barriers only: O(sum q_k^3) work and q_k - 1 rounds a sweep instead of N - 1
+    // rounds of three grid barriers.
+    __shared__ double s_cs[kEigClusterCtaMaxQ];  // (c, s) of the round's q_k / 2 pairs
+    __shared__ double s_red[256 / 32][2];
+    const int ncl = clus[N - 1] + 1;
+    for (int kc = blockIdx.x; kc < ncl; kc += gridDim.x) {
+      int c0 = 0;
+      while (c0 < N && clus[c0] != kc) ++c0;
+      int c1 = c0;
+      while (c1 < N && clus[c1] == kc) ++c1;
+      const int q = c1 - c0;
+      if (q < 2) continue;
+      const int mq = (q % 2 == 0) ? q : q + 1, hq = mq / 2;
+      for (int sweep = 0; sweep < 40; ++sweep) {
+        double off = 0.0, all = 0.0;
+        for (int t = tid; t < q * q; t += nt) {
+          const int i = c0 + t / q, j = c0 + t % q;
+          const double v = S[(long long)i * N + j];
+          all += v * v;
+          if (i != j) off += v * v;
         }
-        cs[2 * k] = c;
-        cs[2 * k + 1] = s;
+        for (int o = 16; o > 0; o >>= 1) {
+          off += __shfl_xor_sync(0xffffffffu, off, o);
+          all += __shfl_xor_sync(0xffffffffu, all, o);
+        }
+        if (lane == 0) {
+          s_red[tid / 32][0] = off;
+          s_red[tid / 32][1] = all;
+        }
+        __syncthreads();
+        off = 0.0;
+        all = 0.0;
+        for (int w = 0; w < nt / 32; ++w) {
+          off += s_red[w][0];
+          all += s_red[w][1];
+        }
+        __syncthreads();
+        if (!(off > 1e-29 * (double)q * q * all)) break;
+        for (int r = 0; r < mq - 1; ++r) {
+          for (int k = tid; k < hq; k += nt) {
+            int p, pq;
+            rr_pair(mq, r, k, &p, &pq);
+            double c = 1.0, sn = 0.0;
+            if (pq < q) {
+              // angle in float32, (c, s) renormalised in float64 (as k_small_eig)
+              const float fa = (float)S[(long long)(c0 + p) * N + c0 + pq];
+              if (fa != 0.0f) {
+                const float tau =
+                    (float)(S[(long long)(c0 + pq) * N + c0 + pq] - S[(long long)(c0 + p) * N + c0 + p]) / (2.0f * fa);
+                const float rt = sqrtf(1.0f + tau * tau);
+                const float tt = (tau >= 0.0f) ? 1.0f / (tau + rt) : -1.0f / (-tau + rt);
+                const float cf = rsqrtf(1.0f + tt * tt);
+                const double cd = cf, sd = (double)(tt * cf);
+                const double nn = cd * cd + sd * sd;
+                double y = 1.5 - 0.5 * nn;
+                y = y * (1.5 - 0.5 * nn * y * y);
+                c = cd * y;
+                sn = sd * y;
+              }
+            }
+            s_cs[2 * k] = c;
+            s_cs[2 * k + 1] = sn;
+          }
+          __syncthreads();
+          // rows p, q of the block <- J^T S
+          for (int t = tid; t < hq * q; t += nt) {
+            const int k = t / q, col = c0 + t % q;
+            int p, pq;
+            rr_pair(mq, r, k, &p, &pq);
+            if (pq >= q) continue;
+            const double c = s_cs[2 * k], sn = s_cs[2 * k + 1];
+            const long long ep = (long long)(c0 + p) * N + col, eq = (long long)(c0 + pq) * N + col;
+            const double sp = S[ep], sq = S[eq];
+            S[ep] = c * sp - sn * sq;
+            S[eq] = sn * sp + c * sq;
+          }
+          __syncthreads();
+          // columns p, q of the block <- S J; V <- V J (V is block diagonal too)
+          for (int t = tid; t < hq * q; t += nt) {
+            const int k = t / q, row = c0 + t % q;
+            int p, pq;
+            rr_pair(mq, r, k, &p, &pq);
+            if (pq >= q) continue;
+            const double c = s_cs[2 * k], sn = s_cs[2 * k + 1];
+            const long long ep = (long long)row * N + c0 + p, eq = (long long)row * N + c0 + pq;
+            const double sp = S[ep], sq = S[eq];
+            S[ep] = c * sp - sn * sq;
+            S[eq] = sn * sp + c * sq;
+            const double vp = V[ep], vq = V[eq];
+            V[ep] = c * vp - sn * vq;
+            V[eq] = sn * vp + c * vq;
+          }
+          __syncthreads();
+        }
+      }
+    }
+  } else {
+    for (int sweep = 0; sweep < 40 && N > 1; ++sweep) {
+      double off = 0.0, all = 0.0;
+      for (long long t = gt; t < NN; t += gs) {
+        const double v = S[t];
+        all += v * v;
+        if (t / N != t % N) off += v * v;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        off += __shfl_xor_sync(0xffffffffu, off, o);
+        all += __shfl_xor_sync(0xffffffffu, all, o);
+      }
+      if (lane == 0) {
+        red[tid / 32][0] = off;
+        red[tid / 32][1] = all;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < nt / 32; ++w) {
+          a += red[w][0];
+          b += red[w][1];
+        }
+        part[2 * blockIdx.x] = a;
+        part[2 * blockIdx.x + 1] = b;
       }
       if (!sync()) return;
-      // rows p, q of S <- J^T S
-      for (long long t = gt; t < (long long)half * N; t += gs) {
-        const int k = (int)(t / N), col = (int)(t % N);
-        int p, q;
-        rr_pair(m, r, k, &p, &q);
-        if (q >= N) continue;
-        const double c = cs[2 * k], s = cs[2 * k + 1];
-        const double sp = S[(long long)p * N + col], sq = S[(long long)q * N + col];
-        S[(long long)p * N + col] = c * sp - s * sq;
-        S[(long long)q * N + col] = s * sp + c * sq;
+      // every CTA sums the partials in the same order: the same decision everywhere
+      off = 0.0;
+      all = 0.0;
+      for (int b = 0; b < (int)gridDim.x; ++b) {
+        off += part[2 * b];
+        all += part[2 * b + 1];
       }
-      if (!sync()) return;
-      // columns p, q of S <- S J; V <- V J
-      for (long long t = gt; t < (long long)half * N; t += gs) {
-        const int k = (int)(t / N), row = (int)(t % N);
-        int p, q;
-        rr_pair(m, r, k, &p, &q);
-        if (q >= N) continue;
-        const double c = cs[2 * k], s = cs[2 * k + 1];
-        const double sp = S[(long long)row * N + p], sq = S[(long long)row * N + q];
-        S[(long long)row * N + p] = c * sp - s * sq;
-        S[(long long)row * N + q] = s * sp + c * sq;
-        const double vp = V[(long long)row * N + p], vq = V[(long long)row * N + q];
-        V[(long long)row * N + p] = c * vp - s * vq;
-        V[(long long)row * N + q] = s * vp + c * vq;
+      if (!(off > 1e-29 * (double)N * N * all)) break;
+      for (int r = 0; r < m - 1; ++r) {
+        for (long long k = gt; k < half; k += gs) {
+          int p, q;
+          rr_pair(m, r, (int)k, &p, &q);
+          double c = 1.0, s = 0.0;
+          if (q < N) {
+            // angle in float32, (c, s) renormalised in float64 (as k_small_eig)
+            const float fa = (float)S[(long long)p * N + q];
+            if (fa != 0.0f) {
+              const float tau = (float)(S[(long long)q * N + q] - S[(long long)p * N + p]) / (2.0f * fa);
+              const float rt = sqrtf(1.0f + tau * tau);
+              const float t = (tau >= 0.0f) ? 1.0f / (tau + rt) : -1.0f / (-tau + rt);
+              const float cf = rsqrtf(1.0f + t * t);
+              const double cd = cf, sd = (double)(t * cf);
+              const double nn = cd * cd + sd * sd;
+              double y = 1.5 - 0.5 * nn;
+              y = y * (1.5 - 0.5 * nn * y * y);
+              c = cd * y;
+              s = sd * y;
+            }
+          }
+          cs[2 * k] = c;
+          cs[2 * k + 1] = s;
+        }
+        if (!sync()) return;
+        // rows p, q of S <- J^T S (cluster-separated: within-cluster entries only, as k_small_eig)
+        for (long long t = gt; t < (long long)half * N; t += gs) {
+          const int k = (int)(t / N), col = (int)(t % N);
+          int p, q;
+          rr_pair(m, r, k, &p, &q);
+          if (q >= N) continue;
+          if (clus != nullptr && (clus[p] != clus[q] || clus[col] != clus[p])) continue;
+          const double c = cs[2 * k], s = cs[2 * k + 1];
+          const double sp = S[(long long)p * N + col], sq = S[(long long)q * N + col];
+          S[(long long)p * N + col] = c * sp - s * sq;
+          S[(long long)q * N + col] = s * sp + c * sq;
+        }
+        if (!sync()) return;
+        // columns p, q of S <- S J; V <- V J
+        for (long long t = gt; t < (long long)half * N; t += gs) {
+          const int k = (int)(t / N), row = (int)(t % N);
+          int p, q;
+          rr_pair(m, r, k, &p, &q);
+          if (q >= N) continue;
+          if (clus != nullptr && (clus[p] != clus[q] || clus[row] != clus[p])) continue;
+          const double c = cs[2 * k], s = cs[2 * k + 1];
+          const double sp = S[(long long)row * N + p], sq = S[(long long)row * N + q];
+          S[(long long)row * N + p] = c * sp - s * sq;
+          S[(long long)row * N + q] = s * sp + c * sq;
+          const double vp = V[(long long)row * N + p], vq = V[(long long)row * N + q];
+          V[(long long)row * N + p] = c * vp - s * vq;
+          V[(long long)row * N + q] = s * vp + c * vq;
+        }
+        if (!sync()) return;
       }
-      if (!sync()) return;
     }
   }
   // every CTA has read the sweep's partial norms (C's scratch) before C is written
