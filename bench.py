@@ -569,6 +569,38 @@ def run_ks(args):
     m.close()
 
 
+def run_clusters(args):
+    """Cluster-separated Rayleigh-Ritz (Section 3): N = 256 orbitals on a 24^3 mesh (so
+    that the small eigenproblem dominates the step), mixed precision, 3 outer iterations
+    timed with one eigenvalue cluster, 4 of 64 and 16 of 16 (not the headline line)."""
+    import torch
+
+    from paper_1405_0260_gb300 import binding as B
+    from paper_1405_0260_gb300 import workloads as W
+
+    N = 256
+    p = W.harmonic(nc=24, L=8.0, N=4, seed=8100, sigma=0.0)
+    m = B.Mesh(p.n, p.lo, p.hi, B.PARO_MIXED)
+    vq = torch.from_numpy(np.ascontiguousarray(p.Vq)).cuda()
+    m.set_potential(vq, 2.0)
+    U0 = torch.from_numpy(W.random_block(p.n, N, seed=8101)).cuda()
+    out = {}
+    for name, sizes in (("1x256", None), ("4x64", [64] * 4), ("16x16", [16] * 16)):
+        U = U0.clone()
+        _, lam, _ = m.iterate(U, None, B.paro_default_params(fixed_outer=1, solve_tol=1e-8))
+        prm = B.paro_default_params(fixed_outer=3, solve_tol=1e-8)
+        if sizes:
+            prm.set_clusters(sizes)
+        rc, lam, st = m.iterate(U, lam, prm)
+        torch.cuda.synchronize()
+        out[name] = {"rc": rc, "ms_rayleigh_ritz_per_outer": st.ms_rr / 3, "ms_source_problems_per_outer": st.ms_solve / 3}
+    line = {"metric": "cluster-separated Rayleigh-Ritz time per outer iteration", "unit": "ms",
+            "workload": f"harmonic V=r^2/2, [-8,8]^3, 24^3 cells ({p.n_interior} dofs), N={N}, sigma=2, mixed",
+            "clusters": out, "data": "synthetic (seeded unit-variance block)"}
+    print(json.dumps(line), flush=True)
+    m.close()
+
+
 def collections_count(values):
     out = {}
     for v in values:
@@ -584,9 +616,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--skip-cpu", action="store_true", help="omit the cpu_baseline leg")
     ap.add_argument("--skip-converge", action="store_true", help="omit the time-to-converge leg")
-    ap.add_argument("--workload", default="harmonic64", choices=["harmonic64", "batch", "large", "ks"],
+    ap.add_argument("--workload", default="harmonic64", choices=["harmonic64", "batch", "large", "ks", "clusters"],
                     help="batch: independent systems (meshes 32-96^3, N 4-48) through paro_batch_iterate; "
-                         "large: 192^3 cells, N = 256; ks: the Kohn-Sham cluster SCF to convergence")
+                         "large: 192^3 cells, N = 256; ks: the Kohn-Sham cluster SCF; "
+                         "clusters: cluster-separated Rayleigh-Ritz at N = 256")
     ap.add_argument("--ks-nc", type=int, default=128, help="ks workload: cells per axis")
     ap.add_argument("--ks-max-outer", type=int, default=1500, help="ks workload: SCF iteration limit")
     ap.add_argument("--ks-mix", type=float, default=0.3, help="ks workload: linear density mixing")
@@ -602,9 +635,9 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
     ws, rank, local = dist_env()
-    if args.workload in ("batch", "large", "ks"):
+    if args.workload in ("batch", "large", "ks", "clusters"):
         if rank == 0 and args.impl == "ours":
-            {"batch": run_batch, "large": run_large, "ks": run_ks}[args.workload](args)
+            {"batch": run_batch, "large": run_large, "ks": run_ks, "clusters": run_clusters}[args.workload](args)
         return
     if args.impl == "reference":
         run_reference(args, ws, rank)
