@@ -220,7 +220,10 @@ def run_ours(args, ws, rank, local):
                 # one orbital block (N <= 32): passes = node passes / interior nodes, and
                 # the share of (node, orbital) pairs still active in those passes
                 "passes_per_launch": round(prof_nodes / nI / prof_n, 2),
-                "active_fraction": round(prof_units / (prof_nodes * N), 4)}
+                "active_fraction": round(prof_units / (prof_nodes * N), 4),
+                # the per-PCG-iteration form of the metric: active (node, orbital)
+                # pairs advanced one CG iteration per second inside the kernel
+                "dof_orbital_cg_iterations_per_s": round(prof_units / (prof_ms * 1e-3))}
 
     # end to end through the C ABI with host buffers
     Uh = torch.empty((nI, N), dtype=torch.float64, pin_memory=True)
