@@ -53,6 +53,23 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(value, dist, device):
+    """The largest of every rank's value (the slowest replica sets the job's time);
+    dist None: a single process."""
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank, ws, t_max_ms):
+    """Whole-job throughput of ws independent replicas: all ranks' units over the slowest time."""
+    return units_per_rank * ws / (t_max_ms * 1e-3)
+
+
 def problem(rank):
     from paper_1405_0260_gb300 import workloads as W
 
@@ -191,13 +208,8 @@ def run_ours(args, ws, rank, local):
     if dist is not None:
         dist.barrier()
     ms = sum(a.elapsed_time(b) for a, b in ev)
-    t_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    units = nI * N * args.steps * ws
-    value = units / (t_max * 1e-3)
+    t_max = max_over_ranks(ms, dist, "cuda")
+    value = replica_throughput(nI * N * args.steps, ws, t_max)
 
     # roofline of the single-reduction CG kernel (the whole float32 CG loop of a
     # correction solve in one cooperative launch, one pass per iteration).  Per unit
