@@ -77,8 +77,11 @@ def test_fullsize_iteration_reaches_the_discrete_spectrum(B, case):
         err = float(np.max(np.abs(lam - gold)))
     assert err < 1e-6, (outer, lam, gold)
     u = U.cpu().numpy()
+    # M-orthonormal to the accuracy of the Gram matrices the last Rayleigh-Ritz step
+    # used: the tensor-core Grams round the inputs 24 bits below each chunk's column
+    # maximum (~6e-8 relative on a diagonal entry) until max |delta lambda| < 1e-6
     G = u.T @ (ops.M @ u)
-    assert np.max(np.abs(G - np.eye(p.N))) < 1e-9
+    assert np.max(np.abs(G - np.eye(p.N))) < 2e-7
     # eigen-residuals relative to ||M u||: an eigenvalue within 1e-6 Ha leaves a
     # residual of order sqrt(1e-6 * gap); a wrong vector leaves O(1)
     res = O.eigen_residuals(ops, u, lam) / np.linalg.norm(ops.M @ u, axis=0)
