@@ -16,9 +16,12 @@ Layouts (shared with the C ABI, see include/paro.h):
 Workloads (paper Section 4 uses molecules on adaptive meshes; these synthetic
 stand-ins keep the structure: Coulomb-like wells, N lowest orbitals, Gaussian
 initial guesses as suggested for Step 1 of Algorithm 3.1):
-  hydrogen_c1   Z=1 at a cell centre, V=-1/r, [-10,10]^3, 32^3 cells, N=5, sigma=2
-  harmonic_c2   V=r^2/2, [-8,8]^3, 64^3 cells, N=20, sigma=0
-  cluster       softened Coulomb -Z/sqrt(r^2+0.25) from random nuclei
+  hydrogen       Z=1 at a cell centre, V=-1/r, [-10,10]^3, 32^3 cells, N=5, sigma=2
+  harmonic       V=r^2/2, [-8,8]^3, 64^3 cells, N=20, sigma=0
+  cluster        softened Coulomb -Z/sqrt(r^2+0.25) from 8 random nuclei (Kohn-Sham SCF)
+  batch_systems  64 independent systems, 1-6 nuclei each, meshes 32-96^3, N 4-48
+  large_cluster  40 nuclei, [-20,20]^3, 192^3 cells, N=256, standard normal initial block
+  random_block   unit-variance orbitals for throughput runs
 """
 from __future__ import annotations
 
