@@ -271,14 +271,18 @@ def test_stored_oscillator_spectra_match_separable_form(key, nc):
 
 
 def test_hydrogen_ground_state_trend():
-    # -Z^2/(2 n^2): the lowest level approaches -1/2 as the mesh is refined
+    # -Z^2/(2 n^2): the n = 1 level approaches -1/2 and the four n = 2 levels
+    # (2s and the 2p triplet, split by the cubic mesh) approach -1/8 from above
+    # as the mesh is refined
     vals = []
     for nc in (16, 32):
         p = W.hydrogen(nc=nc, L=10.0, N=1, seed=1)
         ops = O.assemble(O.Mesh(p.n, p.lo, p.hi), p.Vq, 0.0)
-        vals.append(_lowest(ops, 1, -0.6)[0])
-    assert -0.5 < vals[1] < -0.4
-    assert abs(vals[1] + 0.5) < abs(vals[0] + 0.5)
+        vals.append(_lowest(ops, 5, -0.6))
+    exact = np.array([-0.5, -0.125, -0.125, -0.125, -0.125])
+    assert -0.5 < vals[1][0] < -0.4
+    assert np.all((vals[1][1:] > -0.125) & (vals[1][1:] < -0.1))
+    assert np.all(np.abs(vals[1] - exact) < np.abs(vals[0] - exact))
 
 
 @pytest.mark.slow
