@@ -91,3 +91,44 @@ int main(void) {
     assert sizes[3] == B.paro_stats.prof_ms.offset
     assert sizes[4] == B.paro_stats.prof_dof_orb.offset
     assert sizes[5] == B.paro_params.hartree_precond.offset
+
+
+def test_host_side_argument_checks_need_no_gpu(lib):
+    # every one of these is rejected before any CUDA call, so it runs on a host
+    # without a GPU; the batch calls keep their own host-side bookkeeping
+    from paper_1405_0260_gb300 import binding as B
+
+    assert B.paro_small_eig_static(0, 1, 1, 1, 1) == -1  # PARO_ERR_ARG
+    assert B.paro_small_eig_static(129, 1, 1, 1, 1) == -1  # PARO_ERR_ARG
+    assert B.paro_small_eig_static(4, 0, 1, 1, 1) == -1  # PARO_ERR_ARG
+    b = ctypes.c_void_p()
+    assert lib.paro_batch_create(ctypes.byref(b), 0) == -1
+    assert lib.paro_batch_create(ctypes.byref(b), 257) == -1
+    assert lib.paro_batch_create(ctypes.byref(b), 4) == 0
+    assert lib.paro_batch_size(b) == 0
+    assert lib.paro_batch_add(b, None, 4, None, None, None) == -1  # no handle
+    rc = (ctypes.c_int * 1)()
+    assert lib.paro_batch_iterate(b, rc, None) == 0  # an empty batch has nothing to do
+    assert lib.paro_batch_iterate(None, rc, None) == -1
+    assert lib.paro_batch_destroy(b) == 0
+    assert lib.paro_batch_size(None) == -1
+    assert lib.paro_interior_nodes(None) == -1
+    assert lib.paro_set_potential(None, None, 0.0) == -1
+    assert lib.paro_ks_density_in(None, None) == -1
+    assert lib.paro_orbital_solve(None, 1, None, None, None, None, None) == -1
+    assert lib.paro_rayleigh_ritz(None, 1, None, None, None, None) == -1
+
+
+def test_binding_fails_loudly_without_the_library():
+    # the package has no CPU fallback: with the library absent, loading it raises
+    code = (
+        "import sys; sys.path.insert(0, %r)\n"
+        "from paper_1405_0260_gb300 import binding as B\n"
+        "B.LIB_PATH = '/nonexistent/libparo.so'\n"
+        "try:\n"
+        "    B.lib()\n"
+        "except RuntimeError as e:\n"
+        "    print('raised', 'no CPU fallback' in str(e))\n" % ROOT
+    )
+    out = subprocess.run(["python", "-c", code], capture_output=True, text=True, timeout=120).stdout
+    assert out.strip() == "raised True", out
