@@ -189,8 +189,9 @@ def run_ours(args, ws, rank, local):
             launches += st.kernel_launches
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
-    # Second timed region, same workload: the CG loop launched from the host
-    # (no graph) with CUDA events around every launch of the operator kernel.
+    # Second timed region, same workload: CUDA events on the library's stream
+    # around every launch of the persistent CG kernel (profile = 1: one launch per
+    # float32 correction solve), for the kernel's roofline.
     prof = B.paro_default_params(fixed_outer=1, solve_tol=1e-10, inner_tol=args.inner_tol, profile=1)
     prof_ms = 0.0
     prof_n = 0
