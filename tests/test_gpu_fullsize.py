@@ -78,8 +78,10 @@ def test_fullsize_iteration_reaches_the_discrete_spectrum(B, case):
     assert err < 1e-6, (outer, lam, gold)
     u = U.cpu().numpy()
     # M-orthonormal to the accuracy of the Gram matrices the last Rayleigh-Ritz step
-    # used: the tensor-core Grams round the inputs 24 bits below each chunk's column
-    # maximum (~6e-8 relative on a diagonal entry) until max |delta lambda| < 1e-6
+    # used: until max |delta lambda| < 1e-6 those are the tensor-core Grams, which
+    # round every input 24 bits below its chunk's column maximum (at most ~6e-8
+    # relative on one product; about 5e-10 on a Gram entry at this size, where the
+    # rounding errors of many nodes partly cancel); the bound leaves room for both
     G = u.T @ (ops.M @ u)
     assert np.max(np.abs(G - np.eye(p.N))) < 2e-7
     # eigen-residuals relative to ||M u||: an eigenvalue within 1e-6 Ha leaves a
