@@ -50,7 +50,7 @@ typedef enum {
   PARO_ERR_NOT_SPD = -3,       /* p^T A p <= 0 in CG, or a non-positive Cholesky pivot */
   PARO_ERR_NOT_CONVERGED = -4, /* an iteration limit was reached before its tolerance */
   PARO_ERR_NONFINITE = -5,     /* NaN/Inf met in a reduction */
-  PARO_ERR_TIMEOUT = -6,       /* reserved: a bounded device-side wait ran out */
+  PARO_ERR_TIMEOUT = -6,       /* a bounded device-side wait (grid barrier, mbarrier) ran out */
   PARO_ERR_OOM = -7,           /* device allocation failed */
   PARO_ERR_STATE = -8          /* call out of order (e.g. no potential set) */
 } paro_status;
