@@ -11,12 +11,14 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "paro.h")
+# a declaration: return type (one or more words, optional pointer), then the name
+DECL = r"^\s*(?:const\s+)?(?:\w+\s+)*\w+\s*\*?\s*(paro_\w+)\s*"
 
 
 def declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(paro_\w+)\s*\(", text, flags=re.M)))
+    return sorted(set(re.findall(DECL + r"\(", text, flags=re.M)))
 
 
 @pytest.fixture(scope="module")
@@ -132,3 +134,28 @@ def test_binding_fails_loudly_without_the_library():
     )
     out = subprocess.run(["python", "-c", code], capture_output=True, text=True, timeout=120).stdout
     assert out.strip() == "raised True", out
+
+
+def declared_arity():
+    """{name: parameter count} of every function paro.h declares."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    out = {}
+    for m in re.finditer(DECL + r"\(([^)]*)\)\s*;", text, flags=re.M | re.S):
+        params = m.group(2).strip()
+        out[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_argument_lists_match_the_header(lib):
+    from paper_1405_0260_gb300 import binding as B
+
+    B.paro_small_eig_static(0, 1, 1, 1, 1)  # sets that function's argtypes (rejected: N = 0)
+    arity = declared_arity()
+    assert set(arity) == set(declared_functions())
+    checked = 0
+    for name, n in arity.items():
+        argtypes = getattr(lib, name).argtypes
+        if argtypes is not None:
+            assert len(argtypes) == n, (name, len(argtypes), n)
+            checked += 1
+    assert checked >= len(arity) - 1  # every entry point the binding calls
