@@ -159,3 +159,17 @@ def test_binding_argument_lists_match_the_header(lib):
             assert len(argtypes) == n, (name, len(argtypes), n)
             checked += 1
     assert checked >= len(arity) - 1  # every entry point the binding calls
+
+
+def test_binding_constants_match_the_header():
+    from paper_1405_0260_gb300 import binding as B
+
+    text = open(HEADER).read()
+    defines = {k: int(v) for k, v in re.findall(r"^#define\s+(PARO_\w+)\s+(-?\d+)", text, flags=re.M)}
+    enum = {k: int(v) for k, v in re.findall(r"^\s*(PARO_(?:OK|ERR_\w+))\s*=\s*(-?\d+)", text, flags=re.M)}
+    assert len(enum) == 9 and enum["PARO_OK"] == B.PARO_OK
+    assert {v: k for k, v in enum.items()} == B.STATUS
+    shared = [k for k in defines if hasattr(B, k)]
+    assert len(shared) >= 10, shared
+    for k in shared:
+        assert getattr(B, k) == defines[k], k
