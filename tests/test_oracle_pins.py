@@ -368,3 +368,34 @@ def test_cluster_separated_paro_reaches_the_box_spectrum():
     res = O.paro(ops, U0, tol=1e-12, max_outer=400, pcg_tol=1e-13, clusters=[1, 3])
     ref = _box_spectrum(n, mesh.h)[:4]
     assert np.max(np.abs(res.lam - ref) / ref) < 1e-9
+
+
+@pytest.mark.parametrize("n", [(2, 2, 2), (2, 3, 4), (3, 3, 3)])
+def test_tiny_meshes_have_the_closed_form_spectrum(n):
+    # the smallest meshes: one interior node at 2^3; every mode of the box
+    L = (1.0, 0.7, 1.3)
+    mesh = _mesh(n, L)
+    ops = O.assemble(mesh, np.zeros(8 * n[0] * n[1] * n[2]), 0.0)
+    lam = sla.eigh(ops.H.toarray(), ops.M.toarray(), eigvals_only=True)
+    assert np.max(np.abs(lam - _box_spectrum(n, mesh.h)) / lam) < 1e-13
+
+
+def test_single_orbital_rayleigh_ritz_is_the_rayleigh_quotient():
+    p = W.harmonic(nc=5, L=3.0, N=1, seed=4)
+    ops = O.assemble(O.Mesh(p.n, p.lo, p.hi), p.Vq, 0.0)
+    x = p.U0[:, 0]
+    rr = O.rayleigh_ritz(ops, p.U0)
+    q = (x @ (ops.H @ x)) / (x @ (ops.M @ x))
+    assert abs(rr.lam[0] - q) < 1e-14 * abs(q)
+    assert abs(rr.U[:, 0] @ (ops.M @ rr.U[:, 0]) - 1.0) < 1e-14
+
+
+def test_paro_resumes_from_its_state_bit_for_bit():
+    # the state of the loop is (U, lambda): two outer iterations, then two more
+    # from that state, equal four in one run exactly
+    p = W.hydrogen(nc=6, L=5.0, N=3, seed=31, sigma=2.0)
+    ops = O.assemble(O.Mesh(p.n, p.lo, p.hi), p.Vq, p.sigma)
+    full = O.paro(ops, p.U0, pcg_tol=1e-12, fixed_outer=4)
+    half = O.paro(ops, p.U0, pcg_tol=1e-12, fixed_outer=2)
+    rest = O.paro(ops, half.U, pcg_tol=1e-12, fixed_outer=2, lam0=half.lam)
+    assert np.array_equal(rest.lam, full.lam) and np.array_equal(rest.U, full.U)
