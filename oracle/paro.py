@@ -16,14 +16,19 @@ Discrete, on the interior nodes of a uniform nx x ny x nz Q1 hex mesh:
   A = H + sigma M                   the shifted SPD operator of the source problems
 
 Pins (tests/test_oracle_pins.py):
-  assemble            -> Kronecker closed form of K and M, exact linear-V
-                         integrals, constant-V == c*M, V=0 discrete sine spectrum
+  assemble            -> Kronecker closed form of K and M, exact linear- and
+                         trilinear-V integrals, constant-V == c*M, V=0 discrete
+                         sine spectrum (down to one interior node)
   pcg                 -> direct sparse solve on the same system
   rayleigh_ritz       -> Ritz conditions, M-orthonormality, interlacing against
-                         dense eigenvalues of the assembled pencil
-  paro                -> dense/ARPACK eigenvalues of the same pencil,
-                         harmonic-oscillator levels w(n+3/2) with O(h^2) rate,
-                         hydrogen-like -1/2 trend, fixed-point property
+                         dense eigenvalues of the assembled pencil, the Rayleigh
+                         quotient for one orbital
+  paro                -> dense/ARPACK eigenvalues of the same pencil (the full
+                         32^3 hydrogen workload included), harmonic-oscillator
+                         levels w(n+3/2) with O(h^2) rate, hydrogen-like n = 1, 2
+                         trends, fixed-point property, resume from (U, lambda)
+tests/test_oracle_mutations.py plants plausible mistakes here and checks that
+these pins catch them.
 """
 from __future__ import annotations
 
