@@ -1,0 +1,151 @@
+"""The tiled CG kernel's launch geometry, checked on the CPU.
+
+The single-reduction CG kernel stages r, w and s (with a one-node halo), the
+Jacobi diagonal and the packed operator weights of every input plane by TMA
+into a ring of shared-memory slots, and splits the column-planes of the mesh
+over a grid of CTAs.  Its plan is computed on the host by
+``paro::cg1_candidates`` (exported by libparo.so).  This test compiles a small
+host program against the library, asks for the candidate geometries of many
+meshes (cubic, uneven, odd, small and the largest workload's 192^3) and
+orbital counts (4 to 256), and checks every one against the limits the kernel
+relies on: TMA boxes of at most 256 elements per dimension whose inner extent
+and start coordinate are multiples of 16 bytes, 128-byte aligned slots, a
+transaction count below the mbarrier's 2^20, at most 1024 threads and 227 KB of
+shared memory per CTA, column tiles that cover the interior nodes, orbital
+blocks that cover the orbitals, and a split that hands out every column-plane
+exactly once in order.  Needs nvcc and the built library, no GPU.
+"""
+import os
+import shutil
+import subprocess
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_1405_0260_gb300", "csrc")
+LIBDIR = os.path.join(ROOT, "paper_1405_0260_gb300")
+
+SRC = r'''
+#include <cstdio>
+#include <vector>
+#include "cg.cuh"
+using namespace paro;
+int main() {
+  const int meshes[][3] = {{4, 4, 4}, {5, 7, 6}, {10, 12, 9}, {16, 16, 16}, {33, 17, 65}, {32, 48, 64},
+                           {64, 64, 64}, {96, 96, 96}, {128, 128, 128}, {192, 192, 192}};
+  for (auto& m : meshes) {
+    Grid g{};
+    g.nx = m[0]; g.ny = m[1]; g.nz = m[2];
+    g.Px = g.nx + 1; g.Py = g.ny + 1; g.Pz = g.nz + 1;
+    g.G = (long long)g.Px * g.Py * g.Pz;
+    g.nI = (g.nx - 1) * (g.ny - 1) * (g.nz - 1);
+    g.hx = g.hy = g.hz = 1.0;
+    for (int Np = 4; Np <= 256; Np += 4) {
+      std::vector<K1Geom> c;
+      cg1_candidates(g, Np, 152, &c);
+      std::printf("N %d %d %d %d %zu\n", g.nx, g.ny, g.nz, Np, c.size());
+      for (const K1Geom& G : c) {
+        long long F = (long long)G.nob * G.ncx * G.ncy * (g.nz - 1);
+        int mono = 1;
+        long long maxcost = 0;
+        for (int k = 0; k < G.grid; ++k) {
+          if (G.split[k + 1] < G.split[k]) mono = 0;
+          long long a = G.split[k], b = G.split[k + 1], cost = 0;
+          while (a < b) {  // planes plus two halo planes per column segment
+            long long end = (a / (g.nz - 1) + 1) * (g.nz - 1);
+            long long e = end < b ? end : b;
+            cost += (e - a) + 2;
+            a = e;
+          }
+          if (cost > maxcost) maxcost = cost;
+        }
+        std::printf("G %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %u %zu %d %lld %lld %d %lld\n",
+                    g.nx, g.ny, g.nz, Np, G.TX, G.TY, G.DX, G.ncx, G.ncy, G.nob, G.grid, G.G4, G.npt, G.nthr,
+                    G.off_p, G.off_s, G.off_d, G.off_w, G.slot_bytes, (unsigned)G.tx_bytes, G.smem, G.split[0],
+                    (long long)G.split[G.grid], F, mono, maxcost);
+      }
+    }
+  }
+  return 0;
+}
+'''
+
+FIELDS = ("nx ny nz Np TX TY DX ncx ncy nob grid G4 npt nthr off_p off_s off_d off_w slot tx smem "
+          "s0 sN F mono maxcost").split()
+KWS = 28  # packed operator weights per node (27 + one pad)
+
+
+@pytest.fixture(scope="module")
+def plans():
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    lib = os.path.join(LIBDIR, "libparo.so")
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    if not os.path.exists(lib):
+        import __graft_entry__
+
+        __graft_entry__.build()
+    with tempfile.TemporaryDirectory() as d:
+        src, exe = os.path.join(d, "plan.cu"), os.path.join(d, "plan")
+        with open(src, "w") as f:
+            f.write(SRC)
+        subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-std=c++17", "-I", CSRC,
+                        "-I", os.path.join(ROOT, "include"), src, "-o", exe, "-L", LIBDIR, "-lparo",
+                        "-Xlinker", "-rpath=" + LIBDIR, "-lcuda"], check=True, capture_output=True, timeout=600)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True, timeout=600).stdout
+    counts, geoms = {}, []
+    for line in out.splitlines():
+        t = line.split()
+        if t[0] == "N":
+            counts[tuple(int(v) for v in t[1:5])] = int(t[5])
+        elif t[0] == "G":
+            geoms.append(dict(zip(FIELDS, (int(v) for v in t[1:]))))
+    return counts, geoms
+
+
+def test_every_mesh_and_orbital_count_has_a_geometry(plans):
+    counts, geoms = plans
+    assert len(counts) == 10 * 64
+    assert all(n >= 1 for n in counts.values()), [k for k, n in counts.items() if n == 0]
+    assert len(geoms) == sum(counts.values())
+
+
+def test_tma_boxes_and_slots_obey_the_hardware_rules(plans):
+    for G in plans[1]:
+        bw = 4 * G["G4"]
+        # boxes: [bw][TY+2][TX+2] of r, w, s; [TY+2][DX] of D^-1; [TY][TX][28] of the weights
+        for dim in (bw, G["TX"] + 2, G["TY"] + 2, G["DX"], G["TX"], G["TY"], KWS):
+            assert 1 <= dim <= 256, G
+        # inner extents (float32) and start coordinates (orbital block offsets, column origins) on 16 bytes
+        assert (4 * bw) % 16 == 0 and (4 * G["DX"]) % 16 == 0 and (4 * KWS) % 16 == 0, G
+        assert G["TX"] % 4 == 0, G
+        vec = (G["TX"] + 2) * (G["TY"] + 2) * bw * 4
+        dv = G["DX"] * (G["TY"] + 2) * 4
+        wv = KWS * G["TX"] * G["TY"] * 4
+        assert G["tx"] == 3 * vec + dv + wv and G["tx"] < 2 ** 20, G
+        offs = (0, G["off_p"], G["off_s"], G["off_d"], G["off_w"], G["slot"])
+        assert all(o % 128 == 0 for o in offs), G
+        sizes = (vec, vec, vec, dv, wv)
+        assert all(offs[i + 1] - offs[i] >= sizes[i] for i in range(5)), G
+
+
+def test_launch_shape_fits_one_cta_per_sm_limits(plans):
+    for G in plans[1]:
+        assert G["TX"] * G["TY"] == G["nthr"] * G["npt"], G
+        assert G["nthr"] * G["G4"] <= 1024, G
+        assert G["smem"] <= 227 * 1024, G
+        assert 1 <= G["grid"] <= 512, G
+
+
+def test_tiles_blocks_and_split_cover_the_work_once(plans):
+    for G in plans[1]:
+        assert (G["ncx"] - 1) * G["TX"] < G["nx"] - 1 <= G["ncx"] * G["TX"], G
+        assert (G["ncy"] - 1) * G["TY"] < G["ny"] - 1 <= G["ncy"] * G["TY"], G
+        bw = 4 * G["G4"]
+        assert (G["nob"] - 1) * bw < G["Np"] <= G["nob"] * bw, G
+        assert G["s0"] == 0 and G["sN"] == G["F"] and G["mono"] == 1, G
+        # balanced: no CTA carries much more than an equal share of planes and halo planes
+        nzo = G["nz"] - 1
+        fair = (G["F"] + 2 * (G["F"] // nzo)) / G["grid"]
+        assert G["maxcost"] <= fair + nzo + 4, G
