@@ -13,7 +13,9 @@ and start coordinate are multiples of 16 bytes, 128-byte aligned slots, a
 transaction count below the mbarrier's 2^20, at most 1024 threads and 227 KB of
 shared memory per CTA, column tiles that cover the interior nodes, orbital
 blocks that cover the orbitals, and a split that hands out every column-plane
-exactly once in order.  Needs nvcc and the built library, no GPU.
+exactly once in order.  The same program prints the library's constant mass
+stencil, which is compared with a row of the oracle's assembled mass matrix.
+Needs nvcc and the built library, no GPU.
 """
 import os
 import shutil
@@ -67,6 +69,18 @@ int main() {
       }
     }
   }
+  // the constant mass stencil of the library (host-computed), for three box shapes
+  const double boxes[][3] = {{0.5, 0.5, 0.5}, {0.4, 0.75, 1.3}, {2.0, 0.125, 0.3}};
+  for (auto& h : boxes) {
+    Grid g{};
+    g.nx = g.ny = g.nz = 6;
+    g.hx = h[0]; g.hy = h[1]; g.hz = h[2];
+    Weights27 w{};
+    mass_weights(g, &w);
+    std::printf("M %.17g %.17g %.17g", h[0], h[1], h[2]);
+    for (int o = 0; o < 27; ++o) std::printf(" %.17g", w.w[o]);
+    std::printf("\n");
+  }
   return 0;
 }
 '''
@@ -94,18 +108,20 @@ def plans():
                         "-I", os.path.join(ROOT, "include"), src, "-o", exe, "-L", LIBDIR, "-lparo",
                         "-Xlinker", "-rpath=" + LIBDIR, "-lcuda"], check=True, capture_output=True, timeout=600)
         out = subprocess.run([exe], capture_output=True, text=True, check=True, timeout=600).stdout
-    counts, geoms = {}, []
+    counts, geoms, mass = {}, [], []
     for line in out.splitlines():
         t = line.split()
-        if t[0] == "N":
+        if t[0] == "M":
+            mass.append(([float(v) for v in t[1:4]], [float(v) for v in t[4:]]))
+        elif t[0] == "N":
             counts[tuple(int(v) for v in t[1:5])] = int(t[5])
         elif t[0] == "G":
             geoms.append(dict(zip(FIELDS, (int(v) for v in t[1:]))))
-    return counts, geoms
+    return counts, geoms, mass
 
 
 def test_every_mesh_and_orbital_count_has_a_geometry(plans):
-    counts, geoms = plans
+    counts, geoms, _ = plans
     assert len(counts) == 10 * 64
     assert all(n >= 1 for n in counts.values()), [k for k, n in counts.items() if n == 0]
     assert len(geoms) == sum(counts.values())
@@ -149,3 +165,24 @@ def test_tiles_blocks_and_split_cover_the_work_once(plans):
         nzo = G["nz"] - 1
         fair = (G["F"] + 2 * (G["F"] // nzo)) / G["grid"]
         assert G["maxcost"] <= fair + nzo + 4, G
+
+
+def test_library_mass_stencil_equals_the_oracle_mass_matrix(plans):
+    # the 27 weights the library applies for M (computed on the host at handle
+    # creation) against a row of the oracle's element-by-element assembled M
+    import numpy as np
+
+    from oracle import paro as O
+
+    mass = plans[2]
+    assert len(mass) == 3
+    for h, w in mass:
+        mesh = O.Mesh((6, 6, 6), (0.0, 0.0, 0.0), tuple(6 * v for v in h))
+        M = O.assemble(mesh, np.zeros(8 * 216), 0.0).M.tocsr()
+        row = mesh.interior_index(3, 3, 3)
+        for dz in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    ref = M[row, mesh.interior_index(3 + dx, 3 + dy, 3 + dz)]
+                    got = w[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)]
+                    assert abs(got - ref) <= 1e-15 * abs(ref), (h, dx, dy, dz, got, ref)
