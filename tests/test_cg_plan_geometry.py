@@ -13,7 +13,9 @@ and start coordinate are multiples of 16 bytes, 128-byte aligned slots, a
 transaction count below the mbarrier's 2^20, at most 1024 threads and 227 KB of
 shared memory per CTA, column tiles that cover the interior nodes, orbital
 blocks that cover the orbitals, and a split that hands out every column-plane
-exactly once in order.  The same program prints the library's constant mass
+exactly once in order.  The two-phase CG kernel (the float64 path) gets the
+same checks from ``paro::cg_plan_geometry`` in float32 and float64.  The same
+program prints the library's constant mass
 stencil, which is compared with a row of the oracle's assembled mass matrix.
 Needs nvcc and the built library, no GPU.
 """
@@ -69,6 +71,24 @@ int main() {
       }
     }
   }
+  // the two-phase CG kernel (float64 path, and the float32 fallback): one geometry per (mesh, Np)
+  for (auto& m : meshes) {
+    Grid g{};
+    g.nx = m[0]; g.ny = m[1]; g.nz = m[2];
+    g.Px = g.nx + 1; g.Py = g.ny + 1; g.Pz = g.nz + 1;
+    g.G = (long long)g.Px * g.Py * g.Pz;
+    g.nI = (g.nx - 1) * (g.ny - 1) * (g.nz - 1);
+    for (int Np = 4; Np <= 256; Np += 4)
+      for (int sz = 4; sz <= 8; sz += 4) {
+        K1Geom G{};
+        int bw = 0;
+        cudaError_t e = sz == 4 ? cg_plan_geometry<float>(g, Np, 152, &G, &bw)
+                                : cg_plan_geometry<double>(g, Np, 152, &G, &bw);
+        std::printf("P %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %u %zu\n", g.nx, g.ny, g.nz, Np,
+                    sz, (int)e, bw, G.TX, G.TY, G.DX, G.npt, G.nthr, G.G4, G.nob, G.ncx, G.ncy, G.grid, G.off_p,
+                    G.off_d, G.off_w, (unsigned)G.tx_bytes, G.smem);
+      }
+  }
   // the constant mass stencil of the library (host-computed), for three box shapes
   const double boxes[][3] = {{0.5, 0.5, 0.5}, {0.4, 0.75, 1.3}, {2.0, 0.125, 0.3}};
   for (auto& h : boxes) {
@@ -87,6 +107,7 @@ int main() {
 
 FIELDS = ("nx ny nz Np TX TY DX ncx ncy nob grid G4 npt nthr off_p off_s off_d off_w slot tx smem "
           "s0 sN F mono maxcost").split()
+TWO = "nx ny nz Np sz rc bw TX TY DX npt nthr G4 nob ncx ncy grid off_p off_d off_w tx smem".split()
 KWS = 28  # packed operator weights per node (27 + one pad)
 
 
@@ -108,20 +129,22 @@ def plans():
                         "-I", os.path.join(ROOT, "include"), src, "-o", exe, "-L", LIBDIR, "-lparo",
                         "-Xlinker", "-rpath=" + LIBDIR, "-lcuda"], check=True, capture_output=True, timeout=600)
         out = subprocess.run([exe], capture_output=True, text=True, check=True, timeout=600).stdout
-    counts, geoms, mass = {}, [], []
+    counts, geoms, mass, two = {}, [], [], []
     for line in out.splitlines():
         t = line.split()
-        if t[0] == "M":
+        if t[0] == "P":
+            two.append(dict(zip(TWO, (int(v) for v in t[1:]))))
+        elif t[0] == "M":
             mass.append(([float(v) for v in t[1:4]], [float(v) for v in t[4:]]))
         elif t[0] == "N":
             counts[tuple(int(v) for v in t[1:5])] = int(t[5])
         elif t[0] == "G":
             geoms.append(dict(zip(FIELDS, (int(v) for v in t[1:]))))
-    return counts, geoms, mass
+    return counts, geoms, mass, two
 
 
 def test_every_mesh_and_orbital_count_has_a_geometry(plans):
-    counts, geoms, _ = plans
+    counts, geoms, _, _ = plans
     assert len(counts) == 10 * 64
     assert all(n >= 1 for n in counts.values()), [k for k, n in counts.items() if n == 0]
     assert len(geoms) == sum(counts.values())
@@ -186,3 +209,25 @@ def test_library_mass_stencil_equals_the_oracle_mass_matrix(plans):
                     ref = M[row, mesh.interior_index(3 + dx, 3 + dy, 3 + dz)]
                     got = w[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)]
                     assert abs(got - ref) <= 1e-15 * abs(ref), (h, dx, dy, dz, got, ref)
+
+
+def test_two_phase_kernel_geometry_obeys_the_same_rules(plans):
+    two = plans[3]
+    assert len(two) == 10 * 64 * 2
+    for G in two:
+        assert G["rc"] == 0, G
+        sz, bw = G["sz"], G["bw"]
+        assert bw == 4 * G["G4"] and (G["nob"] - 1) * bw < G["Np"] <= G["nob"] * bw, G
+        for dim in (bw, G["TX"] + 2, G["TY"] + 2, G["DX"], G["TX"], G["TY"], KWS):
+            assert 1 <= dim <= 256, G
+        assert (sz * bw) % 16 == 0 and (sz * G["DX"]) % 16 == 0 and (sz * KWS) % 16 == 0 and G["TX"] % 4 == 0, G
+        vec = (G["TX"] + 2) * (G["TY"] + 2) * bw * sz
+        dv = G["DX"] * (G["TY"] + 2) * sz
+        wv = KWS * G["TX"] * G["TY"] * sz
+        assert G["tx"] == 2 * vec + dv + wv and G["tx"] < 2 ** 20, G
+        offs = (0, G["off_p"], G["off_d"], G["off_w"])
+        assert all(o % 128 == 0 for o in offs) and all(offs[i + 1] - offs[i] >= (vec, vec, dv)[i] for i in range(3)), G
+        assert G["TX"] * G["TY"] == G["nthr"] * G["npt"] and G["nthr"] * G["G4"] <= 1024, G
+        assert G["smem"] <= 227 * 1024 and G["grid"] >= 1, G
+        assert (G["ncx"] - 1) * G["TX"] < G["nx"] - 1 <= G["ncx"] * G["TX"], G
+        assert (G["ncy"] - 1) * G["TY"] < G["ny"] - 1 <= G["ncy"] * G["TY"], G
