@@ -173,3 +173,19 @@ def test_binding_constants_match_the_header():
     assert len(shared) >= 10, shared
     for k in shared:
         assert getattr(B, k) == defines[k], k
+
+
+def test_mesh_creation_without_a_gpu_returns_an_error(lib):
+    # on a host without a usable GPU the library reports the CUDA failure through
+    # its status and message: there is no host fallback to fall into
+    from paper_1405_0260_gb300 import binding as B
+
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    lo = (ctypes.c_double * 3)(-1, -1, -1)
+    hi = (ctypes.c_double * 3)(1, 1, 1)
+    rc = lib.paro_mesh_create(ctypes.byref(h), 4, 4, 4, lo, hi, 0, None)
+    assert rc in (-2, -7) and h.value is None  # PARO_ERR_CUDA or PARO_ERR_OOM, no handle
+    assert "cuda" in B.paro_last_error(None).lower()
