@@ -44,3 +44,10 @@ def test_peak_comes_from_the_measured_file_else_the_fallback(tmp_path, monkeypat
     assert bench.peaks() == (6804.4, "measured")
     monkeypatch.setattr(bench, "PEAKS", str(tmp_path / "absent.json"))
     assert bench.peaks() == (6800.0, "fallback")
+
+
+def test_cores_used_is_cpu_time_over_wall_time():
+    assert bench.cores_used(7.5, 6.7) == 1
+    assert bench.cores_used(31.0, 8.0) == 4
+    assert bench.cores_used(0.1, 10.0) == 1
+    assert bench.cores_used(1.0, 0.0) == 1
