@@ -279,7 +279,8 @@ int paro_small_eig_static(int N, const double* GA, const double* GB, double* C, 
                           void* cuda_stream);
 
 /* Message describing the last error on this handle ("" if none).  NULL handle:
- * the last paro_mesh_create failure.  The string lives until the next call. */
+ * the last paro_mesh_create failure on the calling host thread.  The string
+ * lives until the next call. */
 const char* paro_last_error(paro_mesh m);
 
 /* Interior node count (nx-1)(ny-1)(nz-1) of a handle (PARO_ERR_ARG on NULL). */

@@ -89,7 +89,9 @@ struct paro_mesh_s {
   MGHier mg;
 };
 
-static std::string g_create_err;
+// Message of the last paro_mesh_create failure, one per host thread (creations on
+// different threads do not race on it).
+static thread_local std::string g_create_err;
 
 namespace {
 

@@ -189,3 +189,34 @@ def test_mesh_creation_without_a_gpu_returns_an_error(lib):
     rc = lib.paro_mesh_create(ctypes.byref(h), 4, 4, 4, lo, hi, 0, None)
     assert rc in (-2, -7) and h.value is None  # PARO_ERR_CUDA or PARO_ERR_OOM, no handle
     assert "cuda" in B.paro_last_error(None).lower()
+
+
+def test_create_error_message_is_per_thread(lib):
+    # two host threads whose creations fail for different reasons each read their own message
+    import threading
+
+    from paper_1405_0260_gb300 import binding as B
+
+    lo = (ctypes.c_double * 3)(-1, -1, -1)
+    hi = (ctypes.c_double * 3)(1, 1, 1)
+    cases = {"cells": (1, lo, hi, "cells per axis"), "box": (4, hi, lo, "lo < hi")}
+    seen = {}
+    barrier = threading.Barrier(2)
+
+    def run(name):
+        n, a, b, want = cases[name]
+        ok = True
+        for _ in range(200):
+            h = ctypes.c_void_p()
+            rc = lib.paro_mesh_create(ctypes.byref(h), n, 4, 4, a, b, 0, None)
+            if _ == 0:
+                barrier.wait()
+            ok &= rc == -1 and want in B.paro_last_error(None)
+        seen[name] = ok
+
+    ts = [threading.Thread(target=run, args=(k,)) for k in cases]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert seen == {"cells": True, "box": True}
