@@ -220,3 +220,19 @@ def test_create_error_message_is_per_thread(lib):
     for t in ts:
         t.join()
     assert seen == {"cells": True, "box": True}
+
+
+def test_readme_c_example_compiles_and_links_against_the_library(lib):
+    # the C example of the README stays in step with the header and the exports
+    from paper_1405_0260_gb300 import binding as B
+
+    text = open(os.path.join(ROOT, "README.md")).read()
+    blocks = re.findall(r"```c\n(.*?)```", text, flags=re.S)
+    assert len(blocks) == 1
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "ex.c")
+        so = os.path.join(d, "libex.so")
+        open(c, "w").write(blocks[0])
+        subprocess.run(["gcc", "-shared", "-fPIC", "-Wall", "-Werror", "-I", os.path.dirname(HEADER), c, "-o", so,
+                        "-L", os.path.dirname(B.LIB_PATH), "-lparo", "-Wl,--no-undefined", "-lm"],
+                       check=True, capture_output=True, timeout=120)
