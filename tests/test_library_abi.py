@@ -236,3 +236,18 @@ def test_readme_c_example_compiles_and_links_against_the_library(lib):
         subprocess.run(["gcc", "-shared", "-fPIC", "-Wall", "-Werror", "-I", os.path.dirname(HEADER), c, "-o", so,
                         "-L", os.path.dirname(B.LIB_PATH), "-lparo", "-Wl,--no-undefined", "-lm"],
                        check=True, capture_output=True, timeout=120)
+
+
+def test_product_package_never_reaches_the_oracle():
+    # the oracle is test infrastructure: the package and its CUDA sources neither
+    # import nor include anything of it
+    pkg = os.path.join(ROOT, "paper_1405_0260_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            path = os.path.join(dirpath, f)
+            if f.endswith(".py"):
+                text = open(path).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle\b", text, flags=re.M), path
+            elif f.endswith((".cu", ".cuh", ".h")):
+                text = open(path).read()
+                assert not re.search(r'#include\s+[<"][^>"]*oracle', text), path
