@@ -399,3 +399,18 @@ def test_paro_resumes_from_its_state_bit_for_bit():
     half = O.paro(ops, p.U0, pcg_tol=1e-12, fixed_outer=2)
     rest = O.paro(ops, half.U, pcg_tol=1e-12, fixed_outer=2, lam0=half.lam)
     assert np.array_equal(rest.lam, full.lam) and np.array_equal(rest.U, full.U)
+
+
+def test_buffer_orbitals_converge_the_occupied_ones_in_fewer_iterations():
+    # Algorithm 3.2: iterating N + m orbitals and testing the lowest N converges
+    # those N to the same values, faster: the source problems damp the error in
+    # orbital i by about (lambda_i + sigma) / (lambda_(N+m+1) + sigma) per step
+    outer = []
+    for N in (4, 7, 10):
+        p = W.harmonic(nc=10, L=5.0, N=N, seed=21, sigma=0.0)
+        ops = O.assemble(O.Mesh(p.n, p.lo, p.hi), p.Vq, p.sigma)
+        res = O.paro(ops, p.U0, tol=1e-10, max_outer=500, pcg_tol=1e-12, n_check=4)
+        lam = _lowest(ops, 4, 1.0)
+        assert np.max(np.abs(res.lam[:4] - lam)) < 1e-8
+        outer.append(res.outer)
+    assert outer[0] > outer[1] > outer[2], outer
