@@ -414,3 +414,20 @@ def test_buffer_orbitals_converge_the_occupied_ones_in_fewer_iterations():
         assert np.max(np.abs(res.lam[:4] - lam)) < 1e-8
         outer.append(res.outer)
     assert outer[0] > outer[1] > outer[2], outer
+
+
+@pytest.mark.parametrize("sigma", [0.0, 2.0])
+def test_eigenvalue_error_contracts_at_the_shifted_inverse_iteration_rate(sigma):
+    # one outer step applies (H + sigma M)^-1 (Lambda + sigma) M to the orbitals and
+    # projects: the vector error of the highest tested level falls by about
+    # (lambda_N + sigma) / (lambda_(N+1) + sigma) per step, its eigenvalue error by
+    # the square of that
+    p = W.harmonic(nc=10, L=5.0, N=4, seed=21, sigma=sigma)
+    ops = O.assemble(O.Mesh(p.n, p.lo, p.hi), p.Vq, p.sigma)
+    lam = _lowest(ops, 5, 1.0)
+    res = O.paro(ops, p.U0, tol=1e-13, max_outer=200, pcg_tol=1e-13)
+    err = np.abs(np.array(res.history)[:, 3] - lam[3])
+    mid = (err[:-1] < 1e-4) & (err[1:] > 1e-11)
+    observed = np.median(err[1:][mid] / err[:-1][mid])
+    predicted = ((lam[3] + sigma) / (lam[4] + sigma)) ** 2
+    assert mid.sum() >= 5 and abs(observed / predicted - 1) < 0.06, (observed, predicted)
