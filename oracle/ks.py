@@ -201,6 +201,13 @@ def direct_energy(mesh: P.Mesh, Vext_q: np.ndarray, U: np.ndarray, occ: np.ndarr
 # ---------------------------------------------------------------------------
 
 
+def mix_density(rho_in: np.ndarray, rho_out: np.ndarray, mix: float) -> np.ndarray:
+    """Linear mixing of the next input density: move rho_in the fraction `mix` of
+    the way to the output density (mix = 1: no damping, the plain fixed-point
+    step; mix -> 0: the input density stays)."""
+    return (1.0 - mix) * rho_in + mix * rho_out
+
+
 @dataclass
 class SCFResult:
     U: np.ndarray
@@ -240,7 +247,7 @@ def scf(mesh: P.Mesh, Vext_q: np.ndarray, U0: np.ndarray, occ: np.ndarray, sigma
         dl = np.max(np.abs(rr.lam[:k] - lam[:k]))
         U, lam = rr.U, rr.lam
         rho_out = density_gauss(mesh, U, occ)
-        rho_in = (1.0 - mix) * rho_in + mix * rho_out
+        rho_in = mix_density(rho_in, rho_out, mix)
         history.append(lam.copy())
         charge.append(integrate(mesh, rho_in))
         outer += 1

@@ -118,3 +118,28 @@ def test_total_energy_band_form_equals_direct_definition_at_self_consistency():
     # away from self-consistency the two differ (the pin has teeth)
     rho_off = 0.5 * rho
     assert abs(KS.total_energy(mesh, res.lam, occ, rho_off) - e_direct) > 1e-3
+
+
+def test_mixing_moves_the_input_density_toward_the_output_by_the_mixing_fraction():
+    # one SCF iteration from the same start with three mixing fractions: mix = 1 is
+    # the undamped fixed-point step (the new input density is the output density of
+    # the new orbitals), a tiny mix leaves the input density where it was, and the
+    # change is linear in the fraction.  A mixing rule with the roles of rho_in and
+    # rho_out swapped fails the first two.
+    nc, L = 8, 5.0
+    mesh = O.Mesh((nc, nc, nc), (-L, -L, -L), (L, L, L))
+    X = O.gauss_points(mesh).reshape(-1, 3)
+    Vext = -2.0 / np.sqrt((X ** 2).sum(1) + 0.25)
+    p = W.harmonic(nc=nc, L=L, N=2, seed=23)
+    occ = KS.occupations(2, 2)
+    rho0 = KS.density_gauss(mesh, O.rayleigh_ritz(O.assemble(mesh, Vext, 3.0), p.U0).U, occ)
+    runs = {m: KS.scf(mesh, Vext, p.U0, occ, sigma=3.0, mix=m, fixed_outer=1) for m in (1.0, 1e-3, 0.3)}
+    full = runs[1.0]
+    rho_out = KS.density_gauss(mesh, full.U, occ)
+    step = KS.integrate(mesh, np.abs(rho_out - rho0))
+    assert step > 1e-3  # the first SCF step does move the density
+    assert KS.integrate(mesh, np.abs(full.rho_q - rho_out)) < 1e-12 * step
+    assert KS.integrate(mesh, np.abs(runs[1e-3].rho_q - rho0)) < 2e-3 * step
+    # the orbitals of the first iteration do not depend on the mixing (it acts after them)
+    assert np.allclose(runs[0.3].lam, full.lam, rtol=0, atol=1e-12)
+    assert KS.integrate(mesh, np.abs(runs[0.3].rho_q - (rho0 + 0.3 * (rho_out - rho0)))) < 1e-12 * step

@@ -35,6 +35,7 @@ def test_pins_pass_unmutated():
     KSPINS.test_hartree_of_a_gaussian_charge_converges_at_second_order()
     KSPINS.test_slater_energy_of_a_gaussian_density()
     MGPINS.test_prolongation_evaluates_the_coarse_function((8, 6, 4))
+    KSPINS.test_mixing_moves_the_input_density_toward_the_output_by_the_mixing_fraction()
 
 
 def test_wrong_gauss_abscissa_is_caught(monkeypatch):
@@ -144,3 +145,9 @@ def test_wrong_prolongation_weight_is_caught(monkeypatch):
 
     monkeypatch.setattr(MG, "prolongation_1d", bad)
     _fails(MGPINS.test_prolongation_evaluates_the_coarse_function, (8, 6, 4))
+
+
+def test_swapped_mixing_direction_is_caught(monkeypatch):
+    # rho_in <- mix rho_in + (1 - mix) rho_out: the roles of the two densities swapped
+    monkeypatch.setattr(KS, "mix_density", lambda rho_in, rho_out, mix: mix * rho_in + (1.0 - mix) * rho_out)
+    _fails(KSPINS.test_mixing_moves_the_input_density_toward_the_output_by_the_mixing_fraction)
