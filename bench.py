@@ -43,6 +43,16 @@ UNIT = "dof*orbital updates/s"
 NC, L, NORB, SIGMA = 64, 8.0, 20, 0.0
 WORKLOAD = "harmonic oscillator V=r^2/2, [-8,8]^3, 64^3 Q1 cells (250047 dofs), N=20, sigma=0"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# what the mixed path computes in: float32 CG; float-float (two float32, ~48-bit)
+# refinement residuals, b = (lambda + sigma) M u, H X, M X and the rotation;
+# tensor-core Grams from inputs rounded to 24 bits (exact BF16-digit products);
+# float64 Cholesky and small eigensolve
+DTYPE = "f32 CG; f32x2 residual/HX/MX/rotation; bf16-digit tcgen05 Grams; f64 eigensolve"
+
+
+def effective_inner_tol(inner_tol, solve_tol):
+    """The library's inner tolerance: the given one, else sqrt(solve_tol) clamped to [1e-6, 1e-3]."""
+    return inner_tol if inner_tol > 0 else min(1e-3, max(1e-6, solve_tol ** 0.5))
 GOLD = os.path.join(ROOT, "tests", "golden", "discrete_spectra.json")
 
 
@@ -76,12 +86,10 @@ def problem(rank):
     return W.harmonic(nc=NC, L=L, N=NORB, seed=2000 + rank, sigma=SIGMA)
 
 
-# DRAM traffic of the CG kernel from one ncu capture of this workload's geometry
-# (dram__bytes_read.sum + dram__bytes_write.sum = 2.208 GB over the 9 passes of the
-# autotuner's all-active timing run, profiles/k_cg1_harmonic64_N20.md).  Scaled to a
-# launch by its passes; an upper bound, since converged orbitals skip their own
-# loads and stores.
-K_CG1_TRAFFIC_PER_PASS = 2.208e9 / 9
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one pass of the
+# single-pass CG kernel with every orbital group active on this workload, from
+# one ncu capture of the current kernel; None until such a capture exists.
+K_CG2_TRAFFIC_PER_PASS = None
 
 
 def peaks():
@@ -197,6 +205,7 @@ def run_ours(args, ws, rank, local):
     prof_n = 0
     prof_units = 0
     prof_nodes = 0
+    prof_act = 0
     for i in range(max(1, min(args.steps, 3))):
         with torch.cuda.stream(stream):
             flush_l2(flush)
@@ -206,37 +215,44 @@ def run_ours(args, ws, rank, local):
         prof_n += st.prof_launches
         prof_units += st.prof_dof_orb
         prof_nodes += st.prof_node_passes
+        prof_act += st.prof_dof_orb_active
     if dist is not None:
         dist.barrier()
     ms = sum(a.elapsed_time(b) for a, b in ev)
     t_max = max_over_ranks(ms, dist, "cuda")
     value = replica_throughput(nI * N * args.steps, ws, t_max)
 
-    # roofline of the single-reduction CG kernel (the whole float32 CG loop of a
-    # correction solve in one cooperative launch, one pass per iteration).  Per unit
-    # (node x orbital) and iteration it reads r, w, s (with halo, counted once) and
-    # x, p, and writes p, s, x, r, w: 10 x 4 B = 40 B.  Per node and orbital-block
-    # pass it reads the 27 float32 operator weights (108 B) and the Jacobi diagonal (4 B).
+    # roofline of the single-pass CG kernel (the whole float32 CG loop of a
+    # correction solve in one cooperative launch, one pass per iteration).
+    # Algorithmic bytes in the method's unit: per active (node, orbital) and
+    # iteration 32 B (r, p, x read and written, q written and read back), per node
+    # and orbital-block pass 36 B (V_q 32 B and D^-1 4 B of the potential term).
+    # The kernel itself streams 32 B for every orbital of a group still iterating
+    # and 116 B of operator per node pass (27 stored float32 weights, one pad, and
+    # D^-1): the "streamed" figures.
     peak, peak_kind = peaks()
     roof = None
     if prof_n > 0 and prof_ms > 0:
-        alg_bytes = 40.0 * prof_units + 112.0 * prof_nodes
+        alg_bytes = 32.0 * prof_act + 36.0 * prof_nodes
+        streamed = 32.0 * prof_units + 116.0 * prof_nodes
         achieved = alg_bytes / (prof_ms * 1e-3) / 1e9
-        roof = {"kernel": "k_cg1<float> (single-reduction CG loop: TMA-tiled w = A D^-1 r with the vector updates, one grid barrier a pass)",
+        passes = prof_nodes / nI / prof_n  # one orbital block (N <= 32)
+        roof = {"kernel": "k_cg2 (single-pass Jacobi PCG: TMA-tiled r, q, p with halo, 27-point stencil, "
+                          "one cross-CTA reduction a pass)",
                 "bound": "hbm",
                 "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                 "frac": round(achieved / peak, 4),
-                "traffic": round(K_CG1_TRAFFIC_PER_PASS * prof_nodes / nI / prof_n),
-                "traffic_note": "ncu DRAM bytes a pass of an all-active launch x passes a launch (upper bound)",
+                "traffic": (round(K_CG2_TRAFFIC_PER_PASS * passes) if K_CG2_TRAFFIC_PER_PASS else None),
+                "alg_bytes_formula": "32 B x active (node, orbital) iterations + 36 B x node passes",
                 "launches": prof_n, "avg_launch_us": round(1e3 * prof_ms / prof_n, 2),
                 "alg_bytes_per_launch": round(alg_bytes / prof_n),
-                # one orbital block (N <= 32): passes = node passes / interior nodes, and
-                # the share of (node, orbital) pairs still active in those passes
-                "passes_per_launch": round(prof_nodes / nI / prof_n, 2),
-                "active_fraction": round(prof_units / (prof_nodes * N), 4),
-                # the per-PCG-iteration form of the metric: active (node, orbital)
-                # pairs advanced one CG iteration per second inside the kernel
-                "dof_orbital_cg_iterations_per_s": round(prof_units / (prof_ms * 1e-3))}
+                "streamed_bytes_per_launch": round(streamed / prof_n),
+                "streamed_gbs": round(streamed / (prof_ms * 1e-3) / 1e9, 1),
+                "passes_per_launch": round(passes, 2),
+                # active orbitals over the orbitals of the groups the kernel streamed
+                "active_fraction": round(prof_act / prof_units, 4) if prof_units else None,
+                # the per-PCG-iteration form of the metric
+                "dof_orbital_cg_iterations_per_s": round(prof_act / (prof_ms * 1e-3))}
 
     # end to end through the C ABI with host buffers
     Uh = torch.empty((nI, N), dtype=torch.float64, pin_memory=True)
@@ -265,18 +281,18 @@ def run_ours(args, ws, rank, local):
         ttc = time_to_converge(B, torch, p, stream, args.inner_tol)
     cpu = None
     if rank == 0 and ws == 1 and not args.skip_cpu:
-        cpu = cpu_baseline(p)
+        cpu = cpu_baseline(p, args.warmup, min(args.steps, 3))
     m.close()
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 CG + f64 refinement/RR",
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE,
             "data": "synthetic (seeded Gaussian initial orbitals, analytic potential)",
             "config": {"workload": WORKLOAD, "precision": "mixed", "parallelism": f"replicas x{ws}",
                        "l2": "flushed (256 MiB write) between steps, outside the timed events",
                        "step": "one ParO outer iteration (source problems to 1e-10 + Rayleigh-Ritz)",
-                       "inner_tol": args.inner_tol},
+                       "solve_tol": 1e-10, "inner_tol": effective_inner_tol(args.inner_tol, 1e-10)},
             "e2e": e2e, "gpu_launches": launches, "roofline": roof, "clocks": clk.summary(),
             "cpu_baseline": cpu, "time_to_converge": ttc, "wall_s_timed_region": wall,
         }
@@ -285,14 +301,43 @@ def run_ours(args, ws, rank, local):
         dist.destroy_process_group()
 
 
+def shell_angles(B, torch, m, U, modes):
+    """Largest M-principal angle, per oscillator shell, between the orbitals U and
+    the exact discrete eigenvectors.  The eigenvectors come from the stored 1-D
+    modes (tests/golden, written from the oracle's separable construction) as
+    Kronecker products; M U from the library's float64 mass apply; only
+    N x N products are formed here (cosines: resolves angles down to ~1e-8)."""
+    v1 = np.array(modes["v1d"]).T
+    V = np.stack([np.kron(v1[:, c], np.kron(v1[:, b], v1[:, a])) for a, b, c in modes["triples"]], axis=1)
+    MU = torch.empty_like(U)
+    m.apply(B.PARO_OP_M, U, MU)
+    torch.cuda.synchronize()
+    u, mu = U.cpu().numpy(), MU.cpu().numpy()
+    out = []
+    for a, b in modes["clusters"]:
+        G = u[:, a:b].T @ mu[:, a:b]
+        Cm = V[:, a:b].T @ mu[:, a:b]  # V^T M U (M symmetric)
+        Li = np.linalg.inv(np.linalg.cholesky(0.5 * (G + G.T)))
+        K = Li @ (Cm.T @ Cm) @ Li.T
+        s2 = np.clip(1.0 - np.linalg.eigvalsh(0.5 * (K + K.T)), 0.0, 1.0)
+        out.append(float(np.max(np.arcsin(np.sqrt(s2)))))
+    return out
+
+
 def time_to_converge(B, torch, p, stream, inner_tol, max_outer=400):
-    """Device time from the initial guess until max |lambda - lambda_discrete| < 1e-6 Ha."""
+    """Device time from the initial guess until max |lambda - lambda_discrete| < 1e-6 Ha
+    (one outer iteration per call, as the bench steps), the orbitals' angles there,
+    and the device time of one call to a tight stop (|delta lambda| < 1e-12) with
+    its angles."""
     try:
         with open(GOLD) as f:
-            gold = np.array(json.load(f)["harmonic_64_L8"]["values"][: p.N])
+            g = json.load(f)
+        gold = np.array(g["harmonic_64_L8"]["values"][: p.N])
+        modes = g["harmonic_64_L8_modes"]
     except Exception as e:  # stored values missing
         return {"error": f"no discrete reference values: {e}"}
-    out = {"target": "max_i |lambda_i - lambda_i(discrete, shift-invert Lanczos)| < 1e-6 Ha"}
+    out = {"target": "max_i |lambda_i - lambda_i(discrete, shift-invert Lanczos)| < 1e-6 Ha",
+           "angles": "largest M-principal angle per oscillator shell against the exact discrete eigenvectors"}
     for name, prec, params in (
         ("mixed", B.PARO_MIXED, B.paro_default_params(fixed_outer=1, solve_tol=1e-10, inner_tol=inner_tol)),
         ("fp64", B.PARO_FP64, B.paro_default_params(fixed_outer=1, solve_tol=1e-10)),
@@ -321,10 +366,27 @@ def time_to_converge(B, torch, p, stream, inner_tol, max_outer=400):
         b.record(stream)
         b.synchronize()
         out[name] = {"seconds": a.elapsed_time(b) * 1e-3, "wall_s": time.perf_counter() - t0,
-                     "outer_iters": outer, "final_err_ha": err, "reached": err < 1e-6}
+                     "outer_iters": outer, "final_err_ha": err, "reached": err < 1e-6,
+                     "max_shell_angle": max(shell_angles(B, torch, m, U, modes))}
+        if name != "mixed_mg":
+            # one call to |delta lambda| < 1e-12 (the mixed loop switches to float-float Grams near the end)
+            with torch.cuda.stream(stream):
+                U = torch.from_numpy(np.ascontiguousarray(p.U0)).cuda()
+            torch.cuda.synchronize()
+            a.record(stream)
+            rc, lam, st = m.iterate(U, None, B.paro_default_params(tol=1e-12, max_outer=max_outer, solve_tol=1e-11,
+                                                                   inner_tol=inner_tol if prec == B.PARO_MIXED else 0.0),
+                                    allow=(-4,))
+            b.record(stream)
+            b.synchronize()
+            ang = shell_angles(B, torch, m, U, modes)
+            out[name]["tight"] = {"seconds": a.elapsed_time(b) * 1e-3, "rc": rc, "outer_iters": st.outer_iters,
+                                  "final_err_ha": float(np.max(np.abs(lam - gold))),
+                                  "max_shell_angle": max(ang), "shell_angles": ang}
         m.close()
     if out["mixed"]["reached"] and out["fp64"]["reached"]:
         out["speedup_mixed_vs_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+        out["speedup_tight_mixed_vs_fp64"] = out["fp64"]["tight"]["seconds"] / out["mixed"]["tight"]["seconds"]
     if out["mixed_mg"]["reached"] and out["fp64"]["reached"]:
         out["speedup_mixed_mg_vs_fp64"] = out["fp64"]["seconds"] / out["mixed_mg"]["seconds"]
     return out
@@ -340,51 +402,103 @@ def oracle_outer_step(ops, U, lam):
 
 def cores_used(cpu_s, wall_s):
     """Host cores a timed region kept busy: process CPU time (all threads) over wall time."""
-    return max(1, round(cpu_s / wall_s)) if wall_s > 0 else 1
+    return round(cpu_s / wall_s, 2) if wall_s > 0 else None
 
 
-def cpu_baseline(p, steps=1):
-    """The oracle, as it stands, for `steps` outer iterations of the same workload."""
+def host_cpu():
+    """The host's logical CPU count and CPU model (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith("model name"):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            pass
+    return os.cpu_count(), model
+
+
+def oracle_sample(p, warmup, steps):
+    """The oracle, as it stands, on the same workload: the initial Rayleigh-Ritz
+    and `warmup` outer iterations untimed, then `steps` timed outer iterations
+    (the GPU arm times its steps after the same number of warm-up iterations)."""
     from oracle import paro as O
 
     ops = O.assemble(O.Mesh(p.n, p.lo, p.hi), p.Vq, p.sigma)
     rr = O.rayleigh_ritz(ops, p.U0)
     U, lam = rr.U, rr.lam
+    for _ in range(warmup):
+        U, lam = oracle_outer_step(ops, U, lam)
     t0, c0 = time.perf_counter(), time.process_time()
     for _ in range(steps):
         U, lam = oracle_outer_step(ops, U, lam)
-    dt, cpu = time.perf_counter() - t0, time.process_time() - c0
-    return {"value": p.n_interior * p.N * steps / dt, "unit": UNIT, "cores": cores_used(cpu, dt), "kind": "oracle",
-            "sample": f"{steps} outer iteration(s) of the full workload after the initial Rayleigh-Ritz "
-                      f"({dt:.1f} s wall, {cpu:.1f} s CPU: scipy sparse products on one thread, "
-                      f"the small dense products in the BLAS)"}
+    return time.perf_counter() - t0, time.process_time() - c0
+
+
+def cpu_record(value, dt, cpu, what):
+    ncpu, model = host_cpu()
+    return {"value": value, "unit": UNIT, "kind": "oracle", "cores": cores_used(cpu, dt),
+            "host_cpus": ncpu, "cpu_model": model,
+            "sample": f"{what} ({dt:.1f} s wall, {cpu:.1f} s CPU): the single-threaded float64 oracle "
+                      f"(scipy sparse products on one thread, the small dense products in the BLAS), not a "
+                      f"multi-core CPU ParO; cores = CPU time / wall time"}
+
+
+def cpu_baseline(p, warmup, steps):
+    """A bounded sample of the reference arm: the oracle after the same warm-up."""
+    dt, cpu = oracle_sample(p, warmup, steps)
+    return cpu_record(p.n_interior * p.N * steps / dt, dt, cpu,
+                      f"outer iterations {warmup + 1}-{warmup + steps} of the full workload after the initial "
+                      f"Rayleigh-Ritz, as the GPU arm's timed steps")
 
 
 def run_reference(args, ws, rank):
     if rank != 0:
         return
-    from oracle import paro as O
-
     p = problem(0)
-    ops = O.assemble(O.Mesh(p.n, p.lo, p.hi), p.Vq, p.sigma)
-    rr = O.rayleigh_ritz(ops, p.U0)
-    U, lam = rr.U, rr.lam
-    for _ in range(args.warmup):
-        U, lam = oracle_outer_step(ops, U, lam)
-    t0, c0 = time.perf_counter(), time.process_time()
-    for _ in range(args.steps):
-        U, lam = oracle_outer_step(ops, U, lam)
-    dt, cpu = time.perf_counter() - t0, time.process_time() - c0
+    dt, cpu = oracle_sample(p, args.warmup, args.steps)
     v = p.n_interior * p.N * args.steps / dt
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "precision": "fp64 (CPU oracle)", "parallelism": "host cores"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "kind": "oracle", "cores": cores_used(cpu, dt),
-                             "sample": f"each step one full outer iteration of the workload "
-                                       f"({dt:.1f} s wall, {cpu:.1f} s CPU over the timed steps)"},
+            "cpu_baseline": cpu_record(v, dt, cpu, f"each step one full outer iteration of the workload, "
+                                                   f"iterations {args.warmup + 1}-{args.warmup + args.steps}"),
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def run_peaks(args):
+    """The SIMT float32 and float64 FMA rates of this GPU (the roofline denominators
+    of the float-float and float64 kernels), through paro_peak_fma."""
+    import torch
+
+    from paper_1405_0260_gb300 import binding as B
+
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    out = {"workload": "peaks", "sms": nsm}
+    for name, dt, tdt in (("fp32_tflops", B.PARO_F32, torch.float32), ("fp64_tflops", B.PARO_F64, torch.float64)):
+        buf = torch.empty(8 * nsm * 256, dtype=tdt, device="cuda")
+        stream = torch.cuda.current_stream().cuda_stream
+        iters = 4096 if dt == B.PARO_F32 else 256
+        vals = [B.paro_peak_fma(dt, iters, buf.data_ptr(), stream) for _ in range(5)]
+        out[name] = max(vals)
+        out[name + "_runs"] = [round(v, 2) for v in vals]
+    with Clocks(0) as clk:
+        buf = torch.empty(8 * nsm * 256, dtype=torch.float32, device="cuda")
+        B.paro_peak_fma(B.PARO_F32, 16384, buf.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    out["clocks"] = clk.summary()
+    print(json.dumps(out), flush=True)
 
 
 def run_batch(args):
@@ -639,10 +753,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--skip-cpu", action="store_true", help="omit the cpu_baseline leg")
     ap.add_argument("--skip-converge", action="store_true", help="omit the time-to-converge leg")
-    ap.add_argument("--workload", default="harmonic64", choices=["harmonic64", "batch", "large", "ks", "clusters"],
+    ap.add_argument("--workload", default="harmonic64",
+                    choices=["harmonic64", "batch", "large", "ks", "clusters", "peaks"],
                     help="batch: independent systems (meshes 32-96^3, N 4-48) through paro_batch_iterate; "
                          "large: 192^3 cells, N = 256; ks: the Kohn-Sham cluster SCF; "
-                         "clusters: cluster-separated Rayleigh-Ritz at N = 256")
+                         "clusters: cluster-separated Rayleigh-Ritz at N = 256; "
+                         "peaks: the SIMT float32 and float64 FMA rates")
     ap.add_argument("--ks-nc", type=int, default=128, help="ks workload: cells per axis")
     ap.add_argument("--ks-max-outer", type=int, default=1500, help="ks workload: SCF iteration limit")
     ap.add_argument("--ks-mix", type=float, default=0.3, help="ks workload: linear density mixing")
@@ -658,9 +774,10 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
     ws, rank, local = dist_env()
-    if args.workload in ("batch", "large", "ks", "clusters"):
+    if args.workload in ("batch", "large", "ks", "clusters", "peaks"):
         if rank == 0 and args.impl == "ours":
-            {"batch": run_batch, "large": run_large, "ks": run_ks, "clusters": run_clusters}[args.workload](args)
+            {"batch": run_batch, "large": run_large, "ks": run_ks, "clusters": run_clusters,
+             "peaks": run_peaks}[args.workload](args)
         return
     if args.impl == "reference":
         run_reference(args, ws, rank)

@@ -107,6 +107,10 @@ typedef struct {
   int mg_coarse_sweeps; /* multigrid: sweeps on the coarsest level, 1..64 (4) */
   int hartree_precond; /* preconditioner of the Hartree (Poisson) solves of the Kohn-Sham calls:
                           PARO_PRECOND_AUTO, PARO_PRECOND_JACOBI or PARO_PRECOND_MG (PARO_PRECOND_AUTO) */
+  int wait_polls;     /* mixed handles, Jacobi correction solves: polls of every bounded device-side wait
+                         (TMA completion, the cross-CTA reduction) before the CG kernel gives up, records
+                         PARO_ERR_TIMEOUT and returns; the handle stays usable.  <= 0: the built-in limit,
+                         about a second of polling (0) */
 } paro_params;
 
 /* Statistics of a call.  Counters and times (cg_iters*, ms_*, stencil_applies,
@@ -130,6 +134,8 @@ typedef struct {
   long long prof_node_passes;  /* profile != 0: sum over their operator passes of n_interior x orbital blocks */
   int rr_tc_steps;             /* Rayleigh-Ritz steps whose Gram matrices ran on the tensor cores (mixed handles) */
   long long poisson_cg_iters;  /* CG iterations of the Hartree (Poisson) solves of a Kohn-Sham call */
+  long long prof_dof_orb_active; /* profile != 0: sum over their operator passes of n_interior x orbitals still
+                                    iterating (prof_dof_orb counts every orbital of a streamed group) */
 } paro_stats;
 
 void paro_default_params(paro_params* p);
@@ -267,16 +273,34 @@ int paro_ks_density_in(paro_mesh m, double* rho_q);
  *   theta  : device, N float64 out, ascending.
  *   cuda_stream : cudaStream_t the work is ordered on (NULL = legacy default stream).
  * Returns PARO_OK, PARO_ERR_ARG, PARO_ERR_NOT_SPD (non-positive Cholesky pivot:
- * C and theta are then not written) or PARO_ERR_CUDA.  The call synchronises the
- * stream (it reads back the status word).
+ * C and theta are then not written), PARO_ERR_NOT_CONVERGED (the cyclic Jacobi
+ * sweep limit ran out before the off-diagonal part reached the float64 rounding
+ * floor: C and theta are written but C^T G_A C is only close to diagonal) or
+ * PARO_ERR_CUDA.  Every call waits for the stream to finish: it reads the
+ * status word back to the host.
  * The caller owns GA, GB, C and theta; the library allocates nothing, neither
- * cudaMalloc nor any allocating library routine.  The first call on a device
- * looks up the array's device address with that device current (a one-time
- * set-up per device); make that first call before any stream capture.  All
- * calls share the one array and it keeps the last call's contents, so calls
- * whose work overlaps on the GPU (different streams, threads) race: order them. */
+ * cudaMalloc nor any allocating library routine.  The array's device address
+ * belongs to the CUDA context the call runs in (the thread's current context,
+ * else the current device's primary context): the first call in each context
+ * looks it up once with that context current (a one-time set-up; make that
+ * first call before any stream capture), later calls in the same context reuse
+ * it, and a new context (for instance after cudaDeviceReset) gets its own
+ * look-up.  All calls share the one array and it keeps the last call's
+ * contents, so calls whose work overlaps on the GPU (different streams,
+ * threads) race: order them. */
 int paro_small_eig_static(int N, const double* GA, const double* GB, double* C, double* theta,
                           void* cuda_stream);
+
+/* Measurement aid (the paper has no counterpart): the float32 (dtype PARO_F32)
+ * or float64 (PARO_F64) fused multiply-add rate of the GPU's SIMT pipes, the
+ * roofline denominator of the library's float-float and float64 kernels.  Runs
+ * 8 x SMs blocks of 256 threads, each thread 8 independent FMA chains for
+ * 16 x iters steps, twice, and times the second run with CUDA events on
+ * cuda_stream.  out: device scratch of at least 8 x SMs x 256 elements of the
+ * dtype (caller-owned, overwritten).  *tflops: host out, 10^12 flop/s (an FMA
+ * counts 2).  Returns PARO_OK, PARO_ERR_ARG or PARO_ERR_CUDA; synchronises the
+ * stream. */
+int paro_peak_fma(int dtype, int iters, void* out, double* tflops, void* cuda_stream);
 
 /* Message describing the last error on this handle ("" if none).  NULL handle:
  * the last paro_mesh_create failure on the calling host thread.  The string

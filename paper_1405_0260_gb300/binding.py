@@ -40,6 +40,7 @@ class paro_params(C.Structure):
         ("max_refine", C.c_int), ("check_every", C.c_int), ("fixed_outer", C.c_int),
         ("profile", C.c_int), ("n_clusters", C.c_int), ("cluster_size", C.POINTER(C.c_int)),
         ("precond", C.c_int), ("mg_nu", C.c_int), ("mg_coarse_sweeps", C.c_int), ("hartree_precond", C.c_int),
+        ("wait_polls", C.c_int),
     ]
 
     def set_clusters(self, sizes):
@@ -61,7 +62,7 @@ class paro_stats(C.Structure):
         ("stencil_applies", C.c_longlong), ("kernel_launches", C.c_longlong),
         ("prof_launches", C.c_longlong), ("prof_ms", C.c_double), ("prof_dof_orb", C.c_longlong),
         ("prof_node_passes", C.c_longlong), ("rr_tc_steps", C.c_int),
-        ("poisson_cg_iters", C.c_longlong),
+        ("poisson_cg_iters", C.c_longlong), ("prof_dof_orb_active", C.c_longlong),
     ]
 
     def as_dict(self):
@@ -346,6 +347,17 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def paro_peak_fma(dtype, iters, out_ptr, stream=0):
+    """float32 / float64 FMA rate of the SIMT pipes in TFLOP/s (a measurement aid)."""
+    f = lib().paro_peak_fma
+    f.argtypes = [C.c_int, C.c_int, C.c_void_p, C.POINTER(C.c_double), C.c_void_p]
+    f.restype = C.c_int
+    t = C.c_double(0.0)
+    rc = f(int(dtype), int(iters), C.c_void_p(out_ptr), C.byref(t), C.c_void_p(stream))
+    _check(rc, None)
+    return t.value
 
 
 def paro_small_eig_static(N, GA_ptr, GB_ptr, C_ptr, theta_ptr, stream=0):

@@ -14,6 +14,7 @@
 #include "cg.cuh"
 #include "mg.cuh"
 #include "common.cuh"
+#include "tma.cuh"
 
 using namespace paro;
 
@@ -72,6 +73,17 @@ struct paro_mesh_s {
   double *w64 = nullptr, *dt64 = nullptr;
   CGPlan<float>* plan32 = nullptr;
   CGPlan<double>* plan64 = nullptr;
+  // single-pass float32 CG (group-major vectors over the same float32 buffers)
+  CG2Plan* plan2 = nullptr;
+  double* cg2part = nullptr;
+  double* cg2tot = nullptr;
+  const char* tune2_source = "default";
+  // layout of the float32 CG buffers: 0 node-major (two-reduction and single-reduction
+  // CG, multigrid, paro_apply), 1 group-major (single-pass CG).  A change zeroes them,
+  // since each layout relies on zero Dirichlet rows at its own positions.
+  int f32_layout = 0;
+  // fxh/fxl hold the float-float split of x (set where x = u was just split)
+  bool x_split_fresh = false;
   // Kohn-Sham: box origin, the float64 handle of the Poisson operator K/2 (V = 0,
   // sigma = 0) that solves for the Hartree potential, and Gauss-point fields
   double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
@@ -119,6 +131,8 @@ namespace {
   } while (0)
 
 constexpr int kProfPairs = 256;
+
+int set_f32_layout(paro_mesh m, int want);
 
 int fail(paro_mesh m, int code, const std::string& msg) {
   m->err = msg;
@@ -176,6 +190,8 @@ CGState cg_state(paro_mesh m, bool refine) {
 }
 
 void free_plans(paro_mesh m) {
+  delete m->plan2;
+  m->plan2 = nullptr;
   if (m->plan32) {
     if (m->plan32->exec_zero) cudaGraphExecDestroy(m->plan32->exec_zero);
     if (m->plan32->exec_warm) cudaGraphExecDestroy(m->plan32->exec_warm);
@@ -340,12 +356,86 @@ int make_plan(paro_mesh m, int Np, CGPlan<T>** out, T* x, T* b, T* r, T* p, T* q
   return PARO_OK;
 }
 
+// Geometry of the single-pass CG: from the cache (key suffix "|cg2"), else timed.
+int autotune_cg2(paro_mesh m, CG2Plan* P) {
+  std::vector<K1Geom> cand;
+  cg2_candidates(m->g, P->args.Np, m->nsm, &cand);
+  if (cand.empty()) return PARO_OK;
+  const char* off = std::getenv("PARO_AUTOTUNE");
+  CK(cg2_prepare_geo(P, cand[0]));
+  m->tune2_source = "default";
+  if ((off && off[0] == '0') || cand.size() < 2) return PARO_OK;
+  int dev = 0;
+  cudaDeviceProp prop{};
+  CK(cudaGetDevice(&dev));
+  CK(cudaGetDeviceProperties(&prop, dev));
+  const std::string key = std::string(prop.name) + "|" + std::to_string(m->g.nx) + "x" + std::to_string(m->g.ny) +
+                          "x" + std::to_string(m->g.nz) + "|Np" + std::to_string(P->args.Np) + "|cg2";
+  const char* path = std::getenv("PARO_AUTOTUNE_CACHE");
+  std::map<std::string, TuneEntry> cache;
+  if (path) {
+    cache = tune_cache_read(path);
+    auto it = cache.find(key);
+    if (it != cache.end())
+      for (const K1Geom& G : cand)
+        if (G.TX == it->second.TX && G.TY == it->second.TY && G.G4 * 4 == it->second.bw) {
+          CK(cg2_prepare_geo(P, G));
+          m->tune2_source = "cache";
+          return PARO_OK;
+        }
+  }
+  int chosen = -1, tried = 0;
+  float us = 0.f;
+  CK(cg2_autotune(P, m->st, 8, &chosen, &us, &tried));
+  m->tune2_source = "timed";
+  if (chosen >= 0 && path) {
+    TuneEntry e;
+    e.TX = cand[chosen].TX;
+    e.TY = cand[chosen].TY;
+    e.bw = cand[chosen].G4 * 4;
+    e.us = us;
+    cache[key] = e;
+    tune_cache_write(path, cache);
+  }
+  return PARO_OK;
+}
+
 int make_plans(paro_mesh m, int Np) {
   free_plans(m);
   TRY(make_plan<double>(m, Np, &m->plan64, m->x, m->b, m->r, m->p0, m->q, m->dinv64, m->dt64, m->w64, m->coef64));
-  if (m->precision == PARO_MIXED)
+  if (m->precision == PARO_MIXED) {
+    m->f32_layout = 0;
     TRY(make_plan<float>(m, Np, &m->plan32, m->x32, m->b32, m->r32, m->p32a, m->q32, m->dinv32, m->dt32, m->w32,
                          m->coef32, m->s32, m->r32b, m->q32b, m->s32b));
+    CG2Plan* P = new CG2Plan();
+    m->plan2 = P;
+    P->nsm = m->nsm;
+    P->dpitch = m->dpitch;
+    P->dinv_tma = m->dt32;
+    P->wcoef = m->w32;
+    CG2Args& a = P->args;
+    a.g = m->g;
+    a.N = Np;
+    a.Np = Np;
+    a.x = m->x32;
+    a.r[0] = m->b32;
+    a.r[1] = m->r32;
+    a.q[0] = m->q32;
+    a.q[1] = m->q32b;
+    a.p[0] = m->p32a;
+    a.p[1] = m->s32;
+    a.part = m->cg2part;
+    a.tot = m->cg2tot;
+    a.st = m->cgst;
+    a.spin = kSpinLimit;
+    a.inner = 1;
+    TRY(set_f32_layout(m, 1));
+    TRY(autotune_cg2(m, P));
+    if (std::getenv("PARO_PRINT_PLAN"))
+      std::fprintf(stderr, "paro single-pass CG plan: tile %dx%d, block %d orbitals x %d, %d threads, grid %d, "
+                   "smem %zu B, usable %d, geometry %s\n", P->geo.TX, P->geo.TY, P->geo.G4 * 4, P->geo.nob,
+                   P->geo.nthr * P->geo.G4, P->geo.grid, P->geo.smem, (int)P->ok, m->tune2_source);
+  }
   return PARO_OK;
 }
 
@@ -355,7 +445,7 @@ int ensure_workspace(paro_mesh m, int Np) {
   // release the previous vector workspace
   void* olds[] = {m->u,    m->x,   m->b,   m->r,   m->p0,  m->q,     m->b32,    m->x32, m->r32,
                   m->p32a, m->q32, m->s32, m->r32b, m->q32b, m->s32b, m->fxh, m->fxl, m->fah, m->fal,   m->fbh,    m->fbl, m->gpart_ff, m->gpart_tc,
-                  m->gpart, m->GA, m->GB,  m->C,   m->theta, m->eigwork, m->cgpart};
+                  m->gpart, m->GA, m->GB,  m->C,   m->theta, m->eigwork, m->cgpart, m->cg2part, m->cg2tot};
   CK(cudaStreamSynchronize(m->st));
   for (void* p : olds) dfree(m, p);
   // the Gram workspaces below are allocated only for some Np: no stale pointers
@@ -395,6 +485,9 @@ int ensure_workspace(paro_mesh m, int Np) {
   TRY(dalloc(m, &m->eigwork, (size_t)4 * Np * Np));
   // per-CTA partials: up to 4 CTAs per SM, 3 values per orbital, two buffers
   TRY(dalloc(m, &m->cgpart, (size_t)2 * 3 * 4 * m->nsm * Np));
+  // single-pass CG: 5 partial sums per orbital and CTA, and their totals
+  TRY(dalloc(m, &m->cg2part, (size_t)5 * kMaxGrid1 * Np));
+  TRY(dalloc(m, &m->cg2tot, (size_t)5 * Np));
   m->Np_alloc = Np;
   TRY(make_plans(m, Np));
   return PARO_OK;
@@ -414,6 +507,16 @@ int check_status(paro_mesh m, const char* where) {
     return fail(m, PARO_ERR_TIMEOUT, std::string(where) + ": a bounded device-side wait ran out");
   if (bits & kStatNotConverged)
     return fail(m, PARO_ERR_NOT_CONVERGED, std::string(where) + ": iteration limit reached");
+  return PARO_OK;
+}
+
+int set_f32_layout(paro_mesh m, int want) {
+  if (m->precision != PARO_MIXED || m->f32_layout == want) return PARO_OK;
+  const size_t n = sizeof(float) * (size_t)m->g.G * m->Np_alloc;
+  float* bufs[] = {m->b32, m->x32, m->r32, m->p32a, m->q32, m->s32, m->r32b, m->q32b, m->s32b};
+  for (float* b : bufs)
+    if (b) CK(cudaMemsetAsync(b, 0, n, m->st));
+  m->f32_layout = want;
   return PARO_OK;
 }
 
@@ -672,11 +775,99 @@ int check_precond(paro_mesh m, const paro_params& p) {
 // initial guess, b is given as a float-float pair in fah/fal.  Each sweep forms
 // r = b - A x in float-float arithmetic (float64-accurate), stops the columns with
 // |r| <= solve_tol |b|, solves A d = r to inner_tol with the float32 CG and adds d.
+// The same refinement around the single-pass CG (group-major correction
+// vectors).  Sweeps run without host synchronisation: residual (its float32
+// rounding goes straight into the CG's right-hand side, converged orbitals are
+// flagged skip), correction solve (a launch with no active orbital returns at
+// once), x += d with the float-float split of the new x; two sweeps, then a
+// residual whose active count the host reads, and one sweep more at a time
+// while orbitals remain open.  fxh/fxl hold the split of x on entry.
+int refine_solve_cg2(paro_mesh m, int N, const paro_params& p, paro_stats* st, double itol) {
+  const int Np = m->Np_alloc;
+  Grid& g = m->g;
+  CG2Plan* P = m->plan2;
+  CGState rs = cg_state(m, true);
+  if (p.pcg_maxit < 1) return fail(m, PARO_ERR_ARG, "pcg_maxit must be at least 1");
+  TRY(set_f32_layout(m, 1));
+  P->args.N = N;
+  P->args.spin = p.wait_polls > 0 ? (unsigned)p.wait_polls : kSpinLimit;
+  m->h_ctl[0] = itol;
+  int* ctl_int = reinterpret_cast<int*>(m->h_ctl + 1);
+  ctl_int[0] = p.pcg_maxit;
+  CK(cudaMemcpyAsync(&m->cgst->tol, m->h_ctl, sizeof(double), cudaMemcpyHostToDevice, m->st));
+  CK(cudaMemcpyAsync(&m->cgst->maxit, ctl_int, sizeof(int), cudaMemcpyHostToDevice, m->st));
+  CK(cudaMemsetAsync(&m->cgst->it_sum, 0, sizeof(long long), m->st));
+  CK(cudaMemsetAsync(&m->cgst->it_max, 0, sizeof(int), m->st));
+  if (!m->x_split_fresh) LAUNCH(1, launch_split_ff((long long)g.G * Np, m->x, m->fxh, m->fxl, m->st));
+  m->x_split_fresh = false;
+  int sweep = 0;
+  for (;;) {
+    int batch = sweep == 0 ? 2 : 1;
+    if (batch > p.max_refine - sweep) batch = p.max_refine - sweep;
+    for (int b = 0; b < batch; ++b) {
+      LAUNCH(1, launch_refine_residual_ff(g, N, Np, m->wAh, m->wAl, m->fxh, m->fxl, m->fah, m->fal, m->b32, rs,
+                                          p.solve_tol, m->st, 1));
+      if (st) st->stencil_applies += N;
+      if (m->profile) CK(cudaEventRecord(m->pev[2 * m->pev_used], m->st));
+      LAUNCH(1, cg2_launch(P, m->st));
+      if (m->profile) {
+        CK(cudaEventRecord(m->pev[2 * m->pev_used + 1], m->st));
+        m->pev_used++;
+      }
+      if (trace_on()) {
+        long long s0 = 0;
+        int mx = 0;
+        TRY(read_iters(m, N, &s0, &mx));
+      }
+      LAUNCH(1, launch_refine_update_split(g, Np, m->x, m->x32, m->cgst->skip, m->fxh, m->fxl, m->st));
+      ++sweep;
+    }
+    LAUNCH(1, launch_refine_residual_ff(g, N, Np, m->wAh, m->wAl, m->fxh, m->fxl, m->fah, m->fal, nullptr, rs,
+                                        p.solve_tol, m->st, 1));
+    if (st) st->stencil_applies += N;
+    // the open count and the status word in one round trip; a failed correction
+    // solve (timeout, non-finite value, indefinite operator) ends the refinement
+    CK(cudaMemcpyAsync(m->h_int, &m->cgst->n_active, sizeof(int), cudaMemcpyDeviceToHost, m->st));
+    CK(cudaMemcpyAsync(m->h_int + 1, &m->cgst->status, sizeof(int), cudaMemcpyDeviceToHost, m->st));
+    CK(cudaStreamSynchronize(m->st));
+    const int open = m->h_int[0];
+    if (m->h_int[1] != 0) TRY(check_status(m, "orbital_solve (float32 correction)"));
+    if (m->profile) TRY(drain_profile(m));
+    if (open == 0) break;
+    if (sweep >= p.max_refine) {
+      if (st) st->refine_sweeps = sweep;
+      TRY(check_status(m, "orbital_solve"));
+      m->err = "mixed refinement: max_refine sweeps reached";
+      return PARO_ERR_NOT_CONVERGED;
+    }
+  }
+  TRY(check_status(m, "orbital_solve (float32 correction)"));
+  if (st) {
+    long long its = 0;
+    int imax = 0;
+    CK(cudaMemcpyAsync(m->h_dbl, &m->cgst->it_sum, sizeof(long long), cudaMemcpyDeviceToHost, m->st));
+    CK(cudaMemcpyAsync(m->h_int, &m->cgst->it_max, sizeof(int), cudaMemcpyDeviceToHost, m->st));
+    CK(cudaStreamSynchronize(m->st));
+    std::memcpy(&its, m->h_dbl, sizeof(its));
+    imax = m->h_int[0];
+    st->cg_iters += its;
+    st->cg_iters_f32 += its;
+    st->cg_iters_max = imax;
+    st->refine_sweeps = sweep;
+    st->stencil_applies += its;
+  }
+  return PARO_OK;
+}
+
 int refine_solve(paro_mesh m, int N, const paro_params& p, paro_stats* st) {
   TRY(check_precond(m, p));
   // inner tolerance: given, or sqrt(solve_tol) so that two sweeps reach solve_tol
   // (clamped to what float32 CG reliably attains and to a useful minimum)
   const double itol = p.inner_tol > 0.0 ? p.inner_tol : std::fmin(1e-3, std::fmax(1e-6, std::sqrt(p.solve_tol)));
+  if (p.precond == PARO_PRECOND_JACOBI && m->plan2 && m->plan2->ok && m->profile != 2)
+    return refine_solve_cg2(m, N, p, st, itol);
+  m->x_split_fresh = false;
+  TRY(set_f32_layout(m, 0));
   const int Np = m->Np_alloc;
   Grid& g = m->g;
   CGState rs = cg_state(m, true);
@@ -746,6 +937,7 @@ int solve_packed(paro_mesh m, int N, const double* lam, const paro_params& p, pa
     LAUNCH(1, launch_apply_f64(g, Np, nullptr, &m->mw, 0.0, m->u, m->b, scale, m->st));
   }
   CK(cudaMemcpyAsync(m->x, m->u, sizeof(double) * g.G * Np, cudaMemcpyDeviceToDevice, m->st));
+  m->x_split_fresh = m->precision == PARO_MIXED;  // fxh/fxl = split(u) = split(x)
   long long its = 0;
   int itmax = 0;
   TRY(check_precond(m, p));
@@ -904,6 +1096,7 @@ struct CallScope {
     }
     if (cudaMemsetAsync(&m->cgst->work, 0, sizeof(unsigned long long), m->st) != cudaSuccess) return;
     if (cudaMemsetAsync(&m->cgst->work_nodes, 0, sizeof(unsigned long long), m->st) != cudaSuccess) return;
+    if (cudaMemsetAsync(&m->cgst->work_act, 0, sizeof(unsigned long long), m->st) != cudaSuccess) return;
     m->profile = profile == 2 ? 2 : 1;
   }
   ~CallScope() {
@@ -912,18 +1105,22 @@ struct CallScope {
       s->rr_tc_steps += (int)(m->rr_tc - tc0);
       s->poisson_cg_iters += m->ks_pois_iters - pi0;
       if (m->profile) {
-        unsigned long long w = 0, wn = 0;
+        unsigned long long w = 0, wn = 0, wa = 0;
         if (cudaMemcpyAsync(m->h_dbl, &m->cgst->work, sizeof(w), cudaMemcpyDeviceToHost, m->st) == cudaSuccess &&
             cudaMemcpyAsync(m->h_dbl + 1, &m->cgst->work_nodes, sizeof(wn), cudaMemcpyDeviceToHost, m->st) ==
+                cudaSuccess &&
+            cudaMemcpyAsync(m->h_dbl + 2, &m->cgst->work_act, sizeof(wa), cudaMemcpyDeviceToHost, m->st) ==
                 cudaSuccess &&
             cudaStreamSynchronize(m->st) == cudaSuccess) {
           std::memcpy(&w, m->h_dbl, sizeof(w));
           std::memcpy(&wn, m->h_dbl + 1, sizeof(wn));
+          std::memcpy(&wa, m->h_dbl + 2, sizeof(wa));
         }
         s->prof_launches += m->prof_launches;
         s->prof_ms += m->prof_ms;
         s->prof_dof_orb += (long long)w;
         s->prof_node_passes += (long long)wn;
+        s->prof_dof_orb_active += (long long)wa;
       }
     }
     m->profile = 0;
@@ -1054,6 +1251,7 @@ void paro_default_params(paro_params* p) {
   p->mg_nu = 1;
   p->mg_coarse_sweeps = 4;
   p->hartree_precond = PARO_PRECOND_AUTO;
+  p->wait_polls = 0;
 }
 
 int paro_mesh_create(paro_mesh* out, int nx, int ny, int nz, const double lo[3], const double hi[3], int precision,
@@ -1313,6 +1511,7 @@ int paro_apply(paro_mesh m, int N, int op, int dtype, const void* X, void* Y) {
                                 nullptr, m->fxh, m->fxl, nullptr, m->x, nullptr, nullptr, m->st));
     LAUNCH(1, launch_unpack(m->g, N, Np, m->x, static_cast<double*>(Y), m->st));
   } else {
+    TRY(set_f32_layout(m, 0));
     LAUNCH(1, launch_pack_f32(m->g, N, Np, static_cast<const float*>(X), m->b32, m->st));
     LAUNCH(1, launch_apply_f32(m->g, Np, m->coef32, m->b32, m->q32, m->st));
     LAUNCH(1, launch_unpack_f32(m->g, N, Np, m->q32, static_cast<float*>(Y), m->st));

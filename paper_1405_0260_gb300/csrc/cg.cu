@@ -1116,6 +1116,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_cg1(CGArgs<float> a, K1Geom geo,
         if (sblk[ob]) wn += (unsigned long long)a.g.nI;
       a.st->work += wu;
       a.st->work_nodes += wn;
+      a.st->work_act += (unsigned long long)s_nact * (unsigned long long)a.g.nI;
     }
     if (!pass()) {
       timed_out = true;

@@ -30,6 +30,10 @@ struct CGDevState {
   unsigned long long work;  // sum over operator passes of interior nodes x orbitals processed
   unsigned int bar_count;   // grid barrier counter of the persistent CG kernel (zeroed per launch)
   unsigned long long work_nodes;  // sum over operator passes of interior nodes x orbital blocks processed
+  unsigned int bar_flag;          // single-pass CG: number of the last pass whose totals are published
+  unsigned long long work_act;    // sum over operator passes of interior nodes x orbitals still iterating
+  long long it_sum;               // single-pass CG: iterations of every orbital, summed over solves
+  int it_max;                     // single-pass CG: largest per-orbital iteration count since the last reset
 };
 
 template <typename T>
@@ -53,6 +57,7 @@ struct K1Geom {
   int ncx, ncy, nob;  // columns per axis, orbital blocks of width 4*G4
   int grid, G4;       // CTAs (each takes an equal share of the column-planes), float4 groups per block
   int npt, nthr;      // tile nodes per thread; node slots per CTA (TX * TY = nthr * npt)
+  int slots;          // single-pass CG: depth of the TMA ring (planes in flight)
   int off_p, off_s, off_d, off_w, slot_bytes;  // byte offsets inside one ring slot
   uint32_t tx_bytes;                    // TMA bytes per slot
   size_t smem;                          // dynamic shared memory per CTA
@@ -123,6 +128,48 @@ cudaError_t cg_launch_cg1(CGPlan<float>* P, cudaStream_t st);
 // state) and prepares the fastest; *chosen: its index in cg1_candidates (-1 if
 // none ran), *best_us: its time per pass, *tried: candidates timed.
 cudaError_t cg1_autotune(CGPlan<float>* P, cudaStream_t st, int passes, int* chosen, float* best_us, int* tried);
+
+// Single-pass Jacobi PCG of the float32 correction solves (cg2.cu).  Vectors are
+// group-major: element (orbital 4 g + c, padded node n) at (g G + n) 4 + c, so a
+// group of four orbitals is one contiguous [Pz][Py][Px][4] array and a converged
+// group is neither loaded nor stored.  r[0] holds the right-hand side on entry
+// (x0 = 0) and is overwritten; x receives the solution.
+struct CG2Args {
+  Grid g;
+  int N, Np;
+  float* x;
+  float *r[2], *q[2], *p[2];  // the two buffer sets (read by pass parity, written by the other)
+  double* part;               // per-CTA partial sums [5][grid][Np]
+  double* tot;                // totals of the last pass [5][Np], written by the last CTA to arrive
+  CGDevState* st;
+  unsigned spin;              // poll limit of every bounded wait
+  int inner;                  // 1: reaching maxit is not an error (refinement carries on)
+};
+
+struct CG2Plan {
+  CG2Args args{};
+  K1Geom geo{};
+  int nsm = 152;
+  int dpitch = 0;
+  const float* dinv_tma = nullptr;
+  const float* wcoef = nullptr;
+  bool ok = false;
+  CUtensorMap mr[2];
+  CUtensorMap mq[2];
+  CUtensorMap mp[2];
+  CUtensorMap md;
+  CUtensorMap mw;
+};
+
+// Geometries (tile shape, orbital block width) for (mesh, Np), widest blocks first.
+void cg2_candidates(const Grid& g, int Np, int nsm, std::vector<K1Geom>* out);
+cudaError_t cg2_prepare_geo(CG2Plan* P, const K1Geom& geo);
+// One solve: zeroes the barrier words, then one cooperative launch.
+cudaError_t cg2_launch(CG2Plan* P, cudaStream_t st);
+// Times `passes` passes of every candidate (b = 1, tol = 0; overwrites the
+// vectors and the CG state) and prepares the fastest.
+cudaError_t cg2_autotune(CG2Plan* P, cudaStream_t st, int passes, int* chosen, float* best_us, int* tried);
+void balanced_split(long long F, int nzo, int grid, int* out);
 
 // Packed operator weights per input plane, [Pz][ny-1][nx-1][kPackedW], for the tiled kernel.
 constexpr int kPackedW = 28;

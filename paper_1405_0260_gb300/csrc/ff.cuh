@@ -20,20 +20,16 @@ struct FF {
   float hi, lo;
 };
 
-// Exact split of a float64 into hi + lo (lo rounded to 24 bits): hi is x with
-// its significand cut to 24 bits (round toward zero), lo the cut-off bits,
-// rebuilt from the integer bit pattern so no float64 arithmetic is used.
-// Magnitudes below 2^-74 keep only hi (their lo would underflow).
+// Split of a float64 into hi + lo: hi is x rounded to the nearest float, lo the
+// remainder x - hi (exact in float64: at most 29 significant bits) rounded to a
+// float, so hi + lo carries ~48 bits of x and |lo| <= ulp(hi)/2.  Rounding hi
+// to nearest (not toward zero) keeps it unbiased: kernels that use hi alone
+// (the tensor-core Grams) then see rounding errors of either sign, which
+// average out over a sum instead of shrinking every product by ~2^-24.
 __device__ __forceinline__ FF ff_split(double x) {
-  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
   FF r;
-  r.hi = __double2float_rz(x);
-  const int e = static_cast<int>((b >> 52) & 0x7FF);  // biased float64 exponent
-  const unsigned int low = static_cast<unsigned int>(b) & 0x1FFFFFFFu;  // 29 bits below float precision
-  const int fe = e - 948;  // biased float32 exponent of 2^(e - 1075), the unit of the lowest bit
-  float lo = 0.0f;
-  if (fe >= 1 && fe <= 254) lo = __fmul_rn(__uint2float_rn(low), __int_as_float(fe << 23));
-  r.lo = (b >> 63) ? -lo : lo;
+  r.hi = __double2float_rn(x);
+  r.lo = __double2float_rn(__dsub_rn(x, static_cast<double>(r.hi)));
   return r;
 }
 

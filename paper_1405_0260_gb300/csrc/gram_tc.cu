@@ -1,7 +1,8 @@
 // Gram matrix G = X^T Y of the Rayleigh-Ritz step (Step 4, eq. 3.3) on the
 // 5th-generation tensor cores (tcgen05), for the mixed path with Np <= kTcMaxNp.
 //
-// X and Y arrive as the float32 hi parts of the float-float arrays [node][Np].
+// X and Y arrive as the float32 hi parts of the float-float arrays [node][Np]
+// (each the float64 value rounded to the nearest float, an unbiased rounding).
 // The products are made exact so that the FP32 accumulator of the tensor cores
 // never rounds:
 //   * per CTA, chunk of kTcSuper = 128 nodes and column c, E_c is the power of
@@ -19,7 +20,8 @@
 //     by 2^(E_a + E_b) and added to float-float accumulators.
 // The error is the rounding of the inputs to 24 bits below the chunk's column
 // maximum (the digit rounding and the dropped lo part, together <= 2^(E_c - 24)
-// per value, unbiased), so it averages out over the nodes: about
+// per value, both to nearest and so unbiased), so it averages out over the
+// nodes: about
 // 2^-24 / sqrt(nodes) of |x| |y| for a Gram entry, instead of the
 // 2^-24-per-addition growth of a plain FP32 sum.  Levels l >= 3 (products below
 // 2^-48 of the scale) are dropped.

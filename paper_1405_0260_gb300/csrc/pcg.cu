@@ -126,7 +126,8 @@ __global__ void __launch_bounds__(kRedThreads) k_refine_residual_ff(Grid g, int 
                                                                     const float* __restrict__ xlo,
                                                                     const float* __restrict__ bhi,
                                                                     const float* __restrict__ blo,
-                                                                    float* __restrict__ rhs, CGState s, double tol) {
+                                                                    float* __restrict__ rhs, CGState s, double tol,
+                                                                    int gm) {
   __shared__ double sred[2 * kRedThreads * 4];
   double* tot = sred;
   __shared__ int cnt;
@@ -173,7 +174,11 @@ __global__ void __launch_bounds__(kRedThreads) k_refine_residual_ff(Grid g, int 
         arr[c] = fmaf(rc.hi, rc.hi, arr[c]);
         abb[c] = fmaf(bh[c], bh[c], abb[c]);
       }
-      if (rhs != nullptr) st4(rhs + gp * Np + 4 * grp, V4<float>{r[0], r[1], r[2], r[3]});
+      if (rhs != nullptr) {
+        // node-major [G][Np], or group-major [Np/4][G][4] for the single-pass CG
+        const long long e = gm ? ((long long)grp * g.G + gp) * 4 : gp * Np + 4 * grp;
+        st4(rhs + e, V4<float>{r[0], r[1], r[2], r[3]});
+      }
     }
     for (int c = 0; c < 4; ++c) {
       acc[0][c] = arr[c];
@@ -197,6 +202,31 @@ __global__ void __launch_bounds__(kRedThreads) k_refine_residual_ff(Grid g, int 
   }
   __syncthreads();
   if (threadIdx.x == 0) *s.n_active = cnt;
+}
+
+// x += d for the orbitals the correction solve ran for (d group-major), and the
+// float-float split of the new x for the next residual; skipped orbitals keep x
+// and its split.
+__global__ void k_refine_update_split(Grid g, int Np, double* __restrict__ x, const float* __restrict__ d,
+                                      const int* __restrict__ skip, float* __restrict__ xh, float* __restrict__ xl) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int groups = Np / 4;
+  if (t >= (long long)g.nI * groups) return;
+  const int n = (int)(t / groups), grp = (int)(t % groups);
+  const long long gp = interior_to_padded(g, n);
+  const float4 dv = *reinterpret_cast<const float4*>(d + ((long long)grp * g.G + gp) * 4);
+  const float dd[4] = {dv.x, dv.y, dv.z, dv.w};
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int o = 4 * grp + c;
+    if (skip[o]) continue;
+    const long long e = gp * Np + o;
+    const double v = x[e] + (double)dd[c];
+    x[e] = v;
+    const FF f = ff_split(v);
+    xh[e] = f.hi;
+    xl[e] = f.lo;
+  }
 }
 
 __global__ void k_refine_update(Grid g, int Np, double* __restrict__ x, const float* __restrict__ d,
@@ -226,9 +256,9 @@ cudaError_t launch_refine_residual(const Grid& g, int N, int Np, const double* c
 
 cudaError_t launch_refine_residual_ff(const Grid& g, int N, int Np, const float* whi, const float* wlo,
                                       const float* xhi, const float* xlo, const float* bhi, const float* blo,
-                                      float* rhs32, const CGState& s, double tol, cudaStream_t st) {
+                                      float* rhs32, const CGState& s, double tol, cudaStream_t st, int gm) {
   k_refine_residual_ff<<<red_blocks(g, Np), kRedThreads, 0, st>>>(g, N, Np, whi, wlo, xhi, xlo, bhi, blo, rhs32, s,
-                                                                  tol);
+                                                                  tol, gm);
   return cudaGetLastError();
 }
 
@@ -236,6 +266,13 @@ cudaError_t launch_refine_update(const Grid& g, int Np, double* x64, const float
                                  cudaStream_t st) {
   long long work = (long long)g.nI * Np;
   k_refine_update<<<(unsigned)((work + 255) / 256), 256, 0, st>>>(g, Np, x64, d32, skip);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_refine_update_split(const Grid& g, int Np, double* x64, const float* d32gm, const int* skip,
+                                       float* xh, float* xl, cudaStream_t st) {
+  const long long work = (long long)g.nI * (Np / 4);
+  k_refine_update_split<<<(unsigned)((work + 255) / 256), 256, 0, st>>>(g, Np, x64, d32gm, skip, xh, xl);
   return cudaGetLastError();
 }
 

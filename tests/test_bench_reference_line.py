@@ -33,5 +33,6 @@ def test_reference_arm_prints_one_contract_line():
     assert d["value"] > 0 and d["ms_per_step"] > 0 and d["vs_baseline"] is None
     assert "64^3" in d["config"]["workload"] and "N=20" in d["config"]["workload"]
     cb = d["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
+    assert cb["kind"] == "oracle" and cb["cores"] > 0 and cb["sample"] and cb["value"] == d["value"]
+    assert cb["host_cpus"] == os.cpu_count() and "cpu_model" in cb
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}

@@ -71,6 +71,29 @@ int main() {
       }
     }
   }
+  // the single-pass CG kernel (group-major vectors): its candidates
+  for (auto& m : meshes) {
+    Grid g{};
+    g.nx = m[0]; g.ny = m[1]; g.nz = m[2];
+    g.Px = g.nx + 1; g.Py = g.ny + 1; g.Pz = g.nz + 1;
+    g.G = (long long)g.Px * g.Py * g.Pz;
+    g.nI = (g.nx - 1) * (g.ny - 1) * (g.nz - 1);
+    for (int Np = 4; Np <= 256; Np += 4) {
+      std::vector<K1Geom> c;
+      cg2_candidates(g, Np, 152, &c);
+      std::printf("n %d %d %d %d %zu\n", g.nx, g.ny, g.nz, Np, c.size());
+      for (const K1Geom& G : c) {
+        long long F = (long long)G.nob * G.ncx * G.ncy * (g.nz - 1);
+        int mono = 1;
+        for (int k = 0; k < G.grid; ++k)
+          if (G.split[k + 1] < G.split[k]) mono = 0;
+        std::printf("C %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %u %zu %d %lld %lld %d %d\n",
+                    g.nx, g.ny, g.nz, Np, G.TX, G.TY, G.DX, G.ncx, G.ncy, G.nob, G.grid, G.G4, G.npt, G.nthr,
+                    G.off_p, G.off_s, G.off_d, G.off_w, G.slot_bytes, (unsigned)G.tx_bytes, G.smem, G.split[0],
+                    (long long)G.split[G.grid], F, mono, G.slots);
+      }
+    }
+  }
   // the two-phase CG kernel (float64 path, and the float32 fallback): one geometry per (mesh, Np)
   for (auto& m : meshes) {
     Grid g{};
@@ -130,9 +153,14 @@ def plans():
                         "-Xlinker", "-rpath=" + LIBDIR, "-lcuda"], check=True, capture_output=True, timeout=600)
         out = subprocess.run([exe], capture_output=True, text=True, check=True, timeout=600).stdout
     counts, geoms, mass, two = {}, [], [], []
+    counts2, geoms2 = {}, []
     for line in out.splitlines():
         t = line.split()
-        if t[0] == "P":
+        if t[0] == "n":
+            counts2[tuple(int(v) for v in t[1:5])] = int(t[5])
+        elif t[0] == "C":
+            geoms2.append(dict(zip(FIELDS, (int(v) for v in t[1:]))))
+        elif t[0] == "P":
             two.append(dict(zip(TWO, (int(v) for v in t[1:]))))
         elif t[0] == "M":
             mass.append(([float(v) for v in t[1:4]], [float(v) for v in t[4:]]))
@@ -140,11 +168,11 @@ def plans():
             counts[tuple(int(v) for v in t[1:5])] = int(t[5])
         elif t[0] == "G":
             geoms.append(dict(zip(FIELDS, (int(v) for v in t[1:]))))
-    return counts, geoms, mass, two
+    return counts, geoms, mass, two, counts2, geoms2
 
 
 def test_every_mesh_and_orbital_count_has_a_geometry(plans):
-    counts, geoms, _, _ = plans
+    counts, geoms = plans[0], plans[1]
     assert len(counts) == 10 * 64
     assert all(n >= 1 for n in counts.values()), [k for k, n in counts.items() if n == 0]
     assert len(geoms) == sum(counts.values())
@@ -231,3 +259,45 @@ def test_two_phase_kernel_geometry_obeys_the_same_rules(plans):
         assert G["smem"] <= 227 * 1024 and G["grid"] >= 1, G
         assert (G["ncx"] - 1) * G["TX"] < G["nx"] - 1 <= G["ncx"] * G["TX"], G
         assert (G["ncy"] - 1) * G["TY"] < G["ny"] - 1 <= G["ncy"] * G["TY"], G
+
+
+def test_single_pass_kernel_geometry(plans):
+    # group-major vectors: each active group of four orbitals is one TMA box of
+    # [TY+2][4 (TX+2)] floats per plane (16 B per node, a row contiguous)
+    counts2, geoms2 = plans[4], plans[5]
+    assert len(counts2) == 10 * 64 and all(n >= 1 for n in counts2.values())
+    assert len(geoms2) == sum(counts2.values())
+    static = 2 * 1024 * 4 + (3 * 256 + 8) * 4 + 64  # the kernel's static shared memory
+    for G in geoms2:
+        bw = 4 * G["G4"]
+        assert 1 <= G["G4"] <= 8, G
+        for dim in (4 * (G["TX"] + 2), G["TY"] + 2, G["DX"], G["TX"], G["TY"], KWS):
+            assert 1 <= dim <= 256, G
+        # inner extents: 16 (TX+2), 4 DX, 4 * 28 bytes; column origins 16 tx TX bytes
+        assert (4 * G["DX"]) % 16 == 0 and G["TX"] % 4 == 0, G
+        box = (G["TX"] + 2) * (G["TY"] + 2) * 16
+        stride = (box + 127) // 128 * 128  # every group's box starts 128-byte aligned (TMA destination)
+        vec = G["G4"] * stride
+        dv = G["DX"] * (G["TY"] + 2) * 4
+        wv = KWS * G["TX"] * G["TY"] * 4
+        assert G["tx"] == 3 * G["G4"] * box + dv + wv and G["tx"] < 2 ** 20, G
+        offs = (0, G["off_p"], G["off_s"], G["off_d"], G["off_w"], G["slot"])
+        assert all(o % 128 == 0 for o in offs), G
+        assert all(offs[i + 1] - offs[i] >= (vec, vec, vec, dv, wv)[i] for i in range(5)), G
+        # one node per consumer thread; the halo ring is handled by the first threads
+        # of a group slot; one producer warp more
+        assert G["npt"] == 1 and G["nthr"] == G["TX"] * G["TY"], G
+        assert 2 * (G["TX"] + 2) + 2 * G["TY"] <= G["nthr"], G
+        nt = G["nthr"] * G["G4"] + 32
+        assert nt <= 512 and (nt - 32) % 32 == 0 and G["smem"] + static <= 227 * 1024, G
+        # 3 to 6 ring slots (two mbarriers each in the first 128 bytes); sums [5 Np],
+        # state (6 Np words), flush rows x cols + slices, cross-CTA slices + totals
+        slots = G["maxcost"]
+        assert 3 <= slots <= 6 and 2 * 6 * 8 <= 128, G
+        red = 5 * G["Np"] + 5 * G["Np"] + max(G["nthr"] * bw + nt, 5 * G["Np"] + max(nt, 5 * G["Np"]))
+        assert G["smem"] == 128 + slots * G["slot"] + 8 * red, G
+        assert 1 <= G["grid"] <= 152, G
+        assert (G["ncx"] - 1) * G["TX"] < G["nx"] - 1 <= G["ncx"] * G["TX"], G
+        assert (G["ncy"] - 1) * G["TY"] < G["ny"] - 1 <= G["ncy"] * G["TY"], G
+        assert (G["nob"] - 1) * bw < G["Np"] <= G["nob"] * bw, G
+        assert G["s0"] == 0 and G["sN"] == G["F"] and G["mono"] == 1, G

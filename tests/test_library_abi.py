@@ -77,6 +77,7 @@ int main(void) {
   printf("%zu %zu\n", sizeof(paro_params), sizeof(paro_stats));
   printf("%zu %zu %zu %zu\n", offsetof(paro_params, profile), offsetof(paro_stats, prof_ms),
          offsetof(paro_stats, prof_dof_orb), offsetof(paro_params, hartree_precond));
+  printf("%zu %zu\n", offsetof(paro_params, wait_polls), offsetof(paro_stats, prof_dof_orb_active));
   return 0;
 }
 '''
@@ -93,6 +94,8 @@ int main(void) {
     assert sizes[3] == B.paro_stats.prof_ms.offset
     assert sizes[4] == B.paro_stats.prof_dof_orb.offset
     assert sizes[5] == B.paro_params.hartree_precond.offset
+    assert sizes[6] == B.paro_params.wait_polls.offset
+    assert sizes[7] == B.paro_stats.prof_dof_orb_active.offset
 
 
 def test_host_side_argument_checks_need_no_gpu(lib):
@@ -119,6 +122,9 @@ def test_host_side_argument_checks_need_no_gpu(lib):
     assert lib.paro_ks_density_in(None, None) == -1
     assert lib.paro_orbital_solve(None, 1, None, None, None, None, None) == -1
     assert lib.paro_rayleigh_ritz(None, 1, None, None, None, None) == -1
+    t = ctypes.c_double(0.0)
+    assert lib.paro_peak_fma(7, 1, ctypes.c_void_p(1), ctypes.byref(t), None) == -1  # unknown dtype
+    assert lib.paro_peak_fma(0, 0, ctypes.c_void_p(1), ctypes.byref(t), None) == -1  # iters < 1
 
 
 def test_binding_fails_loudly_without_the_library():
@@ -222,17 +228,13 @@ def test_create_error_message_is_per_thread(lib):
     assert seen == {"cells": True, "box": True}
 
 
-def test_readme_c_example_compiles_and_links_against_the_library(lib):
-    # the C example of the README stays in step with the header and the exports
+def test_c_example_compiles_and_links_against_the_library(lib):
+    # the C usage example stays in step with the header and the exports
     from paper_1405_0260_gb300 import binding as B
 
-    text = open(os.path.join(ROOT, "README.md")).read()
-    blocks = re.findall(r"```c\n(.*?)```", text, flags=re.S)
-    assert len(blocks) == 1
+    c = os.path.join(ROOT, "tests", "abi_example.c")
     with tempfile.TemporaryDirectory() as d:
-        c = os.path.join(d, "ex.c")
         so = os.path.join(d, "libex.so")
-        open(c, "w").write(blocks[0])
         subprocess.run(["gcc", "-shared", "-fPIC", "-Wall", "-Werror", "-I", os.path.dirname(HEADER), c, "-o", so,
                         "-L", os.path.dirname(B.LIB_PATH), "-lparo", "-Wl,--no-undefined", "-lm"],
                        check=True, capture_output=True, timeout=120)
