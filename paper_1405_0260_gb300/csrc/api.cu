@@ -76,7 +76,6 @@ struct paro_mesh_s {
   // single-pass float32 CG (group-major vectors over the same float32 buffers)
   CG2Plan* plan2 = nullptr;
   double* cg2part = nullptr;
-  double* cg2tot = nullptr;
   const char* tune2_source = "default";
   // layout of the float32 CG buffers: 0 node-major (two-reduction and single-reduction
   // CG, multigrid, paro_apply), 1 group-major (single-pass CG).  A change zeroes them,
@@ -425,7 +424,6 @@ int make_plans(paro_mesh m, int Np) {
     a.p[0] = m->p32a;
     a.p[1] = m->s32;
     a.part = m->cg2part;
-    a.tot = m->cg2tot;
     a.st = m->cgst;
     a.spin = kSpinLimit;
     a.inner = 1;
@@ -445,7 +443,7 @@ int ensure_workspace(paro_mesh m, int Np) {
   // release the previous vector workspace
   void* olds[] = {m->u,    m->x,   m->b,   m->r,   m->p0,  m->q,     m->b32,    m->x32, m->r32,
                   m->p32a, m->q32, m->s32, m->r32b, m->q32b, m->s32b, m->fxh, m->fxl, m->fah, m->fal,   m->fbh,    m->fbl, m->gpart_ff, m->gpart_tc,
-                  m->gpart, m->GA, m->GB,  m->C,   m->theta, m->eigwork, m->cgpart, m->cg2part, m->cg2tot};
+                  m->gpart, m->GA, m->GB,  m->C,   m->theta, m->eigwork, m->cgpart, m->cg2part};
   CK(cudaStreamSynchronize(m->st));
   for (void* p : olds) dfree(m, p);
   // the Gram workspaces below are allocated only for some Np: no stale pointers
@@ -485,9 +483,8 @@ int ensure_workspace(paro_mesh m, int Np) {
   TRY(dalloc(m, &m->eigwork, (size_t)4 * Np * Np));
   // per-CTA partials: up to 4 CTAs per SM, 3 values per orbital, two buffers
   TRY(dalloc(m, &m->cgpart, (size_t)2 * 3 * 4 * m->nsm * Np));
-  // single-pass CG: 5 partial sums per orbital and CTA, and their totals
-  TRY(dalloc(m, &m->cg2part, (size_t)5 * kMaxGrid1 * Np));
-  TRY(dalloc(m, &m->cg2tot, (size_t)5 * Np));
+  // single-pass CG: 5 partial sums per orbital and CTA, two buffers
+  TRY(dalloc(m, &m->cg2part, (size_t)2 * 5 * kMaxGrid1 * Np));
   m->Np_alloc = Np;
   TRY(make_plans(m, Np));
   return PARO_OK;

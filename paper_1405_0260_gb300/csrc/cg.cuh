@@ -30,7 +30,6 @@ struct CGDevState {
   unsigned long long work;  // sum over operator passes of interior nodes x orbitals processed
   unsigned int bar_count;   // grid barrier counter of the persistent CG kernel (zeroed per launch)
   unsigned long long work_nodes;  // sum over operator passes of interior nodes x orbital blocks processed
-  unsigned int bar_flag;          // single-pass CG: number of the last pass whose totals are published
   unsigned long long work_act;    // sum over operator passes of interior nodes x orbitals still iterating
   long long it_sum;               // single-pass CG: iterations of every orbital, summed over solves
   int it_max;                     // single-pass CG: largest per-orbital iteration count since the last reset
@@ -139,8 +138,7 @@ struct CG2Args {
   int N, Np;
   float* x;
   float *r[2], *q[2], *p[2];  // the two buffer sets (read by pass parity, written by the other)
-  double* part;               // per-CTA partial sums [5][grid][Np]
-  double* tot;                // totals of the last pass [5][Np], written by the last CTA to arrive
+  double* part;               // per-CTA partial sums [2][5][grid][Np] (two buffers by pass parity)
   CGDevState* st;
   unsigned spin;              // poll limit of every bounded wait
   int inner;                  // 1: reaching maxit is not an error (refinement carries on)

@@ -9,10 +9,12 @@
 //   rho_{k+1} = (r_k - alpha q_k, D^-1 (r_k - alpha q_k))
 //            = rho_k - 2 alpha_k (q_k, z_k) + alpha_k^2 (q_k, D^-1 q_k),
 //   beta_k = rho_{k+1} / rho_k,
-// so pass k, given alpha_{k-1} and beta_{k-1} from the previous reduction, forms
-// on the staged tile and its one-node halo
-//   r_k = r_{k-1} - alpha_{k-1} q_{k-1},  z_k = D^-1 r_k,  p_k = z_k + beta_{k-1} p_{k-1},
-// then q_k = A p_k (27-point stencil), and at its own nodes x_k = x_{k-1} +
+// so pass k, given alpha_{k-1} and beta_{k-1} from the previous reduction and
+// r_{k-1}, q_{k-1}, p_{k-1} staged with a one-node halo, forms
+//   r_k = r_{k-1} - alpha_{k-1} q_{k-1},  z_k = D^-1 r_k,  p_k = z_k + beta_{k-1} p_{k-1}
+// at the 3 x 3 neighbours of each node (every thread for its own stencil: the
+// staged data stay read-only, so no CTA barrier is needed within a plane), then
+// q_k = A p_k (27-point stencil), and at its own nodes x_k = x_{k-1} +
 // alpha_{k-1} p_{k-1}, and the five sums (r_k, z_k), (r_k, r_k), (p_k, q_k),
 // (q_k, z_k), (q_k, D^-1 q_k).  Every pass computes rho_k from the new residual
 // itself, so the expansion above only supplies beta_k and its rounding never
@@ -24,11 +26,11 @@
 // neither loaded nor stored, and the threads that would handle it are whole
 // idle warps (thread = node slot + nthr x active-group slot).
 //
-// Cross-CTA reduction: every CTA writes its partials and takes a ticket; the
-// last CTA to arrive sums the partials in a fixed order, publishes the totals
-// and a pass number; the others wait (bounded) for that number.  Every CTA then
-// derives identical scalars and masks.
+// Cross-CTA reduction: every CTA writes its partials, meets the others at one
+// bounded grid barrier and sums all partials in the same fixed order, so every
+// CTA derives identical scalars and masks.
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <vector>
@@ -72,30 +74,12 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   return v;
 }
 
-__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
 __device__ __forceinline__ void fence_proxy_async_global2() {
   asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
 // Barrier 1 among the nc consumer threads (the producer warp does not take part).
 __device__ __forceinline__ void consumer_sync(int nc) { asm volatile("bar.sync 1, %0;" ::"r"(nc) : "memory"); }
-
-// The same barrier, returning whether any consumer thread passed v = true.
-__device__ __forceinline__ bool consumer_sync_or(int nc, bool v) {
-  int r;
-  asm volatile(
-      "{\n\t.reg .pred pi, po;\n\t"
-      "setp.ne.u32 pi, %1, 0;\n\t"
-      "bar.red.or.pred po, 1, %2, pi;\n\t"
-      "selp.u32 %0, 1, 0, po;\n\t}"
-      : "=r"(r)
-      : "r"((int)v), "r"(nc)
-      : "memory");
-  return r != 0;
-}
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
@@ -177,7 +161,7 @@ __global__ void __launch_bounds__(kMaxThr2, 1) k_cg2(CG2Args a, K1Geom geo, cons
   __shared__ int sgact[kMaxN / 4];      // group still iterating
   __shared__ int slist[kMaxN / 4 + 8];  // per orbital block: its active groups in order
   __shared__ int snact[kMaxN / 4];      // per orbital block: their count
-  __shared__ int s_nact, s_last, s_ok, s_lstep;
+  __shared__ int s_nact, s_ok, s_lstep;
 
   const int nzo = a.g.nz - 1;
   const long long fbeg = geo.split[blockIdx.x];
@@ -267,26 +251,8 @@ __global__ void __launch_bounds__(kMaxThr2, 1) k_cg2(CG2Args a, K1Geom geo, cons
     return true;
   };
 
-  // own node (tx, ty) of the tile; threads j < ring size also update one halo-ring node
+  // own node (tx, ty) of the tile
   const int tx = j % TX, ty = j / TX;
-  const int hown = (ty + 1) * HX + (tx + 1);
-  const int nring = 2 * HX + 2 * TY;
-  int hring = -1;
-  if (j < nring) {
-    int hx, hy;
-    if (j < HX) {
-      hy = 0, hx = j;
-    } else if (j < 2 * HX) {
-      hy = HY - 1, hx = j - HX;
-    } else if (j < 2 * HX + TY) {
-      hy = 1 + (j - 2 * HX), hx = 0;
-    } else {
-      hy = 1 + (j - 2 * HX - TY), hx = HX - 1;
-    }
-    hring = hy * HX + hx;
-  }
-  const int poff = (ty * HX + tx) * 4;  // halo node (tx-1, ty-1) of a group box
-  const int hstep = HX * 4;
   const long long plane = (long long)a.g.Px * a.g.Py;
   const int lane = tid & 31;
 
@@ -310,12 +276,18 @@ __global__ void __launch_bounds__(kMaxThr2, 1) k_cg2(CG2Args a, K1Geom geo, cons
     }
   };
 
-  // consumers: one pass over this CTA's column-planes; false on a timed-out wait
+  // consumers: one pass over this CTA's column-planes; false on a timed-out wait.
+  // No CTA barrier per plane: every thread forms p_k = D^-1 (r - alpha q) + beta p
+  // itself at the 3 x 3 neighbours its stencil reads (the staged slot is never
+  // written), so warps only meet at the ring's mbarriers.  After a timed-out wait a
+  // thread stops waiting and computing but keeps to the loop, so the consumer
+  // barriers of the flush are still reached by everyone.
   auto consume = [&]() -> bool {
     float* const wx = a.x;
     float* const wr = a.r[rd ^ 1];
     float* const wq = a.q[rd ^ 1];
     float* const wp = a.p[rd ^ 1];
+    bool ok = true;
     int cur_ob = -1, cur_na = 0;
     float dt[kDots][4];
 #pragma unroll
@@ -362,97 +334,76 @@ __global__ void __launch_bounds__(kMaxThr2, 1) k_cg2(CG2Args a, K1Geom geo, cons
         const bool own_out = kact && inside && s >= z0 && s < z1;
         const long long eown = (gbase + (long long)s * plane + colnode) * 4;
         const Vec4<float> xv = xnext;
-        if (!first && kact && inside && s + 1 >= z0 && s + 1 < z1) xnext = ldcg4(wx + eown + plane * 4);
-        const bool ok = mbar_wait_n(&full[slot], par, spin);
+        if (ok && !first && kact && inside && s + 1 >= z0 && s + 1 < z1) xnext = ldcg4(wx + eown + plane * 4);
+        if (ok) ok = mbar_wait_n(&full[slot], par, spin);
         Vec4<float> cz{}, cp{};
         float cd = 0.f;
         if (kact && ok) {
-          float* R = slotR(slot) + k * vstr;
+          const float* R = slotR(slot) + k * vstr;
           const float* Q = slotQ(slot) + k * vstr;
-          float* P = slotP(slot) + k * vstr;
+          const float* P = slotP(slot) + k * vstr;
           const float* D = slotD(slot);
-          {
-            const int hy = hown / HX, hx = hown - hy * HX;
-            cd = D[hy * geo.DX + hx];
-            const int e = hown * 4;
-            const Vec4<float> rv = lds4(R + e);
-            Vec4<float> qv{}, pv{};
-            if (!first) {
-              qv = lds4(Q + e);
-              pv = lds4(P + e);
-            }
-            Vec4<float> rn;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-              rn.v[c] = fmaf(-al[c], qv.v[c], rv.v[c]);
-              cz.v[c] = cd * rn.v[c];
-              cp.v[c] = fmaf(be[c], pv.v[c], cz.v[c]);
-            }
-            sts4(P + e, cp);
-            if (own_out) {
-              Vec4<float> xn;
-#pragma unroll
-              for (int c = 0; c < 4; ++c) {
-                xn.v[c] = fmaf(al[c], pv.v[c], xv.v[c]);
-                dt[0][c] = fmaf(rn.v[c], cz.v[c], dt[0][c]);
-                dt[1][c] = fmaf(rn.v[c], rn.v[c], dt[1][c]);
-              }
-              sts4(wr + eown, rn);
-              sts4(wp + eown, cp);
-              sts4(wx + eown, xn);
-            }
-          }
-          if (hring >= 0) {
-            const int hy = hring / HX, hx = hring - hy * HX;
-            const float d = D[hy * geo.DX + hx];
-            const int e = hring * 4;
-            const Vec4<float> rv = lds4(R + e);
-            Vec4<float> qv{}, pv{};
-            if (!first) {
-              qv = lds4(Q + e);
-              pv = lds4(P + e);
-            }
-            Vec4<float> pn;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) pn.v[c] = fmaf(be[c], pv.v[c], d * fmaf(-al[c], qv.v[c], rv.v[c]));
-            sts4(P + e, pn);
-          }
-          // the slot is refilled by TMA (async proxy) once every consumer warp released it
-          fence_proxy_async_smem();
-        }
-        if (consumer_sync_or(NC, !ok)) return false;
-        if (kact) {
-          const float* U = slotP(slot) + k * vstr + poff;
           const float* Wn = slotW(slot) + j * kW2;
           Vec4<float> w[7];
 #pragma unroll
           for (int q = 0; q < 7; ++q) w[q] = lds4(Wn + 4 * q);
+          // the 3 x 3 neighbours (tx-1 .. tx+1, ty-1 .. ty+1) of the staged plane
 #pragma unroll
-          for (int cxi = 0; cxi < 3; ++cxi) {
-            Vec4<float> v[3];
+          for (int cy = 0; cy < 3; ++cy) {
 #pragma unroll
-            for (int r = 0; r < 3; ++r) v[r] = lds4(U + r * hstep + cxi * 4);
+            for (int cxi = 0; cxi < 3; ++cxi) {
+              const int hnode = (ty + cy) * HX + (tx + cxi);
+              const int e = hnode * 4;
+              const float d = D[(ty + cy) * geo.DX + tx + cxi];
+              const Vec4<float> rv = lds4(R + e);
+              Vec4<float> qv{}, pv{};
+              if (!first) {
+                qv = lds4(Q + e);
+                pv = lds4(P + e);
+              }
+              Vec4<float> rn, zn, pn;
 #pragma unroll
-            for (int cy = 0; cy < 3; ++cy) {
+              for (int c = 0; c < 4; ++c) {
+                rn.v[c] = fmaf(-al[c], qv.v[c], rv.v[c]);
+                zn.v[c] = d * rn.v[c];
+                pn.v[c] = fmaf(be[c], pv.v[c], zn.v[c]);
+              }
               const int o = cy * 3 + cxi;
               const float wu = w[o / 4].v[o % 4];
               const float wc = w[(9 + o) / 4].v[(9 + o) % 4];
               const float wd = w[(18 + o) / 4].v[(18 + o) % 4];
 #pragma unroll
               for (int c = 0; c < 4; ++c) {
-                aU.v[c] = fmaf(wu, v[cy].v[c], aU.v[c]);
-                aC.v[c] = fmaf(wc, v[cy].v[c], aC.v[c]);
-                aD.v[c] = fmaf(wd, v[cy].v[c], aD.v[c]);
+                aU.v[c] = fmaf(wu, pn.v[c], aU.v[c]);
+                aC.v[c] = fmaf(wc, pn.v[c], aC.v[c]);
+                aD.v[c] = fmaf(wd, pn.v[c], aD.v[c]);
+              }
+              if (cy == 1 && cxi == 1) {  // the own node: r_k, p_k, x_k and their sums
+                cd = d;
+                cz = zn;
+                cp = pn;
+                if (own_out) {
+                  Vec4<float> xn;
+#pragma unroll
+                  for (int c = 0; c < 4; ++c) {
+                    xn.v[c] = fmaf(al[c], pv.v[c], xv.v[c]);
+                    dt[0][c] = fmaf(rn.v[c], zn.v[c], dt[0][c]);
+                    dt[1][c] = fmaf(rn.v[c], rn.v[c], dt[1][c]);
+                  }
+                  sts4(wr + eown, rn);
+                  sts4(wp + eown, pn);
+                  sts4(wx + eown, xn);
+                }
               }
             }
           }
         }
         // this warp is done with the slot
         __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[slot]);
+        if (lane == 0 && ok) mbar_arrive(&empty[slot]);
         if (kact) {
           // output plane s-1 is complete: q_k there, and its sums
-          const bool prev_out = inside && s - 1 >= z0 && s - 1 < z1;
+          const bool prev_out = ok && inside && s - 1 >= z0 && s - 1 < z1;
           if (prev_out) {
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
@@ -473,7 +424,7 @@ __global__ void __launch_bounds__(kMaxThr2, 1) k_cg2(CG2Args a, K1Geom geo, cons
       }
     }
     if (cur_ob >= 0) flush(cur_ob, cur_na, dt);
-    return true;
+    return ok;
   };
 
   // masks of the next pass: group and block activity, the active-group lists
@@ -534,44 +485,38 @@ __global__ void __launch_bounds__(kMaxThr2, 1) k_cg2(CG2Args a, K1Geom geo, cons
     }
     first = false;
     rd ^= 1;
-    // partials of this CTA, then the ticket; the next pass reads r, q, p by TMA
+    // partials of this CTA (two buffers by pass parity: with one barrier a pass, a
+    // fast CTA writes pass k+1's while slower ones may still read pass k's), then
+    // one bounded grid barrier; the next pass reads r, q, p by TMA
+    double* part = a.part + (long long)(npass & 1) * kDots * gridDim.x * Np;
     for (int t = tid; t < kDots * Np; t += blockDim.x) {
       const int d = t / Np, o = t - d * Np;
-      a.part[((long long)d * gridDim.x + blockIdx.x) * Np + o] = sacc[t];
+      part[((long long)d * gridDim.x + blockIdx.x) * Np + o] = sacc[t];
     }
     fence_proxy_async_global2();
     __threadfence();
     __syncthreads();
-    const unsigned target = (unsigned)(npass + 1) * gridDim.x;
-    if (tid == 0) s_last = (atomicAdd(&a.st->bar_count, 1u) == target - 1u) ? 1 : 0;
-    __syncthreads();
-    if (s_last) {
-      __threadfence();
-      reduce_over_ctas<kDots>(a.part, gridDim.x, Np, scratch, tot);
-      for (int t = tid; t < kDots * Np; t += blockDim.x) a.tot[t] = tot[t];
-      __threadfence();
-      __syncthreads();
-      if (tid == 0) st_release_u32(&a.st->bar_flag, (unsigned)(npass + 1));
-    } else {
-      if (tid == 0) {
-        int okf = 0;
-        for (unsigned i = 0; i < spin; ++i) {
-          if (ld_acquire_u32(&a.st->bar_flag) >= (unsigned)(npass + 1)) {
-            okf = 1;
-            break;
-          }
-          __nanosleep(32);
+    if (tid == 0) {
+      const unsigned target = (unsigned)(npass + 1) * gridDim.x;
+      atomicAdd(&a.st->bar_count, 1u);
+      int okb = 0;
+      for (unsigned i = 0; i < spin; ++i) {
+        if (ld_acquire_u32(&a.st->bar_count) >= target) {
+          okb = 1;
+          break;
         }
-        s_ok = okf;
+        __nanosleep(32);
       }
-      __syncthreads();
-      if (!s_ok) {
-        timed_out = true;
-        break;
-      }
-      for (int t = tid; t < kDots * Np; t += blockDim.x) tot[t] = __ldcg(a.tot + t);
+      __threadfence();
+      s_ok = okb;
     }
     __syncthreads();
+    if (!s_ok) {
+      timed_out = true;
+      break;
+    }
+    // every CTA sums the partials in the same fixed order: identical totals everywhere
+    reduce_over_ctas<kDots>(part, gridDim.x, Np, scratch, tot);
     for (int o = tid; o < Np; o += blockDim.x) {
       if (!st_act[o]) {
         st_al[o] = 0.0;
@@ -724,14 +669,17 @@ void cg2_candidates(const Grid& g, int Np, int nsm, std::vector<K1Geom>* out) {
   out->clear();
   const size_t stat = (size_t)2 * kMaxN * sizeof(float) + (3 * (kMaxN / 4) + 8) * sizeof(int) + 64;
   const size_t limit = 227 * 1024 - stat - 1024;
-  const int shapes[2][2] = {{16, 4}, {8, 8}};
+  // tiles of 64 or 96 nodes (two or three warps per group slot): the larger ones
+  // stage fewer halo nodes per node (1.5x at 16 x 6 against 1.69x at 16 x 4) and
+  // run more warps per SM
+  const int shapes[5][2] = {{16, 4}, {8, 8}, {16, 6}, {24, 4}, {8, 12}};
   int widths = 0;
   for (int nob = (Np + 31) / 32; nob <= Np / 4 && widths < 3; ++nob) {
     int bw = (Np + nob - 1) / nob;
     bw = (bw + 3) / 4 * 4;
     if ((Np + bw - 1) / bw != nob) continue;
     bool any = false;
-    for (int si = 0; si < 2; ++si) {
+    for (int si = 0; si < 5; ++si) {
       const int TX = shapes[si][0], TY = shapes[si][1];
       if (TX * TY * (bw / 4) + 32 > kMaxThr2) continue;  // consumers + the producer warp
       K1Geom G{};
@@ -792,7 +740,6 @@ cudaError_t cg2_launch(CG2Plan* P, cudaStream_t st) {
   CG2Args a = P->args;
   K1Geom geo = P->geo;
   cudaError_t e = cudaMemsetAsync(&a.st->bar_count, 0, sizeof(unsigned int), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(&a.st->bar_flag, 0, sizeof(unsigned int), st);
   if (e != cudaSuccess) return e;
   void* args[] = {&a, &geo, &P->mr[0], &P->mq[0], &P->mp[0], &P->mr[1], &P->mq[1], &P->mp[1], &P->md, &P->mw};
   return cudaLaunchCooperativeKernel(cg2_fn(geo.G4), dim3(geo.grid), dim3(geo.nthr * geo.G4 + 32), args, geo.smem,
@@ -845,6 +792,9 @@ cudaError_t cg2_autotune(CG2Plan* P, cudaStream_t st, int passes, int* chosen, f
       continue;
     }
     ++*tried;
+    if (std::getenv("PARO_PRINT_PLAN"))
+      std::fprintf(stderr, "paro single-pass CG candidate: tile %dx%d, block %d, %d slots, %.2f us a pass\n",
+                   cand[i].TX, cand[i].TY, cand[i].G4 * 4, cand[i].slots, 1e3f * ms / (passes + 1));
     if (*chosen < 0 || ms < best) {
       best = ms;
       *chosen = (int)i;

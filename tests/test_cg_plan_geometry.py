@@ -274,7 +274,7 @@ def test_single_pass_kernel_geometry(plans):
         for dim in (4 * (G["TX"] + 2), G["TY"] + 2, G["DX"], G["TX"], G["TY"], KWS):
             assert 1 <= dim <= 256, G
         # inner extents: 16 (TX+2), 4 DX, 4 * 28 bytes; column origins 16 tx TX bytes
-        assert (4 * G["DX"]) % 16 == 0 and G["TX"] % 4 == 0, G
+        assert (4 * G["DX"]) % 16 == 0 and G["TX"] % 4 == 0 and G["TX"] * G["TY"] % 32 == 0, G
         box = (G["TX"] + 2) * (G["TY"] + 2) * 16
         stride = (box + 127) // 128 * 128  # every group's box starts 128-byte aligned (TMA destination)
         vec = G["G4"] * stride
@@ -284,10 +284,8 @@ def test_single_pass_kernel_geometry(plans):
         offs = (0, G["off_p"], G["off_s"], G["off_d"], G["off_w"], G["slot"])
         assert all(o % 128 == 0 for o in offs), G
         assert all(offs[i + 1] - offs[i] >= (vec, vec, vec, dv, wv)[i] for i in range(5)), G
-        # one node per consumer thread; the halo ring is handled by the first threads
-        # of a group slot; one producer warp more
+        # one node per consumer thread, whole warps per group slot; one producer warp more
         assert G["npt"] == 1 and G["nthr"] == G["TX"] * G["TY"], G
-        assert 2 * (G["TX"] + 2) + 2 * G["TY"] <= G["nthr"], G
         nt = G["nthr"] * G["G4"] + 32
         assert nt <= 512 and (nt - 32) % 32 == 0 and G["smem"] + static <= 227 * 1024, G
         # 3 to 6 ring slots (two mbarriers each in the first 128 bytes); sums [5 Np],
