@@ -53,8 +53,14 @@ def occupations(N: int, n_electrons: int) -> np.ndarray:
     return f
 
 
+def _uniform(mesh: P.Mesh) -> None:
+    if mesh.graded:
+        raise ValueError("the Kohn-Sham pieces are written for uniform meshes")
+
+
 def _cell_values(mesh: P.Mesh, U: np.ndarray) -> np.ndarray:
     """Orbital values at the Gauss points: (n_cells, 8, N), boundary nodes zero."""
+    _uniform(mesh)
     _, _, Pq, _ = P.element_matrices(mesh.h)
     idx = P._cell_node_indices(mesh)  # (n_cells, 8), -1 on the boundary
     U = np.asarray(U, dtype=np.float64)
@@ -71,6 +77,7 @@ def density_gauss(mesh: P.Mesh, U: np.ndarray, occ: np.ndarray) -> np.ndarray:
 
 def integrate(mesh: P.Mesh, fq: np.ndarray) -> float:
     """sum over cells and Gauss points of w_q f(x_q)."""
+    _uniform(mesh)
     _, _, _, wq = P.element_matrices(mesh.h)
     return float(np.einsum("cq,q->", np.asarray(fq).reshape(-1, 8), wq))
 
@@ -95,6 +102,7 @@ def _all_node_index(mesh: P.Mesh):
 
 def monopole(mesh: P.Mesh, rho_q: np.ndarray):
     """Charge Q = int rho and centre x_c = int rho x / Q of a Gauss-point density."""
+    _uniform(mesh)
     _, _, _, wq = P.element_matrices(mesh.h)
     r = np.asarray(rho_q).reshape(-1, 8)
     X = P.gauss_points(mesh).reshape(-1, 8, 3)
@@ -121,6 +129,7 @@ def hartree(mesh: P.Mesh, rho_q: np.ndarray) -> HartreeResult:
     rho is given; the boundary values enter through the interior-boundary
     block of the stiffness matrix.
     """
+    _uniform(mesh)
     nx, ny, nz = mesh.n
     Ke, _, Pq, wq = P.element_matrices(mesh.h)
     idx = _all_node_index(mesh)

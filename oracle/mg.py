@@ -62,6 +62,8 @@ def prolongation_1d(nf: int) -> sp.csr_matrix:
 
 def prolongation(mesh: P_.Mesh) -> sp.csr_matrix:
     """Interior-node prolongation from the halved mesh (x fastest, as in Mesh)."""
+    if mesh.graded:
+        raise ValueError("the multigrid hierarchy is written for uniform meshes")
     nx, ny, nz = mesh.n
     return sp.kron(prolongation_1d(nz), sp.kron(prolongation_1d(ny), prolongation_1d(nx))).tocsr()
 

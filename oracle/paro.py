@@ -44,24 +44,41 @@ import scipy.sparse as sp
 
 @dataclass
 class Mesh:
-    """Uniform hexahedral mesh of the box [lo, hi] with n = (nx, ny, nz) cells.
+    """Hexahedral tensor-product mesh of the box [lo, hi] with n = (nx, ny, nz) cells.
 
-    Unknowns live on interior nodes only (homogeneous Dirichlet data on the
-    whole boundary, the truncated domain of Section 2.2).  Interior node
-    (i, j, k), 1 <= i <= nx-1 etc., has index ((k-1)(ny-1) + (j-1))(nx-1) + (i-1):
-    x varies fastest.
+    Uniform by default.  A graded mesh (Section 2.1: finite element spaces on
+    locally refined meshes, here refined along each axis) gives the node
+    coordinates of every axis in `coords` (n_d + 1 strictly increasing values
+    each; lo and hi are then their end points).  Unknowns live on interior nodes
+    only (homogeneous Dirichlet data on the whole boundary, the truncated domain
+    of Section 2.2).  Interior node (i, j, k), 1 <= i <= nx-1 etc., has index
+    ((k-1)(ny-1) + (j-1))(nx-1) + (i-1): x varies fastest.
     """
 
     n: tuple
     lo: tuple
     hi: tuple
+    coords: tuple | None = None
     h: np.ndarray = field(init=False)
 
     def __post_init__(self):
         self.n = tuple(int(v) for v in self.n)
-        self.lo = tuple(float(v) for v in self.lo)
-        self.hi = tuple(float(v) for v in self.hi)
-        self.h = np.array([(self.hi[d] - self.lo[d]) / self.n[d] for d in range(3)])
+        if self.coords is None:
+            self.lo = tuple(float(v) for v in self.lo)
+            self.hi = tuple(float(v) for v in self.hi)
+            self.nodes = [self.lo[d] + (self.hi[d] - self.lo[d]) / self.n[d] * np.arange(self.n[d] + 1)
+                          for d in range(3)]
+            self.graded = False
+        else:
+            self.nodes = [np.asarray(c, dtype=np.float64) for c in self.coords]
+            for d in range(3):
+                if self.nodes[d].shape != (self.n[d] + 1,) or not np.all(np.diff(self.nodes[d]) > 0):
+                    raise ValueError("coords: n_d + 1 strictly increasing node coordinates per axis")
+            self.lo = tuple(float(c[0]) for c in self.nodes)
+            self.hi = tuple(float(c[-1]) for c in self.nodes)
+            self.graded = True
+        self.hc = [np.diff(self.nodes[d]) for d in range(3)]  # cell sizes per axis
+        self.h = np.array([(self.hi[d] - self.lo[d]) / self.n[d] for d in range(3)])  # mean cell size
 
     @property
     def n_interior(self) -> int:
@@ -80,8 +97,7 @@ class Mesh:
 
     def interior_coords(self) -> np.ndarray:
         """(n_interior, 3) coordinates in unknown order."""
-        nx, ny, nz = self.n
-        xs = [self.lo[d] + self.h[d] * np.arange(1, self.n[d]) for d in range(3)]
+        xs = [self.nodes[d][1:-1] for d in range(3)]
         Z, Y, X = np.meshgrid(xs[2], xs[1], xs[0], indexing="ij")
         return np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
 
@@ -142,12 +158,12 @@ def gauss_points(mesh: Mesh) -> np.ndarray:
     g, _ = gauss_1d()
     nx, ny, nz = mesh.n
     out = np.zeros((nz, ny, nx, 2, 2, 2, 3))
-    cx = mesh.lo[0] + mesh.h[0] * (np.arange(nx)[None, None, :, None, None, None] + g[None, None, None, None, None, :])
-    cy = mesh.lo[1] + mesh.h[1] * (np.arange(ny)[None, :, None, None, None, None] + g[None, None, None, None, :, None])
-    cz = mesh.lo[2] + mesh.h[2] * (np.arange(nz)[:, None, None, None, None, None] + g[None, None, None, :, None, None])
-    out[..., 0] = cx
-    out[..., 1] = cy
-    out[..., 2] = cz
+    px = mesh.nodes[0][:-1, None] + mesh.hc[0][:, None] * g[None, :]  # [cell][q]
+    py = mesh.nodes[1][:-1, None] + mesh.hc[1][:, None] * g[None, :]
+    pz = mesh.nodes[2][:-1, None] + mesh.hc[2][:, None] * g[None, :]
+    out[..., 0] = px[None, None, :, None, None, :]
+    out[..., 1] = py[None, :, None, None, :, None]
+    out[..., 2] = pz[:, None, None, :, None, None]
     return out
 
 
@@ -206,14 +222,51 @@ def assemble(mesh: Mesh, Vq: np.ndarray, sigma: float) -> Operators:
     """
     nx, ny, nz = mesh.n
     Vq = np.asarray(Vq, dtype=np.float64).reshape(nz * ny * nx, 8)  # q = qx + 2qy + 4qz
-    Ke, Me, P, wq = element_matrices(mesh.h)
     n_cells = nx * ny * nz
-    K = _assemble(mesh, np.broadcast_to(Ke, (n_cells, 8, 8)))
-    M = _assemble(mesh, np.broadcast_to(Me, (n_cells, 8, 8)))
-    # MV^e_ab = sum_q w_q V_cq phi_a(q) phi_b(q)
-    MVe = np.einsum("q,cq,qa,qb->cab", wq, Vq, P, P)
+    if not mesh.graded:
+        Ke, Me, P, wq = element_matrices(mesh.h)
+        K = _assemble(mesh, np.broadcast_to(Ke, (n_cells, 8, 8)))
+        M = _assemble(mesh, np.broadcast_to(Me, (n_cells, 8, 8)))
+        # MV^e_ab = sum_q w_q V_cq phi_a(q) phi_b(q)
+        MVe = np.einsum("q,cq,qa,qb->cab", wq, Vq, P, P)
+    else:
+        # every cell its own sizes: with the unit cell's per-direction stiffness parts
+        # S_d (gradients along axis d only), Ke = sum_d (h_x h_y h_z / h_d^2) S_d,
+        # Me = h_x h_y h_z Me(1), and the Gauss weights scale by h_x h_y h_z
+        _, Me1, P, wq1 = element_matrices((1.0, 1.0, 1.0))
+        Sd = _unit_stiffness_parts()
+        hz, hy, hx = np.meshgrid(mesh.hc[2], mesh.hc[1], mesh.hc[0], indexing="ij")
+        hx, hy, hz = hx.ravel(), hy.ravel(), hz.ravel()
+        vol = hx * hy * hz
+        Ke = ((vol / hx ** 2)[:, None, None] * Sd[0] + (vol / hy ** 2)[:, None, None] * Sd[1]
+              + (vol / hz ** 2)[:, None, None] * Sd[2])
+        K = _assemble(mesh, Ke)
+        M = _assemble(mesh, vol[:, None, None] * Me1[None, :, :])
+        MVe = np.einsum("c,q,cq,qa,qb->cab", vol, wq1, Vq, P, P)
     MV = _assemble(mesh, MVe)
     return Operators(mesh, K, M, MV, float(sigma))
+
+
+def _unit_stiffness_parts() -> np.ndarray:
+    """S[d][a, b] = sum_q w_q (d phi_a / d x_d)(d phi_b / d x_d) on the unit cell (2x2x2 Gauss)."""
+    g, gw = gauss_1d()
+    l, dl = q1_shape(g)
+    S = np.zeros((3, 8, 8))
+    for qz in range(2):
+        for qy in range(2):
+            for qx in range(2):
+                w = gw[qx] * gw[qy] * gw[qz]
+                for a in range(8):
+                    ax, ay, az = a & 1, (a >> 1) & 1, (a >> 2) & 1
+                    ga = (dl[ax, qx] * l[ay, qy] * l[az, qz], l[ax, qx] * dl[ay, qy] * l[az, qz],
+                          l[ax, qx] * l[ay, qy] * dl[az, qz])
+                    for b in range(8):
+                        bx, by, bz = b & 1, (b >> 1) & 1, (b >> 2) & 1
+                        gb = (dl[bx, qx] * l[by, qy] * l[bz, qz], l[bx, qx] * dl[by, qy] * l[bz, qz],
+                              l[bx, qx] * l[by, qy] * dl[bz, qz])
+                        for d in range(3):
+                            S[d, a, b] += w * ga[d] * gb[d]
+    return S
 
 
 # ---------------------------------------------------------------------------

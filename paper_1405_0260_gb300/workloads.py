@@ -22,6 +22,7 @@ initial guesses as suggested for Step 1 of Algorithm 3.1):
   batch_systems  64 independent systems, 1-6 nuclei each, meshes 32-96^3, N 4-48
   large_cluster  40 nuclei, [-20,20]^3, 192^3 cells, N=256, standard normal initial block
   random_block   unit-variance orbitals for throughput runs
+  graded_hydrogen  the hydrogen-like nucleus on a mesh graded toward it (Section 2.1)
 """
 from __future__ import annotations
 
@@ -45,6 +46,7 @@ class Problem:
     tol: float  # stop on max |delta lambda| < tol
     nuclei: np.ndarray | None = None  # (M, 4): x, y, z, Z
     n_occ: int | None = None  # orbitals tested for convergence (Algorithm 3.2 buffer)
+    coords: tuple | None = None  # graded mesh: node coordinates per axis (None: uniform)
 
     @property
     def N(self) -> int:
@@ -60,35 +62,53 @@ class Problem:
         return tuple((self.hi[d] - self.lo[d]) / self.n[d] for d in range(3))
 
 
-def gauss_point_coords(n, lo, hi):
-    """Coordinates (x, y, z) of the Gauss points, each shaped (nz, ny, nx, 2, 2, 2)."""
+def _axis_nodes(n, lo, hi, coords):
+    if coords is not None:
+        return [np.asarray(c, dtype=np.float64) for c in coords]
+    return [lo[d] + (hi[d] - lo[d]) / n[d] * np.arange(n[d] + 1) for d in range(3)]
+
+
+def gauss_point_coords(n, lo, hi, coords=None):
+    """Coordinates (x, y, z) of the Gauss points, each shaped (nz, ny, nx, 2, 2, 2);
+    coords: node coordinates per axis of a graded mesh (None: uniform)."""
     nx, ny, nz = n
-    h = [(hi[d] - lo[d]) / n[d] for d in range(3)]
+    nodes = _axis_nodes(n, lo, hi, coords)
     g = np.array(_G)
-    x = lo[0] + h[0] * (np.arange(nx)[None, None, :, None, None, None] + g[None, None, None, None, None, :])
-    y = lo[1] + h[1] * (np.arange(ny)[None, :, None, None, None, None] + g[None, None, None, None, :, None])
-    z = lo[2] + h[2] * (np.arange(nz)[:, None, None, None, None, None] + g[None, None, None, :, None, None])
+    p = [nodes[d][:-1, None] + np.diff(nodes[d])[:, None] * g[None, :] for d in range(3)]  # [cell][q]
+    x = p[0][None, None, :, None, None, :]
+    y = p[1][None, :, None, None, :, None]
+    z = p[2][:, None, None, :, None, None]
     shape = (nz, ny, nx, 2, 2, 2)
     return np.broadcast_to(x, shape), np.broadcast_to(y, shape), np.broadcast_to(z, shape)
 
 
-def interior_node_coords(n, lo, hi):
+def interior_node_coords(n, lo, hi, coords=None):
     """(n_interior, 3) coordinates of the interior nodes in unknown order."""
-    nx, ny, nz = n
-    h = [(hi[d] - lo[d]) / n[d] for d in range(3)]
-    xs = [lo[d] + h[d] * np.arange(1, n[d]) for d in range(3)]
+    nodes = _axis_nodes(n, lo, hi, coords)
+    xs = [nodes[d][1:-1] for d in range(3)]
     Z, Y, X = np.meshgrid(xs[2], xs[1], xs[0], indexing="ij")
     return np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
 
 
-def gaussian_orbitals(n, lo, hi, N, rng, width=(0.5, 3.0), centre=(-1.0, 1.0)):
+def graded_axis(nc, L, beta):
+    """nc + 1 node coordinates on [-L, L], finest at 0: x_i = L sinh(beta t_i) / sinh(beta),
+    t_i = -1 + 2 i / nc (beta -> 0: uniform; cells grow by about e^(2 beta / nc) outward)."""
+    t = -1.0 + 2.0 * np.arange(nc + 1) / nc
+    if beta == 0.0:
+        return L * t
+    x = L * np.sinh(beta * t) / np.sinh(beta)
+    x[0], x[-1] = -L, L
+    return x
+
+
+def gaussian_orbitals(n, lo, hi, N, rng, width=(0.5, 3.0), centre=(-1.0, 1.0), coords=None):
     """N seeded Gaussians exp(-|x-c|^2 / (2 w^2)) at the interior nodes.
 
     Draw order: all N widths w ~ U[width], then the N x 3 centres c ~ U[centre].
     """
     w = rng.uniform(width[0], width[1], size=N)
     c = rng.uniform(centre[0], centre[1], size=(N, 3))
-    xyz = interior_node_coords(n, lo, hi)
+    xyz = interior_node_coords(n, lo, hi, coords)
     d2 = ((xyz[:, None, :] - c[None, :, :]) ** 2).sum(axis=2)
     return np.exp(-d2 / (2.0 * w[None, :] ** 2))
 
@@ -132,6 +152,24 @@ def hydrogen(nc=32, L=10.0, N=5, seed=1000, sigma=2.0, Z=1.0, tol=1e-8):
     U0 = gaussian_orbitals(n, lo, hi, N, rng)
     nuc = np.array([[R[0], R[1], R[2], Z]])
     return Problem(f"hydrogen-{nc}^3-N{N}", n, lo, hi, np.ascontiguousarray(V.ravel()), sigma, U0, tol, nuc)
+
+
+def graded_hydrogen(nc=16, L=10.0, beta=2.0, N=5, seed=1100, sigma=2.0, Z=1.0, tol=1e-8):
+    """Hydrogen-like nucleus at the origin on a graded mesh (Section 2.1: a mesh
+    refined where the orbitals vary fast): every axis graded_axis(nc, L, beta),
+    nc even so the nucleus sits on a node, V = -Z/r at the Gauss points (never
+    singular there), Gaussian initial orbitals as for the uniform workload."""
+    ax = graded_axis(nc, L, beta)
+    coords = (ax, ax, ax)
+    n = (nc, nc, nc)
+    lo, hi = (-L, -L, -L), (L, L, L)
+    x, y, z = gauss_point_coords(n, lo, hi, coords)
+    V = -Z / np.sqrt(x ** 2 + y ** 2 + z ** 2)
+    rng = np.random.default_rng(seed)
+    U0 = gaussian_orbitals(n, lo, hi, N, rng, coords=coords)
+    nuc = np.array([[0.0, 0.0, 0.0, Z]])
+    return Problem(f"graded-hydrogen-{nc}^3-b{beta}-N{N}", n, lo, hi, np.ascontiguousarray(V.ravel()), sigma, U0,
+                   tol, nuc, coords=coords)
 
 
 def harmonic(nc=64, L=8.0, N=20, seed=2000, sigma=0.0, omega=1.0, tol=1e-10):
