@@ -78,6 +78,13 @@ __device__ __forceinline__ void fence_proxy_async_global2() {
   asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
+__device__ __forceinline__ void* smem_align8(void* p) {
+  return reinterpret_cast<void*>((reinterpret_cast<uintptr_t>(p) + 7) & ~(uintptr_t)7);
+}
+__host__ __device__ inline size_t small_state_bytes(int Np, int nob, int G4) {
+  return ((size_t)2 * Np + Np / 4 + nob + (size_t)nob * G4) * 4 + 8;
+}
+
 // Barrier 1 among the nc consumer threads (the producer warp does not take part).
 __device__ __forceinline__ void consumer_sync(int nc) { asm volatile("bar.sync 1, %0;" ::"r"(nc) : "memory"); }
 
@@ -156,11 +163,12 @@ __global__ void __launch_bounds__(kMaxThr2, 1) k_cg2(CG2Args a, K1Geom geo, cons
   double* st_be = st_al + Np;          // beta of the last reduction
   int* st_act = reinterpret_cast<int*>(st_be + Np);
   int* st_it = st_act + Np;
-  double* sred = reinterpret_cast<double*>(st_it + Np);  // block sums / reduction scratch
-  __shared__ float sbeta[kMaxN], salpha[kMaxN];
-  __shared__ int sgact[kMaxN / 4];      // group still iterating
-  __shared__ int slist[kMaxN / 4 + 8];  // per orbital block: its active groups in order
-  __shared__ int snact[kMaxN / 4];      // per orbital block: their count
+  float* sbeta = reinterpret_cast<float*>(st_it + Np);  // [Np] beta and alpha of the pass, float32
+  float* salpha = sbeta + Np;
+  int* sgact = reinterpret_cast<int*>(salpha + Np);      // [Np/4] group still iterating
+  int* snact = sgact + Np / 4;                            // [nob] active groups per orbital block
+  int* slist = snact + geo.nob;                           // [nob G4] the blocks' active groups in order
+  double* sred = reinterpret_cast<double*>(smem_align8(slist + geo.nob * G4));  // sums / reduction scratch
   __shared__ int s_nact, s_ok, s_lstep;
 
   const int nzo = a.g.nz - 1;
@@ -641,7 +649,9 @@ static bool cg2_layout(int Np, int bw, int TX, int TY, size_t limit, K1Geom* G) 
   const size_t nt = (size_t)G->nthr * G4 + 32;
   const size_t blk = (size_t)G->nthr * bw + nt;                      // flush: rows x cols + slices
   const size_t fin = (size_t)kDots * Np + (nt > (size_t)kDots * Np ? nt : (size_t)kDots * Np);
-  const size_t red = ((size_t)kDots * Np + 4 * (size_t)Np + Np + (blk > fin ? blk : fin)) * sizeof(double);
+  const int nob = (Np + bw - 1) / bw;
+  const size_t red = ((size_t)kDots * Np + 4 * (size_t)Np + Np + (blk > fin ? blk : fin)) * sizeof(double) +
+                     small_state_bytes(Np, nob, G4);
   if (128 + red + 3 * (size_t)G->slot_bytes > limit) return false;
   int slots = (int)((limit - 128 - red) / G->slot_bytes);
   if (slots > kMaxSlots2) slots = kMaxSlots2;
@@ -667,11 +677,11 @@ static void cg2_finish(const Grid& g, int Np, int nsm, int bw, K1Geom* G) {
 
 void cg2_candidates(const Grid& g, int Np, int nsm, std::vector<K1Geom>* out) {
   out->clear();
-  const size_t stat = (size_t)2 * kMaxN * sizeof(float) + (3 * (kMaxN / 4) + 8) * sizeof(int) + 64;
+  const size_t stat = 64;  // the kernel's static shared memory (a few ints)
   const size_t limit = 227 * 1024 - stat - 1024;
   // tiles of 64 or 96 nodes (two or three warps per group slot): the larger ones
   // stage fewer halo nodes per node (1.5x at 16 x 6 against 1.69x at 16 x 4) and
-  // run more warps per SM
+  // run more warps per SM (32-node tiles at two CTAs a SM measured slower)
   const int shapes[5][2] = {{16, 4}, {8, 8}, {16, 6}, {24, 4}, {8, 12}};
   int widths = 0;
   for (int nob = (Np + 31) / 32; nob <= Np / 4 && widths < 3; ++nob) {
