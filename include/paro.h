@@ -148,6 +148,19 @@ void paro_default_params(paro_params* p);
 int paro_mesh_create(paro_mesh* out, int nx, int ny, int nz, const double lo[3], const double hi[3],
                      int precision, void* cuda_stream);
 
+/* A graded tensor-product mesh (Section 2.1: finite element spaces on meshes
+ * refined where the orbitals vary fast; here the refinement runs along each
+ * axis): x, y, z are host arrays of nx + 1, ny + 1 and nz + 1 node coordinates,
+ * finite and strictly increasing (the box is [x[0], x[nx]] x ...; Dirichlet on
+ * all faces).  The potential of paro_set_potential is then given at the 2x2x2
+ * Gauss points of these cells (same order).  Every call works as on a uniform
+ * mesh (the Q1 weights follow the cell sizes; the mass matrix is stored per
+ * node), except the Kohn-Sham calls and PARO_PRECOND_MG, which return
+ * PARO_ERR_ARG on a graded handle.  Other arguments and errors as
+ * paro_mesh_create. */
+int paro_mesh_create_graded(paro_mesh* out, int nx, int ny, int nz, const double* x, const double* y,
+                            const double* z, int precision, void* cuda_stream);
+
 /* Release the handle and all library-owned device memory.  Synchronises the stream. */
 int paro_mesh_destroy(paro_mesh m);
 

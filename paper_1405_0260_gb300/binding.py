@@ -154,6 +154,20 @@ def paro_mesh_create(n, lo, hi, precision=PARO_FP64, stream=0):
     return h
 
 
+def paro_mesh_create_graded(n, coords, precision=PARO_FP64, stream=0):
+    """A graded mesh: coords = three arrays of node coordinates (n_d + 1 each)."""
+    h = C.c_void_p()
+    ax = [np.ascontiguousarray(c, dtype=np.float64) for c in coords]
+    L = lib()
+    L.paro_mesh_create_graded.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double),
+                                          C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int, C.c_void_p]
+    L.paro_mesh_create_graded.restype = C.c_int
+    rc = L.paro_mesh_create_graded(C.byref(h), int(n[0]), int(n[1]), int(n[2]), _dptr(ax[0]), _dptr(ax[1]),
+                                   _dptr(ax[2]), int(precision), C.c_void_p(stream))
+    _check(rc, None)
+    return h
+
+
 def paro_mesh_destroy(h):
     return lib().paro_mesh_destroy(h)
 
@@ -192,7 +206,7 @@ def paro_apply(h, N, op, dtype, X_ptr, Y_ptr):
 class Mesh:
     """A mesh handle bound to a torch CUDA stream (torch tensors in and out)."""
 
-    def __init__(self, n, lo, hi, precision=PARO_FP64, stream=None):
+    def __init__(self, n, lo, hi, precision=PARO_FP64, stream=None, coords=None):
         import torch
 
         if not torch.cuda.is_available():
@@ -200,7 +214,10 @@ class Mesh:
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.n = tuple(int(v) for v in n)
         self.n_interior = (self.n[0] - 1) * (self.n[1] - 1) * (self.n[2] - 1)
-        self.h = paro_mesh_create(self.n, lo, hi, precision, self.stream.cuda_stream)
+        if coords is None:
+            self.h = paro_mesh_create(self.n, lo, hi, precision, self.stream.cuda_stream)
+        else:  # graded: node coordinates per axis (lo, hi unused)
+            self.h = paro_mesh_create_graded(self.n, coords, precision, self.stream.cuda_stream)
         self._keep = []
 
     def close(self):

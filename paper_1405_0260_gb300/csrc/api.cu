@@ -31,6 +31,12 @@ struct paro_mesh_s {
   bool have_pot = false;
   double* coef64 = nullptr;
   float* coef32 = nullptr;
+  // graded meshes: cell sizes (device), per-node mass weights, the weights of
+  // H = A - sigma M, and the packed float-float mass weights (mixed handles)
+  double* hcell = nullptr;
+  double* coefM64 = nullptr;
+  double* coefH64 = nullptr;
+  float *wMh = nullptr, *wMl = nullptr;
   double* dinv64 = nullptr;
   float* dinv32 = nullptr;
   Weights27 mw{};
@@ -130,6 +136,22 @@ namespace {
   } while (0)
 
 constexpr int kProfPairs = 256;
+
+// The mass and Hamiltonian applies: constant 27-point weights on uniform meshes,
+// per-node weights on graded ones.
+cudaError_t apply_M_f64(paro_mesh m, int Np, const double* x, double* y, const double* scale) {
+  if (m->g.graded) return launch_apply_f64(m->g, Np, m->coefM64, nullptr, 0.0, x, y, scale, m->st);
+  return launch_apply_f64(m->g, Np, nullptr, &m->mw, 0.0, x, y, scale, m->st);
+}
+cudaError_t apply_H_f64(paro_mesh m, int Np, const double* x, double* y) {
+  if (m->g.graded) return launch_apply_f64(m->g, Np, m->coefH64, nullptr, 0.0, x, y, nullptr, m->st);
+  return launch_apply_f64(m->g, Np, m->coef64, &m->mw, m->sigma, x, y, nullptr, m->st);
+}
+cudaError_t apply_M_ff(paro_mesh m, int Np, const float* xh, const float* xl, const double* scale, double* y64,
+                       float* yh, float* yl) {
+  if (m->g.graded) return launch_ff_apply(m->g, Np, m->wMh, m->wMl, nullptr, xh, xl, scale, y64, yh, yl, m->st);
+  return launch_ff_apply(m->g, Np, nullptr, nullptr, &m->mw, xh, xl, scale, y64, yh, yl, m->st);
+}
 
 int set_f32_layout(paro_mesh m, int want);
 
@@ -759,6 +781,7 @@ int check_precond(paro_mesh m, const paro_params& p) {
   if (p.precond != PARO_PRECOND_JACOBI && p.precond != PARO_PRECOND_MG)
     return fail(m, PARO_ERR_ARG, "unknown preconditioner");
   if (p.precond == PARO_PRECOND_MG) {
+    if (m->g.graded) return fail(m, PARO_ERR_ARG, "the multigrid preconditioner needs a uniform mesh");
     if (m->precision != PARO_MIXED)
       return fail(m, PARO_ERR_ARG, "the multigrid preconditioner runs in the float32 solves of a PARO_MIXED handle");
     if (p.mg_nu < 1 || p.mg_nu > 8 || p.mg_coarse_sweeps < 1 || p.mg_coarse_sweeps > 64)
@@ -928,10 +951,9 @@ int solve_packed(paro_mesh m, int N, const double* lam, const paro_params& p, pa
     // float-float mass apply (float64 accuracy on the float32 pipes); b stays as a
     // hi/lo pair in fah/fal for the solve (the Rayleigh-Ritz step reuses them after)
     LAUNCH(1, launch_split_ff((long long)g.G * Np, m->u, m->fxh, m->fxl, m->st));
-    LAUNCH(1, launch_ff_apply(g, Np, nullptr, nullptr, &m->mw, m->fxh, m->fxl, scale, nullptr, m->fah, m->fal,
-                              m->st));
+    LAUNCH(1, apply_M_ff(m, Np, m->fxh, m->fxl, scale, nullptr, m->fah, m->fal));
   } else {
-    LAUNCH(1, launch_apply_f64(g, Np, nullptr, &m->mw, 0.0, m->u, m->b, scale, m->st));
+    LAUNCH(1, apply_M_f64(m, Np, m->u, m->b, scale));
   }
   CK(cudaMemcpyAsync(m->x, m->u, sizeof(double) * g.G * Np, cudaMemcpyDeviceToDevice, m->st));
   m->x_split_fresh = m->precision == PARO_MIXED;  // fxh/fxl = split(u) = split(x)
@@ -1007,8 +1029,7 @@ int rr_packed(paro_mesh m, int N, const double* src, double* dst, double* lam, R
     LAUNCH(1, launch_split_ff((long long)g.G * Np, src, m->fxh, m->fxl, m->st));
     LAUNCH(1, launch_ff_apply(g, Np, m->wHh, m->wHl, nullptr, m->fxh, m->fxl, nullptr, nullptr, m->fah, m->fal,
                               m->st));
-    LAUNCH(1, launch_ff_apply(g, Np, nullptr, nullptr, &m->mw, m->fxh, m->fxl, nullptr, nullptr, m->fbh, m->fbl,
-                              m->st));
+    LAUNCH(1, apply_M_ff(m, Np, m->fxh, m->fxl, nullptr, nullptr, m->fbh, m->fbl));
     int nch = 0;
     LAUNCH(1, launch_gram_tc(g, Np, m->fxh, m->fah, m->gpart_tc, &nch, &m->cgst->status, m->st));
     LAUNCH(1, launch_gram_reduce1(Np, nch, m->gpart_tc, m->GA, m->st));
@@ -1020,27 +1041,32 @@ int rr_packed(paro_mesh m, int N, const double* src, double* dst, double* lam, R
     LAUNCH(1, launch_split_ff((long long)g.G * Np, src, m->fxh, m->fxl, m->st));
     LAUNCH(1, launch_ff_apply(g, Np, m->wHh, m->wHl, nullptr, m->fxh, m->fxl, nullptr, nullptr, m->fah, m->fal,
                               m->st));
-    LAUNCH(1, launch_ff_apply(g, Np, nullptr, nullptr, &m->mw, m->fxh, m->fxl, nullptr, nullptr, m->fbh, m->fbl,
-                              m->st));
+    LAUNCH(1, apply_M_ff(m, Np, m->fxh, m->fxl, nullptr, nullptr, m->fbh, m->fbl));
     int nch = 0;
     LAUNCH(1, launch_gram2_ff(g, Np, m->fxh, m->fxl, m->fah, m->fal, m->fbh, m->fbl, m->gpart_ff, &nch, m->st));
     LAUNCH(1, launch_gram_reduce(Np, nch, m->gpart_ff, m->GA, m->GB, m->st));
   } else {
-    LAUNCH(1, launch_apply_f64(g, Np, m->coef64, &m->mw, m->sigma, src, m->r, nullptr, m->st));  // H = A - sigma M
-    LAUNCH(1, launch_apply_f64(g, Np, nullptr, &m->mw, 0.0, src, m->q, nullptr, m->st));         // M
+    LAUNCH(1, apply_H_f64(m, Np, src, m->r));           // H = A - sigma M
+    LAUNCH(1, apply_M_f64(m, Np, src, m->q, nullptr));  // M
     LAUNCH(2, launch_gram2(g, N, Np, src, m->r, m->q, m->gpart, nullptr, m->GA, m->GB, m->st));
   }
   LAUNCH(1, launch_small_eig(N, m->GA, m->GB, m->eigwork, m->C, m->theta, &m->cgst->status, m->st,
                              &m->cgst->bar_count, clus));
   TRY(check_status(m, "rayleigh_ritz"));
-  // float-float rotation from the split X (C staged in shared memory whole, or in
-  // column blocks above kRotateFFMaxNp)
-  if (ff || tc)
+  // the rotation: on the tensor cores from the hi parts of X with the tensor-core
+  // Grams (the same 24-bit inputs), else in float-float from the split X (C staged
+  // in shared memory whole, or in column blocks above kRotateFFMaxNp), or float64
+  if (tc && Np <= 128)
+    LAUNCH(1, launch_rotate_tc(g, N, Np, m->fxh, m->C, dst, &m->cgst->status, m->st));
+  else if (ff || tc)
     LAUNCH(1, launch_rotate_ff(g, N, Np, m->fxh, m->fxl, m->C, dst, m->st));
   else
     LAUNCH(1, launch_rotate(g, N, Np, src, m->C, dst, m->st));
+  // the Ritz values and the status word (a bounded wait of the rotation) in one round trip
   CK(cudaMemcpyAsync(m->h_dbl, m->theta, sizeof(double) * N, cudaMemcpyDeviceToHost, m->st));
+  CK(cudaMemcpyAsync(m->h_int, &m->cgst->status, sizeof(int), cudaMemcpyDeviceToHost, m->st));
   CK(cudaStreamSynchronize(m->st));
+  if (m->h_int[0] != 0) TRY(check_status(m, "rayleigh_ritz (rotation)"));
   for (int i = 0; i < N; ++i) lam[i] = m->h_dbl[i];
   return PARO_OK;
 }
@@ -1132,6 +1158,7 @@ struct CallScope {
 long long gauss_count(const Grid& g) { return (long long)g.nx * g.ny * g.nz * 8; }
 
 int ensure_ks(paro_mesh m) {
+  if (m->g.graded) return fail(m, PARO_ERR_ARG, "the Kohn-Sham calls need a uniform mesh");
   if (m->ks_rho) return PARO_OK;
   const long long nq = gauss_count(m->g);
   TRY(dalloc(m, &m->ks_mom, 4));
@@ -1251,8 +1278,44 @@ void paro_default_params(paro_params* p) {
   p->wait_polls = 0;
 }
 
+static int mesh_create(paro_mesh* out, int nx, int ny, int nz, const double lo_in[3], const double hi_in[3],
+                       const double* const ax[3], int precision, void* cuda_stream);
+
 int paro_mesh_create(paro_mesh* out, int nx, int ny, int nz, const double lo[3], const double hi[3], int precision,
                      void* cuda_stream) {
+  const double* const none[3] = {nullptr, nullptr, nullptr};
+  return mesh_create(out, nx, ny, nz, lo, hi, none, precision, cuda_stream);
+}
+
+int paro_mesh_create_graded(paro_mesh* out, int nx, int ny, int nz, const double* x, const double* y,
+                            const double* z, int precision, void* cuda_stream) {
+  if (!out || !x || !y || !z) {
+    g_create_err = "null argument";
+    return PARO_ERR_ARG;
+  }
+  if (nx < 2 || ny < 2 || nz < 2 || nx > 1024 || ny > 1024 || nz > 1024) {
+    g_create_err = "cells per axis must be in [2, 1024]";
+    return PARO_ERR_ARG;
+  }
+  const double* const ax[3] = {x, y, z};
+  const int n[3] = {nx, ny, nz};
+  double lo[3], hi[3];
+  for (int d = 0; d < 3; ++d) {
+    for (int i = 0; i <= n[d]; ++i)
+      if (!std::isfinite(ax[d][i]) || (i > 0 && !(ax[d][i] > ax[d][i - 1]))) {
+        g_create_err = "node coordinates must be finite and strictly increasing along every axis";
+        return PARO_ERR_ARG;
+      }
+    lo[d] = ax[d][0];
+    hi[d] = ax[d][n[d]];
+  }
+  return mesh_create(out, nx, ny, nz, lo, hi, ax, precision, cuda_stream);
+}
+
+static int mesh_create(paro_mesh* out, int nx, int ny, int nz, const double lo_in[3], const double hi_in[3],
+                       const double* const ax[3], int precision, void* cuda_stream) {
+  const double* lo = lo_in;
+  const double* hi = hi_in;
   if (!out || !lo || !hi) {
     g_create_err = "null argument";
     return PARO_ERR_ARG;
@@ -1324,6 +1387,35 @@ int paro_mesh_create(paro_mesh* out, int nx, int ny, int nz, const double lo[3],
     paro_mesh_destroy(m);
     return PARO_ERR_CUDA;
   }
+  if (ax[0] != nullptr) {
+    // graded: cell sizes on the device, the per-node mass weights (fixed by the
+    // mesh) and, on mixed handles, their packed float-float copy
+    const int n3[3] = {nx, ny, nz};
+    std::vector<double> hc;
+    for (int d = 0; d < 3; ++d)
+      for (int c = 0; c < n3[d]; ++c) hc.push_back(ax[d][c + 1] - ax[d][c]);
+    if ((rc = dalloc(m, &m->hcell, hc.size())) || (rc = dalloc(m, &m->coefM64, (size_t)27 * g.G)) ||
+        (rc = dalloc(m, &m->coefH64, (size_t)27 * g.G)) ||
+        (precision == PARO_MIXED && ((rc = dalloc(m, &m->wMh, (size_t)g.G * kPackedW)) ||
+                                     (rc = dalloc(m, &m->wMl, (size_t)g.G * kPackedW))))) {
+      g_create_err = m->err;
+      paro_mesh_destroy(m);
+      return rc;
+    }
+    g.graded = 1;
+    g.hc = m->hcell;
+    e = cudaMemcpyAsync(m->hcell, hc.data(), sizeof(double) * hc.size(), cudaMemcpyHostToDevice, m->st);
+    if (e == cudaSuccess) e = launch_build_mass(g, m->coefM64, m->st);
+    if (e == cudaSuccess && precision == PARO_MIXED) {
+      Weights27 zero{};
+      e = launch_build_wff(g, m->coefM64, zero, 0.0, m->wMh, m->wMl, m->wMh, m->wMl, m->st);
+    }
+    if (e != cudaSuccess) {
+      g_create_err = std::string("graded mesh set-up: ") + cudaGetErrorString(e);
+      paro_mesh_destroy(m);
+      return PARO_ERR_CUDA;
+    }
+  }
   if ((e = cudaStreamSynchronize(m->st)) != cudaSuccess) {
     g_create_err = std::string("stream: ") + cudaGetErrorString(e);
     paro_mesh_destroy(m);
@@ -1360,8 +1452,11 @@ int paro_set_potential(paro_mesh m, const double* Vq, double sigma) {
                                                m->st));
   LAUNCH(2, launch_build_tma_operator<float>(m->g, m->coef32, m->dinv32, m->w32, m->dt32, m->dpitch,
                                               m->st));
+  if (m->g.graded)  // H = A - sigma M with the per-node mass weights
+    LAUNCH(1, launch_sub_scaled((long long)27 * m->g.G, m->coef64, sigma, m->coefM64, m->coefH64, m->st));
   if (m->precision == PARO_MIXED)
-    LAUNCH(1, launch_build_wff(m->g, m->coef64, m->mw, sigma, m->wAh, m->wAl, m->wHh, m->wHl, m->st));
+    LAUNCH(1, launch_build_wff(m->g, m->coef64, m->mw, sigma, m->wAh, m->wAl, m->wHh, m->wHl, m->st,
+                               m->g.graded ? m->coefM64 : nullptr));
   m->sigma = sigma;
   m->have_pot = true;
   m->mg.built = false;
@@ -1494,15 +1589,14 @@ int paro_apply(paro_mesh m, int N, int op, int dtype, const void* X, void* Y) {
   if (dtype == PARO_F64) {
     LAUNCH(1, launch_pack(m->g, N, Np, static_cast<const double*>(X), m->u, m->st));
     if (op == PARO_OP_A) LAUNCH(1, launch_apply_f64(m->g, Np, m->coef64, nullptr, 0.0, m->u, m->x, nullptr, m->st));
-    else if (op == PARO_OP_H) LAUNCH(1, launch_apply_f64(m->g, Np, m->coef64, &m->mw, m->sigma, m->u, m->x, nullptr, m->st));
-    else LAUNCH(1, launch_apply_f64(m->g, Np, nullptr, &m->mw, 0.0, m->u, m->x, nullptr, m->st));
+    else if (op == PARO_OP_H) LAUNCH(1, apply_H_f64(m, Np, m->u, m->x));
+    else LAUNCH(1, apply_M_f64(m, Np, m->u, m->x, nullptr));
     LAUNCH(1, launch_unpack(m->g, N, Np, m->x, static_cast<double*>(Y), m->st));
   } else if (dtype == PARO_FF) {
     LAUNCH(1, launch_pack(m->g, N, Np, static_cast<const double*>(X), m->u, m->st));
     LAUNCH(1, launch_split_ff((long long)m->g.G * Np, m->u, m->fxh, m->fxl, m->st));
     if (op == PARO_OP_M)
-      LAUNCH(1, launch_ff_apply(m->g, Np, nullptr, nullptr, &m->mw, m->fxh, m->fxl, nullptr, m->x, nullptr, nullptr,
-                                m->st));
+      LAUNCH(1, apply_M_ff(m, Np, m->fxh, m->fxl, nullptr, m->x, nullptr, nullptr));
     else
       LAUNCH(1, launch_ff_apply(m->g, Np, op == PARO_OP_A ? m->wAh : m->wHh, op == PARO_OP_A ? m->wAl : m->wHl,
                                 nullptr, m->fxh, m->fxl, nullptr, m->x, nullptr, nullptr, m->st));
@@ -1540,6 +1634,7 @@ int paro_mg_vcycle(paro_mesh m, int N, const float* R, float* Z, const paro_para
 
 int paro_density(paro_mesh m, int N, const double* U, const double* occ, double* rho_q) {
   TRY(check_common(m, N));
+  if (m->g.graded) return fail(m, PARO_ERR_ARG, "the Kohn-Sham calls need a uniform mesh");
   if (!U || !occ || !rho_q) return fail(m, PARO_ERR_ARG, "null pointer");
   const int Np = (N + 3) / 4 * 4;
   TRY(ensure_workspace(m, Np));

@@ -32,8 +32,15 @@ struct Grid {
   int Px, Py, Pz;      // padded nodes per axis
   long long G;         // padded node count
   int nI;              // interior node count
-  double hx, hy, hz;
+  double hx, hy, hz;   // cell sizes (graded meshes: their means)
+  int graded;          // 1: the cell sizes vary along the axes (tensor-product grading)
+  const double* hc;    // graded: device cell sizes, nx of x, then ny of y, then nz of z
 };
+
+// Graded meshes: the size of cell c along axis d (0 x, 1 y, 2 z).
+__device__ __forceinline__ double cell_h(const Grid& g, int d, int c) {
+  return g.hc[(d >= 1 ? g.nx : 0) + (d >= 2 ? g.ny : 0) + c];
+}
 
 template <typename T>
 struct V4 {
@@ -101,6 +108,10 @@ struct Weights27 {
 // stencil.cu
 cudaError_t launch_build_coef(const Grid& g, const double* Vq, double sigma, double* coef64, float* coef32,
                               double* dinv64, float* dinv32, cudaStream_t st);
+// graded meshes: the 27 mass weights of every node (coefM, SoA like coef), and
+// out = a - s b over n values (the H weights A - sigma M)
+cudaError_t launch_build_mass(const Grid& g, double* coefM, cudaStream_t st);
+cudaError_t launch_sub_scaled(long long n, const double* a, double s, const double* b, double* out, cudaStream_t st);
 void mass_weights(const Grid& g, Weights27* mw);  // constant mass stencil M
 // y = scale_o * (op x), op = coef (+ cw * wsub) ; T = float or double.  scale may be null.
 cudaError_t launch_apply_f64(const Grid& g, int Np, const double* coef, const Weights27* cw, double csub,
@@ -144,8 +155,9 @@ cudaError_t launch_refine_update_split(const Grid& g, int Np, double* x64, const
 
 // ff.cu: float64-accurate applies, Grams and rotation in float-float arithmetic
 cudaError_t launch_split_ff(long long n, const double* x, float* hi, float* lo, cudaStream_t st);
+// mcoef (graded meshes, per-node mass weights) replaces the constant mw in H = A - sigma M
 cudaError_t launch_build_wff(const Grid& g, const double* coef64, const Weights27& mw, double sigma, float* ahi,
-                             float* alo, float* hhi, float* hlo, cudaStream_t st);
+                             float* alo, float* hhi, float* hlo, cudaStream_t st, const double* mcoef = nullptr);
 // y = scale_o (W x): W the packed per-node weights (whi/wlo) or the constant weights cw
 cudaError_t launch_ff_apply(const Grid& g, int Np, const float* whi, const float* wlo, const Weights27* cw,
                             const float* xhi, const float* xlo, const double* scale, double* y64, float* yhi,
@@ -161,6 +173,9 @@ constexpr int kTcMaxNp = 256;
 size_t gram_tc_partial_doubles(const Grid& g, int Np);
 cudaError_t launch_gram_tc(const Grid& g, int Np, const float* xh, const float* yh, double* part, int* n_chunks,
                            int* status, cudaStream_t st);
+// gram_tc.cu: the rotation U = X C on the tensor cores (Np <= 128, X as float32 hi parts)
+cudaError_t launch_rotate_tc(const Grid& g, int N, int Np, const float* xh, const double* C, double* U, int* status,
+                             cudaStream_t st);
 constexpr int kRotateFFMaxNp = 144;  // whole C as float-float in shared memory (8 Np^2 bytes); column blocks above
 cudaError_t launch_rotate_ff(const Grid& g, int N, int Np, const float* xh, const float* xl, const double* C,
                              double* U, cudaStream_t st);

@@ -34,7 +34,8 @@ __global__ void k_split(long long n, const double* __restrict__ x, float* __rest
 // Packed float-float operator weights per padded node: w[g][o], o < 27 the
 // weights of row g of A (mode 0) or of H = A - sigma M (mode 1); o = 27 pads.
 __global__ void k_build_wff(Grid g, const double* __restrict__ coef, Weights27 mw, double sigma, float* __restrict__ ahi,
-                            float* __restrict__ alo, float* __restrict__ hhi, float* __restrict__ hlo) {
+                            float* __restrict__ alo, float* __restrict__ hhi, float* __restrict__ hlo,
+                            const double* __restrict__ mcoef) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= g.G * kPackedW) return;
   const long long node = t / kPackedW;
@@ -43,7 +44,7 @@ __global__ void k_build_wff(Grid g, const double* __restrict__ coef, Weights27 m
   const int x = (int)(node % g.Px), y = (int)((node / g.Px) % g.Py), z = (int)(node / ((long long)g.Px * g.Py));
   if (o < 27 && x > 0 && x < g.Px - 1 && y > 0 && y < g.Py - 1 && z > 0 && z < g.Pz - 1) {
     a = coef[(long long)o * g.G + node];
-    h = a - sigma * mw.w[o];
+    h = a - sigma * (mcoef != nullptr ? mcoef[(long long)o * g.G + node] : mw.w[o]);
   }
   const FF fa = ff_split(a), fh = ff_split(h);
   ahi[t] = fa.hi;
@@ -295,8 +296,8 @@ cudaError_t launch_split_ff(long long n, const double* x, float* hi, float* lo, 
 }
 
 cudaError_t launch_build_wff(const Grid& g, const double* coef64, const Weights27& mw, double sigma, float* ahi,
-                             float* alo, float* hhi, float* hlo, cudaStream_t st) {
-  k_build_wff<<<nblk(g.G * kPackedW, 256), 256, 0, st>>>(g, coef64, mw, sigma, ahi, alo, hhi, hlo);
+                             float* alo, float* hhi, float* hlo, cudaStream_t st, const double* mcoef) {
+  k_build_wff<<<nblk(g.G * kPackedW, 256), 256, 0, st>>>(g, coef64, mw, sigma, ahi, alo, hhi, hlo, mcoef);
   return cudaGetLastError();
 }
 

@@ -378,6 +378,221 @@ cudaError_t launch_tc(long long G, int Np, int xr0, int na, int yc0, int nb, con
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// The rotation U = X C of the Rayleigh-Ritz step (Step 4) on the tensor cores,
+// for Np <= kRotTcMaxNp: D[128 nodes][NB columns] = A[128 nodes][K = a] B[K = a][NB]
+// with A the digits of X (the float32 hi parts, one power-of-two scale per node
+// row: the row maximum over a) and B the digits of C (one scale per column b).
+// Three digits each, levels l = i + j <= 2 in their own FP32 accumulators; every
+// level sum over K = a <= 128 terms stays below 2^24, so it is exact.  The three
+// levels are combined in float-float and scaled by 2^(E_g + F_b) in float64.
+// The error is the rounding of X and C to 24 bits below their row / column
+// maximum (unbiased), the accuracy of the tensor-core Grams' inputs.
+// ---------------------------------------------------------------------------
+constexpr int kRotTcMaxNp = 128;
+
+__host__ __device__ constexpr int rot_sbo(int Kp) { return (Kp / 8) * kTcLBO + 16; }
+
+template <int NB>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_rotate_tc(long long G, int N, int Np, int Kp, const float* __restrict__ xh, const double* __restrict__ C,
+                double* __restrict__ U, int* __restrict__ status) {
+  constexpr uint32_t kTmemCols = kTcDigits * NB <= 128 ? 128 : 256;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int sbo = rot_sbo(Kp);
+  const int aPiece = (kTcM / 8) * sbo;                 // one digit plane of A (128 node rows)
+  const int nbp = (Np + NB - 1) / NB * NB;              // C columns, padded to whole N-tiles
+  const int bPiece = (nbp / 8) * sbo;                   // one digit plane of B (all columns)
+  unsigned char* aBuf = smem;
+  unsigned char* bBuf = smem + kTcDigits * aPiece;
+  int* cexpB = reinterpret_cast<int*>(bBuf + kTcDigits * bPiece);  // [nbp] column exponents of C
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_fail;
+  __shared__ unsigned rmax[kTcM];
+  __shared__ int rexp[kTcM];
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  const int koct = Kp / 8;
+
+  // zero the operand planes (K beyond N and rows beyond Np stay zero)
+  const int zbytes = kTcDigits * (aPiece + bPiece);
+  for (int i = tid; i < zbytes / 16; i += kTcThreads) reinterpret_cast<uint4*>(smem)[i] = make_uint4(0, 0, 0, 0);
+  if (tid == 0) {
+    s_fail = 0;
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  __syncthreads();
+  // B: the digits of C, row b (column of C), K = a; one exponent per column
+  for (int b = tid; b < nbp; b += kTcThreads) {
+    unsigned m = 0u;
+    if (b < Np)
+      for (int a = 0; a < N; ++a) m = max(m, __float_as_uint(__double2float_rn(C[(long long)a * Np + b])) & 0x7FFFFFFFu);
+    cexpB[b] = col_exponent(m);
+  }
+  __syncthreads();
+  for (int w = tid; w < nbp * koct; w += kTcThreads) {
+    const int b = w / koct, oct = w % koct;
+    const float sc = pow2f(8 - cexpB[b]);
+    uint32_t q[kTcDigits][4];
+#pragma unroll
+    for (int j = 0; j < 8; j += 2) {
+      const int a0 = 8 * oct + j;
+      const float c0 = (b < Np && a0 < N) ? __double2float_rn(C[(long long)a0 * Np + b]) : 0.f;
+      const float c1 = (b < Np && a0 + 1 < N) ? __double2float_rn(C[(long long)(a0 + 1) * Np + b]) : 0.f;
+      float d0[kTcDigits], d1[kTcDigits];
+      digits3(c0, sc, d0);
+      digits3(c1, sc, d1);
+#pragma unroll
+      for (int p = 0; p < kTcDigits; ++p) q[p][j / 2] = pack_bf16(d0[p], d1[p]);
+    }
+    unsigned char* dst = bBuf + (uint32_t)((b >> 3) * sbo + oct * kTcLBO + (b & 7) * 16);
+#pragma unroll
+    for (int p = 0; p < kTcDigits; ++p)
+      *reinterpret_cast<uint4*>(dst + p * bPiece) = make_uint4(q[p][0], q[p][1], q[p][2], q[p][3]);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+
+  // A conversion items: (node row, octet of a); at most 4 a thread (128 rows x 16 octets)
+  constexpr int kIt = 4;
+  const int nitems = kTcM * koct;
+  float v[kIt][8];
+  const long long ntiles = (G + kTcM - 1) / kTcM;
+  auto load = [&](long long tile) {
+#pragma unroll
+    for (int it = 0; it < kIt; ++it) {
+      const int w = tid + it * kTcThreads;
+      const int r = w / koct, oct = w % koct;
+      const long long g = tile * kTcM + r;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int a = 8 * oct + j;
+        v[it][j] = (w < nitems && tile < ntiles && g < G && a < N) ? __ldg(xh + g * Np + a) : 0.f;
+      }
+    }
+  };
+  const uint32_t idesc = idesc_bf16(kTcM, NB);
+  const uint32_t aBase = smem_u32(aBuf), bBase = smem_u32(bBuf);
+  const int row = 32 * (warp % 4) + lane;  // node row of this thread in the read-out
+  constexpr int kColsT = NB / 4;           // columns a thread reads out
+  const int col0 = (warp / 4) * kColsT;
+  uint32_t phase = 0;
+  load(blockIdx.x);
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    // row maxima -> exponents, then the digits of this tile's X rows
+    for (int i = tid; i < kTcM; i += kTcThreads) rmax[i] = 0u;
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < kIt; ++it) {
+      const int w = tid + it * kTcThreads;
+      if (w < nitems) {
+        unsigned m = 0u;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) m = max(m, __float_as_uint(v[it][j]) & 0x7FFFFFFFu);
+        if (m) atomicMax(&rmax[w / koct], m);
+      }
+    }
+    __syncthreads();
+    for (int i = tid; i < kTcM; i += kTcThreads) rexp[i] = col_exponent(rmax[i]);
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < kIt; ++it) {
+      const int w = tid + it * kTcThreads;
+      if (w < nitems) {
+        const int r = w / koct, oct = w % koct;
+        const float sc = pow2f(8 - rexp[r]);
+        uint32_t q[kTcDigits][4];
+#pragma unroll
+        for (int j = 0; j < 8; j += 2) {
+          float d0[kTcDigits], d1[kTcDigits];
+          digits3(v[it][j], sc, d0);
+          digits3(v[it][j + 1], sc, d1);
+#pragma unroll
+          for (int p = 0; p < kTcDigits; ++p) q[p][j / 2] = pack_bf16(d0[p], d1[p]);
+        }
+        unsigned char* dst = aBuf + (uint32_t)((r >> 3) * sbo + oct * kTcLBO + (r & 7) * 16);
+#pragma unroll
+        for (int p = 0; p < kTcDigits; ++p)
+          *reinterpret_cast<uint4*>(dst + p * aPiece) = make_uint4(q[p][0], q[p][1], q[p][2], q[p][3]);
+      }
+    }
+    fence_proxy_async_smem();  // generic writes -> the MMA's async-proxy reads
+    load(tile + gridDim.x);    // the next tile's X rows are in flight during the MMAs
+    const long long g = tile * kTcM + row;
+    const int eg = rexp[row];
+    for (int n0 = 0; n0 < Np; n0 += NB) {
+      tc_fence_before();
+      __syncthreads();
+      if (tid == 0) {
+        tc_fence_after();
+#pragma unroll
+        for (int l = 0; l < kTcDigits; ++l)
+#pragma unroll
+          for (int i = 0; i <= l; ++i)
+            for (int ks = 0; ks < Kp / 16; ++ks) {
+              const uint64_t ad = smem_desc(aBase + i * aPiece + ks * 2 * kTcLBO, kTcLBO, sbo);
+              const uint64_t bd =
+                  smem_desc(bBase + (l - i) * bPiece + (n0 / 8) * sbo + ks * 2 * kTcLBO, kTcLBO, sbo);
+              mma_bf16(tmem + (uint32_t)(l * NB), ad, bd, idesc, (i > 0 || ks > 0) ? 1u : 0u);
+            }
+        mma_commit(&bar);
+      }
+      bool ok = mbar_wait(&bar, phase);
+      if (!ok) {
+        s_fail = 1;
+        ok = mbar_wait(&bar, phase);  // let the MMAs in flight end before the memory is freed (bounded)
+      }
+      phase ^= 1;
+      tc_fence_after();
+      __syncthreads();
+      if (s_fail) break;
+      // U[g][n0 + b] = 2^(E_g + F_b - 16) (L0 + L1 2^-8 + L2 2^-16)
+#pragma unroll
+      for (int c = 0; c < kColsT; c += 8) {
+        const uint32_t ta = tmem + ((uint32_t)(32 * (warp % 4)) << 16) + (uint32_t)(col0 + c);
+        float v0[8], v1[8];
+        tmem_ld8(ta, v0);
+        tmem_ld8(ta + NB, v1);
+        FF tsum[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) two_sum(v0[i], __fmul_rn(v1[i], 0x1p-8f), tsum[i].hi, tsum[i].lo);
+        tmem_ld8(ta + 2 * NB, v0);
+        double out[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          ff_add(tsum[i], FF{__fmul_rn(v0[i], 0x1p-16f), 0.f});
+          const int b = n0 + col0 + c + i;
+          out[i] = b < Np ? ldexp(ff_to_double(ff_norm(tsum[i])), eg + cexpB[b] - 16) : 0.0;
+        }
+        const int b0 = n0 + col0 + c;
+        if (g < G && b0 < Np) {
+          double* dst = U + g * Np + b0;
+#pragma unroll
+          for (int i = 0; i < 8; i += 2)
+            if (b0 + i < Np) *reinterpret_cast<double2*>(dst + i) = make_double2(out[i], out[i + 1]);
+        }
+      }
+    }
+    if (s_fail) break;
+  }
+  if (s_fail && tid == 0) atomicOr(status, kStatTimeout);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
 }  // namespace
 
 // One CTA per SM (>= 150 KB of shared memory), chunks a multiple of kTcSuper nodes.
@@ -414,6 +629,34 @@ cudaError_t launch_gram_tc(const Grid& g, int Np, const float* xh, const float* 
       if (e != cudaSuccess) return e;
     }
   return cudaSuccess;
+}
+
+}  // namespace paro
+
+namespace paro {
+
+// U = X C on the tensor cores (Np <= kRotTcMaxNp): X as the float32 hi parts
+// [G][Np], C float64 [Np][Np] (zero beyond N), U float64 [G][Np].
+cudaError_t launch_rotate_tc(const Grid& g, int N, int Np, const float* xh, const double* C, double* U, int* status,
+                             cudaStream_t st) {
+  if (Np < 4 || Np % 4 != 0 || Np > kRotTcMaxNp || N > Np) return cudaErrorInvalidValue;
+  const int Kp = (Np + 15) / 16 * 16;
+  const long long ntiles = (g.G + kTcM - 1) / kTcM;
+  const int grid = (int)(ntiles < 152 ? ntiles : 152);
+  if (Np <= 32) {
+    const int nbp = 32;
+    const size_t smem = (size_t)kTcDigits * ((kTcM / 8) + nbp / 8) * rot_sbo(Kp) + sizeof(int) * nbp;
+    cudaError_t e = allow_max_dyn_smem((const void*)k_rotate_tc<32>);
+    if (e != cudaSuccess) return e;
+    k_rotate_tc<32><<<grid, kTcThreads, smem, st>>>(g.G, N, Np, Kp, xh, C, U, status);
+  } else {
+    const int nbp = (Np + 63) / 64 * 64;
+    const size_t smem = (size_t)kTcDigits * ((kTcM / 8) + nbp / 8) * rot_sbo(Kp) + sizeof(int) * nbp;
+    cudaError_t e = allow_max_dyn_smem((const void*)k_rotate_tc<64>);
+    if (e != cudaSuccess) return e;
+    k_rotate_tc<64><<<grid, kTcThreads, smem, st>>>(g.G, N, Np, Kp, xh, C, U, status);
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace paro

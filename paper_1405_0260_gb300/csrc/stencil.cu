@@ -39,14 +39,24 @@ __global__ void k_build_coef(Grid g, const double* __restrict__ Vq, double sigma
   int k = t / iy + 1;
   long long gp = ((long long)k * g.Py + j) * g.Px + i;
   double w[27];
+  // 1-D stiffness and mass rows at the node, from the sizes of its two cells
+  // along each axis (uniform: k = (-1, 2, -1)/h, m = (1, 4, 1) h/6)
+  double kr[3][3], mr[3][3];
+  const int ijk[3] = {i, j, k};
+  const double hu[3] = {g.hx, g.hy, g.hz};
+  for (int d = 0; d < 3; ++d) {
+    const double hl = g.graded ? cell_h(g, d, ijk[d] - 1) : hu[d];
+    const double hr = g.graded ? cell_h(g, d, ijk[d]) : hu[d];
+    kr[d][0] = -1.0 / hl, kr[d][1] = 1.0 / hl + 1.0 / hr, kr[d][2] = -1.0 / hr;
+    mr[d][0] = hl / 6.0, mr[d][1] = (hl + hr) / 3.0, mr[d][2] = hr / 6.0;
+  }
   for (int dz = -1; dz <= 1; ++dz)
     for (int dy = -1; dy <= 1; ++dy)
       for (int dx = -1; dx <= 1; ++dx) {
-        double kk = k1(dx, g.hx) * m1(dy, g.hy) * m1(dz, g.hz) + m1(dx, g.hx) * k1(dy, g.hy) * m1(dz, g.hz) +
-                    m1(dx, g.hx) * m1(dy, g.hy) * k1(dz, g.hz);
+        double kk = kr[0][dx + 1] * mr[1][dy + 1] * mr[2][dz + 1] + mr[0][dx + 1] * kr[1][dy + 1] * mr[2][dz + 1] +
+                    mr[0][dx + 1] * mr[1][dy + 1] * kr[2][dz + 1];
         w[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)] = 0.5 * kk;
       }
-  const double wq = g.hx * g.hy * g.hz / 8.0;
   // The 8 cells around the node; (cx, cy, cz) selects the cell, the node sits at
   // local corner a = (1-cx, 1-cy, 1-cz) of it.
   for (int cz = 0; cz < 2; ++cz)
@@ -54,6 +64,9 @@ __global__ void k_build_coef(Grid g, const double* __restrict__ Vq, double sigma
       for (int cx = 0; cx < 2; ++cx) {
         int ex = i - 1 + cx, ey = j - 1 + cy, ez = k - 1 + cz;
         long long cell = ((long long)ez * g.ny + ey) * g.nx + ex;
+        // Gauss weight of the cell: its volume / 8
+        const double wq = g.graded ? cell_h(g, 0, ex) * cell_h(g, 1, ey) * cell_h(g, 2, ez) / 8.0
+                                   : g.hx * g.hy * g.hz / 8.0;
         // row a of the cell's potential matrix: sum_q (V_q + sigma) phi_a(x_q) phi_b(x_q)
         // for the 8 corners b, i.e. the values (V + sigma) phi_a at the Gauss points
         // projected on the corners (the transpose of interp8, which has the same form)
@@ -75,6 +88,31 @@ __global__ void k_build_coef(Grid g, const double* __restrict__ Vq, double sigma
   }
   dinv64[gp] = 1.0 / w[13];
   dinv32[gp] = 1.0f / (float)w[13];
+}
+
+// Graded meshes: the mass weights of every interior node, m_x (x) m_y (x) m_z with
+// the 1-D mass rows of the node's two cells per axis; zero on boundary nodes.
+__global__ void k_build_mass(Grid g, double* __restrict__ coefM) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= g.nI) return;
+  const int ix = g.nx - 1, iy = g.ny - 1;
+  const int i = n % ix + 1, t = n / ix;
+  const int j = t % iy + 1, k = t / iy + 1;
+  const long long gp = ((long long)k * g.Py + j) * g.Px + i;
+  const int ijk[3] = {i, j, k};
+  double mr[3][3];
+  for (int d = 0; d < 3; ++d) {
+    const double hl = cell_h(g, d, ijk[d] - 1), hr = cell_h(g, d, ijk[d]);
+    mr[d][0] = hl / 6.0, mr[d][1] = (hl + hr) / 3.0, mr[d][2] = hr / 6.0;
+  }
+  for (int o = 0; o < 27; ++o)
+    coefM[(long long)o * g.G + gp] = mr[0][o % 3] * mr[1][(o / 3) % 3] * mr[2][o / 9];
+}
+
+__global__ void k_sub_scaled(long long n, const double* __restrict__ a, double s, const double* __restrict__ b,
+                             double* __restrict__ out) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) out[t] = a[t] - s * b[t];
 }
 
 // MODE 0: y = coef x.  MODE 1: y = (coef - csub * cw) x.  MODE 2: y = cw x.
@@ -235,6 +273,16 @@ void mass_weights(const Grid& g, Weights27* mw) {
 cudaError_t launch_build_coef(const Grid& g, const double* Vq, double sigma, double* coef64, float* coef32,
                               double* dinv64, float* dinv32, cudaStream_t st) {
   k_build_coef<<<nblk(g.nI, 128), 128, 0, st>>>(g, Vq, sigma, coef64, coef32, dinv64, dinv32);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_mass(const Grid& g, double* coefM, cudaStream_t st) {
+  k_build_mass<<<nblk(g.nI, 128), 128, 0, st>>>(g, coefM);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sub_scaled(long long n, const double* a, double s, const double* b, double* out, cudaStream_t st) {
+  k_sub_scaled<<<nblk(n, 256), 256, 0, st>>>(n, a, s, b, out);
   return cudaGetLastError();
 }
 

@@ -47,3 +47,26 @@ def gram_tc_error(n, X, Y):
     var = vx.T @ (Y ** 2) + (X ** 2).T @ vy
     entries = X.shape[1] * Y.shape[1]
     return float(np.sqrt(2.0 * np.max(var)) * np.sqrt(2.0 * np.log(max(entries, 2))))
+
+
+def rotation_tc_error(X, C, MU):
+    """Expected largest entry error of U^T M U added by the tensor-core rotation U = X C.
+
+    The rotation rounds every X row to 24 bits below its largest |value| (over the
+    orbitals) and every C column to 24 bits below its largest |value|, to nearest;
+    dU = dX C + X dC has per-entry variances var_U[g, i] = sum_a (var(dX_ga) C_ai^2
+    + X_ga^2 var(dC_ai)), and (U + dU)^T M (U + dU) - U^T M U ~ dU^T M U + U^T M dU
+    has entry variances sum_g (var_U[g, i] MU_gj^2 + var_U[g, j] MU_gi^2).  Returned:
+    the largest standard deviation times sqrt(2 ln N^2), as gram_tc_error.
+    """
+    def step2(A, axis):
+        amax = np.max(np.abs(A), axis=axis, keepdims=True)
+        E = np.where(amax > 0, np.floor(np.log2(np.where(amax > 0, amax, 1.0))) + 1.0, 0.0)
+        return np.where(amax > 0, 2.0 ** (2 * (E - 24)) / 12.0, 0.0)
+
+    vx = step2(X, 1)  # per node row
+    vc = step2(C, 0)  # per column of C
+    varU = vx * np.sum(C ** 2, axis=0)[None, :] + (X ** 2) @ np.broadcast_to(vc, C.shape)
+    var = varU.T @ (MU ** 2) + (MU ** 2).T @ varU
+    N = C.shape[1]
+    return float(np.sqrt(np.max(var)) * np.sqrt(2.0 * np.log(max(N * N, 2))))

@@ -16,7 +16,7 @@ import os
 import numpy as np
 import pytest
 
-from gram_budget import gram_tc_error
+from gram_budget import gram_tc_error, rotation_tc_error
 from oracle import paro as O
 from paper_1405_0260_gb300 import workloads as W
 
@@ -299,7 +299,10 @@ def test_rayleigh_ritz_tensor_core_grams_match_oracle(B, N):
     assert err < 1e-6  # the mixed path's eigenvalue target
     u = host(U)
     orth = np.max(np.abs(u.T @ (ops.M @ u) - np.eye(N)))
-    assert orth < 10 * eB / lmin, (orth, eB / lmin)
+    # N <= 128: the rotation U = X C runs on the tensor cores too, from the same
+    # 24-bit inputs; its rounding adds rotation_tc_error
+    eR = rotation_tc_error(X0, ref.C, ops.M @ ref.U) if N <= 128 else 0.0
+    assert orth < 10 * (eB / lmin + eR), (orth, eB / lmin, eR)
     # single Ritz vectors whose Ritz value is separated from its neighbours (M-principal
     # angles: normalisation errors of the size bounded above do not count as angles)
     gaps = np.minimum(np.diff(ref.lam, prepend=-np.inf), np.diff(ref.lam, append=np.inf))

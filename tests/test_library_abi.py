@@ -122,6 +122,17 @@ def test_host_side_argument_checks_need_no_gpu(lib):
     assert lib.paro_ks_density_in(None, None) == -1
     assert lib.paro_orbital_solve(None, 1, None, None, None, None, None) == -1
     assert lib.paro_rayleigh_ritz(None, 1, None, None, None, None) == -1
+    # graded meshes: node coordinates must be finite and strictly increasing (checked on the host)
+    h = ctypes.c_void_p()
+    ok = (ctypes.c_double * 4)(0.0, 1.0, 2.0, 3.0)
+    bad = (ctypes.c_double * 4)(0.0, 1.0, 1.0, 3.0)
+    lib.paro_mesh_create_graded.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                            ctypes.c_void_p]
+    assert lib.paro_mesh_create_graded(ctypes.byref(h), 3, 3, 3, ok, bad, ok, 0, None) == -1
+    assert "strictly increasing" in B.paro_last_error(None)
+    assert lib.paro_mesh_create_graded(ctypes.byref(h), 1, 3, 3, ok, ok, ok, 0, None) == -1
+    assert lib.paro_mesh_create_graded(ctypes.byref(h), 3, 3, 3, None, ok, ok, 0, None) == -1
     t = ctypes.c_double(0.0)
     assert lib.paro_peak_fma(7, 1, ctypes.c_void_p(1), ctypes.byref(t), None) == -1  # unknown dtype
     assert lib.paro_peak_fma(0, 0, ctypes.c_void_p(1), ctypes.byref(t), None) == -1  # iters < 1
