@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 import scipy.sparse as sp
 
+import test_oracle_graded as GRADED
 import test_oracle_ks as KSPINS
 import test_oracle_mg as MGPINS
 import test_oracle_pins as PINS
@@ -36,6 +37,7 @@ def test_pins_pass_unmutated():
     KSPINS.test_slater_energy_of_a_gaussian_density()
     MGPINS.test_prolongation_evaluates_the_coarse_function((8, 6, 4))
     KSPINS.test_mixing_moves_the_input_density_toward_the_output_by_the_mixing_fraction()
+    GRADED.test_graded_stiffness_and_mass_are_kronecker_products((6, 5, 7), (2.0, 1.5, 3.0), (1.5, 0.8, 2.5))
 
 
 def test_wrong_gauss_abscissa_is_caught(monkeypatch):
@@ -151,3 +153,11 @@ def test_swapped_mixing_direction_is_caught(monkeypatch):
     # rho_in <- mix rho_in + (1 - mix) rho_out: the roles of the two densities swapped
     monkeypatch.setattr(KS, "mix_density", lambda rho_in, rho_out, mix: mix * rho_in + (1.0 - mix) * rho_out)
     _fails(KSPINS.test_mixing_moves_the_input_density_toward_the_output_by_the_mixing_fraction)
+
+
+def test_graded_stiffness_with_the_axes_swapped_is_caught(monkeypatch):
+    # the unit cell's gradient parts paired with the wrong cell sizes (x with h_z):
+    # invisible on a uniform mesh, and on a graded mesh with equal spacing per axis
+    orig = O._unit_stiffness_parts
+    monkeypatch.setattr(O, "_unit_stiffness_parts", lambda: orig()[::-1].copy())
+    _fails(GRADED.test_graded_stiffness_and_mass_are_kronecker_products, (6, 5, 7), (2.0, 1.5, 3.0), (1.5, 0.8, 2.5))
