@@ -446,6 +446,7 @@ int make_plans(paro_mesh m, int Np) {
     a.p[0] = m->p32a;
     a.p[1] = m->s32;
     a.part = m->cg2part;
+    a.pub = m->cg2part + (size_t)2 * 5 * kMaxGrid1 * Np;
     a.st = m->cgst;
     a.spin = kSpinLimit;
     a.inner = 1;
@@ -506,7 +507,7 @@ int ensure_workspace(paro_mesh m, int Np) {
   // per-CTA partials: up to 4 CTAs per SM, 3 values per orbital, two buffers
   TRY(dalloc(m, &m->cgpart, (size_t)2 * 3 * 4 * m->nsm * Np));
   // single-pass CG: 5 partial sums per orbital and CTA, two buffers
-  TRY(dalloc(m, &m->cg2part, (size_t)2 * 5 * kMaxGrid1 * Np));
+  TRY(dalloc(m, &m->cg2part, (size_t)2 * 5 * kMaxGrid1 * Np + (size_t)2 * 4 * Np));  // partials, then steps
   m->Np_alloc = Np;
   TRY(make_plans(m, Np));
   return PARO_OK;

@@ -138,7 +138,8 @@ struct CG2Args {
   int N, Np;
   float* x;
   float *r[2], *q[2], *p[2];  // the two buffer sets (read by pass parity, written by the other)
-  double* part;               // per-CTA partial sums [2][5][grid][Np] (two buffers by pass parity)
+  double* part;               // per-CTA partial sums [2][Np][5][grid] (two buffers by pass parity)
+  double* pub;                // per-orbital step of a pass, [2][Np][4]: alpha, beta, still iterating
   CGDevState* st;
   unsigned spin;              // poll limit of every bounded wait
   int inner;                  // 1: reaching maxit is not an error (refinement carries on)

@@ -26,9 +26,13 @@
 // neither loaded nor stored, and the threads that would handle it are whole
 // idle warps (thread = node slot + nthr x active-group slot).
 //
-// Cross-CTA reduction: every CTA writes its partials, meets the others at one
-// bounded grid barrier and sums all partials in the same fixed order, so every
-// CTA derives identical scalars and masks.
+// Cross-CTA reduction: every CTA writes its partials and meets the others at a
+// bounded grid barrier; the owner CTA of orbital o (o mod grid) then sums that
+// orbital's partials over all CTAs in a fixed order, takes the scalar step
+// (alpha, beta, convergence) and publishes it; a second barrier, and every CTA
+// reads the published steps.  Each partial is read once (not by every CTA: 152
+// CTAs reading the same 120 KB of partials took ~9 us a pass at 64^3 x 20), and
+// the results are identical everywhere and run to run.
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -267,21 +271,35 @@ __global__ void __launch_bounds__(kMaxThr2, 1) k_cg2(CG2Args a, K1Geom geo, cons
   bool timed_out = false;
   int status = 0;
 
-  // adds the consumers' per-orbital sums of the block's active groups into sacc
-  auto flush = [&](int ob, int na, const float (&dt)[kDots][4]) {
-    const int cols = 4 * na;
-    double* tmp = sred + (size_t)nthr * cols;
+  // adds the consumers' per-orbital sums of the block's active groups into sacc: a
+  // float32 butterfly over the 32 node slots of each warp (a warp holds one group
+  // slot: nthr is a multiple of 32), then the warps of a group slot in order, in
+  // float64 (two consumer barriers, the order fixed)
+  auto flush = [&](int ob, int na, float (&dt)[kDots][4]) {
+    const int wpg = nthr >> 5;
 #pragma unroll
-    for (int d = 0; d < kDots; ++d) {
-      if (k < na) {
+    for (int d = 0; d < kDots; ++d)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) sred[j * cols + 4 * k + c] = (double)dt[d][c];
+      for (int c = 0; c < 4; ++c) {
+        float v = dt[d][c];
+#pragma unroll
+        for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+        dt[d][c] = v;
       }
-      consumer_sync(NC);
-      consumer_colsum(sred, nthr, cols, tmp, NC);
-      for (int t = tid; t < cols; t += NC) sacc[d * Np + 4 * slist[ob * G4 + t / 4] + t % 4] += tmp[t];
-      consumer_sync(NC);
+    if (lane == 0 && k < na) {
+#pragma unroll
+      for (int d = 0; d < kDots; ++d)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) sred[(tid >> 5) * (kDots * 4) + d * 4 + c] = (double)dt[d][c];
     }
+    consumer_sync(NC);
+    for (int t = tid; t < kDots * 4 * na; t += NC) {
+      const int kk = t / (kDots * 4), e = t - kk * (kDots * 4);
+      double v = 0.0;
+      for (int q = 0; q < wpg; ++q) v += sred[(kk * wpg + q) * (kDots * 4) + e];
+      sacc[(e >> 2) * Np + 4 * slist[ob * G4 + kk] + (e & 3)] += v;
+    }
+    consumer_sync(NC);
   };
 
   // consumers: one pass over this CTA's column-planes; false on a timed-out wait.
@@ -453,8 +471,26 @@ __global__ void __launch_bounds__(kMaxThr2, 1) k_cg2(CG2Args a, K1Geom geo, cons
     __syncthreads();
   };
 
-  double* tot = sred;                              // [5 Np] totals
-  double* scratch = sred + (size_t)kDots * Np;     // reduction slices
+  // bounded grid barrier: arrival `target` of the launch's counter
+  auto grid_sync = [&](unsigned target) -> bool {
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) {
+      atomicAdd(&a.st->bar_count, 1u);
+      int okb = 0;
+      for (unsigned i = 0; i < spin; ++i) {
+        if (ld_acquire_u32(&a.st->bar_count) >= target) {
+          okb = 1;
+          break;
+        }
+        __nanosleep(32);
+      }
+      __threadfence();
+      s_ok = okb;
+    }
+    __syncthreads();
+    return s_ok != 0;
+  };
   for (int npass = 0;; ++npass) {
     if (tid == 0) s_nact = 0;
     __syncthreads();
@@ -493,77 +529,85 @@ __global__ void __launch_bounds__(kMaxThr2, 1) k_cg2(CG2Args a, K1Geom geo, cons
     }
     first = false;
     rd ^= 1;
-    // partials of this CTA (two buffers by pass parity: with one barrier a pass, a
-    // fast CTA writes pass k+1's while slower ones may still read pass k's), then
-    // one bounded grid barrier; the next pass reads r, q, p by TMA
-    double* part = a.part + (long long)(npass & 1) * kDots * gridDim.x * Np;
+    // partials of this CTA as [o][d][CTA], then the first bounded grid barrier (the
+    // owners read them before the second one, which every CTA passes before it
+    // writes the next pass's)
+    const unsigned nG = gridDim.x;
+    double* part = a.part + (long long)(npass & 1) * kDots * nG * Np;
     for (int t = tid; t < kDots * Np; t += blockDim.x) {
       const int d = t / Np, o = t - d * Np;
-      part[((long long)d * gridDim.x + blockIdx.x) * Np + o] = sacc[t];
+      part[((long long)o * kDots + d) * nG + blockIdx.x] = sacc[t];
     }
-    fence_proxy_async_global2();
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) {
-      const unsigned target = (unsigned)(npass + 1) * gridDim.x;
-      atomicAdd(&a.st->bar_count, 1u);
-      int okb = 0;
-      for (unsigned i = 0; i < spin; ++i) {
-        if (ld_acquire_u32(&a.st->bar_count) >= target) {
-          okb = 1;
-          break;
-        }
-        __nanosleep(32);
-      }
-      __threadfence();
-      s_ok = okb;
-    }
-    __syncthreads();
-    if (!s_ok) {
+    fence_proxy_async_global2();  // this pass's generic stores before the next pass's TMA reads
+    if (!grid_sync((2u * npass + 1u) * nG)) {
       timed_out = true;
       break;
     }
-    // every CTA sums the partials in the same fixed order: identical totals everywhere
-    reduce_over_ctas<kDots>(part, gridDim.x, Np, scratch, tot);
+    // the owner of each still-iterating orbital: its five sums over the CTAs (one
+    // warp a sum, lanes over CTAs, then a butterfly), the scalar step, published
+    double* pub = a.pub + (long long)(npass & 1) * 4 * Np;
+    const int nwarp = blockDim.x >> 5;
+    for (int o = blockIdx.x; o < Np; o += nG) {
+      if (!st_act[o]) continue;  // the same for the whole CTA
+      for (int d = tid >> 5; d < kDots; d += nwarp) {
+        const double* src = part + ((long long)o * kDots + d) * nG;
+        double v = 0.0;
+#pragma unroll 4
+        for (unsigned c = lane; c < nG; c += 32) v += __ldcg(src + c);
+#pragma unroll
+        for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+        if (lane == 0) sred[d] = v;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        const double rho = sred[0], rr = sred[1], pq = sred[2], qz = sred[3], qdq = sred[4];
+        bool act = true;
+        double alpha = 0.0, beta = 0.0;
+        if (npass == 0) {
+          st_bb[o] = rr;  // r_0 = b
+        } else {
+          st_it[o] += 1;  // x was updated in this pass
+          a.st->rr[o] = rr;
+        }
+        if (!(isfinite(rho) && isfinite(rr) && isfinite(pq) && isfinite(qz) && isfinite(qdq))) {
+          status |= kStatNonFinite;
+          act = false;
+        } else if (npass > 0 && rr <= tol * tol * st_bb[o]) {
+          act = false;
+        } else if (npass > 0 && st_it[o] >= maxit) {
+          if (!a.inner) status |= kStatNotConverged;
+          act = false;
+        }
+        if (act) {
+          if (!(rho > 0.0) || !(pq > 0.0)) {
+            status |= kStatNotSPD;
+            act = false;
+          } else {
+            alpha = rho / pq;
+            const double rho1 = rho - 2.0 * alpha * qz + alpha * alpha * qdq;
+            beta = rho1 > 0.0 ? rho1 / rho : 0.0;
+          }
+        }
+        st_rho[o] = rho;
+        pub[4 * o] = act ? alpha : 0.0;
+        pub[4 * o + 1] = act ? beta : 0.0;
+        pub[4 * o + 2] = act ? 1.0 : 0.0;
+      }
+      __syncthreads();
+    }
+    if (!grid_sync((2u * npass + 2u) * nG)) {
+      timed_out = true;
+      break;
+    }
     for (int o = tid; o < Np; o += blockDim.x) {
       if (!st_act[o]) {
         st_al[o] = 0.0;
         st_be[o] = 0.0;
         continue;
       }
-      const double rho = tot[o], rr = tot[Np + o], pq = tot[2 * Np + o];
-      const double qz = tot[3 * Np + o], qdq = tot[4 * Np + o];
-      bool act = true;
-      double alpha = 0.0, beta = 0.0;
-      if (npass == 0) {
-        st_bb[o] = rr;  // r_0 = b
-      } else {
-        st_it[o] += 1;  // x was updated in this pass
-        if (blockIdx.x == 0) a.st->rr[o] = rr;
-      }
-      if (!(isfinite(rho) && isfinite(rr) && isfinite(pq) && isfinite(qz) && isfinite(qdq))) {
-        status |= kStatNonFinite;
-        act = false;
-      } else if (npass > 0 && rr <= tol * tol * st_bb[o]) {
-        act = false;
-      } else if (npass > 0 && st_it[o] >= maxit) {
-        if (!a.inner) status |= kStatNotConverged;
-        act = false;
-      }
-      if (act) {
-        if (!(rho > 0.0) || !(pq > 0.0)) {
-          status |= kStatNotSPD;
-          act = false;
-        } else {
-          alpha = rho / pq;
-          const double rho1 = rho - 2.0 * alpha * qz + alpha * alpha * qdq;
-          beta = rho1 > 0.0 ? rho1 / rho : 0.0;
-        }
-      }
-      st_rho[o] = rho;
-      st_al[o] = act ? alpha : 0.0;
-      st_be[o] = act ? beta : 0.0;
-      st_act[o] = act ? 1 : 0;
+      st_al[o] = __ldcg(pub + 4 * o);
+      st_be[o] = __ldcg(pub + 4 * o + 1);
+      st_act[o] = __ldcg(pub + 4 * o + 2) != 0.0 ? 1 : 0;
     }
     __syncthreads();
   }
@@ -575,23 +619,28 @@ __global__ void __launch_bounds__(kMaxThr2, 1) k_cg2(CG2Args a, K1Geom geo, cons
       for (int q = cstep; q < s_lstep; ++q) mbar_wait_n(&full[q % S], (q / S) & 1, kSpinLimit);
     }
   }
-  if (status && blockIdx.x == 0) atomicOr(&a.st->status, status);
+  if (status) atomicOr(&a.st->status, status);
   __syncthreads();
-  if (blockIdx.x == 0) {
-    if (tid == 0) s_nact = 0;
-    __syncthreads();
+  // the owners: their orbitals' iteration counts and ||b||^2; CTA 0: the flags
+  if (tid == 0) {
     long long isum = 0;
     int imax = 0;
-    for (int o = tid; o < Np; o += blockDim.x) {
-      a.st->active[o] = st_act[o];
+    for (int o = blockIdx.x; o < Np; o += gridDim.x) {
       a.st->iters[o] = st_it[o];
       a.st->bb[o] = st_bb[o];
-      if (st_act[o]) atomicAdd(&s_nact, 1);
       isum += st_it[o];
       imax = st_it[o] > imax ? st_it[o] : imax;
     }
     if (isum) atomicAdd(reinterpret_cast<unsigned long long*>(&a.st->it_sum), (unsigned long long)isum);
     if (imax) atomicMax(&a.st->it_max, imax);
+  }
+  if (blockIdx.x == 0) {
+    if (tid == 0) s_nact = 0;
+    __syncthreads();
+    for (int o = tid; o < Np; o += blockDim.x) {
+      a.st->active[o] = st_act[o];
+      if (st_act[o]) atomicAdd(&s_nact, 1);
+    }
     __syncthreads();
     if (tid == 0) a.st->n_active = s_nact;
   }
@@ -625,7 +674,7 @@ __global__ void k_fill_interior_gm(Grid g, int Np, float* b) {
 // Shared-memory footprint: a ring of slots of r, q, p boxes for up to G4 groups
 // (each [TY+2][TX+2][4], 128-byte aligned), D^-1 [TY+2][DX] and the packed
 // weights [TY][TX][28]; then the sums [5 Np], per-orbital state (4 Np doubles,
-// 2 Np ints) and the block-sum / cross-CTA scratch.  The ring takes as many
+// 2 Np ints), the flush's per-warp sums and an owner's five totals.  The ring takes as many
 // slots (3 to 6) as fit in `limit` bytes; false if not even 3 do.
 static bool cg2_layout(int Np, int bw, int TX, int TY, size_t limit, K1Geom* G) {
   const size_t sz = sizeof(float);
@@ -647,10 +696,9 @@ static bool cg2_layout(int Np, int bw, int TX, int TY, size_t limit, K1Geom* G) 
   G->slot_bytes = (int)(G->off_w + al(wv));
   G->tx_bytes = (uint32_t)(3 * (size_t)G4 * HX * HY * 16 + dv + wv);  // all groups active
   const size_t nt = (size_t)G->nthr * G4 + 32;
-  const size_t blk = (size_t)G->nthr * bw + nt;                      // flush: rows x cols + slices
-  const size_t fin = (size_t)kDots * Np + (nt > (size_t)kDots * Np ? nt : (size_t)kDots * Np);
+  const size_t wsum = (nt - 32) / 32 * kDots * 4 + 8;  // flush: per-warp sums; an owner's five totals
   const int nob = (Np + bw - 1) / bw;
-  const size_t red = ((size_t)kDots * Np + 4 * (size_t)Np + Np + (blk > fin ? blk : fin)) * sizeof(double) +
+  const size_t red = ((size_t)kDots * Np + 4 * (size_t)Np + Np + wsum) * sizeof(double) +
                      small_state_bytes(Np, nob, G4);
   if (128 + red + 3 * (size_t)G->slot_bytes > limit) return false;
   int slots = (int)((limit - 128 - red) / G->slot_bytes);

@@ -289,10 +289,11 @@ def test_single_pass_kernel_geometry(plans):
         nt = G["nthr"] * G["G4"] + 32
         assert nt <= 512 and (nt - 32) % 32 == 0 and G["smem"] + static <= 227 * 1024, G
         # 3 to 6 ring slots (two mbarriers each in the first 128 bytes); sums [5 Np],
-        # state (6 Np words), flush rows x cols + slices, cross-CTA slices + totals
+        # state (6 Np words), the flush's per-warp sums (5 x 4 per consumer warp) and
+        # an owner's five totals
         slots = G["maxcost"]
         assert 3 <= slots <= 6 and 2 * 6 * 8 <= 128, G
-        red = 5 * G["Np"] + 5 * G["Np"] + max(G["nthr"] * bw + nt, 5 * G["Np"] + max(nt, 5 * G["Np"]))
+        red = 5 * G["Np"] + 5 * G["Np"] + (nt - 32) // 32 * 20 + 8
         # float32 alpha, beta [Np]; group flags [Np/4]; per block counts and lists; 8 B of alignment
         small = (2 * G["Np"] + G["Np"] // 4 + G["nob"] + G["nob"] * G["G4"]) * 4 + 8
         assert G["smem"] == 128 + slots * G["slot"] + 8 * red + small, G
