@@ -89,6 +89,9 @@ struct paro_mesh_s {
   int f32_layout = 0;
   // fxh/fxl hold the float-float split of x (set where x = u was just split)
   bool x_split_fresh = false;
+  // fxh/fxl = split(x) when a single-pass refinement has just ended (the
+  // Rayleigh-Ritz step that follows in the ParO loop reuses it)
+  bool x_split_valid = false;
   // Kohn-Sham: box origin, the float64 handle of the Poisson operator K/2 (V = 0,
   // sigma = 0) that solves for the Hartree potential, and Gauss-point fields
   double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
@@ -863,6 +866,7 @@ int refine_solve_cg2(paro_mesh m, int N, const paro_params& p, paro_stats* st, d
     }
   }
   TRY(check_status(m, "orbital_solve (float32 correction)"));
+  m->x_split_valid = true;  // every sweep ended with x and its split updated together
   if (st) {
     long long its = 0;
     int imax = 0;
@@ -944,6 +948,7 @@ int refine_solve(paro_mesh m, int N, const paro_params& p, paro_stats* st) {
 int solve_packed(paro_mesh m, int N, const double* lam, const paro_params& p, paro_stats* st) {
   const int Np = m->Np_alloc;
   Grid& g = m->g;
+  m->x_split_valid = false;
   // b = (lambda + sigma) M u
   for (int i = 0; i < Np; ++i) m->h_dbl[i] = i < N ? lam[i] + m->sigma : 0.0;
   double* scale = m->dscal + S_SCALE * kMaxN;
@@ -1017,17 +1022,19 @@ RRMode next_rr_mode(paro_mesh m, RRMode cur, double dl, const std::vector<double
 // kRRFP64 is used for the start on user guesses, whose overlap matrix can be
 // ill-conditioned far beyond what the mixed path's Grams resolve (their error is
 // amplified by cond(X^T M X)); inside the ParO loop X stays near M-orthonormal.
+// src_split: fxh/fxl already hold the float-float split of src.
 int rr_packed(paro_mesh m, int N, const double* src, double* dst, double* lam, RRMode mode = kRRFast,
-              const int* clus = nullptr) {
+              const int* clus = nullptr, bool src_split = false) {
   const int Np = m->Np_alloc;
   Grid& g = m->g;
+  m->x_split_valid = false;
   const bool mixed = m->precision == PARO_MIXED;
   const bool tc = mixed && mode == kRRFast && m->gpart_tc != nullptr;
   const bool ff = mixed && mode == kRRAccurate && m->gpart_ff != nullptr;
   if (tc) {
     // float-float X, HX and MX; both Grams on the tensor cores from their hi parts
     // (exact BF16 digit products, float-float across 128-node chunks)
-    LAUNCH(1, launch_split_ff((long long)g.G * Np, src, m->fxh, m->fxl, m->st));
+    if (!src_split) LAUNCH(1, launch_split_ff((long long)g.G * Np, src, m->fxh, m->fxl, m->st));
     LAUNCH(1, launch_ff_apply(g, Np, m->wHh, m->wHl, nullptr, m->fxh, m->fxl, nullptr, nullptr, m->fah, m->fal,
                               m->st));
     LAUNCH(1, apply_M_ff(m, Np, m->fxh, m->fxl, nullptr, nullptr, m->fbh, m->fbl));
@@ -1039,7 +1046,7 @@ int rr_packed(paro_mesh m, int N, const double* src, double* dst, double* lam, R
     ++m->rr_tc;
   } else if (ff) {
     // float-float: HX and MX as hi/lo arrays, both Grams and the rotation from the split X
-    LAUNCH(1, launch_split_ff((long long)g.G * Np, src, m->fxh, m->fxl, m->st));
+    if (!src_split) LAUNCH(1, launch_split_ff((long long)g.G * Np, src, m->fxh, m->fxl, m->st));
     LAUNCH(1, launch_ff_apply(g, Np, m->wHh, m->wHl, nullptr, m->fxh, m->fxl, nullptr, nullptr, m->fah, m->fal,
                               m->st));
     LAUNCH(1, apply_M_ff(m, Np, m->fxh, m->fxl, nullptr, nullptr, m->fbh, m->fbl));
@@ -1551,7 +1558,7 @@ int paro_iterate(paro_mesh m, int N, double* U, double* lambda, const paro_param
     }
     {
       Timer t(m, s ? &s->ms_rr : nullptr);
-      TRY(rr_packed(m, N, m->x, m->u, lam_new.data(), rr_mode, clus));
+      TRY(rr_packed(m, N, m->x, m->u, lam_new.data(), rr_mode, clus, m->x_split_valid));
     }
     dl = 0.0;
     for (int i = 0; i < nchk; ++i) dl = std::fmax(dl, std::fabs(lam_new[i] - lam[i]));
@@ -1701,7 +1708,7 @@ int paro_scf_iterate(paro_mesh m, int N, const double* occ, const double* vext_q
     }
     {
       Timer t(m, s ? &s->ms_rr : nullptr);
-      TRY(rr_packed(m, N, m->x, m->u, lam_new.data(), rr_mode));
+      TRY(rr_packed(m, N, m->x, m->u, lam_new.data(), rr_mode, nullptr, m->x_split_valid));
     }
     LAUNCH(1, launch_density(m->g, N, Np, m->u, m->ks_occ, m->ks_rho2, m->st));
     LAUNCH(1, launch_mix(gauss_count(m->g), mix, m->ks_rho, m->ks_rho2, m->st));
