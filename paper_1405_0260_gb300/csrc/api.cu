@@ -1058,8 +1058,10 @@ int rr_packed(paro_mesh m, int N, const double* src, double* dst, double* lam, R
     LAUNCH(1, apply_M_f64(m, Np, src, m->q, nullptr));  // M
     LAUNCH(2, launch_gram2(g, N, Np, src, m->r, m->q, m->gpart, nullptr, m->GA, m->GB, m->st));
   }
+  // mixed handles inside the loop: the eigensolve in float-float on the float32
+  // pipes; the start on user guesses (ill-conditioned overlaps) stays float64
   LAUNCH(1, launch_small_eig(N, m->GA, m->GB, m->eigwork, m->C, m->theta, &m->cgst->status, m->st,
-                             &m->cgst->bar_count, clus));
+                             &m->cgst->bar_count, clus, mixed && mode != kRRFP64));
   TRY(check_status(m, "rayleigh_ritz"));
   // the rotation: on the tensor cores from the hi parts of X with the tensor-core
   // Grams (the same 24-bit inputs), else in float-float from the split X (C staged

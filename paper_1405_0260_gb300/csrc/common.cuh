@@ -189,8 +189,10 @@ size_t gram_partial_doubles(const Grid& g, int Np);
 constexpr int kEigGridMinN = 64;
 // clus (device, N cluster ids ascending, optional): cluster-separated form, the
 // eigenproblem of each cluster's diagonal block alone, sorted within clusters.
+// ff: float-float arithmetic on the float32 pipes (one CTA, N <= 64, no clusters).
 cudaError_t launch_small_eig(int N, const double* GA, const double* GB, double* work, double* C, double* theta,
-                             int* status, cudaStream_t st, unsigned* bar = nullptr, const int* clus = nullptr);
+                             int* status, cudaStream_t st, unsigned* bar = nullptr, const int* clus = nullptr,
+                             bool ff = false);
 cudaError_t launch_rotate(const Grid& g, int N, int Np, const double* X, const double* C, double* U,
                           cudaStream_t st);
 

@@ -10,6 +10,7 @@
 #include "../../include/paro.h"
 
 #include "common.cuh"
+#include "ff.cuh"
 
 namespace paro {
 
@@ -765,11 +766,304 @@ __global__ void __launch_bounds__(256) k_small_eig_grid(int N, int Np, const dou
   }
 }
 
+// ---------------------------------------------------------------------------
+// The small generalized eigensolve of Step 4 in float-float arithmetic (mixed
+// precision handles, N <= kEigFFMaxN, no clusters).  On this GPU a float64
+// instruction costs ~60x a float32 one, and the one-CTA float64 solve above
+// spent ~220 us at N = 20 (Cholesky 21, two triangular solves 20, 44 a Jacobi
+// sweep) on a handful of float64 operations a thread between CTA barriers.  Here
+// every step runs on hi + lo float pairs (~48 bits, ff.cuh):
+//   G_B = Lt D Lt^T           LDL^T elimination, one barrier a column (Lt unit lower)
+//   T = Lt^-1 G_A Lt^-T       two unit-triangular solves, one barrier a column
+//   S = D^-1/2 T D^-1/2       (= L^-1 G_A L^-T with L = Lt D^1/2)
+//   S = Q Theta Q^T           parallel cyclic Jacobi: the pairs of a round are
+//                             disjoint, so each thread updates whole 2 x 2 blocks
+//                             R_k S_kk' R_k'^T: two barriers a round
+//   C = Lt^-T D^-1/2 Q        one barrier a row, columns sorted by ascending theta
+// Rotation angles are taken in float32 and (c, s) renormalised so that
+// c^2 + s^2 = 1 to float-float precision: every rotation is orthogonal to ~2^-48
+// and annihilates its pair to a float32-relative residue that the next sweep
+// removes.  A pair rotates while |S_pq| > 2^-44 max(|S_pp|, |S_qq|) + 2^-47 ||S||_F:
+// the rotations' own rounding leaves ~2^-48 of the entries they combine, so a
+// threshold at that level (tried first) never let a sweep end without rotations.
+constexpr int kEigFFMaxN = 64;
+constexpr int kJacobiSweepsFF = 40;
+
+__device__ __forceinline__ FF ffe_fast(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return FF{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ FF ffe_mul(FF a, FF b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return ffe_fast(p, e);
+}
+__device__ __forceinline__ FF ffe_add(FF a, FF b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  return ffe_fast(s, e);
+}
+__device__ __forceinline__ FF ffe_sub(FF a, FF b) { return ffe_add(a, FF{-b.hi, -b.lo}); }
+// 1/d and 1/sqrt(d) by two Newton steps from the float32 estimate
+__device__ __forceinline__ FF ffe_recip(FF d) {
+  FF x{__frcp_rn(d.hi), 0.f};
+  for (int it = 0; it < 2; ++it) x = ffe_add(x, ffe_mul(x, ffe_sub(FF{1.f, 0.f}, ffe_mul(d, x))));
+  return x;
+}
+__device__ __forceinline__ FF ffe_rsqrt(FF d) {
+  FF y{rsqrtf(d.hi), 0.f};
+  for (int it = 0; it < 2; ++it) {
+    const FF r = ffe_sub(FF{1.f, 0.f}, ffe_mul(d, ffe_mul(y, y)));
+    y = ffe_add(y, ffe_mul(y, FF{0.5f * r.hi, 0.5f * r.lo}));
+  }
+  return y;
+}
+
+__global__ void __launch_bounds__(512) k_small_eig_ff(int N, int Np, const double* __restrict__ GA,
+                                                      const double* __restrict__ GB, double* __restrict__ C,
+                                                      double* __restrict__ theta, int* __restrict__ status) {
+  extern __shared__ float fsm[];
+  const int LD = N | 1;  // odd row pitch: column walks hit distinct banks
+  const int NN = N * LD;
+  float* Bh = fsm;  // G_B, then Lt (strict lower) and D (diagonal)
+  float* Bl = Bh + NN;
+  float* Sh = Bl + NN;  // G_A, then W, then S
+  float* Sl = Sh + NN;
+  float* Vh = Sl + NN;  // the second solve's right-hand side, then Q, then X
+  float* Vl = Vh + NN;
+  float* yv = Vl + NN;  // [2N] D^-1/2 (hi, lo)
+  float* csv = yv + 2 * N;  // [4 * half] rotation of each pair of a round
+  __shared__ int pr[kEigFFMaxN / 2][2];
+  __shared__ int s_fail, s_big, s_nan;
+  __shared__ unsigned s_norm;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  auto ld = [&](const float* h, const float* l, int i, int j) { return FF{h[i * LD + j], l[i * LD + j]}; };
+  auto st = [&](float* h, float* l, int i, int j, FF v) {
+    h[i * LD + j] = v.hi;
+    l[i * LD + j] = v.lo;
+  };
+  if (tid == 0) {
+    s_fail = 0;
+    s_big = 0;
+    s_nan = 0;
+    s_norm = 0u;
+  }
+  for (int t = tid; t < N * N; t += nt) {
+    const int i = t / N, j = t % N;
+    st(Bh, Bl, i, j, ff_split(0.5 * (GB[(long long)i * Np + j] + GB[(long long)j * Np + i])));
+    st(Sh, Sl, i, j, ff_split(0.5 * (GA[(long long)i * Np + j] + GA[(long long)j * Np + i])));
+  }
+  __syncthreads();
+  // LDL^T: step k removes column k from the trailing lower triangle
+  for (int k = 0; k < N - 1; ++k) {
+    const FF rd = ffe_recip(ld(Bh, Bl, k, k));
+    const int m = N - 1 - k;
+    for (int t = tid; t < m * m; t += nt) {
+      const int i = k + 1 + t / m, j = k + 1 + t % m;
+      if (j > i) continue;
+      const FF bik = ld(Bh, Bl, i, k), bjk = ld(Bh, Bl, j, k);
+      st(Bh, Bl, i, j, ffe_sub(ld(Bh, Bl, i, j), ffe_mul(bik, ffe_mul(bjk, rd))));
+    }
+    __syncthreads();
+  }
+  // D > 0 (G_B positive definite), Lt = B / d_k below the diagonal, D^-1/2
+  for (int k = tid; k < N; k += nt) {
+    const FF d = ld(Bh, Bl, k, k);
+    if (!(d.hi > 0.f) || !isfinite(d.hi)) atomicOr(&s_fail, 1);
+    const FF y = ffe_rsqrt(d);
+    yv[2 * k] = y.hi;
+    yv[2 * k + 1] = y.lo;
+  }
+  __syncthreads();
+  if (s_fail) {
+    if (tid == 0) atomicOr(status, kStatNotSPD);
+    return;
+  }
+  for (int t = tid; t < N * N; t += nt) {
+    const int i = t / N, k = t % N;
+    if (k < i) {
+      const FF y = FF{yv[2 * k], yv[2 * k + 1]};
+      st(Bh, Bl, i, k, ffe_mul(ld(Bh, Bl, i, k), ffe_mul(y, y)));
+    }
+  }
+  __syncthreads();
+  // W = Lt^-1 G_A (in S), then V = W^T, V = Lt^-1 V
+  for (int pass = 0; pass < 2; ++pass) {
+    float* Xh = pass == 0 ? Sh : Vh;
+    float* Xl = pass == 0 ? Sl : Vl;
+    if (pass == 1) {
+      for (int t = tid; t < N * N; t += nt) {
+        const int i = t / N, j = t % N;
+        st(Vh, Vl, i, j, ld(Sh, Sl, j, i));
+      }
+      __syncthreads();
+    }
+    for (int k = 0; k < N - 1; ++k) {
+      const int m = N - 1 - k;
+      for (int t = tid; t < m * N; t += nt) {
+        const int i = k + 1 + t / N, j = t % N;
+        st(Xh, Xl, i, j, ffe_sub(ld(Xh, Xl, i, j), ffe_mul(ld(Bh, Bl, i, k), ld(Xh, Xl, k, j))));
+      }
+      __syncthreads();
+    }
+  }
+  // S = D^-1/2 T D^-1/2, symmetrised; V = I; ||S||_F^2 (rotation-invariant)
+  float nrm = 0.f;
+  for (int t = tid; t < N * N; t += nt) {
+    const int i = t / N, j = t % N;
+    const FF yi{yv[2 * i], yv[2 * i + 1]}, yj{yv[2 * j], yv[2 * j + 1]};
+    const FF a = ld(Vh, Vl, i, j), b = ld(Vh, Vl, j, i);
+    const FF s = ffe_mul(ffe_mul(ffe_add(a, b), FF{0.5f, 0.f}), ffe_mul(yi, yj));
+    st(Sh, Sl, i, j, s);
+    nrm = fmaf(s.hi, s.hi, nrm);
+  }
+  __syncthreads();
+  for (int t = tid; t < N * N; t += nt) {
+    const int i = t / N, j = t % N;
+    st(Vh, Vl, i, j, FF{i == j ? 1.f : 0.f, 0.f});
+  }
+  for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+  if ((tid & 31) == 0) atomicAdd(reinterpret_cast<float*>(&s_norm), nrm);
+  __syncthreads();
+  const float tg = 0x1p-47f * sqrtf(__uint_as_float(s_norm));
+  auto thr = [&](int p, int q) { return fmaf(0x1p-44f, fmaxf(fabsf(Sh[p * LD + p]), fabsf(Sh[q * LD + q])), tg); };
+  const int m = (N % 2 == 0) ? N : N + 1;
+  const int half = m / 2;
+  bool converged = N <= 1;
+  for (int sweep = 0; sweep < kJacobiSweepsFF && N > 1; ++sweep) {
+    // another sweep while some pair is above its threshold (or a value is NaN)
+    for (int t = tid; t < N * N; t += nt) {
+      const int p = t / N, q = t % N;
+      const float a = Sh[p * LD + q];
+      if (isnan(a)) s_nan = 1;
+      else if (p != q && fabsf(a) > thr(p, q)) s_big = 1;
+    }
+    __syncthreads();
+    if (s_nan || !s_big) {
+      converged = !s_nan;
+      break;
+    }
+    for (int r = 0; r < m - 1; ++r) {
+      // the rotation of each pair (identity for a pair with the padding index, or
+      // whose |a_pq| is at the rounding level)
+      for (int k = tid; k < half; k += nt) {
+        int p, q;
+        rr_pair(m, r, k, &p, &q);
+        FF c{1.f, 0.f}, s{0.f, 0.f};
+        if (q < N) {
+          const FF apq = ld(Sh, Sl, p, q), app = ld(Sh, Sl, p, p), aqq = ld(Sh, Sl, q, q);
+          if (fabsf(apq.hi) > thr(p, q)) {
+            const float a = __fadd_rn(apq.hi, apq.lo);
+            const float dd = __fadd_rn(__fsub_rn(aqq.hi, app.hi), __fsub_rn(aqq.lo, app.lo));
+            const float tau = dd / (2.f * a);
+            const float rt = sqrtf(fmaf(tau, tau, 1.f));
+            const float t = isfinite(rt) ? ((tau >= 0.f) ? 1.f / (tau + rt) : -1.f / (-tau + rt)) : 0.f;
+            const float cf = rsqrtf(fmaf(t, t, 1.f)), sf = t * cf;
+            // (c, s) = (cf, sf) (cf^2 + sf^2)^-1/2 to float-float precision
+            float p1, e1, p2, e2;
+            p1 = __fmul_rn(cf, cf);
+            e1 = __fmaf_rn(cf, cf, -p1);
+            p2 = __fmul_rn(sf, sf);
+            e2 = __fmaf_rn(sf, sf, -p2);
+            const FF dl = ffe_sub(ffe_add(FF{p1, e1}, FF{p2, e2}), FF{1.f, 0.f});
+            FF y = ffe_sub(FF{1.f, 0.f}, FF{0.5f * dl.hi, 0.5f * dl.lo});
+            y = ffe_add(y, FF{0.375f * dl.hi * dl.hi, 0.f});
+            c = ffe_mul(FF{cf, 0.f}, y);
+            s = ffe_mul(FF{sf, 0.f}, y);
+          }
+        }
+        csv[4 * k] = c.hi;
+        csv[4 * k + 1] = c.lo;
+        csv[4 * k + 2] = s.hi;
+        csv[4 * k + 3] = s.lo;
+        pr[k][0] = p;
+        pr[k][1] = q;
+      }
+      __syncthreads();
+      // S_kk' <- R_k S_kk' R_k'^T for every pair of pairs (disjoint 2 x 2 blocks),
+      // V <- V R^T, R = [[c, -s], [s, c]]
+      const int nblk = half * half;
+      for (int t = tid; t < nblk + N * half; t += nt) {
+        if (t < nblk) {
+          const int k = t / half, kk = t % half;
+          const int p = pr[k][0], q = pr[k][1], p2 = pr[kk][0], q2 = pr[kk][1];
+          const FF c{csv[4 * k], csv[4 * k + 1]}, s{csv[4 * k + 2], csv[4 * k + 3]};
+          const FF c2{csv[4 * kk], csv[4 * kk + 1]}, s2{csv[4 * kk + 2], csv[4 * kk + 3]};
+          const bool qv = q < N, q2v = q2 < N;
+          const FF z{0.f, 0.f};
+          const FF b00 = ld(Sh, Sl, p, p2), b01 = q2v ? ld(Sh, Sl, p, q2) : z;
+          const FF b10 = qv ? ld(Sh, Sl, q, p2) : z, b11 = (qv && q2v) ? ld(Sh, Sl, q, q2) : z;
+          // rows: R_k B
+          const FF t00 = ffe_sub(ffe_mul(c, b00), ffe_mul(s, b10)), t01 = ffe_sub(ffe_mul(c, b01), ffe_mul(s, b11));
+          const FF t10 = ffe_add(ffe_mul(s, b00), ffe_mul(c, b10)), t11 = ffe_add(ffe_mul(s, b01), ffe_mul(c, b11));
+          // columns: (R_k B) R_k'^T
+          st(Sh, Sl, p, p2, ffe_sub(ffe_mul(c2, t00), ffe_mul(s2, t01)));
+          if (q2v) st(Sh, Sl, p, q2, ffe_add(ffe_mul(s2, t00), ffe_mul(c2, t01)));
+          if (qv) st(Sh, Sl, q, p2, ffe_sub(ffe_mul(c2, t10), ffe_mul(s2, t11)));
+          if (qv && q2v) st(Sh, Sl, q, q2, ffe_add(ffe_mul(s2, t10), ffe_mul(c2, t11)));
+        } else {
+          const int u = t - nblk, row = u / half, kk = u % half;
+          const int p2 = pr[kk][0], q2 = pr[kk][1];
+          if (q2 >= N) continue;
+          const FF c2{csv[4 * kk], csv[4 * kk + 1]}, s2{csv[4 * kk + 2], csv[4 * kk + 3]};
+          const FF vp = ld(Vh, Vl, row, p2), vq = ld(Vh, Vl, row, q2);
+          st(Vh, Vl, row, p2, ffe_sub(ffe_mul(c2, vp), ffe_mul(s2, vq)));
+          st(Vh, Vl, row, q2, ffe_add(ffe_mul(s2, vp), ffe_mul(c2, vq)));
+        }
+      }
+      __syncthreads();
+    }
+    if (tid == 0) s_big = 0;
+    __syncthreads();
+  }
+  if (!converged && tid == 0) atomicOr(status, kStatNotConverged);
+  // X = D^-1/2 Q, then X = Lt^-T X (unit upper), row k final at step k
+  for (int t = tid; t < N * N; t += nt) {
+    const int i = t / N, j = t % N;
+    st(Vh, Vl, i, j, ffe_mul(ld(Vh, Vl, i, j), FF{yv[2 * i], yv[2 * i + 1]}));
+  }
+  __syncthreads();
+  for (int k = N - 1; k > 0; --k) {
+    for (int t = tid; t < k * N; t += nt) {
+      const int i = t / N, j = t % N;
+      st(Vh, Vl, i, j, ffe_sub(ld(Vh, Vl, i, j), ffe_mul(ld(Bh, Bl, k, i), ld(Vh, Vl, k, j))));
+    }
+    __syncthreads();
+  }
+  // columns by ascending Ritz value (ties by index)
+  for (int j = tid; j < N; j += nt) {
+    const FF tj = ld(Sh, Sl, j, j);
+    int rank = 0;
+    for (int i = 0; i < N; ++i) {
+      const FF ti = ld(Sh, Sl, i, i);
+      if (ti.hi < tj.hi || (ti.hi == tj.hi && (ti.lo < tj.lo || (ti.lo == tj.lo && i < j)))) ++rank;
+    }
+    theta[rank] = ff_to_double(tj);
+    for (int i = 0; i < N; ++i) C[(long long)i * Np + rank] = ff_to_double(ld(Vh, Vl, i, j));
+  }
+  for (int t = tid; t < Np * Np; t += nt) {
+    const int i = t / Np, j = t % Np;
+    if (i >= N || j >= N) C[t] = 0.0;
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_small_eig(int N, const double* GA, const double* GB, double* work, double* C, double* theta,
-                             int* status, cudaStream_t st, unsigned* bar, const int* clus) {
+                             int* status, cudaStream_t st, unsigned* bar, const int* clus, bool ff) {
   int Np = (N + 3) / 4 * 4;
+  if (ff && clus == nullptr && N <= kEigFFMaxN) {
+    const int LD = N | 1;
+    const size_t smem = ((size_t)6 * N * LD + 2 * N + 4 * ((N + 1) / 2)) * sizeof(float);
+    cudaError_t e = allow_max_dyn_smem((const void*)k_small_eig_ff);
+    if (e != cudaSuccess) return e;
+    const int nt = N <= 32 ? 256 : 512;
+    k_small_eig_ff<<<1, nt, smem, st>>>(N, Np, GA, GB, C, theta, status);
+    return cudaGetLastError();
+  }
   if (bar != nullptr && N > kEigGridMinN) {
     // the whole GPU: a cooperative grid of up to 128 CTAs (co-resident by construction)
     int dev = 0, nsm = 0;
