@@ -571,7 +571,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         for (int i = 0; i < 8; ++i) {
           ff_add(tsum[i], FF{__fmul_rn(v0[i], 0x1p-16f), 0.f});
           const int b = n0 + col0 + c + i;
-          out[i] = b < Np ? ldexp(ff_to_double(ff_norm(tsum[i])), eg + cexpB[b] - 16) : 0.0;
+          // the scale 2^sc on the float pair (exact power-of-two products), then one
+          // float64 addition; ldexp in float64 only for scales outside the float range
+          const int sc = eg + (b < Np ? cexpB[b] : 0) - 16;
+          const FF tn = ff_norm(tsum[i]);
+          if (b >= Np) out[i] = 0.0;
+          else if (sc >= -100 && sc <= 100) out[i] = ff_to_double(FF{__fmul_rn(tn.hi, pow2f(sc)), __fmul_rn(tn.lo, pow2f(sc))});
+          else out[i] = ldexp(ff_to_double(tn), sc);
         }
         const int b0 = n0 + col0 + c;
         if (g < G && b0 < Np) {

@@ -206,27 +206,30 @@ __global__ void __launch_bounds__(kRedThreads) k_refine_residual_ff(Grid g, int 
 
 // x += d for the orbitals the correction solve ran for (d group-major), and the
 // float-float split of the new x for the next residual; skipped orbitals keep x
-// and its split.
+// (and, the split being a function of x, the same split).  Vector loads and
+// stores of a thread's four orbitals; one float64 addition an element.
 __global__ void k_refine_update_split(Grid g, int Np, double* __restrict__ x, const float* __restrict__ d,
                                       const int* __restrict__ skip, float* __restrict__ xh, float* __restrict__ xl) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int groups = Np / 4;
   if (t >= (long long)g.nI * groups) return;
   const int n = (int)(t / groups), grp = (int)(t % groups);
+  const int4 sk = *reinterpret_cast<const int4*>(skip + 4 * grp);
+  if (sk.x && sk.y && sk.z && sk.w) return;
   const long long gp = interior_to_padded(g, n);
   const float4 dv = *reinterpret_cast<const float4*>(d + ((long long)grp * g.G + gp) * 4);
-  const float dd[4] = {dv.x, dv.y, dv.z, dv.w};
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    const int o = 4 * grp + c;
-    if (skip[o]) continue;
-    const long long e = gp * Np + o;
-    const double v = x[e] + (double)dd[c];
-    x[e] = v;
-    const FF f = ff_split(v);
-    xh[e] = f.hi;
-    xl[e] = f.lo;
-  }
+  const long long e = gp * Np + 4 * grp;
+  double2* xp = reinterpret_cast<double2*>(x + e);
+  const double2 a = xp[0], b = xp[1];
+  const double v0 = sk.x ? a.x : a.x + f2d_exact(dv.x);
+  const double v1 = sk.y ? a.y : a.y + f2d_exact(dv.y);
+  const double v2 = sk.z ? b.x : b.x + f2d_exact(dv.z);
+  const double v3 = sk.w ? b.y : b.y + f2d_exact(dv.w);
+  xp[0] = make_double2(v0, v1);
+  xp[1] = make_double2(v2, v3);
+  const FF f0 = ff_split(v0), f1 = ff_split(v1), f2 = ff_split(v2), f3 = ff_split(v3);
+  *reinterpret_cast<float4*>(xh + e) = make_float4(f0.hi, f1.hi, f2.hi, f3.hi);
+  *reinterpret_cast<float4*>(xl + e) = make_float4(f0.lo, f1.lo, f2.lo, f3.lo);
 }
 
 __global__ void k_refine_update(Grid g, int Np, double* __restrict__ x, const float* __restrict__ d,
