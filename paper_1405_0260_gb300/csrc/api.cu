@@ -92,6 +92,8 @@ struct paro_mesh_s {
   // fxh/fxl = split(x) when a single-pass refinement has just ended (the
   // Rayleigh-Ritz step that follows in the ParO loop reuses it)
   bool x_split_valid = false;
+  // h_dbl holds the last refinement's ||r_i||^2 and ||b_i||^2 (read with its final check)
+  bool relres_staged = false;
   // Kohn-Sham: box origin, the float64 handle of the Poisson operator K/2 (V = 0,
   // sigma = 0) that solves for the Hartree potential, and Gauss-point fields
   double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
@@ -385,6 +387,15 @@ int autotune_cg2(paro_mesh m, CG2Plan* P) {
   std::vector<K1Geom> cand;
   cg2_candidates(m->g, P->args.Np, m->nsm, &cand);
   if (cand.empty()) return PARO_OK;
+  // PARO_CG2_GEOMETRY=<i>: candidate i, untimed (the tests run every geometry this way)
+  if (const char* f = std::getenv("PARO_CG2_GEOMETRY")) {
+    const int i = std::atoi(f);
+    if (i >= 0 && i < (int)cand.size()) {
+      CK(cg2_prepare_geo(P, cand[i]));
+      m->tune2_source = "forced";
+      return PARO_OK;
+    }
+  }
   const char* off = std::getenv("PARO_AUTOTUNE");
   CK(cg2_prepare_geo(P, cand[0]));
   m->tune2_source = "default";
@@ -456,8 +467,9 @@ int make_plans(paro_mesh m, int Np) {
     TRY(set_f32_layout(m, 1));
     TRY(autotune_cg2(m, P));
     if (std::getenv("PARO_PRINT_PLAN"))
-      std::fprintf(stderr, "paro single-pass CG plan: tile %dx%d, block %d orbitals x %d, %d threads, grid %d, "
-                   "smem %zu B, usable %d, geometry %s\n", P->geo.TX, P->geo.TY, P->geo.G4 * 4, P->geo.nob,
+      std::fprintf(stderr, "paro single-pass CG plan: tile %dx%d, %d nodes a thread, block %d orbitals x %d, %d threads, "
+                   "grid %d, smem %zu B, usable %d, geometry %s\n", P->geo.TX, P->geo.TY, P->geo.npt, P->geo.G4 * 4,
+                   P->geo.nob,
                    P->geo.nthr * P->geo.G4, P->geo.grid, P->geo.smem, (int)P->ok, m->tune2_source);
   }
   return PARO_OK;
@@ -849,10 +861,19 @@ int refine_solve_cg2(paro_mesh m, int N, const paro_params& p, paro_stats* st, d
     LAUNCH(1, launch_refine_residual_ff(g, N, Np, m->wAh, m->wAl, m->fxh, m->fxl, m->fah, m->fal, nullptr, rs,
                                         p.solve_tol, m->st, 1));
     if (st) st->stencil_applies += N;
-    // the open count and the status word in one round trip; a failed correction
-    // solve (timeout, non-finite value, indefinite operator) ends the refinement
+    // the open count and the status word in one round trip (with the statistics'
+    // iteration counts and residual norms when they are asked for); a failed
+    // correction solve (timeout, non-finite value, indefinite operator) ends the
+    // refinement
     CK(cudaMemcpyAsync(m->h_int, &m->cgst->n_active, sizeof(int), cudaMemcpyDeviceToHost, m->st));
     CK(cudaMemcpyAsync(m->h_int + 1, &m->cgst->status, sizeof(int), cudaMemcpyDeviceToHost, m->st));
+    if (st) {
+      CK(cudaMemcpyAsync(m->h_int + 2, &m->cgst->it_sum, sizeof(long long), cudaMemcpyDeviceToHost, m->st));
+      CK(cudaMemcpyAsync(m->h_int + 4, &m->cgst->it_max, sizeof(int), cudaMemcpyDeviceToHost, m->st));
+      CK(cudaMemcpyAsync(m->h_dbl, m->dscal + S_RRR * kMaxN, sizeof(double) * N, cudaMemcpyDeviceToHost, m->st));
+      CK(cudaMemcpyAsync(m->h_dbl + kMaxN, m->dscal + S_RBB * kMaxN, sizeof(double) * N, cudaMemcpyDeviceToHost,
+                         m->st));
+    }
     CK(cudaStreamSynchronize(m->st));
     const int open = m->h_int[0];
     if (m->h_int[1] != 0) TRY(check_status(m, "orbital_solve (float32 correction)"));
@@ -869,12 +890,9 @@ int refine_solve_cg2(paro_mesh m, int N, const paro_params& p, paro_stats* st, d
   m->x_split_valid = true;  // every sweep ended with x and its split updated together
   if (st) {
     long long its = 0;
-    int imax = 0;
-    CK(cudaMemcpyAsync(m->h_dbl, &m->cgst->it_sum, sizeof(long long), cudaMemcpyDeviceToHost, m->st));
-    CK(cudaMemcpyAsync(m->h_int, &m->cgst->it_max, sizeof(int), cudaMemcpyDeviceToHost, m->st));
-    CK(cudaStreamSynchronize(m->st));
-    std::memcpy(&its, m->h_dbl, sizeof(its));
-    imax = m->h_int[0];
+    std::memcpy(&its, m->h_int + 2, sizeof(its));
+    const int imax = m->h_int[4];
+    m->relres_staged = true;  // h_dbl holds the final ||r||^2 and ||b||^2
     st->cg_iters += its;
     st->cg_iters_f32 += its;
     st->cg_iters_max = imax;
@@ -949,6 +967,7 @@ int solve_packed(paro_mesh m, int N, const double* lam, const paro_params& p, pa
   const int Np = m->Np_alloc;
   Grid& g = m->g;
   m->x_split_valid = false;
+  m->relres_staged = false;
   // b = (lambda + sigma) M u
   for (int i = 0; i < Np; ++i) m->h_dbl[i] = i < N ? lam[i] + m->sigma : 0.0;
   double* scale = m->dscal + S_SCALE * kMaxN;
@@ -982,11 +1001,14 @@ int solve_packed(paro_mesh m, int N, const double* lam, const paro_params& p, pa
     TRY(refine_solve(m, N, p, st));
   }
   if (st) {
-    double* rr = m->dscal + S_RRR * kMaxN;
-    double* bb = m->dscal + S_RBB * kMaxN;
-    CK(cudaMemcpyAsync(m->h_dbl, rr, sizeof(double) * N, cudaMemcpyDeviceToHost, m->st));
-    CK(cudaMemcpyAsync(m->h_dbl + kMaxN, bb, sizeof(double) * N, cudaMemcpyDeviceToHost, m->st));
-    CK(cudaStreamSynchronize(m->st));
+    if (!m->relres_staged) {
+      double* rr = m->dscal + S_RRR * kMaxN;
+      double* bb = m->dscal + S_RBB * kMaxN;
+      CK(cudaMemcpyAsync(m->h_dbl, rr, sizeof(double) * N, cudaMemcpyDeviceToHost, m->st));
+      CK(cudaMemcpyAsync(m->h_dbl + kMaxN, bb, sizeof(double) * N, cudaMemcpyDeviceToHost, m->st));
+      CK(cudaStreamSynchronize(m->st));
+    }
+    m->relres_staged = false;
     double worst = 0.0;
     for (int i = 0; i < N; ++i) {
       double b = m->h_dbl[kMaxN + i];

@@ -126,9 +126,14 @@ __device__ void consumer_colsum(const double* in, int rows, int cols, double* tm
 // Threads: nthr x G4 consumers (node slot j = tid % nthr, active-group slot
 // k = tid / nthr), then one producer warp whose first lane stages the planes by
 // TMA into a ring of geo.slots slots: full[s] completes when a slot's copies
-// have landed, empty[s] when every consumer warp is done with it.
-template <int G4>
-__global__ void __launch_bounds__(kMaxThr2, 1) k_cg2(CG2Args a, K1Geom geo, const __grid_constant__ CUtensorMap mr0,
+// have landed, empty[s] when every consumer warp is done with it.  A node slot
+// holds NPT nodes stacked in y (NPT = 2: the two 3 x 3 neighbourhoods share six
+// nodes, so a thread forms r, z, p at 12 staged nodes for two outputs instead of
+// at 18, and has twice the independent work; up to 384 threads, 170 registers).
+constexpr int cg2_max_threads(int npt) { return npt == 1 ? kMaxThr2 : 384; }
+
+template <int G4, int NPT>
+__global__ void __launch_bounds__(cg2_max_threads(NPT), 1) k_cg2(CG2Args a, K1Geom geo, const __grid_constant__ CUtensorMap mr0,
                                                      const __grid_constant__ CUtensorMap mq0,
                                                      const __grid_constant__ CUtensorMap mp0,
                                                      const __grid_constant__ CUtensorMap mr1,
@@ -140,7 +145,7 @@ __global__ void __launch_bounds__(kMaxThr2, 1) k_cg2(CG2Args a, K1Geom geo, cons
   extern __shared__ __align__(128) unsigned char smem[];
   const int TX = geo.TX, TY = geo.TY;
   const int HX = TX + 2, HY = TY + 2;
-  const int nthr = geo.nthr;  // TX * TY: one tile node per consumer thread
+  const int nthr = geo.nthr;  // TX * TY / NPT: NPT tile nodes per consumer thread
   const int NC = nthr * G4;   // consumer threads
   const int S = geo.slots;
   const int tid = threadIdx.x;
@@ -263,8 +268,8 @@ __global__ void __launch_bounds__(kMaxThr2, 1) k_cg2(CG2Args a, K1Geom geo, cons
     return true;
   };
 
-  // own node (tx, ty) of the tile
-  const int tx = j % TX, ty = j / TX;
+  // own nodes (tx, ty0 + i), i < NPT, of the tile
+  const int tx = j % TX, ty0 = (j / TX) * NPT;
   const long long plane = (long long)a.g.Px * a.g.Py;
   const int lane = tid & 31;
 
@@ -346,41 +351,63 @@ __global__ void __launch_bounds__(kMaxThr2, 1) k_cg2(CG2Args a, K1Geom geo, cons
         al[c] = kact ? salpha[4 * gam + c] : 0.f;
         be[c] = kact ? sbeta[4 * gam + c] : 0.f;
       }
-      const int xg = x0 + tx, yg = y0 + ty;
-      const bool inside = xg <= a.g.nx - 1 && yg <= a.g.ny - 1;
-      const long long colnode = (long long)yg * a.g.Px + xg;
+      const int xg = x0 + tx;
       const long long gbase = (long long)gam * G;
-      Vec4<float> aU{}, aC{}, aD{};
-      Vec4<float> pv_z{}, pv_p{};  // own node z_k and p_k of the previous input plane
-      float pv_d = 0.f;
-      Vec4<float> xnext{};         // x of the next plane, loaded one plane ahead
+      bool inside[NPT];
+      long long colnode[NPT];
+      Vec4<float> aU[NPT], aC[NPT], aD[NPT];
+      Vec4<float> pv_z[NPT], pv_p[NPT];  // own nodes' z_k and p_k of the previous input plane
+      float pv_d[NPT];
+      Vec4<float> xnext[NPT];             // x of the next plane, loaded one plane ahead
+#pragma unroll
+      for (int i = 0; i < NPT; ++i) {
+        const int yg = y0 + ty0 + i;
+        inside[i] = xg <= a.g.nx - 1 && yg <= a.g.ny - 1;
+        colnode[i] = (long long)yg * a.g.Px + xg;
+        aU[i] = aC[i] = aD[i] = pv_z[i] = pv_p[i] = xnext[i] = Vec4<float>{};
+        pv_d[i] = 0.f;
+      }
       for (int s = z0 - 1; s <= z1; ++s) {
         const int slot = cstep % S;
         const uint32_t par = (cstep / S) & 1;
-        const bool own_out = kact && inside && s >= z0 && s < z1;
-        const long long eown = (gbase + (long long)s * plane + colnode) * 4;
-        const Vec4<float> xv = xnext;
-        if (ok && !first && kact && inside && s + 1 >= z0 && s + 1 < z1) xnext = ldcg4(wx + eown + plane * 4);
+        const bool zout = s >= z0 && s < z1;
+        long long eown[NPT];
+        Vec4<float> xv[NPT];
+#pragma unroll
+        for (int i = 0; i < NPT; ++i) {
+          eown[i] = (gbase + (long long)s * plane + colnode[i]) * 4;
+          xv[i] = xnext[i];
+          if (ok && !first && kact && inside[i] && s + 1 >= z0 && s + 1 < z1) xnext[i] = ldcg4(wx + eown[i] + plane * 4);
+        }
         if (ok) ok = mbar_wait_n(&full[slot], par, spin);
-        Vec4<float> cz{}, cp{};
-        float cd = 0.f;
+        Vec4<float> cz[NPT], cp[NPT];
+        float cd[NPT];
+#pragma unroll
+        for (int i = 0; i < NPT; ++i) {
+          cz[i] = cp[i] = Vec4<float>{};
+          cd[i] = 0.f;
+        }
         if (kact && ok) {
           const float* R = slotR(slot) + k * vstr;
           const float* Q = slotQ(slot) + k * vstr;
           const float* P = slotP(slot) + k * vstr;
           const float* D = slotD(slot);
-          const float* Wn = slotW(slot) + j * kW2;
-          Vec4<float> w[7];
+          Vec4<float> w[NPT][7];
 #pragma unroll
-          for (int q = 0; q < 7; ++q) w[q] = lds4(Wn + 4 * q);
-          // the 3 x 3 neighbours (tx-1 .. tx+1, ty-1 .. ty+1) of the staged plane
+          for (int i = 0; i < NPT; ++i) {
+            const float* Wn = slotW(slot) + ((ty0 + i) * TX + tx) * kW2;
 #pragma unroll
-          for (int cy = 0; cy < 3; ++cy) {
+            for (int q = 0; q < 7; ++q) w[i][q] = lds4(Wn + 4 * q);
+          }
+          // the staged rows ty0 .. ty0 + NPT + 1 (halo-relative), columns tx - 1 .. tx + 1:
+          // every node's r_k, z_k, p_k once, then its weight in each own node's stencil
+#pragma unroll
+          for (int cy = 0; cy < NPT + 2; ++cy) {
 #pragma unroll
             for (int cxi = 0; cxi < 3; ++cxi) {
-              const int hnode = (ty + cy) * HX + (tx + cxi);
+              const int hnode = (ty0 + cy) * HX + (tx + cxi);
               const int e = hnode * 4;
-              const float d = D[(ty + cy) * geo.DX + tx + cxi];
+              const float d = D[(ty0 + cy) * geo.DX + tx + cxi];
               const Vec4<float> rv = lds4(R + e);
               Vec4<float> qv{}, pv{};
               if (!first) {
@@ -394,31 +421,36 @@ __global__ void __launch_bounds__(kMaxThr2, 1) k_cg2(CG2Args a, K1Geom geo, cons
                 zn.v[c] = d * rn.v[c];
                 pn.v[c] = fmaf(be[c], pv.v[c], zn.v[c]);
               }
-              const int o = cy * 3 + cxi;
-              const float wu = w[o / 4].v[o % 4];
-              const float wc = w[(9 + o) / 4].v[(9 + o) % 4];
-              const float wd = w[(18 + o) / 4].v[(18 + o) % 4];
 #pragma unroll
-              for (int c = 0; c < 4; ++c) {
-                aU.v[c] = fmaf(wu, pn.v[c], aU.v[c]);
-                aC.v[c] = fmaf(wc, pn.v[c], aC.v[c]);
-                aD.v[c] = fmaf(wd, pn.v[c], aD.v[c]);
-              }
-              if (cy == 1 && cxi == 1) {  // the own node: r_k, p_k, x_k and their sums
-                cd = d;
-                cz = zn;
-                cp = pn;
-                if (own_out) {
-                  Vec4<float> xn;
+              for (int i = 0; i < NPT; ++i) {
+                const int cyr = cy - i;
+                if (cyr < 0 || cyr > 2) continue;
+                const int o = cyr * 3 + cxi;
+                const float wu = w[i][o / 4].v[o % 4];
+                const float wc = w[i][(9 + o) / 4].v[(9 + o) % 4];
+                const float wd = w[i][(18 + o) / 4].v[(18 + o) % 4];
 #pragma unroll
-                  for (int c = 0; c < 4; ++c) {
-                    xn.v[c] = fmaf(al[c], pv.v[c], xv.v[c]);
-                    dt[0][c] = fmaf(rn.v[c], zn.v[c], dt[0][c]);
-                    dt[1][c] = fmaf(rn.v[c], rn.v[c], dt[1][c]);
+                for (int c = 0; c < 4; ++c) {
+                  aU[i].v[c] = fmaf(wu, pn.v[c], aU[i].v[c]);
+                  aC[i].v[c] = fmaf(wc, pn.v[c], aC[i].v[c]);
+                  aD[i].v[c] = fmaf(wd, pn.v[c], aD[i].v[c]);
+                }
+                if (cyr == 1 && cxi == 1) {  // own node i: r_k, p_k, x_k and their sums
+                  cd[i] = d;
+                  cz[i] = zn;
+                  cp[i] = pn;
+                  if (zout && inside[i]) {
+                    Vec4<float> xn;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                      xn.v[c] = fmaf(al[c], pv.v[c], xv[i].v[c]);
+                      dt[0][c] = fmaf(rn.v[c], zn.v[c], dt[0][c]);
+                      dt[1][c] = fmaf(rn.v[c], rn.v[c], dt[1][c]);
+                    }
+                    sts4(wr + eown[i], rn);
+                    sts4(wp + eown[i], pn);
+                    sts4(wx + eown[i], xn);
                   }
-                  sts4(wr + eown, rn);
-                  sts4(wp + eown, pn);
-                  sts4(wx + eown, xn);
                 }
               }
             }
@@ -428,24 +460,30 @@ __global__ void __launch_bounds__(kMaxThr2, 1) k_cg2(CG2Args a, K1Geom geo, cons
         __syncwarp();
         if (lane == 0 && ok) mbar_arrive(&empty[slot]);
         if (kact) {
-          // output plane s-1 is complete: q_k there, and its sums
-          const bool prev_out = ok && inside && s - 1 >= z0 && s - 1 < z1;
-          if (prev_out) {
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-              dt[2][c] = fmaf(pv_p.v[c], aD.v[c], dt[2][c]);
-              dt[3][c] = fmaf(aD.v[c], pv_z.v[c], dt[3][c]);
-              dt[4][c] = fmaf(aD.v[c], pv_d * aD.v[c], dt[4][c]);
+          for (int i = 0; i < NPT; ++i) {
+            // output plane s-1 is complete: q_k there, and its sums
+            const bool prev_out = ok && inside[i] && s - 1 >= z0 && s - 1 < z1;
+            if (prev_out) {
+#pragma unroll
+              for (int c = 0; c < 4; ++c) {
+                dt[2][c] = fmaf(pv_p[i].v[c], aD[i].v[c], dt[2][c]);
+                dt[3][c] = fmaf(aD[i].v[c], pv_z[i].v[c], dt[3][c]);
+                dt[4][c] = fmaf(aD[i].v[c], pv_d[i] * aD[i].v[c], dt[4][c]);
+              }
+              sts4(wq + eown[i] - plane * 4, aD[i]);
             }
-            sts4(wq + eown - plane * 4, aD);
+            aD[i] = aC[i];
+            aC[i] = aU[i];
+            aU[i] = Vec4<float>{};
           }
-          aD = aC;
-          aC = aU;
-          aU = Vec4<float>{};
         }
-        pv_z = cz;
-        pv_p = cp;
-        pv_d = cd;
+#pragma unroll
+        for (int i = 0; i < NPT; ++i) {
+          pv_z[i] = cz[i];
+          pv_p[i] = cp[i];
+          pv_d[i] = cd[i];
+        }
         ++cstep;
       }
     }
@@ -646,19 +684,22 @@ __global__ void __launch_bounds__(kMaxThr2, 1) k_cg2(CG2Args a, K1Geom geo, cons
   }
 }
 
-void* cg2_fn(int G4) {
+template <int NPT>
+void* cg2_fn_npt(int G4) {
   switch (G4) {
-    case 1: return (void*)k_cg2<1>;
-    case 2: return (void*)k_cg2<2>;
-    case 3: return (void*)k_cg2<3>;
-    case 4: return (void*)k_cg2<4>;
-    case 5: return (void*)k_cg2<5>;
-    case 6: return (void*)k_cg2<6>;
-    case 7: return (void*)k_cg2<7>;
-    case 8: return (void*)k_cg2<8>;
+    case 1: return (void*)k_cg2<1, NPT>;
+    case 2: return (void*)k_cg2<2, NPT>;
+    case 3: return (void*)k_cg2<3, NPT>;
+    case 4: return (void*)k_cg2<4, NPT>;
+    case 5: return (void*)k_cg2<5, NPT>;
+    case 6: return (void*)k_cg2<6, NPT>;
+    case 7: return (void*)k_cg2<7, NPT>;
+    case 8: return (void*)k_cg2<8, NPT>;
   }
   return nullptr;
 }
+
+void* cg2_fn(int G4, int npt) { return npt == 2 ? cg2_fn_npt<2>(G4) : npt == 1 ? cg2_fn_npt<1>(G4) : nullptr; }
 
 // b = 1 at the interior nodes of every group (boundary rows stay zero), group-major
 __global__ void k_fill_interior_gm(Grid g, int Np, float* b) {
@@ -676,13 +717,13 @@ __global__ void k_fill_interior_gm(Grid g, int Np, float* b) {
 // weights [TY][TX][28]; then the sums [5 Np], per-orbital state (4 Np doubles,
 // 2 Np ints), the flush's per-warp sums and an owner's five totals.  The ring takes as many
 // slots (3 to 6) as fit in `limit` bytes; false if not even 3 do.
-static bool cg2_layout(int Np, int bw, int TX, int TY, size_t limit, K1Geom* G) {
+static bool cg2_layout(int Np, int bw, int TX, int TY, int npt, size_t limit, K1Geom* G) {
   const size_t sz = sizeof(float);
   const int G4 = bw / 4;
   G->TX = TX;
   G->TY = TY;
-  G->npt = 1;
-  G->nthr = TX * TY;
+  G->npt = npt;
+  G->nthr = TX * TY / npt;
   const int HX = TX + 2, HY = TY + 2;
   G->DX = TX + 4;
   const size_t vec = (size_t)G4 * box_stride_floats(HX, HY) * sz;
@@ -730,18 +771,21 @@ void cg2_candidates(const Grid& g, int Np, int nsm, std::vector<K1Geom>* out) {
   // tiles of 64 or 96 nodes (two or three warps per group slot): the larger ones
   // stage fewer halo nodes per node (1.5x at 16 x 6 against 1.69x at 16 x 4) and
   // run more warps per SM (32-node tiles at two CTAs a SM measured slower)
-  const int shapes[5][2] = {{16, 4}, {8, 8}, {16, 6}, {24, 4}, {8, 12}};
+  // (TX, TY, nodes a thread): the two-node slots take taller tiles (128 nodes: 1.41
+  // staged nodes a node against 1.5-1.69 for the 64- and 96-node tiles)
+  const int shapes[8][3] = {{16, 4, 1}, {8, 8, 1}, {16, 6, 1}, {24, 4, 1}, {8, 12, 1},
+                            {16, 8, 2}, {32, 4, 2}, {8, 16, 2}};
   int widths = 0;
   for (int nob = (Np + 31) / 32; nob <= Np / 4 && widths < 3; ++nob) {
     int bw = (Np + nob - 1) / nob;
     bw = (bw + 3) / 4 * 4;
     if ((Np + bw - 1) / bw != nob) continue;
     bool any = false;
-    for (int si = 0; si < 5; ++si) {
-      const int TX = shapes[si][0], TY = shapes[si][1];
-      if (TX * TY * (bw / 4) + 32 > kMaxThr2) continue;  // consumers + the producer warp
+    for (int si = 0; si < 8; ++si) {
+      const int TX = shapes[si][0], TY = shapes[si][1], npt = shapes[si][2];
+      if (TX * TY / npt * (bw / 4) + 32 > cg2_max_threads(npt)) continue;  // consumers + the producer warp
       K1Geom G{};
-      if (!cg2_layout(Np, bw, TX, TY, limit, &G)) continue;
+      if (!cg2_layout(Np, bw, TX, TY, npt, limit, &G)) continue;
       cg2_finish(g, Np, nsm, bw, &G);
       out->push_back(G);
       any = true;
@@ -782,7 +826,7 @@ cudaError_t cg2_prepare_geo(CG2Plan* P, const K1Geom& geo) {
     uint32_t box[4] = {(uint32_t)kW2, (uint32_t)G.TX, (uint32_t)G.TY, 1};
     if ((e = encode_tiled(&P->mw, ty, 4, (void*)P->wcoef, dims, str, box)) != cudaSuccess) return e;
   }
-  void* f = cg2_fn(G.G4);
+  void* f = cg2_fn(G.G4, G.npt);
   if (!f) return cudaErrorInvalidValue;
   if ((e = allow_max_dyn_smem(f)) != cudaSuccess) return e;
   int nb = 0, dev = 0, coop = 0;
@@ -800,7 +844,7 @@ cudaError_t cg2_launch(CG2Plan* P, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(&a.st->bar_count, 0, sizeof(unsigned int), st);
   if (e != cudaSuccess) return e;
   void* args[] = {&a, &geo, &P->mr[0], &P->mq[0], &P->mp[0], &P->mr[1], &P->mq[1], &P->mp[1], &P->md, &P->mw};
-  return cudaLaunchCooperativeKernel(cg2_fn(geo.G4), dim3(geo.grid), dim3(geo.nthr * geo.G4 + 32), args, geo.smem,
+  return cudaLaunchCooperativeKernel(cg2_fn(geo.G4, geo.npt), dim3(geo.grid), dim3(geo.nthr * geo.G4 + 32), args, geo.smem,
                                      st);
 }
 
@@ -851,8 +895,9 @@ cudaError_t cg2_autotune(CG2Plan* P, cudaStream_t st, int passes, int* chosen, f
     }
     ++*tried;
     if (std::getenv("PARO_PRINT_PLAN"))
-      std::fprintf(stderr, "paro single-pass CG candidate: tile %dx%d, block %d, %d slots, %.2f us a pass\n",
-                   cand[i].TX, cand[i].TY, cand[i].G4 * 4, cand[i].slots, 1e3f * ms / (passes + 1));
+      std::fprintf(stderr, "paro single-pass CG candidate: tile %dx%d, %d nodes a thread, block %d, %d slots, "
+                   "%.2f us a pass\n", cand[i].TX, cand[i].TY, cand[i].npt, cand[i].G4 * 4, cand[i].slots,
+                   1e3f * ms / (passes + 1));
     if (*chosen < 0 || ms < best) {
       best = ms;
       *chosen = (int)i;

@@ -47,8 +47,19 @@ __device__ bool reduce_partials(const double (&acc)[K][4], int Np, int grp, int 
   int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nwarps = blockDim.x / 32;
   for (int t = warp; t < K * Np; t += nwarps) {
     int k = t / Np, o = t % Np;
+    const double* src = partial + (long long)k * kMaxRedBlocks * Np + o;
     double s = 0.0;
-    for (int b = lane; b < (int)gridDim.x; b += 32) s += __ldcg(&partial[((long long)k * kMaxRedBlocks + b) * Np + o]);
+    // eight loads in flight a lane before the additions (one L2 round trip per 256 blocks)
+    for (int b0 = lane; b0 < (int)gridDim.x; b0 += 32 * 8) {
+      double v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int b = b0 + 32 * q;
+        v[q] = b < (int)gridDim.x ? __ldcg(src + (long long)b * Np) : 0.0;
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) s += v[q];
+    }
     for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
     if (lane == 0) tot[t] = s;
   }
@@ -120,7 +131,7 @@ __global__ void __launch_bounds__(kRedThreads) k_refine_residual(Grid g, int N, 
 
 // The same residual in float-float arithmetic (ff.cuh): x and b as hi/lo arrays,
 // the packed per-node float-float weights of A.
-__global__ void __launch_bounds__(kRedThreads) k_refine_residual_ff(Grid g, int N, int Np, const float* __restrict__ whi,
+__global__ void __launch_bounds__(kRedThreads, 4) k_refine_residual_ff(Grid g, int N, int Np, const float* __restrict__ whi,
                                                                     const float* __restrict__ wlo,
                                                                     const float* __restrict__ xhi,
                                                                     const float* __restrict__ xlo,
@@ -260,8 +271,9 @@ cudaError_t launch_refine_residual(const Grid& g, int N, int Np, const double* c
 cudaError_t launch_refine_residual_ff(const Grid& g, int N, int Np, const float* whi, const float* wlo,
                                       const float* xhi, const float* xlo, const float* bhi, const float* blo,
                                       float* rhs32, const CGState& s, double tol, cudaStream_t st, int gm) {
-  k_refine_residual_ff<<<red_blocks(g, Np), kRedThreads, 0, st>>>(g, N, Np, whi, wlo, xhi, xlo, bhi, blo, rhs32, s,
-                                                                  tol, gm);
+  // one wave: four 256-thread blocks a SM (64 registers a thread)
+  const int grid = red_blocks(g, Np) < 152 * 4 ? red_blocks(g, Np) : 152 * 4;
+  k_refine_residual_ff<<<grid, kRedThreads, 0, st>>>(g, N, Np, whi, wlo, xhi, xlo, bhi, blo, rhs32, s, tol, gm);
   return cudaGetLastError();
 }
 

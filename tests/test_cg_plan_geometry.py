@@ -284,10 +284,12 @@ def test_single_pass_kernel_geometry(plans):
         offs = (0, G["off_p"], G["off_s"], G["off_d"], G["off_w"], G["slot"])
         assert all(o % 128 == 0 for o in offs), G
         assert all(offs[i + 1] - offs[i] >= (vec, vec, vec, dv, wv)[i] for i in range(5)), G
-        # one node per consumer thread, whole warps per group slot; one producer warp more
-        assert G["npt"] == 1 and G["nthr"] == G["TX"] * G["TY"], G
+        # one or two nodes (stacked in y) per consumer thread, whole warps per group
+        # slot; one producer warp more (512 threads at most, 384 with two nodes a thread)
+        assert G["npt"] in (1, 2) and G["nthr"] * G["npt"] == G["TX"] * G["TY"] and G["TY"] % G["npt"] == 0, G
         nt = G["nthr"] * G["G4"] + 32
-        assert nt <= 512 and (nt - 32) % 32 == 0 and G["smem"] + static <= 227 * 1024, G
+        assert nt <= (512 if G["npt"] == 1 else 384), G
+        assert (nt - 32) % 32 == 0 and G["nthr"] % 32 == 0 and G["smem"] + static <= 227 * 1024, G
         # 3 to 6 ring slots (two mbarriers each in the first 128 bytes); sums [5 Np],
         # state (6 Np words), the flush's per-warp sums (5 x 4 per consumer warp) and
         # an owner's five totals
