@@ -327,10 +327,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc_fence_after();
     __syncthreads();
     if (s_fail) break;
-    // combine the three exact level sums of the 128 nodes and add them to the accumulators
+    // combine the three exact level sums of the 128 nodes and add them to the
+    // accumulators; only the warps whose TMEM lanes hold rows a < na (the rest of
+    // the 128 MMA rows are zero padding: 12 of 16 warps at Np <= 32)
     const float sa = pow2f(cexp[row] - 8);
 #pragma unroll
-    for (int c = 0; c < kCols; c += 8) {
+    for (int c = 0; c < kCols && 32 * (warp % 4) < na; c += 8) {
       const uint32_t ta = tmem + ((uint32_t)(32 * (warp % 4)) << 16) + (uint32_t)(col0 + c);
       float v0[8], v1[8];
       tmem_ld8(ta, v0);
@@ -555,9 +557,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       tc_fence_after();
       __syncthreads();
       if (s_fail) break;
-      // U[g][n0 + b] = 2^(E_g + F_b - 16) (L0 + L1 2^-8 + L2 2^-16)
+      // U[g][n0 + b] = 2^(E_g + F_b - 16) (L0 + L1 2^-8 + L2 2^-16), by the warps whose
+      // columns include some b < Np
 #pragma unroll
-      for (int c = 0; c < kColsT; c += 8) {
+      for (int c = 0; c < kColsT && n0 + col0 < Np; c += 8) {
         const uint32_t ta = tmem + ((uint32_t)(32 * (warp % 4)) << 16) + (uint32_t)(col0 + c);
         float v0[8], v1[8];
         tmem_ld8(ta, v0);
