@@ -324,8 +324,20 @@ const char* paro_last_error(paro_mesh m);
 long long paro_interior_nodes(paro_mesh m);
 
 /* Batches of independent systems (meshes, orbital counts and potentials of
- * their own): paro_batch_iterate runs paro_iterate on every system from a pool
- * of n_workers host threads, the largest system (interior nodes x N) first.
+ * their own), Step 3 of Algorithm 3.1 solved for many systems at once.
+ * paro_batch_iterate runs paro_iterate on every system.  Batched mode (the
+ * default, paro_batch_set_fused(b, 1)): one host thread per system, and the
+ * float32 correction solves of every PARO_MIXED, Jacobi-preconditioned system
+ * (at least two, at most 256; profile = 0) run as ONE cooperative launch per
+ * refinement sweep over all of them: work items (system, orbital block, tile
+ * column, z-chunk) are taken from a counter in global memory, so converged
+ * systems drop out and the rest spread over every SM.  The systems advance in
+ * lockstep, one correction solve at a time; everything between two solves runs
+ * on each system's own stream.  Float64 and multigrid systems iterate alone in
+ * their threads.  The first call plans and autotunes the batched kernel over
+ * the systems' buffers (PARO_AUTOTUNE=0: untuned).  Pool mode
+ * (paro_batch_set_fused(b, 0)): a pool of n_workers host threads runs
+ * paro_iterate per system, largest (interior nodes x N) first.
  * Give every handle its own CUDA stream (paro_mesh_create's cuda_stream): the
  * kernels of different systems then overlap on the GPU and the host-side waits
  * of one system hide behind the others' work; handles that share a stream stay
@@ -342,6 +354,15 @@ int paro_batch_size(paro_batch b);
  * every system's status; stats: host[size] out or NULL.  Returns PARO_OK if all
  * converged, else the status of the first failing system in index order. */
 int paro_batch_iterate(paro_batch b, int* rc, paro_stats* stats);
+/* on = 1: batched correction solves (default); 0: the pool of host workers.
+ * PARO_ERR_ARG for other values or a NULL batch. */
+int paro_batch_set_fused(paro_batch b, int on);
+/* Batched launches of the last paro_batch_iterate (0: no batch was formed, e.g.
+ * fewer than two qualifying systems, or pool mode). */
+long long paro_batch_fused_launches(paro_batch b);
+/* Message of the last batch-level failure (planning the batched kernel); the
+ * systems' own failures are in paro_last_error of their handles. */
+const char* paro_batch_last_error(paro_batch b);
 int paro_batch_destroy(paro_batch b); /* the handles are not destroyed */
 
 #ifdef __cplusplus

@@ -112,10 +112,15 @@ def lib():
     L.paro_batch_size.argtypes = [vp]
     L.paro_batch_iterate.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(paro_stats)]
     L.paro_batch_destroy.argtypes = [vp]
+    L.paro_batch_set_fused.argtypes = [vp, ip]
+    L.paro_batch_fused_launches.argtypes = [vp]
+    L.paro_batch_fused_launches.restype = C.c_longlong
+    L.paro_batch_last_error.argtypes = [vp]
+    L.paro_batch_last_error.restype = C.c_char_p
     for f in ("paro_mesh_create", "paro_mesh_destroy", "paro_set_potential", "paro_orbital_solve",
               "paro_rayleigh_ritz", "paro_iterate", "paro_apply", "paro_mg_vcycle", "paro_density", "paro_ks_potential",
               "paro_scf_iterate", "paro_ks_density_in", "paro_ks_energy", "paro_batch_create", "paro_batch_add", "paro_batch_size",
-              "paro_batch_iterate", "paro_batch_destroy"):
+              "paro_batch_iterate", "paro_batch_destroy", "paro_batch_set_fused"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -322,20 +327,33 @@ class Mesh:
 
 
 class Batch:
-    """Independent systems advanced by paro_batch_iterate from a pool of host threads.
+    """Independent systems advanced together by paro_batch_iterate.
 
+    fused=True (default): the correction solves of the mixed-precision systems
+    run as one batched launch per refinement sweep; fused=False: a pool of
+    `workers` host threads runs each system's loop on its own.
     add(mesh, U, lam=None, params=None): U a CUDA float64 tensor (n_interior x N)
     on the mesh's stream, updated in place; lam None starts with a Rayleigh-Ritz.
-    iterate() returns the per-system status codes, eigenvalues and statistics.
+    iterate() returns the per-system status codes, eigenvalues and statistics;
+    fused_launches() the batched launches of the last iterate.
     """
 
-    def __init__(self, workers=4):
+    def __init__(self, workers=4, fused=True):
         h = C.c_void_p()
         rc = lib().paro_batch_create(C.byref(h), int(workers))
         if rc != PARO_OK:
             raise ParoError(rc, "paro_batch_create")
         self.h = h
         self.items = []
+        rc = lib().paro_batch_set_fused(self.h, 1 if fused else 0)
+        if rc != PARO_OK:
+            raise ParoError(rc, "paro_batch_set_fused")
+
+    def fused_launches(self):
+        return int(lib().paro_batch_fused_launches(self.h))
+
+    def last_error(self):
+        return lib().paro_batch_last_error(self.h).decode()
 
     def add(self, mesh, U, lam=None, params=None):
         N = U.shape[1]
@@ -351,7 +369,9 @@ class Batch:
         n = len(self.items)
         rc = (C.c_int * max(n, 1))()
         st = (paro_stats * max(n, 1))()
-        lib().paro_batch_iterate(self.h, rc, st)
+        r = lib().paro_batch_iterate(self.h, rc, st)
+        if r != PARO_OK and all(int(rc[i]) == PARO_OK for i in range(n)):
+            raise ParoError(r, "paro_batch_iterate: " + self.last_error())
         return [int(rc[i]) for i in range(n)], [it[2] for it in self.items], [st[i] for i in range(n)]
 
     def close(self):

@@ -4,9 +4,12 @@
 // only sequences launches on the handle's stream and reads back the per-orbital
 // convergence counters and the Ritz values.
 #include <cmath>
+#include <condition_variable>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -18,8 +21,16 @@
 
 using namespace paro;
 
+namespace {
+struct BatchCG;
+}
+
 struct paro_mesh_s {
   Grid g{};
+  // a batch whose correction solves this handle joins (one batched launch for
+  // every system of the batch), and the handle's index in it
+  BatchCG* bcg = nullptr;
+  int bcg_index = -1;
   long long rr_tc = 0;  // Rayleigh-Ritz steps with tensor-core Grams (for paro_stats)
   int* clus = nullptr;  // cluster ids of the cluster-separated Rayleigh-Ritz (device, kMaxN)
   const char* tune_source = "default";  // how the float32 CG geometry was chosen
@@ -806,6 +817,79 @@ int check_precond(paro_mesh m, const paro_params& p) {
   return PARO_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Batches: the correction solves of every system in one launch.
+// Each system of a batch runs its own ParO loop (paro_iterate) in a host thread
+// of its own.  When a system reaches a float32 correction solve it records an
+// event on its stream and waits here; once every system still iterating has
+// arrived, the last one makes the batch stream wait on all their events,
+// launches the batched single-pass CG over them (the systems' bits in the
+// launch mask), records `done`, and every system's stream waits on it.  A
+// system that finishes its loop leaves, and a launch is issued for the others
+// if they are all waiting.  Systems therefore advance in lockstep at the
+// granularity of a correction solve, while everything between two solves
+// (right-hand sides, refinement residuals, Rayleigh-Ritz) runs on each system's
+// own stream, overlapping the others.
+// ---------------------------------------------------------------------------
+struct BatchCG {
+  std::mutex mu;
+  std::condition_variable cv;
+  CG2BPlan plan;
+  cudaStream_t st = nullptr;
+  cudaEvent_t done = nullptr;
+  std::vector<cudaEvent_t> ready;
+  std::vector<paro_mesh> ms;
+  std::vector<char> waiting_flag;
+  std::vector<unsigned> spin;
+  int live = 0, waiting = 0;
+  unsigned long long gen = 0;
+  cudaError_t launch_err = cudaSuccess;
+  long long launches = 0;
+  int chosen = -1, tried = 0;
+  float best_us = 0.f;
+  std::vector<CG2BSysDesc> desc;  // what the plan was built over (reuse check)
+};
+
+void bcg_launch_locked(BatchCG* B) {
+  unsigned long long mask[kMaxBatchSys / 64] = {0, 0, 0, 0};
+  unsigned spin = kSpinLimit;
+  cudaError_t e = cudaSuccess;
+  for (size_t i = 0; i < B->ms.size(); ++i) {
+    if (!B->waiting_flag[i]) continue;
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(B->st, B->ready[i], 0);
+    mask[i >> 6] |= 1ull << (i & 63);
+    if (B->spin[i] < spin) spin = B->spin[i];
+    B->waiting_flag[i] = 0;
+  }
+  if (e == cudaSuccess) e = cg2b_launch(&B->plan, mask, spin, B->st);
+  if (e == cudaSuccess) e = cudaEventRecord(B->done, B->st);
+  B->launch_err = e;
+  ++B->launches;
+  B->waiting = 0;
+  ++B->gen;
+  B->cv.notify_all();
+}
+
+// Replaces the single-system launch in the refinement sweeps of a batch member.
+int batch_cg_solve(paro_mesh m, unsigned spin) {
+  BatchCG* B = m->bcg;
+  std::unique_lock<std::mutex> lk(B->mu);
+  const int i = m->bcg_index;
+  CK(cudaEventRecord(B->ready[i], m->st));
+  B->waiting_flag[i] = 1;
+  B->spin[i] = spin;
+  ++B->waiting;
+  const unsigned long long g0 = B->gen;
+  if (B->waiting == B->live) bcg_launch_locked(B);
+  else B->cv.wait(lk, [&] { return B->gen != g0; });
+  // the next launch needs this system to arrive again: B->done and launch_err
+  // still describe the launch that ran its solve
+  if (B->launch_err != cudaSuccess)
+    return fail(m, PARO_ERR_CUDA, std::string("batched CG launch: ") + cudaGetErrorString(B->launch_err));
+  CK(cudaStreamWaitEvent(m->st, B->done, 0));
+  return PARO_OK;
+}
+
 // Step 3 on the packed buffers: u (current orbitals) -> x (source solutions).
 // Mixed-precision solve of A x = b for N columns: x (float64, padded) holds the
 // initial guess, b is given as a float-float pair in fah/fal.  Each sweep forms
@@ -845,7 +929,12 @@ int refine_solve_cg2(paro_mesh m, int N, const paro_params& p, paro_stats* st, d
                                           p.solve_tol, m->st, 1));
       if (st) st->stencil_applies += N;
       if (m->profile) CK(cudaEventRecord(m->pev[2 * m->pev_used], m->st));
-      LAUNCH(1, cg2_launch(P, m->st));
+      if (m->bcg) {
+        TRY(batch_cg_solve(m, P->args.spin));
+        m->launches += 1;
+      } else {
+        LAUNCH(1, cg2_launch(P, m->st));
+      }
       if (m->profile) {
         CK(cudaEventRecord(m->pev[2 * m->pev_used + 1], m->st));
         m->pev_used++;
@@ -1045,8 +1134,47 @@ RRMode next_rr_mode(paro_mesh m, RRMode cur, double dl, const std::vector<double
 // ill-conditioned far beyond what the mixed path's Grams resolve (their error is
 // amplified by cond(X^T M X)); inside the ParO loop X stays near M-orthonormal.
 // src_split: fxh/fxl already hold the float-float split of src.
+// Host check of an overlap matrix G (N x N, leading dimension ld) before the
+// fast Rayleigh-Ritz trusts Grams from 24-bit inputs: with G scaled to unit
+// diagonal, its Cholesky factor L exists and trace(G^-1) = ||L^-1||_F^2 stays
+// below 4 N (near M-orthonormal X gives ~N).  The Grams' relative error is
+// amplified by ||G^-1|| <= trace(G^-1), so raw, nearly dependent guesses fail
+// the check.
+static bool overlap_well_conditioned(const std::vector<double>& G, int N, int ld) {
+  std::vector<double> L((size_t)N * N, 0.0), d(N);
+  for (int i = 0; i < N; ++i) {
+    const double gii = G[(size_t)i * ld + i];
+    if (!(gii > 0.0) || !std::isfinite(gii)) return false;
+    d[i] = 1.0 / std::sqrt(gii);
+  }
+  for (int j = 0; j < N; ++j) {
+    double s = G[(size_t)j * ld + j] * d[j] * d[j];
+    for (int k = 0; k < j; ++k) s -= L[(size_t)j * N + k] * L[(size_t)j * N + k];
+    if (!(s > 0.0)) return false;
+    const double ljj = std::sqrt(s);
+    L[(size_t)j * N + j] = ljj;
+    for (int i = j + 1; i < N; ++i) {
+      double t = 0.5 * (G[(size_t)i * ld + j] + G[(size_t)j * ld + i]) * d[i] * d[j];
+      for (int k = 0; k < j; ++k) t -= L[(size_t)i * N + k] * L[(size_t)j * N + k];
+      L[(size_t)i * N + j] = t / ljj;
+    }
+  }
+  // ||L^-1||_F^2, column by column of L^-1 (forward substitution)
+  double tr = 0.0;
+  std::vector<double> y(N);
+  for (int c = 0; c < N; ++c) {
+    for (int i = 0; i < N; ++i) {
+      double t = (i == c) ? 1.0 : 0.0;
+      for (int k = c; k < i; ++k) t -= L[(size_t)i * N + k] * y[k];
+      y[i] = i < c ? 0.0 : t / L[(size_t)i * N + i];
+      tr += y[i] * y[i];
+    }
+  }
+  return std::isfinite(tr) && tr <= 4.0 * N;
+}
+
 int rr_packed(paro_mesh m, int N, const double* src, double* dst, double* lam, RRMode mode = kRRFast,
-              const int* clus = nullptr, bool src_split = false) {
+              const int* clus = nullptr, bool src_split = false, bool guard = false) {
   const int Np = m->Np_alloc;
   Grid& g = m->g;
   m->x_split_valid = false;
@@ -1065,6 +1193,14 @@ int rr_packed(paro_mesh m, int N, const double* src, double* dst, double* lam, R
     LAUNCH(1, launch_gram_reduce1(Np, nch, m->gpart_tc, m->GA, m->st));
     LAUNCH(1, launch_gram_tc(g, Np, m->fxh, m->fbh, m->gpart_tc, &nch, &m->cgst->status, m->st));
     LAUNCH(1, launch_gram_reduce1(Np, nch, m->gpart_tc, m->GB, m->st));
+    if (guard) {
+      // arbitrary X (the public call): an overlap too ill-conditioned for these
+      // Grams takes the float64 step instead
+      std::vector<double> hG((size_t)Np * Np);
+      CK(cudaMemcpyAsync(hG.data(), m->GB, sizeof(double) * Np * Np, cudaMemcpyDeviceToHost, m->st));
+      CK(cudaStreamSynchronize(m->st));
+      if (!overlap_well_conditioned(hG, N, Np)) return rr_packed(m, N, src, dst, lam, kRRFP64, clus, false);
+    }
     ++m->rr_tc;
   } else if (ff) {
     // float-float: HX and MX as hi/lo arrays, both Grams and the rotation from the split X
@@ -1084,7 +1220,16 @@ int rr_packed(paro_mesh m, int N, const double* src, double* dst, double* lam, R
   // pipes; the start on user guesses (ill-conditioned overlaps) stays float64
   LAUNCH(1, launch_small_eig(N, m->GA, m->GB, m->eigwork, m->C, m->theta, &m->cgst->status, m->st,
                              &m->cgst->bar_count, clus, mixed && mode != kRRFP64));
-  TRY(check_status(m, "rayleigh_ritz"));
+  {
+    // an input the fast arithmetic cannot resolve (the overlap of raw guesses can
+    // be ill-conditioned far beyond the Grams' 24-bit inputs): the eigensolve
+    // reports an indefinite overlap or its sweep limit, and the step is redone
+    // in float64 (Grams, eigensolve and rotation) from the same X
+    const int rc = check_status(m, "rayleigh_ritz");
+    if ((rc == PARO_ERR_NOT_CONVERGED || rc == PARO_ERR_NOT_SPD) && mixed && mode != kRRFP64)
+      return rr_packed(m, N, src, dst, lam, kRRFP64, clus, false);
+    TRY(rc);
+  }
   // the rotation: on the tensor cores from the hi parts of X with the tensor-core
   // Grams (the same 24-bit inputs), else in float-float from the split X (C staged
   // in shared memory whole, or in column blocks above kRotateFFMaxNp), or float64
@@ -1286,6 +1431,165 @@ int upload_occ(paro_mesh m, int N, const double* occ) {
 }
 
 }  // namespace
+
+namespace paro {
+
+// Joins the mixed-precision, Jacobi-preconditioned systems of a batch (at least
+// two, at most kMaxBatchSys) to one coordinator: their workspaces and
+// single-pass plans are made, the batched plan is built over their CG buffers
+// and autotuned (PARO_AUTOTUNE=0: the first candidate; PARO_CG2B_GEOMETRY=<i>:
+// candidate i), and each handle points to the coordinator.  *coord carries the
+// coordinator from one paro_batch_iterate to the next: it is kept when the same
+// systems come back with the same buffers, else rebuilt.  *coord is null when
+// fewer than two systems qualify or the batched kernel cannot run co-resident;
+// the systems then solve alone.
+static bool same_desc(const CG2BSysDesc& a, const CG2BSysDesc& b) {
+  return a.Np == b.Np && a.N == b.N && a.x == b.x && a.r[0] == b.r[0] && a.r[1] == b.r[1] && a.q[0] == b.q[0] &&
+         a.q[1] == b.q[1] && a.p[0] == b.p[0] && a.p[1] == b.p[1] && a.st == b.st && a.dinv_tma == b.dinv_tma &&
+         a.dpitch == b.dpitch && a.wcoef == b.wcoef && a.g.nx == b.g.nx && a.g.ny == b.g.ny && a.g.nz == b.g.nz;
+}
+
+void batch_cg_destroy(void* h) {
+  BatchCG* B = static_cast<BatchCG*>(h);
+  if (!B) return;
+  if (B->st) cudaStreamSynchronize(B->st);
+  cg2b_destroy(&B->plan);
+  for (auto ev : B->ready)
+    if (ev) cudaEventDestroy(ev);
+  if (B->done) cudaEventDestroy(B->done);
+  if (B->st) cudaStreamDestroy(B->st);
+  delete B;
+}
+
+int batch_cg_begin(const std::vector<paro_mesh>& ms, const std::vector<int>& Ns, const std::vector<paro_params>& ps,
+                   void** coord, std::string* err) {
+  std::vector<int> idx;
+  for (size_t i = 0; i < ms.size(); ++i) {
+    paro_mesh m = ms[i];
+    if (m->precision != PARO_MIXED || ps[i].precond != PARO_PRECOND_JACOBI || ps[i].profile) continue;
+    const int N = Ns[i];
+    if (N < 1 || N > kMaxN || !m->have_pot) continue;
+    const int rc = ensure_workspace(m, (N + 3) / 4 * 4);
+    if (rc != PARO_OK) {
+      *err = m->err;
+      return rc;
+    }
+    if (m->plan2 && m->plan2->ok) idx.push_back((int)i);
+  }
+  if (idx.size() < 2 || idx.size() > (size_t)kMaxBatchSys) {
+    batch_cg_destroy(*coord);
+    *coord = nullptr;
+    return PARO_OK;
+  }
+  std::vector<CG2BSysDesc> desc;
+  for (int i : idx) {
+    paro_mesh m = ms[i];
+    const int rc = set_f32_layout(m, 1);
+    if (rc != PARO_OK) {
+      *err = m->err;
+      return rc;
+    }
+    const CG2Plan* P = m->plan2;
+    CG2BSysDesc d{};
+    d.g = m->g;
+    d.Np = P->args.Np;
+    d.N = Ns[i];
+    d.x = P->args.x;
+    for (int b = 0; b < 2; ++b) {
+      d.r[b] = P->args.r[b];
+      d.q[b] = P->args.q[b];
+      d.p[b] = P->args.p[b];
+    }
+    d.st = m->cgst;
+    d.dinv_tma = P->dinv_tma;
+    d.dpitch = P->dpitch;
+    d.wcoef = P->wcoef;
+    desc.push_back(d);
+  }
+  BatchCG* B = static_cast<BatchCG*>(*coord);
+  bool reuse = B && B->desc.size() == desc.size();
+  for (size_t k = 0; reuse && k < desc.size(); ++k) reuse = B->ms[k] == ms[idx[k]] && same_desc(B->desc[k], desc[k]);
+  if (!reuse) {
+    batch_cg_destroy(B);
+    *coord = nullptr;
+    B = new BatchCG();
+    B->desc = desc;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&B->st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cg2b_create(&B->plan, desc, ms[idx[0]]->nsm);
+    const char* off = std::getenv("PARO_AUTOTUNE");
+    const char* force = std::getenv("PARO_CG2B_GEOMETRY");  // candidate i, untimed (tests run several)
+    if (e == cudaSuccess && force) {
+      std::vector<K1Geom> cand;
+      cg2b_candidates(&B->plan, &cand);
+      const int i = std::atoi(force);
+      if (i >= 0 && i < (int)cand.size()) {
+        e = cg2b_prepare_geo(&B->plan, cand[i]);
+        B->chosen = i;
+      }
+    } else if (e == cudaSuccess && !(off && off[0] == '0')) {
+      e = cg2b_autotune(&B->plan, B->st, 4, &B->chosen, &B->best_us, &B->tried);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(B->st);
+    B->ready.assign(idx.size(), nullptr);
+    for (size_t k = 0; k < idx.size() && e == cudaSuccess; ++k)
+      e = cudaEventCreateWithFlags(&B->ready[k], cudaEventDisableTiming);
+    if (e != cudaSuccess || !B->plan.ok) {
+      const bool cuda_failed = e != cudaSuccess;
+      if (cuda_failed) *err = std::string("batched CG plan: ") + cudaGetErrorString(e);
+      (void)cudaGetLastError();
+      batch_cg_destroy(B);
+      return cuda_failed ? PARO_ERR_CUDA : PARO_OK;
+    }
+    if (std::getenv("PARO_PRINT_PLAN"))
+      std::fprintf(stderr, "paro batched CG plan: %zu systems, tile %dx%d, %d nodes a thread, block %d, %d slots, "
+                   "z-chunk %d, %d items, %d orbital blocks, candidate %d (%d timed, %.1f us a pass)\n", idx.size(),
+                   B->plan.geo.TX, B->plan.geo.TY, B->plan.geo.npt, B->plan.geo.G4 * 4, B->plan.geo.slots,
+                   B->plan.args.zlen, B->plan.args.nitems, B->plan.args.njobs, B->chosen, B->tried, B->best_us);
+    for (size_t k = 0; k < idx.size(); ++k) B->ms.push_back(ms[idx[k]]);
+    *coord = B;
+  } else {
+    // the systems' streams may still run earlier work on these buffers
+    for (int i : idx) {
+      paro_mesh m = ms[i];
+      CK(cudaStreamSynchronize(m->st));
+    }
+  }
+  for (size_t k = 0; k < idx.size(); ++k) {
+    paro_mesh m = ms[idx[k]];
+    m->bcg = B;
+    m->bcg_index = (int)k;
+  }
+  B->live = (int)idx.size();
+  B->waiting = 0;
+  B->launches = 0;
+  B->launch_err = cudaSuccess;
+  B->waiting_flag.assign(idx.size(), 0);
+  B->spin.assign(idx.size(), kSpinLimit);
+  return PARO_OK;
+}
+
+// The system's loop has ended (converged, limit or error): it no longer takes
+// part, and the others are launched if they were all waiting for it.
+void batch_cg_leave(paro_mesh m) {
+  BatchCG* B = m->bcg;
+  if (!B) return;
+  std::lock_guard<std::mutex> lk(B->mu);
+  m->bcg = nullptr;
+  --B->live;
+  if (B->live > 0 && B->waiting == B->live) bcg_launch_locked(B);
+}
+
+// After every system has left: the batched launches of this paro_batch_iterate.
+long long batch_cg_finish(void* h) {
+  BatchCG* B = static_cast<BatchCG*>(h);
+  if (!B) return 0;
+  cudaStreamSynchronize(B->st);
+  return B->launches;
+}
+
+}  // namespace paro
 
 extern "C" {
 
@@ -1525,7 +1829,7 @@ int paro_rayleigh_ritz(paro_mesh m, int N, const double* X, double* U_out, doubl
   CallScope cs(m, s, 0);
   LAUNCH(1, launch_pack(m->g, N, Np, X, m->x, m->st));
   Timer t(m, s ? &s->ms_rr : nullptr);
-  TRY(rr_packed(m, N, m->x, m->u, lambda_out));
+  TRY(rr_packed(m, N, m->x, m->u, lambda_out, kRRFast, nullptr, false, true));
   t.stop();
   LAUNCH(1, launch_unpack(m->g, N, Np, m->u, U_out, m->st));
   CK(cudaStreamSynchronize(m->st));

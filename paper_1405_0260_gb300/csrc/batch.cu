@@ -1,11 +1,18 @@
 // Batches of independent systems: many meshes, each with its own orbital block,
-// advanced to convergence by paro_iterate (Algorithm A.1 per system) from a pool
-// of host worker threads.  Every system is a mesh handle with its own CUDA
-// stream, so the kernels of different systems overlap on the GPU and the
-// host-side waits of one system (the |delta lambda| test, the refinement
-// sweeps' active counts) hide behind the other systems' kernels.  Systems are
-// taken largest first (interior nodes x orbitals) so that the long ones start
-// early.
+// advanced to convergence by paro_iterate (Algorithm A.1 per system).
+//
+// Batched mode (the default): every system runs its loop in a host thread of
+// its own, and the float32 correction solves of all mixed-precision, Jacobi
+// systems run as one batched launch per refinement sweep (a coordinator in
+// api.cu gathers them; cg2b.cu is the kernel), so the GPU streams the work of
+// every system still iterating at once.  The rest of each loop runs on the
+// system's own stream.  Other systems (float64, multigrid) iterate alone in
+// their threads.
+//
+// Pool mode: a pool of n_workers host threads runs paro_iterate per system,
+// largest first (interior nodes x orbitals), each system's kernels on its own
+// stream, so that systems overlap on the GPU and one system's host-side waits
+// hide behind the others' kernels.
 #include <algorithm>
 #include <atomic>
 #include <string>
@@ -13,6 +20,14 @@
 #include <vector>
 
 #include "../../include/paro.h"
+
+namespace paro {
+int batch_cg_begin(const std::vector<paro_mesh>& ms, const std::vector<int>& Ns, const std::vector<paro_params>& ps,
+                   void** coord, std::string* err);
+void batch_cg_leave(paro_mesh m);
+long long batch_cg_finish(void* coord);
+void batch_cg_destroy(void* coord);
+}  // namespace paro
 
 struct paro_batch_s {
   struct System {
@@ -25,6 +40,10 @@ struct paro_batch_s {
   };
   std::vector<System> sys;
   int workers = 1;
+  int fused = 1;               // batched correction solves (else the pool of workers)
+  long long fused_launches = 0;  // batched launches of the last paro_batch_iterate
+  std::string err;
+  void* coord = nullptr;  // the batched-solve coordinator, kept across calls
 };
 
 extern "C" {
@@ -55,8 +74,7 @@ int paro_batch_add(paro_batch b, paro_mesh m, int N, double* U, double* lambda, 
 
 int paro_batch_size(paro_batch b) { return b ? (int)b->sys.size() : PARO_ERR_ARG; }
 
-int paro_batch_iterate(paro_batch b, int* rc, paro_stats* stats) {
-  if (!b || !rc) return PARO_ERR_ARG;
+static int batch_iterate_pool(paro_batch b, int* rc, paro_stats* stats) {
   const int n = (int)b->sys.size();
   std::vector<int> order(n);
   for (int i = 0; i < n; ++i) order[i] = i;
@@ -79,13 +97,63 @@ int paro_batch_iterate(paro_batch b, int* rc, paro_stats* stats) {
   pool.reserve(nw);
   for (int w = 0; w < nw; ++w) pool.emplace_back(worker);
   for (auto& t : pool) t.join();
+  return PARO_OK;
+}
+
+// One host thread per system; the coordinator batches the correction solves of
+// the systems it accepted (the others solve alone).
+static int batch_iterate_fused(paro_batch b, int* rc, paro_stats* stats) {
+  const int n = (int)b->sys.size();
+  std::vector<paro_mesh> ms(n);
+  std::vector<int> Ns(n);
+  std::vector<paro_params> ps(n);
+  for (int i = 0; i < n; ++i) {
+    ms[i] = b->sys[i].m;
+    Ns[i] = b->sys[i].N;
+    ps[i] = b->sys[i].p;
+  }
+  const int rcb = paro::batch_cg_begin(ms, Ns, ps, &b->coord, &b->err);
+  if (rcb != PARO_OK) return rcb;
+  std::vector<std::thread> th;
+  th.reserve(n);
+  for (int i = 0; i < n; ++i)
+    th.emplace_back([&, i]() {
+      auto& s = b->sys[i];
+      paro_stats local{};
+      rc[i] = paro_iterate(s.m, s.N, s.U, s.lambda, &s.p, stats ? &local : nullptr);
+      paro::batch_cg_leave(s.m);  // also after an error: the others must not wait for it
+      if (stats) stats[i] = local;
+    });
+  for (auto& t : th) t.join();
+  b->fused_launches = paro::batch_cg_finish(b->coord);
+  return PARO_OK;
+}
+
+int paro_batch_iterate(paro_batch b, int* rc, paro_stats* stats) {
+  if (!b || !rc) return PARO_ERR_ARG;
+  const int n = (int)b->sys.size();
+  b->fused_launches = 0;
+  b->err.clear();
+  const int r = b->fused && n > 1 ? batch_iterate_fused(b, rc, stats) : batch_iterate_pool(b, rc, stats);
+  if (r != PARO_OK) return r;
   for (int i = 0; i < n; ++i)
     if (rc[i] != PARO_OK) return rc[i];
   return PARO_OK;
 }
 
+int paro_batch_set_fused(paro_batch b, int on) {
+  if (!b || (on != 0 && on != 1)) return PARO_ERR_ARG;
+  b->fused = on;
+  return PARO_OK;
+}
+
+long long paro_batch_fused_launches(paro_batch b) { return b ? b->fused_launches : (long long)PARO_ERR_ARG; }
+
+const char* paro_batch_last_error(paro_batch b) { return b ? b->err.c_str() : "null batch"; }
+
 int paro_batch_destroy(paro_batch b) {
   if (!b) return PARO_ERR_ARG;
+  paro::batch_cg_destroy(b->coord);
   delete b;
   return PARO_OK;
 }

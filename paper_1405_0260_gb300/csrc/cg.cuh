@@ -170,6 +170,101 @@ cudaError_t cg2_launch(CG2Plan* P, cudaStream_t st);
 cudaError_t cg2_autotune(CG2Plan* P, cudaStream_t st, int passes, int* chosen, float* best_us, int* tried);
 void balanced_split(long long F, int nzo, int grid, int* out);
 
+// Batched single-pass CG (cg2b.cu): the float32 correction solves of several
+// independent systems (meshes, orbital counts, potentials) in one cooperative
+// launch.  Work items are (system, orbital block, tile column, z-chunk); each
+// pass the CTAs take items from a counter in global memory (dynamic balance as
+// systems converge), and every system's vectors keep the group-major layout
+// of the single-system kernel.
+struct CG2BSys {
+  Grid g;
+  int Np, N;      // orbitals allocated (a multiple of 4) and solved
+  int ncx, ncy;   // tile columns of the batch geometry
+  int o0;         // first orbital of the system in the batch's numbering
+  int job0;       // first orbital block (job) of the system
+  float* x;
+  float *r[2], *q[2], *p[2];
+  CGDevState* st;
+};
+struct CG2BJob {
+  int sys, ob, ng;  // system, orbital block, groups of four orbitals in the block
+  int it0, nit;     // the block's work items [it0, it0 + nit)
+  int pad[3];
+};
+constexpr int kMaxBatchSys = 256;
+struct CG2BArgs {
+  const CG2BSys* sys;
+  const CG2BJob* jobs;
+  const int4* items;      // (job, tile x, tile y, z-chunk)
+  const CUtensorMap* maps;  // [system][8]: r0 q0 p0 r1 q1 p1 D^-1 weights
+  const int* osys;        // system of each batch orbital
+  int nsys, njobs, nitems, norb;
+  int zlen;               // planes of a z-chunk
+  int wpg;                // consumer warps per group slot (per-warp partial sums)
+  unsigned long long part_mask[kMaxBatchSys / 64];  // systems taking part in the launch
+  double* part;           // [item][warp of the group slot][5][block width]
+  double* obb;            // [norb] ||b||^2
+  int* oit;               // [norb] iterations
+  int* oact;              // [norb] still iterating
+  float *oal, *obe;       // [norb] alpha, beta of the next pass
+  unsigned* jmask;        // [2][njobs] active groups of each block, by pass parity
+  unsigned* bar;          // grid barrier counter (zeroed per launch)
+  unsigned long long* ictr;  // work-item counter (zeroed per launch)
+  unsigned spin;
+  int inner;              // 1: reaching maxit is not an error (refinement carries on)
+};
+// One system of a batch plan: its float32 CG buffers and operator (the
+// single-system plan's group-major vectors, D^-1 and packed weights).
+struct CG2BSysDesc {
+  Grid g;
+  int Np, N;
+  float* x;
+  float *r[2], *q[2], *p[2];
+  CGDevState* st;
+  const float* dinv_tma;
+  int dpitch;
+  const float* wcoef;
+};
+struct CG2BPlan {
+  CG2BArgs args{};
+  K1Geom geo{};
+  int nsm = 152;
+  bool ok = false;
+  std::vector<CG2BSysDesc> desc;
+  std::vector<CG2BSys> hsys;
+  // device buffers owned by the plan
+  CG2BSys* dsys = nullptr;
+  CG2BJob* djobs = nullptr;
+  int4* ditems = nullptr;
+  CUtensorMap* dmaps = nullptr;
+  int* dosys = nullptr;
+  double* dpart = nullptr;
+  size_t part_cap = 0;
+  size_t jobs_cap = 0, items_cap = 0;
+  double* dobb = nullptr;
+  int *doit = nullptr, *doact = nullptr;
+  float *doal = nullptr, *dobe = nullptr;
+  unsigned* djmask = nullptr;
+  unsigned* dbar = nullptr;  // [0]: barrier; then the item counter (8-byte aligned)
+};
+// A plan over the given systems (device buffers allocated here; every call
+// returns a CUDA status).  The geometry is the first candidate until
+// cg2b_autotune or cg2b_prepare_geo picks another.
+cudaError_t cg2b_create(CG2BPlan* P, const std::vector<CG2BSysDesc>& sys, int nsm);
+void cg2b_destroy(CG2BPlan* P);
+void cg2b_candidates(const CG2BPlan* P, std::vector<K1Geom>* out);
+// Host only: the orbital blocks (jobs) and work items of a geometry (G.TX, G.TY,
+// G.G4, G.grid), and the z-chunk length.
+void cg2b_tables(const std::vector<CG2BSysDesc>& desc, const K1Geom& G, std::vector<CG2BJob>* jobs,
+                 std::vector<int4>* items, int* zlen);
+cudaError_t cg2b_prepare_geo(CG2BPlan* P, const K1Geom& geo);
+// One batched solve of the systems whose bit is set in mask (their CG state:
+// tol, maxit, skip, and r[0] = b, as for the single-system kernel).
+cudaError_t cg2b_launch(CG2BPlan* P, const unsigned long long* mask, unsigned spin, cudaStream_t st);
+// Times `passes` passes of every candidate over all systems (b = 1, tol = 0;
+// overwrites their vectors and CG state) and prepares the fastest.
+cudaError_t cg2b_autotune(CG2BPlan* P, cudaStream_t st, int passes, int* chosen, float* best_us, int* tried);
+
 // Packed operator weights per input plane, [Pz][ny-1][nx-1][kPackedW], for the tiled kernel.
 constexpr int kPackedW = 28;
 __host__ __device__ inline size_t packed_weights_count(const Grid& g) { return (size_t)kPackedW * g.Pz * (g.ny - 1) * (g.nx - 1); }

@@ -267,6 +267,25 @@ def test_rayleigh_ritz_matches_oracle(B, N):
     m.close()
 
 
+def test_rayleigh_ritz_of_ill_conditioned_guesses_on_a_mixed_handle(B):
+    """48 raw Gaussian guesses on a 12^3 mesh (overlap condition ~7e7): the fast
+    Rayleigh-Ritz of a mixed handle (tensor-core Grams from 24-bit inputs,
+    float-float eigensolve) cannot resolve them, so the step falls back to float64
+    Grams and eigensolve; the Ritz values match the oracle's float64 step."""
+    p = W.harmonic(nc=12, L=5.0, N=48, seed=7100, sigma=0.0)
+    ops = oracle_ops(p)
+    ref = O.rayleigh_ritz(ops, p.U0)
+    m = make_mesh(B, p, B.PARO_MIXED)
+    X = dev(p.U0)
+    U = torch.empty_like(X)
+    lam, st = m.rayleigh_ritz(X, U)
+    # float64 arithmetic on an overlap of condition ~7e7: agreement to ~1e-16 x cond
+    assert np.max(np.abs(lam - ref.lam) / np.abs(ref.lam)) < 1e-7, np.max(np.abs(lam - ref.lam) / np.abs(ref.lam))
+    u = host(U)
+    assert np.max(np.abs(u.T @ (ops.M @ u) - np.eye(48))) < 1e-7
+    m.close()
+
+
 @pytest.mark.parametrize("N", [3, 20, 33, 64, 90, 128, 200])
 def test_rayleigh_ritz_tensor_core_grams_match_oracle(B, N):
     # mixed handles form both Gram matrices on the tensor cores (tcgen05, exact
