@@ -73,6 +73,11 @@ struct paro_mesh_s {
   // queued copy (the per-orbital right-hand-side scales) when a solve starts
   double* h_ctl = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
+  // phase timings of the statistics: event pairs recorded on the stream and read
+  // once at the end of the call (no synchronisation per phase)
+  std::vector<cudaEvent_t> tev;
+  int tev_used = 0;
+  std::vector<std::pair<double*, int>> tev_pending;
   std::vector<void*> allocs;
   // launch accounting and optional per-launch timing of the CG operator kernel
   long long launches = 0;
@@ -100,6 +105,9 @@ struct paro_mesh_s {
   int f32_layout = 0;
   // fxh/fxl hold the float-float split of x (set where x = u was just split)
   bool x_split_fresh = false;
+  // x holds the start of a mixed solve only logically: x = u, not yet copied (the
+  // first refinement update reads u and writes x)
+  bool x_pending_u = false;
   // fxh/fxl = split(x) when a single-pass refinement has just ended (the
   // Rayleigh-Ritz step that follows in the ParO loop reuses it)
   bool x_split_valid = false;
@@ -902,7 +910,21 @@ int batch_cg_solve(paro_mesh m, unsigned spin) {
 // once), x += d with the float-float split of the new x; two sweeps, then a
 // residual whose active count the host reads, and one sweep more at a time
 // while orbitals remain open.  fxh/fxl hold the split of x on entry.
+// x = u when no refinement update wrote x (no sweep ran, or an early return):
+// every return of the single-pass refinement leaves x materialised.
+struct MaterialiseX {
+  paro_mesh m;
+  ~MaterialiseX() {
+    if (!m->x_pending_u) return;
+    if (cudaMemcpyAsync(m->x, m->u, sizeof(double) * m->g.G * m->Np_alloc, cudaMemcpyDeviceToDevice, m->st) !=
+        cudaSuccess)
+      (void)cudaGetLastError();
+    m->x_pending_u = false;
+  }
+};
+
 int refine_solve_cg2(paro_mesh m, int N, const paro_params& p, paro_stats* st, double itol) {
+  MaterialiseX mx{m};
   const int Np = m->Np_alloc;
   Grid& g = m->g;
   CG2Plan* P = m->plan2;
@@ -944,7 +966,9 @@ int refine_solve_cg2(paro_mesh m, int N, const paro_params& p, paro_stats* st, d
         int mx = 0;
         TRY(read_iters(m, N, &s0, &mx));
       }
-      LAUNCH(1, launch_refine_update_split(g, Np, m->x, m->x32, m->cgst->skip, m->fxh, m->fxl, m->st));
+      LAUNCH(1, launch_refine_update_split(g, Np, m->x_pending_u ? m->u : m->x, m->x, m->x32, m->cgst->skip, m->fxh,
+                                           m->fxl, m->st));
+      m->x_pending_u = false;
       ++sweep;
     }
     LAUNCH(1, launch_refine_residual_ff(g, N, Np, m->wAh, m->wAl, m->fxh, m->fxl, m->fah, m->fal, nullptr, rs,
@@ -998,6 +1022,10 @@ int refine_solve(paro_mesh m, int N, const paro_params& p, paro_stats* st) {
   const double itol = p.inner_tol > 0.0 ? p.inner_tol : std::fmin(1e-3, std::fmax(1e-6, std::sqrt(p.solve_tol)));
   if (p.precond == PARO_PRECOND_JACOBI && m->plan2 && m->plan2->ok && m->profile != 2)
     return refine_solve_cg2(m, N, p, st, itol);
+  if (m->x_pending_u) {
+    CK(cudaMemcpyAsync(m->x, m->u, sizeof(double) * m->g.G * m->Np_alloc, cudaMemcpyDeviceToDevice, m->st));
+    m->x_pending_u = false;
+  }
   m->x_split_fresh = false;
   TRY(set_f32_layout(m, 0));
   const int Np = m->Np_alloc;
@@ -1069,7 +1097,11 @@ int solve_packed(paro_mesh m, int N, const double* lam, const paro_params& p, pa
   } else {
     LAUNCH(1, apply_M_f64(m, Np, m->u, m->b, scale));
   }
-  CK(cudaMemcpyAsync(m->x, m->u, sizeof(double) * g.G * Np, cudaMemcpyDeviceToDevice, m->st));
+  if (m->precision == PARO_MIXED) {
+    m->x_pending_u = true;  // x = u: the refinement materialises it
+  } else {
+    CK(cudaMemcpyAsync(m->x, m->u, sizeof(double) * g.G * Np, cudaMemcpyDeviceToDevice, m->st));
+  }
   m->x_split_fresh = m->precision == PARO_MIXED;  // fxh/fxl = split(u) = split(x)
   long long its = 0;
   int itmax = 0;
@@ -1199,7 +1231,10 @@ int rr_packed(paro_mesh m, int N, const double* src, double* dst, double* lam, R
       std::vector<double> hG((size_t)Np * Np);
       CK(cudaMemcpyAsync(hG.data(), m->GB, sizeof(double) * Np * Np, cudaMemcpyDeviceToHost, m->st));
       CK(cudaStreamSynchronize(m->st));
-      if (!overlap_well_conditioned(hG, N, Np)) return rr_packed(m, N, src, dst, lam, kRRFP64, clus, false);
+      if (!overlap_well_conditioned(hG, N, Np)) {
+        if (trace_on()) std::fprintf(stderr, "paro rayleigh_ritz: ill-conditioned overlap, float64 step\n");
+        return rr_packed(m, N, src, dst, lam, kRRFP64, clus, false);
+      }
     }
     ++m->rr_tc;
   } else if (ff) {
@@ -1217,17 +1252,25 @@ int rr_packed(paro_mesh m, int N, const double* src, double* dst, double* lam, R
     LAUNCH(2, launch_gram2(g, N, Np, src, m->r, m->q, m->gpart, nullptr, m->GA, m->GB, m->st));
   }
   // mixed handles inside the loop: the eigensolve in float-float on the float32
-  // pipes; the start on user guesses (ill-conditioned overlaps) stays float64
+  // pipes; the start on user guesses (ill-conditioned overlaps) and the public
+  // call on arbitrary X (guard) stay float64: the float-float Jacobi reaches its
+  // sweep limit on an X that already diagonalises the pencil with degenerate
+  // Ritz values (the converged orbitals of a shell)
   LAUNCH(1, launch_small_eig(N, m->GA, m->GB, m->eigwork, m->C, m->theta, &m->cgst->status, m->st,
-                             &m->cgst->bar_count, clus, mixed && mode != kRRFP64));
-  {
-    // an input the fast arithmetic cannot resolve (the overlap of raw guesses can
-    // be ill-conditioned far beyond the Grams' 24-bit inputs): the eigensolve
-    // reports an indefinite overlap or its sweep limit, and the step is redone
-    // in float64 (Grams, eigensolve and rotation) from the same X
+                             &m->cgst->bar_count, clus, mixed && mode != kRRFP64 && !guard));
+  // An input the fast arithmetic cannot resolve (the overlap of raw guesses can
+  // be ill-conditioned far beyond the Grams' 24-bit inputs) makes the fast
+  // eigensolve report an indefinite overlap or its sweep limit; the step is then
+  // redone in float64 (Grams, eigensolve and rotation) from the same X, which the
+  // fast step leaves untouched.  Inside the ParO loop the status is read with the
+  // Ritz values after the rotation (one round trip a step); elsewhere before it.
+  const bool fast = mixed && mode != kRRFP64;
+  if (!fast || guard) {
     const int rc = check_status(m, "rayleigh_ritz");
-    if ((rc == PARO_ERR_NOT_CONVERGED || rc == PARO_ERR_NOT_SPD) && mixed && mode != kRRFP64)
+    if ((rc == PARO_ERR_NOT_CONVERGED || rc == PARO_ERR_NOT_SPD) && fast) {
+      if (trace_on()) std::fprintf(stderr, "paro rayleigh_ritz: fast eigensolve %s, float64 step\n", m->err.c_str());
       return rr_packed(m, N, src, dst, lam, kRRFP64, clus, false);
+    }
     TRY(rc);
   }
   // the rotation: on the tensor cores from the hi parts of X with the tensor-core
@@ -1243,7 +1286,14 @@ int rr_packed(paro_mesh m, int N, const double* src, double* dst, double* lam, R
   CK(cudaMemcpyAsync(m->h_dbl, m->theta, sizeof(double) * N, cudaMemcpyDeviceToHost, m->st));
   CK(cudaMemcpyAsync(m->h_int, &m->cgst->status, sizeof(int), cudaMemcpyDeviceToHost, m->st));
   CK(cudaStreamSynchronize(m->st));
-  if (m->h_int[0] != 0) TRY(check_status(m, "rayleigh_ritz (rotation)"));
+  if (m->h_int[0] != 0) {
+    const int rc = check_status(m, "rayleigh_ritz");
+    if ((rc == PARO_ERR_NOT_CONVERGED || rc == PARO_ERR_NOT_SPD) && fast && !guard) {
+      if (trace_on()) std::fprintf(stderr, "paro rayleigh_ritz: fast eigensolve %s, float64 step\n", m->err.c_str());
+      return rr_packed(m, N, src, dst, lam, kRRFP64, clus, false);
+    }
+    TRY(rc);
+  }
   for (int i = 0; i < N; ++i) lam[i] = m->h_dbl[i];
   return PARO_OK;
 }
@@ -1255,19 +1305,48 @@ int check_common(paro_mesh m, int N) {
   return PARO_OK;
 }
 
+constexpr int kTimerPairs = 64;
+
+// Adds the elapsed time of every stopped phase to its statistic (waits for the
+// last of them) and frees the event pairs.
+void timers_resolve(paro_mesh m) {
+  for (const auto& pk : m->tev_pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(m->tev[2 * pk.second + 1]) == cudaSuccess &&
+        cudaEventElapsedTime(&ms, m->tev[2 * pk.second], m->tev[2 * pk.second + 1]) == cudaSuccess)
+      *pk.first += ms;
+  }
+  (void)cudaGetLastError();
+  m->tev_pending.clear();
+  m->tev_used = 0;
+}
+
+// One timed phase of a call (statistics only): events around it on the stream,
+// read when the call ends (CallScope) or when the pool of pairs is used up.
 struct Timer {
   paro_mesh m;
   double* acc;
+  int k = -1;
   Timer(paro_mesh mm, double* a) : m(mm), acc(a) {
-    if (acc) cudaEventRecord(m->e0, m->st);
+    if (!acc) return;
+    if (m->tev_used >= kTimerPairs) timers_resolve(m);
+    k = m->tev_used;
+    while ((int)m->tev.size() < 2 * (k + 1)) {
+      cudaEvent_t e = nullptr;
+      if (cudaEventCreate(&e) != cudaSuccess) {
+        (void)cudaGetLastError();
+        acc = nullptr;
+        return;
+      }
+      m->tev.push_back(e);
+    }
+    ++m->tev_used;
+    cudaEventRecord(m->tev[2 * k], m->st);
   }
   void stop() {
     if (!acc) return;
-    cudaEventRecord(m->e1, m->st);
-    cudaEventSynchronize(m->e1);
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, m->e0, m->e1);
-    *acc += ms;
+    cudaEventRecord(m->tev[2 * k + 1], m->st);
+    m->tev_pending.push_back({acc, k});
     acc = nullptr;
   }
   ~Timer() { stop(); }
@@ -1300,6 +1379,7 @@ struct CallScope {
     m->profile = profile == 2 ? 2 : 1;
   }
   ~CallScope() {
+    timers_resolve(m);
     if (s) {
       s->kernel_launches += m->launches - l0;
       s->rr_tc_steps += (int)(m->rr_tc - tc0);
@@ -1774,6 +1854,8 @@ int paro_mesh_destroy(paro_mesh m) {
   if (m->e0) cudaEventDestroy(m->e0);
   if (m->e1) cudaEventDestroy(m->e1);
   for (auto e : m->pev)
+    if (e) cudaEventDestroy(e);
+  for (auto e : m->tev)
     if (e) cudaEventDestroy(e);
   delete m;
   return PARO_OK;

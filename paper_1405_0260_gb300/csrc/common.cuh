@@ -149,9 +149,10 @@ cudaError_t launch_refine_update(const Grid& g, int Np, double* x64, const float
 cudaError_t launch_refine_residual_ff(const Grid& g, int N, int Np, const float* whi, const float* wlo,
                                       const float* xhi, const float* xlo, const float* bhi, const float* blo,
                                       float* rhs32, const CGState& s, double tol, cudaStream_t st, int gm = 0);
-// x64 += d (group-major, orbitals not skipped) and the float-float split of the new x
-cudaError_t launch_refine_update_split(const Grid& g, int Np, double* x64, const float* d32gm, const int* skip,
-                                       float* xh, float* xl, cudaStream_t st);
+// x64 = x_in + d (group-major d, orbitals not skipped; x_in for the skipped ones)
+// and the float-float split of the new x; x_in may be x64 (in place)
+cudaError_t launch_refine_update_split(const Grid& g, int Np, const double* x_in, double* x64, const float* d32gm,
+                                       const int* skip, float* xh, float* xl, cudaStream_t st);
 
 // ff.cu: float64-accurate applies, Grams and rotation in float-float arithmetic
 cudaError_t launch_split_ff(long long n, const double* x, float* hi, float* lo, cudaStream_t st);

@@ -219,19 +219,24 @@ __global__ void __launch_bounds__(kRedThreads, 4) k_refine_residual_ff(Grid g, i
 // float-float split of the new x for the next residual; skipped orbitals keep x
 // (and, the split being a function of x, the same split).  Vector loads and
 // stores of a thread's four orbitals; one float64 addition an element.
-__global__ void k_refine_update_split(Grid g, int Np, double* __restrict__ x, const float* __restrict__ d,
+// x = x_in + d for the orbitals not skipped, x = x_in for the others, and the
+// float-float split of the new x.  x_in == x: in place (groups whose four
+// orbitals are all skipped are left alone); x_in != x (the first sweep, x_in
+// the orbitals u the solve starts from): every group is written.
+__global__ void k_refine_update_split(Grid g, int Np, const double* x_in, double* x, const float* __restrict__ d,
                                       const int* __restrict__ skip, float* __restrict__ xh, float* __restrict__ xl) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int groups = Np / 4;
   if (t >= (long long)g.nI * groups) return;
   const int n = (int)(t / groups), grp = (int)(t % groups);
   const int4 sk = *reinterpret_cast<const int4*>(skip + 4 * grp);
-  if (sk.x && sk.y && sk.z && sk.w) return;
+  if (x_in == x && sk.x && sk.y && sk.z && sk.w) return;
   const long long gp = interior_to_padded(g, n);
   const float4 dv = *reinterpret_cast<const float4*>(d + ((long long)grp * g.G + gp) * 4);
   const long long e = gp * Np + 4 * grp;
+  const double2* xq = reinterpret_cast<const double2*>(x_in + e);
   double2* xp = reinterpret_cast<double2*>(x + e);
-  const double2 a = xp[0], b = xp[1];
+  const double2 a = xq[0], b = xq[1];
   const double v0 = sk.x ? a.x : a.x + f2d_exact(dv.x);
   const double v1 = sk.y ? a.y : a.y + f2d_exact(dv.y);
   const double v2 = sk.z ? b.x : b.x + f2d_exact(dv.z);
@@ -284,10 +289,10 @@ cudaError_t launch_refine_update(const Grid& g, int Np, double* x64, const float
   return cudaGetLastError();
 }
 
-cudaError_t launch_refine_update_split(const Grid& g, int Np, double* x64, const float* d32gm, const int* skip,
-                                       float* xh, float* xl, cudaStream_t st) {
+cudaError_t launch_refine_update_split(const Grid& g, int Np, const double* x_in, double* x64, const float* d32gm,
+                                       const int* skip, float* xh, float* xl, cudaStream_t st) {
   const long long work = (long long)g.nI * (Np / 4);
-  k_refine_update_split<<<(unsigned)((work + 255) / 256), 256, 0, st>>>(g, Np, x64, d32gm, skip, xh, xl);
+  k_refine_update_split<<<(unsigned)((work + 255) / 256), 256, 0, st>>>(g, Np, x_in, x64, d32gm, skip, xh, xl);
   return cudaGetLastError();
 }
 
