@@ -1221,10 +1221,19 @@ int rr_packed(paro_mesh m, int N, const double* src, double* dst, double* lam, R
                               m->st));
     LAUNCH(1, apply_M_ff(m, Np, m->fxh, m->fxl, nullptr, nullptr, m->fbh, m->fbl));
     int nch = 0;
-    LAUNCH(1, launch_gram_tc(g, Np, m->fxh, m->fah, m->gpart_tc, &nch, &m->cgst->status, m->st));
-    LAUNCH(1, launch_gram_reduce1(Np, nch, m->gpart_tc, m->GA, m->st));
-    LAUNCH(1, launch_gram_tc(g, Np, m->fxh, m->fbh, m->gpart_tc, &nch, &m->cgst->status, m->st));
-    LAUNCH(1, launch_gram_reduce1(Np, nch, m->gpart_tc, m->GB, m->st));
+    if (Np <= 32) {
+      // both Grams in one launch (X loaded and converted once)
+      double* partB = m->gpart_tc + gram_tc_partial_doubles(g, Np) / 2;
+      LAUNCH(1, launch_gram_tc_pair(g, Np, m->fxh, m->fah, m->fbh, m->gpart_tc, partB, &nch, &m->cgst->status,
+                                    m->st));
+      LAUNCH(1, launch_gram_reduce1(Np, nch, m->gpart_tc, m->GA, m->st));
+      LAUNCH(1, launch_gram_reduce1(Np, nch, partB, m->GB, m->st));
+    } else {
+      LAUNCH(1, launch_gram_tc(g, Np, m->fxh, m->fah, m->gpart_tc, &nch, &m->cgst->status, m->st));
+      LAUNCH(1, launch_gram_reduce1(Np, nch, m->gpart_tc, m->GA, m->st));
+      LAUNCH(1, launch_gram_tc(g, Np, m->fxh, m->fbh, m->gpart_tc, &nch, &m->cgst->status, m->st));
+      LAUNCH(1, launch_gram_reduce1(Np, nch, m->gpart_tc, m->GB, m->st));
+    }
     if (guard) {
       // arbitrary X (the public call): an overlap too ill-conditioned for these
       // Grams takes the float64 step instead

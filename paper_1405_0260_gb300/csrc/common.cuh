@@ -174,6 +174,9 @@ constexpr int kTcMaxNp = 256;
 size_t gram_tc_partial_doubles(const Grid& g, int Np);
 cudaError_t launch_gram_tc(const Grid& g, int Np, const float* xh, const float* yh, double* part, int* n_chunks,
                            int* status, cudaStream_t st);
+// both Grams X^T A and X^T B in one launch (Np <= 32), partials into partA and partB
+cudaError_t launch_gram_tc_pair(const Grid& g, int Np, const float* xh, const float* ah, const float* bh,
+                                double* partA, double* partB, int* n_chunks, int* status, cudaStream_t st);
 // gram_tc.cu: the rotation U = X C on the tensor cores (Np <= 128, X as float32 hi parts)
 cudaError_t launch_rotate_tc(const Grid& g, int N, int Np, const float* xh, const double* C, double* U, int* status,
                              cudaStream_t st);

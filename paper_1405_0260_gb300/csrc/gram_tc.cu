@@ -156,10 +156,13 @@ __host__ __device__ constexpr int tc_smem_bytes() {
 // columns b = yc0 .. yc0 + nb - 1 (nb <= NCOL = 32 or 64, the MMA's N side) of
 // G = X^T Y, X and Y [node][Np].  For the read-out warp w takes TMEM lanes
 // 32 (w % 4) .. and the column group w / 4 (of 4).
+// Two Grams in one launch (yh2 != null): columns b < nb1 from yh (G = X^T Y into
+// part), b >= nb1 from yh2 (X^T Y2 into part2): X is loaded and converted once.
 template <int NCOL>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_gram_tc(long long G, int Np, int xr0, int na, int yc0, int nb, const float* __restrict__ xh,
-              const float* __restrict__ yh, double* __restrict__ part, long long chunk, int* __restrict__ status) {
+              const float* __restrict__ yh, double* __restrict__ part, long long chunk, int* __restrict__ status,
+              const float* __restrict__ yh2, int nb1, double* __restrict__ part2) {
   constexpr int kCols = NCOL / 4;  // columns a thread reads out
   constexpr uint32_t kTmemCols = kTcDigits * NCOL <= 128 ? 128 : 256;
   constexpr int kAPiece = (kTcM / 8) * kTcSBO;  // bytes of one A digit plane (128 rows x 64 nodes)
@@ -217,7 +220,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const int w = tid + it * kTcThreads;
       int arr, oct, o;
       item(w, arr, oct, o);
-      const float* src = arr ? yh + yc0 + o : xh + xr0 + o;
+      const float* src = !arr ? xh + xr0 + o : (o < nb1 ? yh + yc0 + o : yh2 + (o - nb1));
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const long long node = n1 + 8 * oct + j;
@@ -364,19 +367,24 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   // the block's partial, G[xr0 + a][yc0 + b], written row-major with coalesced columns
   const long long NN = (long long)Np * Np;
   double* dst = part + (long long)blockIdx.x * NN;
+  double* dst2 = part2 ? part2 + (long long)blockIdx.x * NN : nullptr;
   for (int t = tid; t < na * nb; t += kTcThreads) {
     const int a = t / nb, b = t % nb;
-    dst[(long long)(xr0 + a) * Np + yc0 + b] = ff_to_double(ff_norm(accs[b * kTcM + a]));
+    const double v = ff_to_double(ff_norm(accs[b * kTcM + a]));
+    if (b < nb1) dst[(long long)(xr0 + a) * Np + yc0 + b] = v;
+    else dst2[(long long)(xr0 + a) * Np + (b - nb1)] = v;
   }
 }
 
 template <int NCOL>
 cudaError_t launch_tc(long long G, int Np, int xr0, int na, int yc0, int nb, const float* xh, const float* yh,
-                      double* part, long long chunk, int nch, int* status, cudaStream_t st) {
+                      double* part, long long chunk, int nch, int* status, cudaStream_t st,
+                      const float* yh2 = nullptr, int nb1 = 1 << 30, double* part2 = nullptr) {
   const size_t smem = (size_t)tc_smem_bytes<NCOL>();
   cudaError_t e = allow_max_dyn_smem((const void*)k_gram_tc<NCOL>);
   if (e != cudaSuccess) return e;
-  k_gram_tc<NCOL><<<nch, kTcThreads, smem, st>>>(G, Np, xr0, na, yc0, nb, xh, yh, part, chunk, status);
+  k_gram_tc<NCOL><<<nch, kTcThreads, smem, st>>>(G, Np, xr0, na, yc0, nb, xh, yh, part, chunk, status, yh2, nb1,
+                                                   part2);
   return cudaGetLastError();
 }
 
@@ -617,7 +625,20 @@ size_t gram_tc_partial_doubles(const Grid& g, int Np) {
   long long chunk;
   int nch;
   gram_tc_shape(g, &chunk, &nch);
-  return (size_t)nch * Np * Np;
+  return (size_t)nch * Np * Np * (Np <= 32 ? 2 : 1);  // Np <= 32: both Grams' partials
+}
+
+// Both Grams of the Rayleigh-Ritz step, G_A = X^T (HX) into partA and G_B =
+// X^T (MX) into partB (per-CTA partials [nch][Np][Np] each), in one launch of
+// the 64-column kernel with the columns of HX then MX (Np <= 32).
+cudaError_t launch_gram_tc_pair(const Grid& g, int Np, const float* xh, const float* ah, const float* bh,
+                                double* partA, double* partB, int* n_chunks, int* status, cudaStream_t st) {
+  long long chunk;
+  int nch;
+  gram_tc_shape(g, &chunk, &nch);
+  *n_chunks = nch;
+  if (Np < 4 || Np % 4 != 0 || Np > 32) return cudaErrorInvalidValue;
+  return launch_tc<64>(g.G, Np, 0, Np, 0, 2 * Np, xh, ah, partA, chunk, nch, status, st, bh, Np, partB);
 }
 
 // One Gram G = X^T Y into per-CTA partials part[nch][Np][Np] (Np <= kTcMaxNp, a
