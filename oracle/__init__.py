@@ -17,6 +17,10 @@ orbital-updating approach for electronic structure calculations":
   * Step 5: the loop, stopped on max |Delta lambda|.
 Module ``oracle.ks`` adds the Kohn-Sham pieces of Section 2.2 (density,
 Hartree by a Poisson solve, Slater exchange) for the SCF workload.
+Module ``oracle.adapt`` holds the adaptive loop of Section 2.1 on tensor-product
+meshes: residual error indicators per cell (Estimate), Doerfler and maximum
+marking, eqs. (2.2)-(2.3) (Mark), bisection of the marked cells' axis intervals
+(Refine) and the nested transfer of the orbitals.
 
 Parity status per function is listed in each module header.
 """
