@@ -774,6 +774,87 @@ def collections_count(values):
     return out
 
 
+def run_adapt(args):
+    """The adaptive loop of Section 2.1 (not the headline line): a hydrogen-like
+    nucleus off the nodes of a coarse uniform mesh; each step solves with
+    paro_iterate (mixed precision, source problems to 1e-10, |delta lambda| <
+    1e-9), estimates (paro_estimate), marks with Doerfler's strategy (theta
+    0.5), refines the marked cells' axis intervals and moves the orbitals to the
+    new mesh (paro_transfer).  Beside it, uniform meshes with about the same
+    unknowns: the ground level a graded mesh reaches for its unknowns."""
+    import math
+
+    import torch
+
+    from paper_1405_0260_gb300 import binding as B
+    from paper_1405_0260_gb300 import workloads as W
+
+    L, nc0, N, R = 10.0, args.adapt_nc, 5, (0.31, -0.23, 0.17)
+    params = B.paro_default_params(tol=1e-9, max_outer=400, solve_tol=1e-10)
+
+    def coulomb(n, coords):
+        x, y, z = W.gauss_point_coords(n, None, None, coords)
+        return np.ascontiguousarray((-1.0 / np.sqrt((x - R[0]) ** 2 + (y - R[1]) ** 2 + (z - R[2]) ** 2)).ravel())
+
+    def handle(coords):
+        n = tuple(len(c) - 1 for c in coords)
+        m = B.Mesh(n, None, None, B.PARO_MIXED, coords=coords)
+        Vd = torch.from_numpy(coulomb(n, coords)).cuda()
+        m.set_potential(Vd, 2.0)
+        return m, Vd
+
+    def solve(m, U0):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, lam, st = m.iterate(U0, None, params, allow=(-4,))
+        torch.cuda.synchronize()
+        return rc, lam, st, time.perf_counter() - t0
+
+    ax = np.linspace(-L, L, nc0 + 1)
+    coords = (ax, ax, ax)
+    p = W.hydrogen(nc=nc0, L=L, N=N, seed=8700, sigma=2.0)
+    U = torch.from_numpy(np.ascontiguousarray(p.U0)).cuda()
+    steps, prev = [], None
+    for k in range(args.adapt_steps):
+        n = tuple(len(c) - 1 for c in coords)
+        m, Vd = handle(coords)
+        if prev is not None:
+            Un = torch.empty(((n[0] - 1) * (n[1] - 1) * (n[2] - 1), N), dtype=torch.float64, device="cuda")
+            prev.transfer_to(m, U, Un)
+            prev.close()
+            U = Un
+        rc, lam, st, t_solve = solve(m, U)
+        eta2 = torch.empty(n[0] * n[1] * n[2], dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m.estimate(U, lam, Vd, eta2)
+        torch.cuda.synchronize()
+        t_est = time.perf_counter() - t0
+        e = eta2.cpu().numpy().reshape(n[2], n[1], n[0])
+        marked = B.mark(e, B.PARO_MARK_DORFLER, 0.5)
+        steps.append({"cells": list(n), "unknowns": int((n[0] - 1) * (n[1] - 1) * (n[2] - 1)), "rc": int(rc),
+                      "lambda": [float(v) for v in lam], "outer_iters": int(st.outer_iters),
+                      "solve_s": t_solve, "estimate_s": t_est, "eta": float(np.sqrt(e.sum())),
+                      "marked": int(marked.sum())})
+        coords = B.refine_coords(n, coords, marked)
+        prev = m
+    prev.close()
+    uniform = []
+    for nc in sorted({int(round(math.pow(s["unknowns"], 1.0 / 3.0))) + 1 for s in steps[-2:]}):
+        ax = np.linspace(-L, L, nc + 1)
+        q = W.hydrogen(nc=nc, L=L, N=N, seed=8700, sigma=2.0)
+        m, _ = handle((ax, ax, ax))
+        rc, lam, st, t = solve(m, torch.from_numpy(np.ascontiguousarray(q.U0)).cuda())
+        uniform.append({"cells": nc, "unknowns": (nc - 1) ** 3, "rc": int(rc), "lambda": [float(v) for v in lam],
+                        "solve_s": t})
+        m.close()
+    print(json.dumps({"metric": "adaptive loop (Solve -> Estimate -> Mark -> Refine) on tensor-product meshes",
+                      "workload": f"hydrogen-like Z=1 at {list(R)}, [-{L},{L}]^3, {nc0}^3 start, N={N}, sigma=2, "
+                                  "mixed precision, Doerfler theta=0.5",
+                      "steps": steps, "uniform": uniform,
+                      "data": "synthetic (seeded Gaussian initial orbitals, analytic potential)"}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -783,11 +864,12 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true", help="omit the cpu_baseline leg")
     ap.add_argument("--skip-converge", action="store_true", help="omit the time-to-converge leg")
     ap.add_argument("--workload", default="harmonic64",
-                    choices=["harmonic64", "batch", "large", "ks", "clusters", "peaks"],
+                    choices=["harmonic64", "batch", "large", "ks", "clusters", "peaks", "adapt"],
                     help="batch: independent systems (meshes 32-96^3, N 4-48) through paro_batch_iterate; "
                          "large: 192^3 cells, N = 256; ks: the Kohn-Sham cluster SCF; "
                          "clusters: cluster-separated Rayleigh-Ritz at N = 256; "
-                         "peaks: the SIMT float32 and float64 FMA rates")
+                         "peaks: the SIMT float32 and float64 FMA rates; "
+                         "adapt: the adaptive loop on a hydrogen-like problem")
     ap.add_argument("--ks-nc", type=int, default=128, help="ks workload: cells per axis")
     ap.add_argument("--ks-max-outer", type=int, default=1500, help="ks workload: SCF iteration limit")
     ap.add_argument("--ks-mix", type=float, default=0.3, help="ks workload: linear density mixing")
@@ -799,14 +881,16 @@ def main():
     ap.add_argument("--large-nc", type=int, default=192, help="large workload: cells per axis")
     ap.add_argument("--systems", type=int, default=64, help="batch workload: number of systems")
     ap.add_argument("--workers", type=int, default=8, help="batch workload: host worker threads")
+    ap.add_argument("--adapt-nc", type=int, default=16, help="adapt workload: cells per axis of the first mesh")
+    ap.add_argument("--adapt-steps", type=int, default=5, help="adapt workload: adaptive steps")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     ws, rank, local = dist_env()
-    if args.workload in ("batch", "large", "ks", "clusters", "peaks"):
+    if args.workload in ("batch", "large", "ks", "clusters", "peaks", "adapt"):
         if rank == 0 and args.impl == "ours":
             {"batch": run_batch, "large": run_large, "ks": run_ks, "clusters": run_clusters,
-             "peaks": run_peaks}[args.workload](args)
+             "peaks": run_peaks, "adapt": run_adapt}[args.workload](args)
         return
     if args.impl == "reference":
         run_reference(args, ws, rank)

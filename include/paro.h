@@ -323,6 +323,58 @@ const char* paro_last_error(paro_mesh m);
 /* Interior node count (nx-1)(ny-1)(nz-1) of a handle (PARO_ERR_ARG on NULL). */
 long long paro_interior_nodes(paro_mesh m);
 
+/* The adaptive loop of Section 2.1 (Solve -> Estimate -> Mark -> Refine) on
+ * tensor-product meshes: solve on a handle (paro_iterate), estimate the error
+ * per cell, mark cells, refine the axis coordinates, create the handle of the
+ * refined mesh (paro_mesh_create_graded), move the orbitals to it
+ * (paro_transfer) and solve again. */
+#define PARO_MARK_DORFLER 0 /* eq. (2.2): least-cardinality set with sum eta^2 >= theta sum eta^2 */
+#define PARO_MARK_MAXIMUM 1 /* eq. (2.3): eta >= theta max eta */
+
+/* Estimate (Section 2.1: an a-posteriori indicator eta(., tau) per element; the
+ * paper gives no formula, this is the residual indicator of -1/2 Lap u + V u =
+ * lambda u for Q1 elements, summed over the N orbitals):
+ *   eta_tau^2 = sum_i [ h_tau^2 ||(lambda_i - V) u_i||^2_tau
+ *                       + 1/2 sum_{interior faces F of tau} h_F ||1/2 [d_n u_i]||^2_F ]
+ * (Lap u = 0 inside trilinear elements; V at the cell's 2x2x2 Gauss points; the
+ * normal-derivative jump is integrated exactly on each face; h_tau, h_F cell and
+ * face diameters; Dirichlet boundary faces carry no jump).  U: device
+ * (n_interior x N) float64 orbitals of this handle's mesh; lambda: host[N];
+ * Vq: device potential at the Gauss points (layout of paro_set_potential);
+ * eta2: device out, nx*ny*nz float64 in [cz][cy][cx] order.  Uses the handle's
+ * workspace (not thread-safe with other calls on the handle); synchronises its
+ * stream.  Errors: PARO_ERR_ARG (null pointer, N out of range), PARO_ERR_STATE
+ * (no potential set), PARO_ERR_CUDA. */
+int paro_estimate(paro_mesh m, int N, const double* U, const double* lambda, const double* Vq, double* eta2);
+
+/* Mark (Section 2.1, eqs. (2.2)-(2.3)), on the host: marked[c] = 1 for the chosen
+ * cells, 0 for the others.  PARO_MARK_DORFLER takes the largest indicators first
+ * (ties by cell index) until their sum reaches theta of the total;
+ * PARO_MARK_MAXIMUM marks eta >= theta max eta.  eta2: host[ncells] (>= 0,
+ * finite); theta in (0, 1).  Returns the number of marked cells, or
+ * PARO_ERR_ARG / PARO_ERR_NONFINITE. */
+int paro_mark(long long ncells, const double* eta2, int strategy, double theta, unsigned char* marked);
+
+/* Refine (Section 2.1: every marked element refined at least once), on the host:
+ * on a tensor-product mesh every axis interval that holds a marked cell is
+ * bisected (the cells sharing it are bisected too, so the mesh stays a tensor
+ * product).  n: cells per axis; coords: host, the nx+1 x, then ny+1 y, then
+ * nz+1 z node coordinates (strictly increasing); marked: host[nx*ny*nz] in
+ * [cz][cy][cx] order; n_out: the new cell counts; coords_out: host, room for
+ * (2nx+1) + (2ny+1) + (2nz+1) values, filled like coords.  PARO_ERR_ARG on null
+ * pointers, fewer than 2 cells an axis or coordinates not increasing. */
+int paro_refine_coords(const int n[3], const double* coords, const unsigned char* marked, int n_out[3],
+                       double* coords_out);
+
+/* Move N orbitals from one mesh to another covering the same box: the trilinear
+ * interpolant of U_from's nodal values (zero on the boundary) at the interior
+ * nodes of `to`.  Exact when `to` refines `from` (nested Q1 spaces).  U_from:
+ * device (n_interior(from) x N), read after from's stream has synchronised;
+ * U_to: device (n_interior(to) x N) out, must not alias U_from.  Runs on to's
+ * stream and synchronises it.  PARO_ERR_ARG for different boxes, N out of range
+ * or null / aliased pointers. */
+int paro_transfer(paro_mesh from, paro_mesh to, int N, const double* U_from, double* U_to);
+
 /* Batches of independent systems (meshes, orbital counts and potentials of
  * their own), Step 3 of Algorithm 3.1 solved for many systems at once.
  * paro_batch_iterate runs paro_iterate on every system.  Batched mode (the

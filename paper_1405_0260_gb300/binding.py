@@ -29,6 +29,7 @@ STATUS = {
 }
 PARO_FP64, PARO_MIXED = 0, 1
 PARO_OP_A, PARO_OP_H, PARO_OP_M = 0, 1, 2
+PARO_MARK_DORFLER, PARO_MARK_MAXIMUM = 0, 1
 PARO_F64, PARO_F32, PARO_FF = 0, 1, 2
 PARO_PRECOND_AUTO, PARO_PRECOND_JACOBI, PARO_PRECOND_MG = -1, 0, 1
 
@@ -112,6 +113,10 @@ def lib():
     L.paro_batch_size.argtypes = [vp]
     L.paro_batch_iterate.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(paro_stats)]
     L.paro_batch_destroy.argtypes = [vp]
+    L.paro_estimate.argtypes = [vp, ip, vp, dp, vp, vp]
+    L.paro_mark.argtypes = [C.c_longlong, dp, ip, C.c_double, C.POINTER(C.c_ubyte)]
+    L.paro_refine_coords.argtypes = [C.POINTER(C.c_int), dp, C.POINTER(C.c_ubyte), C.POINTER(C.c_int), dp]
+    L.paro_transfer.argtypes = [vp, vp, ip, vp, vp]
     L.paro_batch_set_fused.argtypes = [vp, ip]
     L.paro_batch_fused_launches.argtypes = [vp]
     L.paro_batch_fused_launches.restype = C.c_longlong
@@ -120,7 +125,8 @@ def lib():
     for f in ("paro_mesh_create", "paro_mesh_destroy", "paro_set_potential", "paro_orbital_solve",
               "paro_rayleigh_ritz", "paro_iterate", "paro_apply", "paro_mg_vcycle", "paro_density", "paro_ks_potential",
               "paro_scf_iterate", "paro_ks_density_in", "paro_ks_energy", "paro_batch_create", "paro_batch_add", "paro_batch_size",
-              "paro_batch_iterate", "paro_batch_destroy", "paro_batch_set_fused"):
+              "paro_batch_iterate", "paro_batch_destroy", "paro_batch_set_fused", "paro_estimate", "paro_mark",
+              "paro_refine_coords", "paro_transfer"):
         getattr(L, f).restype = C.c_int
     _lib = L
     return L
@@ -204,6 +210,33 @@ def paro_iterate(h, N, U_ptr, lam: np.ndarray, params=None, stats=None, allow=()
     return _check(rc, h, allow)
 
 
+def mark(eta2: np.ndarray, strategy=PARO_MARK_DORFLER, theta=0.5) -> np.ndarray:
+    """Marked cells (booleans, the shape of eta2) by paro_mark (host logic)."""
+    e = np.ascontiguousarray(eta2, dtype=np.float64)
+    out = np.zeros(e.size, dtype=np.uint8)
+    rc = lib().paro_mark(e.size, _dptr(e), int(strategy), float(theta), out.ctypes.data_as(C.POINTER(C.c_ubyte)))
+    if rc < 0:
+        raise ParoError(rc, "paro_mark")
+    return out.reshape(e.shape).astype(bool)
+
+
+def refine_coords(n, coords, marked):
+    """The node coordinates per axis after paro_refine_coords (host logic)."""
+    cat = np.ascontiguousarray(np.concatenate([np.asarray(c, dtype=np.float64) for c in coords]))
+    mk = np.ascontiguousarray(marked, dtype=np.uint8).ravel()
+    nn = (C.c_int * 3)(*[int(v) for v in n])
+    nout = (C.c_int * 3)()
+    out = np.zeros(sum(2 * int(v) + 1 for v in n))
+    rc = lib().paro_refine_coords(nn, _dptr(cat), mk.ctypes.data_as(C.POINTER(C.c_ubyte)), nout, _dptr(out))
+    if rc != PARO_OK:
+        raise ParoError(rc, "paro_refine_coords")
+    res, o = [], 0
+    for d in range(3):
+        res.append(out[o:o + nout[d] + 1].copy())
+        o += nout[d] + 1
+    return tuple(res)
+
+
 def paro_apply(h, N, op, dtype, X_ptr, Y_ptr):
     return _check(lib().paro_apply(h, int(N), int(op), int(dtype), C.c_void_p(X_ptr), C.c_void_p(Y_ptr)), h)
 
@@ -273,6 +306,16 @@ class Mesh:
         st = paro_stats()
         rc = paro_iterate(self.h, N, self._dev(U), lam, params, st, allow)
         return rc, lam, st
+
+    def estimate(self, U, lam, Vq, eta2):
+        """eta2 (device, nx*ny*nz float64) = the error indicators of orbitals U (paro_estimate)."""
+        lam = np.ascontiguousarray(lam, dtype=np.float64)
+        _check(lib().paro_estimate(self.h, U.shape[1], self._dev(U), _dptr(lam), self._dev(Vq), self._dev(eta2)),
+               self.h)
+
+    def transfer_to(self, other, U_from, U_to):
+        """U_to (orbitals on `other`'s mesh) = U_from interpolated (paro_transfer)."""
+        _check(lib().paro_transfer(self.h, other.h, U_from.shape[1], self._dev(U_from), self._dev(U_to)), other.h)
 
     def apply(self, op, X, Y, float_float=False):
         """Y = op X.  float32 tensors: float32 weights; float64 tensors: float64

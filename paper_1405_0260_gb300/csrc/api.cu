@@ -3,6 +3,7 @@
 // arithmetic step runs in the kernels of stencil.cu, pcg.cu and rr.cu; this file
 // only sequences launches on the handle's stream and reads back the per-orbital
 // convergence counters and the Ritz values.
+#include <algorithm>
 #include <cmath>
 #include <condition_variable>
 #include <cstdio>
@@ -116,6 +117,12 @@ struct paro_mesh_s {
   // Kohn-Sham: box origin, the float64 handle of the Poisson operator K/2 (V = 0,
   // sigma = 0) that solves for the Hartree potential, and Gauss-point fields
   double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+  // node coordinates per axis on the host (uniform or graded), for the transfer
+  // of orbitals between meshes; per-axis maps of a transfer on the device
+  std::vector<double> nodes[3];
+  int* xmap_k = nullptr;
+  double* xmap_t = nullptr;
+  int xmap_cap = 0;
   paro_mesh pois = nullptr;
   double* ks_mom = nullptr;   // [Q, x_c, y_c, z_c]
   double* ks_part = nullptr;  // block partials of the moments
@@ -1777,6 +1784,10 @@ static int mesh_create(paro_mesh* out, int nx, int ny, int nz, const double lo_i
   for (int d = 0; d < 3; ++d) {
     m->lo[d] = lo[d];
     m->hi[d] = hi[d];
+    const int nd = d == 0 ? nx : (d == 1 ? ny : nz);
+    m->nodes[d].resize(nd + 1);
+    for (int i = 0; i <= nd; ++i)
+      m->nodes[d][i] = ax[d] ? ax[d][i] : (i == nd ? hi[d] : lo[d] + (hi[d] - lo[d]) * i / nd);
   }
   mass_weights(g, &m->mw);
   m->dpitch = (g.Px + 3) / 4 * 4;
@@ -1999,6 +2010,68 @@ int paro_iterate(paro_mesh m, int N, double* U, double* lambda, const paro_param
   CK(cudaStreamSynchronize(m->st));
   if (rc != PARO_OK) m->err = "paro_iterate: max_outer reached before tol";
   return rc;
+}
+
+int paro_estimate(paro_mesh m, int N, const double* U, const double* lambda, const double* Vq, double* eta2) {
+  TRY(check_common(m, N));
+  if (!U || !lambda || !Vq || !eta2) return fail(m, PARO_ERR_ARG, "null pointer");
+  const int Np = (N + 3) / 4 * 4;
+  TRY(ensure_workspace(m, Np));
+  LAUNCH(1, launch_pack(m->g, N, Np, U, m->u, m->st));
+  double* lam_d = m->dscal + S_SCALE * kMaxN;
+  for (int i = 0; i < N; ++i) m->h_dbl[i] = lambda[i];
+  CK(cudaMemcpyAsync(lam_d, m->h_dbl, sizeof(double) * N, cudaMemcpyHostToDevice, m->st));
+  LAUNCH(1, launch_estimate(m->g, N, Np, m->u, lam_d, Vq, eta2, m->st));
+  CK(cudaStreamSynchronize(m->st));
+  return PARO_OK;
+}
+
+int paro_transfer(paro_mesh from, paro_mesh to, int N, const double* U_from, double* U_to) {
+  if (!from || !to) return PARO_ERR_ARG;
+  paro_mesh m = to;
+  if (N < 1 || N > kMaxN) return fail(m, PARO_ERR_ARG, "N out of range [1, 1024]");
+  if (!U_from || !U_to || (const void*)U_from == (const void*)U_to) return fail(m, PARO_ERR_ARG, "U_from, U_to must be non-null and distinct");
+  for (int d = 0; d < 3; ++d) {
+    const auto& c = from->nodes[d];
+    const auto& f = to->nodes[d];
+    if (std::fabs(c.front() - f.front()) > 1e-12 * (1.0 + std::fabs(c.front())) ||
+        std::fabs(c.back() - f.back()) > 1e-12 * (1.0 + std::fabs(c.back())))
+      return fail(m, PARO_ERR_ARG, "paro_transfer: the two meshes must cover the same box");
+  }
+  // per-axis maps of the new interior nodes: the old interval and the local coordinate
+  const int fx = to->g.nx - 1, fy = to->g.ny - 1, fz = to->g.nz - 1;
+  const int total = fx + fy + fz;
+  std::vector<int> km(total);
+  std::vector<double> tm(total);
+  int o = 0;
+  for (int d = 0; d < 3; ++d) {
+    const auto& c = from->nodes[d];
+    const auto& f = to->nodes[d];
+    for (size_t i = 1; i + 1 < f.size(); ++i) {
+      const double p = f[i];
+      long k = (long)(std::upper_bound(c.begin(), c.end(), p) - c.begin()) - 1;
+      if (k < 0) k = 0;
+      if (k > (long)c.size() - 2) k = (long)c.size() - 2;
+      km[o] = (int)k;
+      tm[o] = (p - c[k]) / (c[k + 1] - c[k]);
+      ++o;
+    }
+  }
+  if (total > m->xmap_cap) {
+    if (m->xmap_k) dfree(m, m->xmap_k);
+    if (m->xmap_t) dfree(m, m->xmap_t);
+    m->xmap_k = nullptr;
+    m->xmap_t = nullptr;
+    TRY(dalloc(m, &m->xmap_k, (size_t)total, false));
+    TRY(dalloc(m, &m->xmap_t, (size_t)total, false));
+    m->xmap_cap = total;
+  }
+  CK(cudaStreamSynchronize(from->st));  // U_from is ordered on the coarse handle's stream
+  CK(cudaMemcpyAsync(m->xmap_k, km.data(), sizeof(int) * total, cudaMemcpyHostToDevice, m->st));
+  CK(cudaMemcpyAsync(m->xmap_t, tm.data(), sizeof(double) * total, cudaMemcpyHostToDevice, m->st));
+  LAUNCH(1, launch_transfer(from->g, to->g, N, U_from, m->xmap_k, m->xmap_t, U_to, m->st));
+  CK(cudaStreamSynchronize(m->st));
+  return PARO_OK;
 }
 
 int paro_apply(paro_mesh m, int N, int op, int dtype, const void* X, void* Y) {

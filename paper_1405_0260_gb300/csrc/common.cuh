@@ -200,6 +200,16 @@ cudaError_t launch_small_eig(int N, const double* GA, const double* GB, double* 
 cudaError_t launch_rotate(const Grid& g, int N, int Np, const double* X, const double* C, double* U,
                           cudaStream_t st);
 
+// adapt.cu: the adaptive loop on tensor-product meshes (Section 2.1)
+// eta2[cell] = residual indicator of the orbitals u (padded [G][Np]), lam device[N],
+// Vq the potential at the Gauss points ([cz][cy][cx][qz][qy][qx])
+cudaError_t launch_estimate(const Grid& g, int N, int Np, const double* u, const double* lam, const double* Vq,
+                            double* eta2, cudaStream_t st);
+// Uf (fine interior rows x N) = trilinear interpolation of Uc (coarse interior rows x N);
+// kmap/tmap: coarse interval and local coordinate of the fine interior nodes, x then y then z
+cudaError_t launch_transfer(const Grid& gc, const Grid& gf, int N, const double* Uc, const int* kmap,
+                            const double* tmap, double* Uf, cudaStream_t st);
+
 // ks.cu: Kohn-Sham pieces (fields at the Gauss points)
 cudaError_t launch_density(const Grid& g, int N, int Np, const double* U, const double* occ, double* rho,
                            cudaStream_t st);

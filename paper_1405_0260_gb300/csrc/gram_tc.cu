@@ -403,11 +403,16 @@ constexpr int kRotTcMaxNp = 128;
 
 __host__ __device__ constexpr int rot_sbo(int Kp) { return (Kp / 8) * kTcLBO + 16; }
 
+// Threads of a rotation CTA: 256 for Np <= 32 (two CTAs a SM: one converts and
+// reads out while the other's MMAs run; 96 TMEM columns each), 512 above.
+__host__ __device__ constexpr int rot_threads(int NB) { return NB == 32 ? 256 : 512; }
+
 template <int NB>
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __launch_bounds__(rot_threads(NB), NB == 32 ? 2 : 1)
     k_rotate_tc(long long G, int N, int Np, int Kp, const float* __restrict__ xh, const double* __restrict__ C,
                 double* __restrict__ U, int* __restrict__ status) {
   constexpr uint32_t kTmemCols = kTcDigits * NB <= 128 ? 128 : 256;
+  constexpr int kThr = rot_threads(NB);
   extern __shared__ __align__(1024) unsigned char smem[];
   const int sbo = rot_sbo(Kp);
   const int aPiece = (kTcM / 8) * sbo;                 // one digit plane of A (128 node rows)
@@ -426,7 +431,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
   // zero the operand planes (K beyond N and rows beyond Np stay zero)
   const int zbytes = kTcDigits * (aPiece + bPiece);
-  for (int i = tid; i < zbytes / 16; i += kTcThreads) reinterpret_cast<uint4*>(smem)[i] = make_uint4(0, 0, 0, 0);
+  for (int i = tid; i < zbytes / 16; i += kThr) reinterpret_cast<uint4*>(smem)[i] = make_uint4(0, 0, 0, 0);
   if (tid == 0) {
     s_fail = 0;
     mbar_init(&bar, 1);
@@ -440,14 +445,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   }
   __syncthreads();
   // B: the digits of C, row b (column of C), K = a; one exponent per column
-  for (int b = tid; b < nbp; b += kTcThreads) {
+  for (int b = tid; b < nbp; b += kThr) {
     unsigned m = 0u;
     if (b < Np)
       for (int a = 0; a < N; ++a) m = max(m, __float_as_uint(__double2float_rn(C[(long long)a * Np + b])) & 0x7FFFFFFFu);
     cexpB[b] = col_exponent(m);
   }
   __syncthreads();
-  for (int w = tid; w < nbp * koct; w += kTcThreads) {
+  for (int w = tid; w < nbp * koct; w += kThr) {
     const int b = w / koct, oct = w % koct;
     const float sc = pow2f(8 - cexpB[b]);
     uint32_t q[kTcDigits][4];
@@ -472,15 +477,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   tc_fence_after();
   const uint32_t tmem = tmem_base;
 
-  // A conversion items: (node row, octet of a); at most 4 a thread (128 rows x 16 octets)
-  constexpr int kIt = 4;
+  // A conversion items: (node row, octet of a): 128 rows x Kp / 8 octets, at most
+  // 4 a thread at 512 threads (Kp <= 128) and 2 at 256 threads (NB = 32: Kp <= 32)
+  constexpr int kIt = kTcM * (NB == 32 ? 32 : kRotTcMaxNp) / 8 / kThr;
   const int nitems = kTcM * koct;
   float v[kIt][8];
   const long long ntiles = (G + kTcM - 1) / kTcM;
   auto load = [&](long long tile) {
 #pragma unroll
     for (int it = 0; it < kIt; ++it) {
-      const int w = tid + it * kTcThreads;
+      const int w = tid + it * kThr;
       const int r = w / koct, oct = w % koct;
       const long long g = tile * kTcM + r;
 #pragma unroll
@@ -493,17 +499,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const uint32_t idesc = idesc_bf16(kTcM, NB);
   const uint32_t aBase = smem_u32(aBuf), bBase = smem_u32(bBuf);
   const int row = 32 * (warp % 4) + lane;  // node row of this thread in the read-out
-  constexpr int kColsT = NB / 4;           // columns a thread reads out
+  constexpr int kColsT = NB / (kThr / 128);  // columns a thread reads out (4 warps per column group)
   const int col0 = (warp / 4) * kColsT;
   uint32_t phase = 0;
   load(blockIdx.x);
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     // row maxima -> exponents, then the digits of this tile's X rows
-    for (int i = tid; i < kTcM; i += kTcThreads) rmax[i] = 0u;
+    for (int i = tid; i < kTcM; i += kThr) rmax[i] = 0u;
     __syncthreads();
 #pragma unroll
     for (int it = 0; it < kIt; ++it) {
-      const int w = tid + it * kTcThreads;
+      const int w = tid + it * kThr;
       if (w < nitems) {
         unsigned m = 0u;
 #pragma unroll
@@ -512,11 +518,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
     }
     __syncthreads();
-    for (int i = tid; i < kTcM; i += kTcThreads) rexp[i] = col_exponent(rmax[i]);
+    for (int i = tid; i < kTcM; i += kThr) rexp[i] = col_exponent(rmax[i]);
     __syncthreads();
 #pragma unroll
     for (int it = 0; it < kIt; ++it) {
-      const int w = tid + it * kTcThreads;
+      const int w = tid + it * kThr;
       if (w < nitems) {
         const int r = w / koct, oct = w % koct;
         const float sc = pow2f(8 - rexp[r]);
@@ -672,19 +678,20 @@ cudaError_t launch_rotate_tc(const Grid& g, int N, int Np, const float* xh, cons
   if (Np < 4 || Np % 4 != 0 || Np > kRotTcMaxNp || N > Np) return cudaErrorInvalidValue;
   const int Kp = (Np + 15) / 16 * 16;
   const long long ntiles = (g.G + kTcM - 1) / kTcM;
-  const int grid = (int)(ntiles < 152 ? ntiles : 152);
   if (Np <= 32) {
+    const int grid = (int)(ntiles < 2 * 152 ? ntiles : 2 * 152);
     const int nbp = 32;
     const size_t smem = (size_t)kTcDigits * ((kTcM / 8) + nbp / 8) * rot_sbo(Kp) + sizeof(int) * nbp;
     cudaError_t e = allow_max_dyn_smem((const void*)k_rotate_tc<32>);
     if (e != cudaSuccess) return e;
-    k_rotate_tc<32><<<grid, kTcThreads, smem, st>>>(g.G, N, Np, Kp, xh, C, U, status);
+    k_rotate_tc<32><<<grid, rot_threads(32), smem, st>>>(g.G, N, Np, Kp, xh, C, U, status);
   } else {
+    const int grid = (int)(ntiles < 152 ? ntiles : 152);
     const int nbp = (Np + 63) / 64 * 64;
     const size_t smem = (size_t)kTcDigits * ((kTcM / 8) + nbp / 8) * rot_sbo(Kp) + sizeof(int) * nbp;
     cudaError_t e = allow_max_dyn_smem((const void*)k_rotate_tc<64>);
     if (e != cudaSuccess) return e;
-    k_rotate_tc<64><<<grid, kTcThreads, smem, st>>>(g.G, N, Np, Kp, xh, C, U, status);
+    k_rotate_tc<64><<<grid, rot_threads(64), smem, st>>>(g.G, N, Np, Kp, xh, C, U, status);
   }
   return cudaGetLastError();
 }
