@@ -381,14 +381,7 @@ int make_plan(paro_mesh m, int Np, CGPlan<T>** out, T* x, T* b, T* r, T* p, T* q
     delete P;
     return fail(m, PARO_ERR_CUDA, std::string("CG plan: ") + cudaGetErrorString(e));
   }
-  if constexpr (sizeof(T) == 4) {
-    m->tune_source = "default";
-    const int rc = autotune_cg1(m, P);
-    if (rc != PARO_OK) {
-      delete P;
-      return rc;
-    }
-  }
+  if constexpr (sizeof(T) == 4) m->tune_source = "default";  // tuned in make_plans when it is the solver used
   if (std::getenv("PARO_PRINT_PLAN"))
     std::fprintf(stderr, "paro CG plan (%s): tile %dx%d, %d node(s)/thread, block %d orbitals x %d, %d threads, grid %d, "
                  "smem %zu B, persistent %d\n", sizeof(T) == 4 ? "float32" : "float64", P->geo.TX, P->geo.TY,
@@ -492,6 +485,9 @@ int make_plans(paro_mesh m, int Np) {
     a.inner = 1;
     TRY(set_f32_layout(m, 1));
     TRY(autotune_cg2(m, P));
+    // the single-reduction kernel solves the float32 correction problems only where
+    // the single-pass plan cannot run: its geometry is timed only then
+    if (!P->ok) TRY(autotune_cg1(m, m->plan32));
     if (std::getenv("PARO_PRINT_PLAN"))
       std::fprintf(stderr, "paro single-pass CG plan: tile %dx%d, %d nodes a thread, block %d orbitals x %d, %d threads, "
                    "grid %d, smem %zu B, usable %d, geometry %s\n", P->geo.TX, P->geo.TY, P->geo.npt, P->geo.G4 * 4,
