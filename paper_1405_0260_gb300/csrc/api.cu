@@ -1288,7 +1288,7 @@ int rr_packed(paro_mesh m, int N, const double* src, double* dst, double* lam, R
   // the rotation: on the tensor cores from the hi parts of X with the tensor-core
   // Grams (the same 24-bit inputs), else in float-float from the split X (C staged
   // in shared memory whole, or in column blocks above kRotateFFMaxNp), or float64
-  if (tc && Np <= 128)
+  if (tc && Np <= kRotTcMaxNp)
     LAUNCH(1, launch_rotate_tc(g, N, Np, m->fxh, m->C, dst, &m->cgst->status, m->st));
   else if (ff || tc)
     LAUNCH(1, launch_rotate_ff(g, N, Np, m->fxh, m->fxl, m->C, dst, m->st));

@@ -177,7 +177,9 @@ cudaError_t launch_gram_tc(const Grid& g, int Np, const float* xh, const float* 
 // both Grams X^T A and X^T B in one launch (Np <= 32), partials into partA and partB
 cudaError_t launch_gram_tc_pair(const Grid& g, int Np, const float* xh, const float* ah, const float* bh,
                                 double* partA, double* partB, int* n_chunks, int* status, cudaStream_t st);
-// gram_tc.cu: the rotation U = X C on the tensor cores (Np <= 128, X as float32 hi parts)
+// gram_tc.cu: the rotation U = X C on the tensor cores (Np <= kRotTcMaxNp, X as float32 hi parts;
+// above 128 in blocks of 128 K rows and columns, later K blocks added in float64)
+constexpr int kRotTcMaxNp = 256;
 cudaError_t launch_rotate_tc(const Grid& g, int N, int Np, const float* xh, const double* C, double* U, int* status,
                              cudaStream_t st);
 constexpr int kRotateFFMaxNp = 144;  // whole C as float-float in shared memory (8 Np^2 bytes); column blocks above

@@ -399,7 +399,7 @@ cudaError_t launch_tc(long long G, int Np, int xr0, int na, int yc0, int nb, con
 // The error is the rounding of X and C to 24 bits below their row / column
 // maximum (unbiased), the accuracy of the tensor-core Grams' inputs.
 // ---------------------------------------------------------------------------
-constexpr int kRotTcMaxNp = 128;
+constexpr int kRotTcBlk = 128;  // K rows and columns of one launch (exact FP32 level sums, shared memory)
 
 __host__ __device__ constexpr int rot_sbo(int Kp) { return (Kp / 8) * kTcLBO + 16; }
 
@@ -410,13 +410,13 @@ __host__ __device__ constexpr int rot_threads(int NB) { return NB == 32 ? 256 : 
 template <int NB>
 __global__ void __launch_bounds__(rot_threads(NB), NB == 32 ? 2 : 1)
     k_rotate_tc(long long G, int N, int Np, int Kp, const float* __restrict__ xh, const double* __restrict__ C,
-                double* __restrict__ U, int* __restrict__ status) {
+                double* __restrict__ U, int* __restrict__ status, int k0, int c0, int Nc, int acc) {
   constexpr uint32_t kTmemCols = kTcDigits * NB <= 128 ? 128 : 256;
   constexpr int kThr = rot_threads(NB);
   extern __shared__ __align__(1024) unsigned char smem[];
   const int sbo = rot_sbo(Kp);
   const int aPiece = (kTcM / 8) * sbo;                 // one digit plane of A (128 node rows)
-  const int nbp = (Np + NB - 1) / NB * NB;              // C columns, padded to whole N-tiles
+  const int nbp = (Nc + NB - 1) / NB * NB;              // this block's C columns, padded to whole N-tiles
   const int bPiece = (nbp / 8) * sbo;                   // one digit plane of B (all columns)
   unsigned char* aBuf = smem;
   unsigned char* bBuf = smem + kTcDigits * aPiece;
@@ -429,7 +429,7 @@ __global__ void __launch_bounds__(rot_threads(NB), NB == 32 ? 2 : 1)
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int koct = Kp / 8;
 
-  // zero the operand planes (K beyond N and rows beyond Np stay zero)
+  // zero the operand planes (K beyond N and columns beyond Nc stay zero)
   const int zbytes = kTcDigits * (aPiece + bPiece);
   for (int i = tid; i < zbytes / 16; i += kThr) reinterpret_cast<uint4*>(smem)[i] = make_uint4(0, 0, 0, 0);
   if (tid == 0) {
@@ -447,8 +447,9 @@ __global__ void __launch_bounds__(rot_threads(NB), NB == 32 ? 2 : 1)
   // B: the digits of C, row b (column of C), K = a; one exponent per column
   for (int b = tid; b < nbp; b += kThr) {
     unsigned m = 0u;
-    if (b < Np)
-      for (int a = 0; a < N; ++a) m = max(m, __float_as_uint(__double2float_rn(C[(long long)a * Np + b])) & 0x7FFFFFFFu);
+    if (b < Nc)
+      for (int a = 0; a < N; ++a)
+        m = max(m, __float_as_uint(__double2float_rn(C[(long long)(k0 + a) * Np + c0 + b])) & 0x7FFFFFFFu);
     cexpB[b] = col_exponent(m);
   }
   __syncthreads();
@@ -459,11 +460,11 @@ __global__ void __launch_bounds__(rot_threads(NB), NB == 32 ? 2 : 1)
 #pragma unroll
     for (int j = 0; j < 8; j += 2) {
       const int a0 = 8 * oct + j;
-      const float c0 = (b < Np && a0 < N) ? __double2float_rn(C[(long long)a0 * Np + b]) : 0.f;
-      const float c1 = (b < Np && a0 + 1 < N) ? __double2float_rn(C[(long long)(a0 + 1) * Np + b]) : 0.f;
+      const float cv0 = (b < Nc && a0 < N) ? __double2float_rn(C[(long long)(k0 + a0) * Np + c0 + b]) : 0.f;
+      const float cv1 = (b < Nc && a0 + 1 < N) ? __double2float_rn(C[(long long)(k0 + a0 + 1) * Np + c0 + b]) : 0.f;
       float d0[kTcDigits], d1[kTcDigits];
-      digits3(c0, sc, d0);
-      digits3(c1, sc, d1);
+      digits3(cv0, sc, d0);
+      digits3(cv1, sc, d1);
 #pragma unroll
       for (int p = 0; p < kTcDigits; ++p) q[p][j / 2] = pack_bf16(d0[p], d1[p]);
     }
@@ -479,7 +480,7 @@ __global__ void __launch_bounds__(rot_threads(NB), NB == 32 ? 2 : 1)
 
   // A conversion items: (node row, octet of a): 128 rows x Kp / 8 octets, at most
   // 4 a thread at 512 threads (Kp <= 128) and 2 at 256 threads (NB = 32: Kp <= 32)
-  constexpr int kIt = kTcM * (NB == 32 ? 32 : kRotTcMaxNp) / 8 / kThr;
+  constexpr int kIt = kTcM * (NB == 32 ? 32 : kRotTcBlk) / 8 / kThr;
   const int nitems = kTcM * koct;
   float v[kIt][8];
   const long long ntiles = (G + kTcM - 1) / kTcM;
@@ -492,7 +493,7 @@ __global__ void __launch_bounds__(rot_threads(NB), NB == 32 ? 2 : 1)
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const int a = 8 * oct + j;
-        v[it][j] = (w < nitems && tile < ntiles && g < G && a < N) ? __ldg(xh + g * Np + a) : 0.f;
+        v[it][j] = (w < nitems && tile < ntiles && g < G && a < N) ? __ldg(xh + g * Np + k0 + a) : 0.f;
       }
     }
   };
@@ -545,7 +546,7 @@ __global__ void __launch_bounds__(rot_threads(NB), NB == 32 ? 2 : 1)
     load(tile + gridDim.x);    // the next tile's X rows are in flight during the MMAs
     const long long g = tile * kTcM + row;
     const int eg = rexp[row];
-    for (int n0 = 0; n0 < Np; n0 += NB) {
+    for (int n0 = 0; n0 < Nc; n0 += NB) {
       tc_fence_before();
       __syncthreads();
       if (tid == 0) {
@@ -572,9 +573,9 @@ __global__ void __launch_bounds__(rot_threads(NB), NB == 32 ? 2 : 1)
       __syncthreads();
       if (s_fail) break;
       // U[g][n0 + b] = 2^(E_g + F_b - 16) (L0 + L1 2^-8 + L2 2^-16), by the warps whose
-      // columns include some b < Np
+      // columns include some b < Nc
 #pragma unroll
-      for (int c = 0; c < kColsT && n0 + col0 < Np; c += 8) {
+      for (int c = 0; c < kColsT && n0 + col0 < Nc; c += 8) {
         const uint32_t ta = tmem + ((uint32_t)(32 * (warp % 4)) << 16) + (uint32_t)(col0 + c);
         float v0[8], v1[8];
         tmem_ld8(ta, v0);
@@ -590,18 +591,26 @@ __global__ void __launch_bounds__(rot_threads(NB), NB == 32 ? 2 : 1)
           const int b = n0 + col0 + c + i;
           // the scale 2^sc on the float pair (exact power-of-two products), then one
           // float64 addition; ldexp in float64 only for scales outside the float range
-          const int sc = eg + (b < Np ? cexpB[b] : 0) - 16;
+          const int sc = eg + (b < Nc ? cexpB[b] : 0) - 16;
           const FF tn = ff_norm(tsum[i]);
-          if (b >= Np) out[i] = 0.0;
+          if (b >= Nc) out[i] = 0.0;
           else if (sc >= -100 && sc <= 100) out[i] = ff_to_double(FF{__fmul_rn(tn.hi, pow2f(sc)), __fmul_rn(tn.lo, pow2f(sc))});
           else out[i] = ldexp(ff_to_double(tn), sc);
         }
         const int b0 = n0 + col0 + c;
-        if (g < G && b0 < Np) {
-          double* dst = U + g * Np + b0;
+        if (g < G && b0 < Nc) {
+          double* dst = U + g * Np + c0 + b0;
 #pragma unroll
           for (int i = 0; i < 8; i += 2)
-            if (b0 + i < Np) *reinterpret_cast<double2*>(dst + i) = make_double2(out[i], out[i + 1]);
+            if (b0 + i < Nc) {
+              double2 o = make_double2(out[i], out[i + 1]);
+              if (acc) {
+                const double2 u = *reinterpret_cast<const double2*>(dst + i);
+                o.x += u.x;
+                o.y += u.y;
+              }
+              *reinterpret_cast<double2*>(dst + i) = o;
+            }
         }
       }
     }
@@ -676,24 +685,34 @@ namespace paro {
 cudaError_t launch_rotate_tc(const Grid& g, int N, int Np, const float* xh, const double* C, double* U, int* status,
                              cudaStream_t st) {
   if (Np < 4 || Np % 4 != 0 || Np > kRotTcMaxNp || N > Np) return cudaErrorInvalidValue;
-  const int Kp = (Np + 15) / 16 * 16;
   const long long ntiles = (g.G + kTcM - 1) / kTcM;
   if (Np <= 32) {
+    const int Kp = (N + 15) / 16 * 16;
     const int grid = (int)(ntiles < 2 * 152 ? ntiles : 2 * 152);
     const int nbp = 32;
     const size_t smem = (size_t)kTcDigits * ((kTcM / 8) + nbp / 8) * rot_sbo(Kp) + sizeof(int) * nbp;
     cudaError_t e = allow_max_dyn_smem((const void*)k_rotate_tc<32>);
     if (e != cudaSuccess) return e;
-    k_rotate_tc<32><<<grid, rot_threads(32), smem, st>>>(g.G, N, Np, Kp, xh, C, U, status);
-  } else {
-    const int grid = (int)(ntiles < 152 ? ntiles : 152);
-    const int nbp = (Np + 63) / 64 * 64;
-    const size_t smem = (size_t)kTcDigits * ((kTcM / 8) + nbp / 8) * rot_sbo(Kp) + sizeof(int) * nbp;
-    cudaError_t e = allow_max_dyn_smem((const void*)k_rotate_tc<64>);
-    if (e != cudaSuccess) return e;
-    k_rotate_tc<64><<<grid, rot_threads(64), smem, st>>>(g.G, N, Np, Kp, xh, C, U, status);
+    k_rotate_tc<32><<<grid, rot_threads(32), smem, st>>>(g.G, N, Np, Kp, xh, C, U, status, 0, 0, Np, 0);
+    return cudaGetLastError();
   }
-  return cudaGetLastError();
+  // U[:, c0 : c0 + Nc] = sum over K blocks of X[:, k0 : k0 + Kn] C[k0 : k0 + Kn, c0 : c0 + Nc]: blocks of at
+  // most 128 in K and in columns, the later K blocks added to U in float64
+  const int grid = (int)(ntiles < 152 ? ntiles : 152);
+  cudaError_t e = allow_max_dyn_smem((const void*)k_rotate_tc<64>);
+  if (e != cudaSuccess) return e;
+  for (int c0 = 0; c0 < Np; c0 += kRotTcBlk) {
+    const int Nc = Np - c0 < kRotTcBlk ? Np - c0 : kRotTcBlk;
+    const int nbp = (Nc + 63) / 64 * 64;
+    for (int k0 = 0; k0 < N; k0 += kRotTcBlk) {
+      const int Kn = N - k0 < kRotTcBlk ? N - k0 : kRotTcBlk;
+      const int Kp = (Kn + 15) / 16 * 16;
+      const size_t smem = (size_t)kTcDigits * ((kTcM / 8) + nbp / 8) * rot_sbo(Kp) + sizeof(int) * nbp;
+      k_rotate_tc<64><<<grid, rot_threads(64), smem, st>>>(g.G, Kn, Np, Kp, xh, C, U, status, k0, c0, Nc, k0 > 0);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
 }
 
 }  // namespace paro

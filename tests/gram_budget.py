@@ -49,24 +49,29 @@ def gram_tc_error(n, X, Y):
     return float(np.sqrt(2.0 * np.max(var)) * np.sqrt(2.0 * np.log(max(entries, 2))))
 
 
-def rotation_tc_error(X, C, MU):
+def rotation_tc_error(X, C, MU, blk=128):
     """Expected largest entry error of U^T M U added by the tensor-core rotation U = X C.
 
-    The rotation rounds every X row to 24 bits below its largest |value| (over the
-    orbitals) and every C column to 24 bits below its largest |value|, to nearest;
-    dU = dX C + X dC has per-entry variances var_U[g, i] = sum_a (var(dX_ga) C_ai^2
-    + X_ga^2 var(dC_ai)), and (U + dU)^T M (U + dU) - U^T M U ~ dU^T M U + U^T M dU
-    has entry variances sum_g (var_U[g, i] MU_gj^2 + var_U[g, j] MU_gi^2).  Returned:
-    the largest standard deviation times sqrt(2 ln N^2), as gram_tc_error.
+    The rotation runs in blocks of at most `blk` orbitals along K (the columns of X,
+    the rows of C): within a block it rounds every X row to 24 bits below its
+    largest |value| over the block and every C column to 24 bits below its largest
+    |value| over the block's rows, to nearest; dU = dX C + X dC has per-entry
+    variances var_U[g, i] = sum_a (var(dX_ga) C_ai^2 + X_ga^2 var(dC_ai)), and
+    (U + dU)^T M (U + dU) - U^T M U ~ dU^T M U + U^T M dU has entry variances
+    sum_g (var_U[g, i] MU_gj^2 + var_U[g, j] MU_gi^2).  Returned: the largest
+    standard deviation times sqrt(2 ln N^2), as gram_tc_error.
     """
     def step2(A, axis):
         amax = np.max(np.abs(A), axis=axis, keepdims=True)
         E = np.where(amax > 0, np.floor(np.log2(np.where(amax > 0, amax, 1.0))) + 1.0, 0.0)
         return np.where(amax > 0, 2.0 ** (2 * (E - 24)) / 12.0, 0.0)
 
-    vx = step2(X, 1)  # per node row
-    vc = step2(C, 0)  # per column of C
-    varU = vx * np.sum(C ** 2, axis=0)[None, :] + (X ** 2) @ np.broadcast_to(vc, C.shape)
+    varU = np.zeros((X.shape[0], C.shape[1]))
+    for k0 in range(0, C.shape[0], blk):
+        Xb, Cb = X[:, k0:k0 + blk], C[k0:k0 + blk, :]
+        vx = step2(Xb, 1)  # per node row of the block
+        vc = step2(Cb, 0)  # per column of the block
+        varU += vx * np.sum(Cb ** 2, axis=0)[None, :] + (Xb ** 2) @ np.broadcast_to(vc, Cb.shape)
     var = varU.T @ (MU ** 2) + (MU ** 2).T @ varU
     N = C.shape[1]
     return float(np.sqrt(np.max(var)) * np.sqrt(2.0 * np.log(max(N * N, 2))))

@@ -318,9 +318,9 @@ def test_rayleigh_ritz_tensor_core_grams_match_oracle(B, N):
     assert err < 1e-6  # the mixed path's eigenvalue target
     u = host(U)
     orth = np.max(np.abs(u.T @ (ops.M @ u) - np.eye(N)))
-    # N <= 128: the rotation U = X C runs on the tensor cores too, from the same
-    # 24-bit inputs; its rounding adds rotation_tc_error
-    eR = rotation_tc_error(X0, ref.C, ops.M @ ref.U) if N <= 128 else 0.0
+    # the rotation U = X C runs on the tensor cores too (in 128-orbital K and column
+    # blocks above 128), from the same 24-bit inputs; its rounding adds rotation_tc_error
+    eR = rotation_tc_error(X0, ref.C, ops.M @ ref.U)
     assert orth < 10 * (eB / lmin + eR), (orth, eB / lmin, eR)
     # single Ritz vectors whose Ritz value is separated from its neighbours (M-principal
     # angles: normalisation errors of the size bounded above do not count as angles)
@@ -450,9 +450,9 @@ def test_errors_are_reported_not_raised_on_device(B):
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_256_orbitals_solve_and_rayleigh_ritz(B, prec):
     # the widest orbital count of the large workload on a small mesh: 8 CG orbital
-    # blocks, tensor-core Grams in 2 x 4 blocks (mixed), the float64 rotation
-    # (Np > the float-float rotation's shared memory), the small eigensolve at
-    # N = 256 with its work matrices in global memory
+    # blocks, tensor-core Grams in 2 x 4 blocks and the tensor-core rotation in 2 x 2
+    # blocks of 128 (mixed; float64 rotation on float64 handles), the small
+    # eigensolve at N = 256 with its work matrices in global memory
     N = 256
     p = W.harmonic(nc=12, L=6.0, N=N, seed=4300, sigma=1.0)
     ops = oracle_ops(p)
