@@ -398,6 +398,9 @@ cudaError_t launch_tc(long long G, int Np, int xr0, int na, int yc0, int nb, con
 // levels are combined in float-float and scaled by 2^(E_g + F_b) in float64.
 // The error is the rounding of X and C to 24 bits below their row / column
 // maximum (unbiased), the accuracy of the tensor-core Grams' inputs.
+// One launch covers K rows k0 .. k0 + Kn - 1 of C (Kn <= 128) and its columns
+// c0 .. c0 + Nc - 1; above 128 orbitals the launcher runs blocks of 128 in K and
+// in columns, the later K blocks adding into U in float64 (acc).
 // ---------------------------------------------------------------------------
 constexpr int kRotTcBlk = 128;  // K rows and columns of one launch (exact FP32 level sums, shared memory)
 
