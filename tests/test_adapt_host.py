@@ -3,6 +3,8 @@ libparo.so) against the oracle (oracle/adapt.py), on the CPU: Doerfler and
 maximum marking (eqs. 2.2-2.3) of random indicator sets give the same cells,
 refinement of marked cells gives the same coordinates, and bad arguments are
 refused."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -54,3 +56,15 @@ def test_bad_arguments_are_refused(B):
     with pytest.raises(B.ParoError):  # coordinates not increasing
         B.refine_coords((2, 2, 2), (np.array([0.0, 1.0, 0.5]), np.arange(3.0), np.arange(3.0)),
                         np.zeros((2, 2, 2), dtype=bool))
+
+
+def test_device_entry_points_refuse_null_handles_without_a_gpu(B):
+    # paro_estimate and paro_transfer check their handles and sizes before any CUDA call
+    lib = B.lib()
+    lam = (ctypes.c_double * 1)(0.0)
+    assert lib.paro_estimate(None, 1, None, lam, None, None) == -1  # PARO_ERR_ARG
+    assert lib.paro_transfer(None, None, 1, None, None) == -1
+    n = (ctypes.c_int * 3)(2, 2, 2)
+    out = (ctypes.c_int * 3)()
+    assert lib.paro_refine_coords(n, None, None, out, None) == -1
+    assert lib.paro_mark(0, None, 0, 0.5, None) == -1
