@@ -1060,8 +1060,15 @@ cudaError_t launch_small_eig(int N, const double* GA, const double* GB, double* 
     const size_t smem = ((size_t)6 * N * LD + 2 * N + 4 * ((N + 1) / 2)) * sizeof(float);
     cudaError_t e = allow_max_dyn_smem((const void*)k_small_eig_ff);
     if (e != cudaSuccess) return e;
-    // one thread per 2 x 2 block and per V row segment of a round where possible
-    k_small_eig_ff<<<1, 512, smem, st>>>(N, Np, GA, GB, C, theta, status);
+    // one thread per 2 x 2 block and per V row segment of a round, and per entry of
+    // an elimination or solve step, where possible: no more warps than that (their
+    // barriers are the kernel's latency), 64 to 512 threads
+    const int half = (N + 1) / 2;
+    int need = half * half + N * half;
+    if (N * (N - 1) > need) need = N * (N - 1);
+    int nt = (need + 31) / 32 * 32;
+    nt = nt < 64 ? 64 : (nt > 512 ? 512 : nt);
+    k_small_eig_ff<<<1, nt, smem, st>>>(N, Np, GA, GB, C, theta, status);
     return cudaGetLastError();
   }
   if (bar != nullptr && N > kEigGridMinN) {
