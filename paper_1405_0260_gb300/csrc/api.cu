@@ -112,6 +112,7 @@ struct paro_mesh_s {
   // fxh/fxl = split(x) when a single-pass refinement has just ended (the
   // Rayleigh-Ritz step that follows in the ParO loop reuses it)
   bool x_split_valid = false;
+  bool hm_ready = false;  // fah/fal = H x and fbh/fbl = M x of the current x (the refinement's closing check)
   // h_dbl holds the last refinement's ||r_i||^2 and ||b_i||^2 (read with its final check)
   bool relres_staged = false;
   // Kohn-Sham: box origin, the float64 handle of the Poisson operator K/2 (V = 0,
@@ -926,7 +927,7 @@ struct MaterialiseX {
   }
 };
 
-int refine_solve_cg2(paro_mesh m, int N, const paro_params& p, paro_stats* st, double itol) {
+int refine_solve_cg2(paro_mesh m, int N, const paro_params& p, paro_stats* st, double itol, bool rr_next) {
   MaterialiseX mx{m};
   const int Np = m->Np_alloc;
   Grid& g = m->g;
@@ -974,8 +975,16 @@ int refine_solve_cg2(paro_mesh m, int N, const paro_params& p, paro_stats* st, d
       m->x_pending_u = false;
       ++sweep;
     }
-    LAUNCH(1, launch_refine_residual_ff(g, N, Np, m->wAh, m->wAl, m->fxh, m->fxl, m->fah, m->fal, nullptr, rs,
-                                        p.solve_tol, m->st, 1));
+    if (rr_next) {
+      // a Rayleigh-Ritz step on this x follows: M x, then H x with the check
+      // r = b - H x - sigma M x, H x written over b (both applies of that step)
+      LAUNCH(1, apply_M_ff(m, Np, m->fxh, m->fxl, nullptr, nullptr, m->fbh, m->fbl));
+      LAUNCH(1, launch_refine_check_hff(g, N, Np, m->wHh, m->wHl, m->fxh, m->fxl, m->fbh, m->fbl, m->sigma, m->fah,
+                                        m->fal, rs, p.solve_tol, m->st));
+    } else {
+      LAUNCH(1, launch_refine_residual_ff(g, N, Np, m->wAh, m->wAl, m->fxh, m->fxl, m->fah, m->fal, nullptr, rs,
+                                          p.solve_tol, m->st, 1));
+    }
     if (st) st->stencil_applies += N;
     // the open count and the status word in one round trip (with the statistics'
     // iteration counts and residual norms when they are asked for); a failed
@@ -994,7 +1003,15 @@ int refine_solve_cg2(paro_mesh m, int N, const paro_params& p, paro_stats* st, d
     const int open = m->h_int[0];
     if (m->h_int[1] != 0) TRY(check_status(m, "orbital_solve (float32 correction)"));
     if (m->profile) TRY(drain_profile(m));
-    if (open == 0) break;
+    if (open == 0) {
+      m->hm_ready = rr_next;
+      break;
+    }
+    if (rr_next) {
+      // b was overwritten by H x: b = (lambda + sigma) M u again, u's split staged in fbh/fbl
+      LAUNCH(1, launch_split_ff((long long)g.G * Np, m->u, m->fbh, m->fbl, m->st));
+      LAUNCH(1, apply_M_ff(m, Np, m->fbh, m->fbl, m->dscal + S_SCALE * kMaxN, nullptr, m->fah, m->fal));
+    }
     if (sweep >= p.max_refine) {
       if (st) st->refine_sweeps = sweep;
       TRY(check_status(m, "orbital_solve"));
@@ -1018,13 +1035,13 @@ int refine_solve_cg2(paro_mesh m, int N, const paro_params& p, paro_stats* st, d
   return PARO_OK;
 }
 
-int refine_solve(paro_mesh m, int N, const paro_params& p, paro_stats* st) {
+int refine_solve(paro_mesh m, int N, const paro_params& p, paro_stats* st, bool rr_next = false) {
   TRY(check_precond(m, p));
   // inner tolerance: given, or sqrt(solve_tol) so that two sweeps reach solve_tol
   // (clamped to what float32 CG reliably attains and to a useful minimum)
   const double itol = p.inner_tol > 0.0 ? p.inner_tol : std::fmin(1e-3, std::fmax(1e-6, std::sqrt(p.solve_tol)));
   if (p.precond == PARO_PRECOND_JACOBI && m->plan2 && m->plan2->ok && m->profile != 2)
-    return refine_solve_cg2(m, N, p, st, itol);
+    return refine_solve_cg2(m, N, p, st, itol, rr_next);
   if (m->x_pending_u) {
     CK(cudaMemcpyAsync(m->x, m->u, sizeof(double) * m->g.G * m->Np_alloc, cudaMemcpyDeviceToDevice, m->st));
     m->x_pending_u = false;
@@ -1083,10 +1100,11 @@ int refine_solve(paro_mesh m, int N, const paro_params& p, paro_stats* st) {
   return PARO_OK;
 }
 
-int solve_packed(paro_mesh m, int N, const double* lam, const paro_params& p, paro_stats* st) {
+int solve_packed(paro_mesh m, int N, const double* lam, const paro_params& p, paro_stats* st, bool rr_next = false) {
   const int Np = m->Np_alloc;
   Grid& g = m->g;
   m->x_split_valid = false;
+  m->hm_ready = false;
   m->relres_staged = false;
   // b = (lambda + sigma) M u
   for (int i = 0; i < Np; ++i) m->h_dbl[i] = i < N ? lam[i] + m->sigma : 0.0;
@@ -1122,7 +1140,7 @@ int solve_packed(paro_mesh m, int N, const double* lam, const paro_params& p, pa
     CGState rs = cg_state(m, true);
     LAUNCH(1, launch_refine_residual(g, N, Np, m->coef64, m->x, m->b, nullptr, rs, p.solve_tol, m->st));
   } else {
-    TRY(refine_solve(m, N, p, st));
+    TRY(refine_solve(m, N, p, st, rr_next));
   }
   if (st) {
     if (!m->relres_staged) {
@@ -1213,6 +1231,9 @@ int rr_packed(paro_mesh m, int N, const double* src, double* dst, double* lam, R
   const int Np = m->Np_alloc;
   Grid& g = m->g;
   m->x_split_valid = false;
+  // H X and M X already formed by the refinement's closing check on this X
+  const bool hm = m->hm_ready && src_split && src == m->x;
+  m->hm_ready = false;
   const bool mixed = m->precision == PARO_MIXED;
   const bool tc = mixed && mode == kRRFast && m->gpart_tc != nullptr;
   const bool ff = mixed && mode == kRRAccurate && m->gpart_ff != nullptr;
@@ -1220,9 +1241,11 @@ int rr_packed(paro_mesh m, int N, const double* src, double* dst, double* lam, R
     // float-float X, HX and MX; both Grams on the tensor cores from their hi parts
     // (exact BF16 digit products, float-float across 128-node chunks)
     if (!src_split) LAUNCH(1, launch_split_ff((long long)g.G * Np, src, m->fxh, m->fxl, m->st));
-    LAUNCH(1, launch_ff_apply(g, Np, m->wHh, m->wHl, nullptr, m->fxh, m->fxl, nullptr, nullptr, m->fah, m->fal,
-                              m->st));
-    LAUNCH(1, apply_M_ff(m, Np, m->fxh, m->fxl, nullptr, nullptr, m->fbh, m->fbl));
+    if (!hm) {
+      LAUNCH(1, launch_ff_apply(g, Np, m->wHh, m->wHl, nullptr, m->fxh, m->fxl, nullptr, nullptr, m->fah, m->fal,
+                                m->st));
+      LAUNCH(1, apply_M_ff(m, Np, m->fxh, m->fxl, nullptr, nullptr, m->fbh, m->fbl));
+    }
     int nch = 0;
     if (Np <= 32) {
       // both Grams in one launch (X loaded and converted once)
@@ -1252,9 +1275,11 @@ int rr_packed(paro_mesh m, int N, const double* src, double* dst, double* lam, R
   } else if (ff) {
     // float-float: HX and MX as hi/lo arrays, both Grams and the rotation from the split X
     if (!src_split) LAUNCH(1, launch_split_ff((long long)g.G * Np, src, m->fxh, m->fxl, m->st));
-    LAUNCH(1, launch_ff_apply(g, Np, m->wHh, m->wHl, nullptr, m->fxh, m->fxl, nullptr, nullptr, m->fah, m->fal,
-                              m->st));
-    LAUNCH(1, apply_M_ff(m, Np, m->fxh, m->fxl, nullptr, nullptr, m->fbh, m->fbl));
+    if (!hm) {
+      LAUNCH(1, launch_ff_apply(g, Np, m->wHh, m->wHl, nullptr, m->fxh, m->fxl, nullptr, nullptr, m->fah, m->fal,
+                                m->st));
+      LAUNCH(1, apply_M_ff(m, Np, m->fxh, m->fxl, nullptr, nullptr, m->fbh, m->fbl));
+    }
     int nch = 0;
     LAUNCH(1, launch_gram2_ff(g, Np, m->fxh, m->fxl, m->fah, m->fal, m->fbh, m->fbl, m->gpart_ff, &nch, m->st));
     LAUNCH(1, launch_gram_reduce(Np, nch, m->gpart_ff, m->GA, m->GB, m->st));
@@ -1979,7 +2004,7 @@ int paro_iterate(paro_mesh m, int N, double* U, double* lambda, const paro_param
   while (outer < limit) {
     {
       Timer t(m, s ? &s->ms_solve : nullptr);
-      int r1 = solve_packed(m, N, lam.data(), pp, s);
+      int r1 = solve_packed(m, N, lam.data(), pp, s, true);
       if (r1 != PARO_OK) return r1;
     }
     {
@@ -2191,7 +2216,7 @@ int paro_scf_iterate(paro_mesh m, int N, const double* occ, const double* vext_q
     TRY(paro_set_potential(m, m->ks_v, sigma));
     {
       Timer t(m, s ? &s->ms_solve : nullptr);
-      int r1 = solve_packed(m, N, lam.data(), pp, s);
+      int r1 = solve_packed(m, N, lam.data(), pp, s, true);
       if (r1 != PARO_OK) return r1;
     }
     {

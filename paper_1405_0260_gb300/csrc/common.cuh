@@ -146,6 +146,12 @@ cudaError_t launch_refine_residual(const Grid& g, int N, int Np, const double* c
 cudaError_t launch_refine_update(const Grid& g, int Np, double* x64, const float* d32, const int* skip,
                                  cudaStream_t st);
 // The same residual in float-float arithmetic (x and b as hi/lo arrays, packed weights of A).
+// pcg.cu: the refinement's closing check before a Rayleigh-Ritz step on the same x:
+// H x written over b (hi/lo), r = b - H x - sigma M x (M x given), norms and skip flags
+cudaError_t launch_refine_check_hff(const Grid& g, int N, int Np, const float* whi, const float* wlo,
+                                    const float* xhi, const float* xlo, const float* mhi, const float* mlo,
+                                    double sigma, float* bhy, float* bly, const CGState& s, double tol,
+                                    cudaStream_t st);
 cudaError_t launch_refine_residual_ff(const Grid& g, int N, int Np, const float* whi, const float* wlo,
                                       const float* xhi, const float* xlo, const float* bhi, const float* blo,
                                       float* rhs32, const CGState& s, double tol, cudaStream_t st, int gm = 0);

@@ -215,6 +215,99 @@ __global__ void __launch_bounds__(kRedThreads, 2) k_refine_residual_ff(Grid g, i
   if (threadIdx.x == 0) *s.n_active = cnt;
 }
 
+// The refinement's closing check when a Rayleigh-Ritz step follows on the same x:
+// y = H x (27 points, float-float, the packed H weights), r = b - y - sigma M x
+// with M x given (mhi, mlo), the norms and skip flags as in k_refine_residual_ff
+// (A = H + sigma M), and y written over b (each thread reads b at its own node
+// before writing y there), so the Rayleigh-Ritz step finds H x and M x formed.
+__global__ void __launch_bounds__(kRedThreads, 2) k_refine_check_hff(Grid g, int N, int Np, const float* __restrict__ whi,
+                                                                  const float* __restrict__ wlo,
+                                                                  const float* __restrict__ xhi,
+                                                                  const float* __restrict__ xlo,
+                                                                  const float* __restrict__ mhi,
+                                                                  const float* __restrict__ mlo, FF sig, float* bhy,
+                                                                  float* bly, CGState s, double tol) {
+  __shared__ double sred[2 * kRedThreads * 4];
+  double* tot = sred;
+  __shared__ int cnt;
+  NodeMap nm = node_map(Np);
+  int grp = threadIdx.x % nm.groups;
+  int nl = threadIdx.x / nm.groups;
+  bool live = nl < nm.npb;
+  double acc[2][4] = {};
+  if (live) {
+    float arr[4] = {0, 0, 0, 0}, abb[4] = {0, 0, 0, 0};
+    for (int n = blockIdx.x * nm.npb + nl; n < g.nI; n += gridDim.x * nm.npb) {
+      long long gp = interior_to_padded(g, n);
+      float wh[28], wl[28];
+#pragma unroll
+      for (int q = 0; q < 7; ++q) {
+        const float4 a = reinterpret_cast<const float4*>(whi + gp * kPackedW)[q];
+        const float4 c = reinterpret_cast<const float4*>(wlo + gp * kPackedW)[q];
+        wh[4 * q] = a.x, wh[4 * q + 1] = a.y, wh[4 * q + 2] = a.z, wh[4 * q + 3] = a.w;
+        wl[4 * q] = c.x, wl[4 * q + 1] = c.y, wl[4 * q + 2] = c.z, wl[4 * q + 3] = c.w;
+      }
+      FF hx[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+#pragma unroll
+      for (int o = 0; o < 27; ++o) {
+        const int dz = o / 9 - 1, dy = (o / 3) % 3 - 1, dx = o % 3 - 1;
+        const long long nb = gp + ((long long)dz * g.Py + dy) * g.Px + dx;
+        const FF w{wh[o], wl[o]};
+        const float4 h = *reinterpret_cast<const float4*>(xhi + nb * Np + 4 * grp);
+        const float4 l = *reinterpret_cast<const float4*>(xlo + nb * Np + 4 * grp);
+        ff_mac(hx[0], FF{h.x, l.x}, w);
+        ff_mac(hx[1], FF{h.y, l.y}, w);
+        ff_mac(hx[2], FF{h.z, l.z}, w);
+        ff_mac(hx[3], FF{h.w, l.w}, w);
+      }
+      const long long e = gp * Np + 4 * grp;
+      const float4 bh4 = *reinterpret_cast<const float4*>(bhy + e);
+      const float4 bl4 = *reinterpret_cast<const float4*>(bly + e);
+      const float4 mh4 = *reinterpret_cast<const float4*>(mhi + e);
+      const float4 ml4 = *reinterpret_cast<const float4*>(mlo + e);
+      const float bh[4] = {bh4.x, bh4.y, bh4.z, bh4.w}, bl[4] = {bl4.x, bl4.y, bl4.z, bl4.w};
+      const float mh[4] = {mh4.x, mh4.y, mh4.z, mh4.w}, ml[4] = {ml4.x, ml4.y, ml4.z, ml4.w};
+      float yh[4], yl[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const FF y = ff_norm(hx[c]);
+        yh[c] = y.hi;
+        yl[c] = y.lo;
+        FF t = y;  // H x + sigma M x = A x
+        ff_mac(t, FF{mh[c], ml[c]}, sig);
+        FF rc{bh[c], bl[c]};
+        ff_add(rc, ff_neg(ff_norm(t)));
+        rc = ff_norm(rc);
+        arr[c] = fmaf(rc.hi, rc.hi, arr[c]);
+        abb[c] = fmaf(bh[c], bh[c], abb[c]);
+      }
+      *reinterpret_cast<float4*>(bhy + e) = make_float4(yh[0], yh[1], yh[2], yh[3]);
+      *reinterpret_cast<float4*>(bly + e) = make_float4(yl[0], yl[1], yl[2], yl[3]);
+    }
+    for (int c = 0; c < 4; ++c) {
+      acc[0][c] = arr[c];
+      acc[1][c] = abb[c];
+    }
+  }
+  if (!reduce_partials<2>(acc, Np, grp, nl, live, s.partial, s.ticket, sred, tot)) return;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  for (int o = threadIdx.x; o < Np; o += blockDim.x) {
+    double rr = tot[o], bb = tot[Np + o];
+    s.rr[o] = rr;
+    s.bb[o] = bb;
+    bool done = (o >= N) || rr <= tol * tol * bb;
+    if (o < N && !(isfinite(rr) && isfinite(bb))) {
+      atomicOr(s.status, kStatNonFinite);
+      done = true;
+    }
+    s.skip[o] = done ? 1 : 0;
+    if (!done) atomicAdd(&cnt, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *s.n_active = cnt;
+}
+
 // x += d for the orbitals the correction solve ran for (d group-major), and the
 // float-float split of the new x for the next residual; skipped orbitals keep x
 // (and, the split being a function of x, the same split).  Vector loads and
@@ -279,6 +372,16 @@ cudaError_t launch_refine_residual_ff(const Grid& g, int N, int Np, const float*
   // two 256-thread blocks resident a SM (up to 128 registers a thread), two waves
   const int grid = red_blocks(g, Np) < 152 * 4 ? red_blocks(g, Np) : 152 * 4;
   k_refine_residual_ff<<<grid, kRedThreads, 0, st>>>(g, N, Np, whi, wlo, xhi, xlo, bhi, blo, rhs32, s, tol, gm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_refine_check_hff(const Grid& g, int N, int Np, const float* whi, const float* wlo,
+                                    const float* xhi, const float* xlo, const float* mhi, const float* mlo,
+                                    double sigma, float* bhy, float* bly, const CGState& s, double tol,
+                                    cudaStream_t st) {
+  const int grid = red_blocks(g, Np) < 152 * 4 ? red_blocks(g, Np) : 152 * 4;
+  k_refine_check_hff<<<grid, kRedThreads, 0, st>>>(g, N, Np, whi, wlo, xhi, xlo, mhi, mlo, ff_split_host(sigma), bhy,
+                                                   bly, s, tol);
   return cudaGetLastError();
 }
 
