@@ -388,6 +388,29 @@ def test_mixed_iterate_matches_oracle_to_1e6(B):
     m.close()
 
 
+def test_mixed_iterate_with_extra_refinement_sweeps_matches_oracle(B):
+    # a loose inner tolerance leaves the first two refinement sweeps short of
+    # solve_tol, so the outer iterations take further sweeps after the closing
+    # check (which writes H x over the right-hand side; the sweeps after it form
+    # the right-hand side again): the same Ritz values and subspaces as the oracle
+    p = W.harmonic(nc=12, L=6.0, N=10, seed=2300, sigma=0.0)
+    ops = oracle_ops(p)
+    ref = O.paro(ops, p.U0, tol=1e-12, max_outer=300, pcg_tol=1e-12)
+    m = make_mesh(B, p, B.PARO_MIXED)
+    U = dev(p.U0)
+    loose = dict(solve_tol=1e-11, inner_tol=1e-2, max_refine=40)
+    rc, lam, st = m.iterate(U, None, B.paro_default_params(fixed_outer=1, **loose))
+    assert rc == 0
+    assert st.refine_sweeps > 2  # the first outer iteration from the initial guesses
+    rc, lam, st = m.iterate(U, lam, B.paro_default_params(tol=1e-12, max_outer=400, **loose))
+    assert rc == 0
+    assert np.max(np.abs(lam - ref.lam)) < 1e-6
+    u = host(U)
+    for a, b in ((0, 1), (1, 4), (4, 10)):
+        assert np.max(O.subspace_angles_M(ops.M, u[:, a:b], ref.U[:, a:b])) < 1e-5
+    m.close()
+
+
 def test_harmonic_32_mixed_converges_to_discrete_spectrum(B):
     with open(os.path.join(HERE, "golden", "discrete_spectra.json")) as f:
         gold = np.array(json.load(f)["harmonic_32_L8"]["values"][:10])
